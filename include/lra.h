@@ -1,0 +1,185 @@
+/*
+ * lra.h -- fixed-precision randomized low-rank approximation on one GB300 GPU.
+ *
+ * The library runs the blocked farPCA loop (arxiv 2506.03859, Alg. 1; Alg. 2
+ * for the standardized Bernoulli test matrix) with the paper's cheap test
+ * matrices Omega (Def. 2.1-2.4) generated on the device from Philox4x32-10
+ * counters.  Given a dense A (m x n) it builds, block of b columns by block,
+ * an orthonormal Q (m x l) and B = Q^T A (l x n) until the Frobenius error
+ * indicator E = ||A||_F^2 - ||B||_F^2 = ||A - QB||_F^2 (Sec. 2.1) drops below
+ * eps^2 ||A||_F^2 (the relative test of Sec. 5.2), or a fixed rank is reached.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are column-major (element (i, j) at ptr[i + j * ld]), FP64.
+ *  - "device" pointers are CUDA device memory of the current device; "host"
+ *    pointers are ordinary (ideally pinned) host memory.  The library never
+ *    frees memory it did not allocate.
+ *  - All device work is ordered on the stream given to lra_create.
+ *  - Return values: LRA_OK (0) or a positive status describing a run that
+ *    ended early but left valid results; negative values are errors, after
+ *    which lra_last_error(ctx) holds a message and outputs of the failing call
+ *    are undefined.  A NULL ctx or NULL required pointer gives
+ *    LRA_ERR_INVALID_ARG.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef LRA_H
+#define LRA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LRA_VERSION 1
+#define LRA_MAX_B 64      /* largest block size b */
+#define LRA_MAX_P 8       /* largest number of power steps P */
+#define LRA_MAX_ZETA 256  /* largest nonzeros per column, fixed-zeta sparse sign */
+
+typedef enum {
+  LRA_OK = 0,
+  LRA_NOT_CONVERGED = 1,   /* block cap reached before E < eps^2 ||A||_F^2     */
+  LRA_BREAKDOWN = 2,       /* a new block was numerically rank deficient: the
+                              Cholesky pivot of its Gram matrix was not above
+                              1e-13 times the diagonal entry; results are those
+                              of the blocks before it                            */
+  LRA_ERR_INVALID_ARG = -1,
+  LRA_ERR_OOM = -2,
+  LRA_ERR_CUDA = -3,
+  LRA_ERR_TIMEOUT = -4,
+  LRA_ERR_UNSUPPORTED = -5
+} lra_status;
+
+/* Test-matrix kinds (arxiv 2506.03859 Sec. 2.2). */
+typedef enum {
+  LRA_OMEGA_GAUSSIAN = 0,        /* standard Gaussian (farPCA, Alg. 1)                       */
+  LRA_OMEGA_STD_BERNOULLI = 1,   /* standardized Bernoulli, Def. 2.3 (farPCASB, Alg. 2):
+                                    sketch = A B_j - z, z = A (p 1), scale dropped          */
+  LRA_OMEGA_SPARSE_SIGN = 2,     /* sparse sign, zeta distinct nonzeros +-1/sqrt(zeta) per
+                                    column (the fixed-nonzero form after Def. 2.2)         */
+  LRA_OMEGA_SPARSE_SIGN_IID = 3, /* sparse sign, i.i.d. form of Def. 2.2, +-1/sqrt(p)       */
+  LRA_OMEGA_SPARSE_GAUSSIAN = 4, /* sparse Gaussian, Def. 2.4, B o G / sqrt(p)              */
+  LRA_OMEGA_BERNOULLI = 5        /* Bernoulli matrix, Def. 2.1 (farPCAB of Sec. 5)          */
+} lra_omega_kind;
+
+typedef enum { LRA_F64 = 0, LRA_F32 = 1 } lra_dtype;
+
+/* Flags for lra_params.flags. */
+#define LRA_FLAG_KEEP_Y 1u  /* keep every block's pre-projection sketch Y_j (the
+                               paper's cumulative Y of Alg. 1); costs m x l_max FP64 */
+
+/* A borrowed, read-only dense matrix. */
+typedef struct {
+  int64_t m, n;       /* rows, columns (>= 1)                                     */
+  int64_t lda;        /* leading dimension in elements, >= m                      */
+  int32_t dtype;      /* lra_dtype; LRA_F64 only (others: LRA_ERR_UNSUPPORTED)     */
+  int32_t reserved;   /* must be 0                                                */
+  const void* data;   /* device, column-major; must stay valid while a call runs  */
+} lra_matrix;
+
+/* Arguments of the problem statement (Alg. 1 / Alg. 2 REQUIRE lines). */
+typedef struct {
+  double eps;          /* relative Frobenius tolerance, > 0 in fixed-precision mode   */
+  int64_t k;           /* fixed-rank mode: run ceil(k/b) blocks; 0 = fixed precision   */
+  int32_t b;           /* block size, 1..min(m, n, LRA_MAX_B)                          */
+  int32_t P;           /* power steps, 0..LRA_MAX_P                                    */
+  int32_t kind;        /* lra_omega_kind                                               */
+  int32_t zeta;        /* fixed-zeta sparse sign: nonzeros per column, 1..min(n,
+                          LRA_MAX_ZETA); sparse Gaussian with p == 0: p = zeta / n     */
+  double p;            /* Bernoulli probability of the i.i.d. kinds, in (0, 1);
+                          0 selects Sec. 5.1's p1 = max(1e-3, ln n / n) for the
+                          standardized Bernoulli kind, p2 = max(1e-3, 10/n) otherwise  */
+  uint64_t seed;       /* Philox key: Omega_j depends only on (seed, j, kind, n, b)    */
+  int32_t max_blocks;  /* block cap; 0 = ceil(min(m, n) / (2b)) (Sec. 5.2)             */
+  uint32_t flags;      /* LRA_FLAG_* bits                                              */
+} lra_params;
+
+/* State after lra_farpca_run.  Device pointers are owned by the context and
+   stay valid until the next run on it or lra_destroy. */
+typedef struct {
+  int32_t status;        /* lra_status of the last run                          */
+  int32_t reserved;
+  int64_t rank;          /* l = blocks * b                                      */
+  int64_t blocks;
+  double E;              /* indicator after the last accepted block             */
+  double normA2;         /* ||A||_F^2                                           */
+  double rel_err;        /* sqrt(max(E, 0) / normA2), 0 when normA2 == 0        */
+  const double* Q;       /* device, m x rank, column-major, ld = ldq            */
+  int64_t ldq;
+  const double* B;       /* device, rank x n, column-major, ld = ldb            */
+  int64_t ldb;
+  const double* Y;       /* device, m x rank pre-projection sketches, or NULL   */
+  int64_t ldy;
+} lra_result_t;
+
+typedef struct lra_ctx lra_ctx;
+
+/* Create a context for m x n inputs: validates *params, allocates the device
+   workspace for the largest rank the run can reach (l_max = block cap * b), and
+   binds `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
+   Errors: LRA_ERR_INVALID_ARG, LRA_ERR_OOM, LRA_ERR_CUDA.  *out is NULL on error. */
+lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* params,
+                      void* cuda_stream);
+
+/* Free the context and everything it allocated.  NULL is ignored. */
+void lra_destroy(lra_ctx* ctx);
+
+/* Largest rank a run of this context can return (l_max); -1 for NULL. */
+int64_t lra_capacity(const lra_ctx* ctx);
+
+/* Sketch pass (Alg. 1 G_j / Alg. 2 steps 4-7): Y = A [Omega_j0 ... Omega_{j0+nblk-1}]
+   with the context's kind, seed and b; for the standardized Bernoulli kind each
+   block is A B_j - z, z = A (p 1) (Sec. 3.1).  A must be m x n as at create.
+   Y: device, m x (nblk * b), column-major, ld = ldy >= m, caller-owned.
+   nblk = 0 is a no-op.  Errors: LRA_ERR_INVALID_ARG, LRA_ERR_CUDA. */
+lra_status lra_sketch(lra_ctx* ctx, const lra_matrix* A, int64_t j0, int64_t nblk,
+                      double* Y, int64_t ldy);
+
+/* Run the blocked farPCA loop on A (device, m x n as at create) until
+   E < eps^2 ||A||_F^2 (LRA_OK), the block cap (LRA_NOT_CONVERGED), a rank-deficient
+   block (LRA_BREAKDOWN) or, with k > 0, ceil(k/b) blocks (LRA_OK).
+   ||A||_F = 0 gives rank 0 and LRA_OK; a non-finite ||A||_F^2 gives
+   LRA_ERR_INVALID_ARG.  Synchronises the stream once per block for the stop test. */
+lra_status lra_farpca_run(lra_ctx* ctx, const lra_matrix* A);
+
+/* Copy the state of the last run into *out (no device work). */
+lra_status lra_result(const lra_ctx* ctx, lra_result_t* out);
+
+/* End-to-end form with host buffers: copy A_host (m x n, ld lda_host) to a
+   device buffer owned by the context (allocated on the first call), run
+   lra_farpca_run, and copy Q into Q_host (m x rank, ld ldq_host >= m) and B
+   into B_host (rank x n, ld ldb_host >= lra_capacity); both must hold
+   lra_capacity(ctx) columns / rows.  Q_host or B_host may be NULL to skip that
+   copy.  Returns the run's status; *out (if not NULL) receives lra_result. */
+lra_status lra_farpca_host(lra_ctx* ctx, const double* A_host, int64_t lda_host,
+                           double* Q_host, int64_t ldq_host, double* B_host,
+                           int64_t ldb_host, lra_result_t* out);
+
+/* Omega_j as generated on the device, copied to host buffers (for bit-exact
+   comparison).  counts[b]: nonzeros of each column; rows[c * cap + t] and
+   vals[c * cap + t], t < counts[c]: row index and value of column c's t-th entry,
+   in generation order (draw order for the fixed-zeta kind, increasing row for
+   the others; every row for the Gaussian kind).  For the standardized Bernoulli
+   kind the entries are those of the Bernoulli matrix B_j (value 1).  cap must be
+   >= zeta (fixed-zeta kind) or >= n (other kinds).  Synchronises the stream.
+   Errors: LRA_ERR_INVALID_ARG, LRA_ERR_CUDA. */
+lra_status lra_copy_omega(lra_ctx* ctx, int64_t j, int64_t cap, int32_t* counts,
+                          int32_t* rows, double* vals);
+
+/* Message for the last error on ctx ("" if none); never NULL. */
+const char* lra_last_error(const lra_ctx* ctx);
+
+/* Name of a status code. */
+const char* lra_status_string(int32_t status);
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t lra_kernel_launches(void);
+
+/* LRA_VERSION of the built library. */
+int32_t lra_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LRA_H */

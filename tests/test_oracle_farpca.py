@@ -1,0 +1,264 @@
+"""Pins for oracle.farpca (QB form) and oracle.farpca_paper (Alg. 1 / 2 as printed).
+
+What fixes each part, independently of the oracle's own code:
+  * orth: numpy's Householder QR with sign(diag R) fixed (a library routine).
+  * the loop: Q^T Q = I; E equals ||A - QB||_F^2 computed directly (Sec. 2.1's
+    identity); B = Q^T A; Eckart-Young lower bound and eq. (4.9) upper bound from
+    a full SVD; exact-rank inputs end with E ~ 0; P = 0 span equals the span of
+    the raw sketches; span(Q) = span(Y) through W Z^{-1} W^T = B^T B.
+  * the paper-literal form (separate code): same rank, E within 1e-8.
+  * Table 1 (Sec. 5.2, n = 5000): attained ranks and achieved errors.
+  * planted mistakes (dropped deflation, flipped sign, skipped re-projection)
+    make at least one pin fail.
+"""
+import math
+import os
+import types
+
+import numpy as np
+import pytest
+
+from lra_inputs import exact_rank_matrix, low_rank_matrix, workload_matrix
+from oracle import farpca as F
+from oracle import farpca_paper as FP
+from oracle import omega as om
+
+KINDS_P = [(om.GAUSSIAN, 0.0), (om.STD_BERNOULLI, 0.5), (om.STD_BERNOULLI, 0.0), (om.SPARSE_SIGN, 0.0),
+           (om.SPARSE_SIGN_IID, 0.0), (om.SPARSE_GAUSSIAN, 0.0), (om.BERNOULLI, 0.0)]
+
+
+def qr_pos(X):
+    q, r = np.linalg.qr(X)
+    s = np.sign(np.diag(r))
+    s[s == 0] = 1
+    return q * s[None, :]
+
+
+def test_orth_equals_householder_qr():
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((500, 30)) @ np.diag(np.logspace(0, -3, 30))
+    Q = F.orth(X)
+    assert np.abs(Q - qr_pos(X)).max() < 1e-12
+    assert np.abs(Q.T @ Q - np.eye(30)).max() < 1e-14
+
+
+def test_cholesky_matches_library_and_flags_breakdown():
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((80, 12))
+    S = X.T @ X
+    R = F.cholesky_upper(S)
+    assert np.allclose(R, np.linalg.cholesky(S).T, rtol=1e-13, atol=1e-13)
+    X[:, 5] = X[:, 2] * 3.0          # dependent column
+    assert F.cholesky_upper(X.T @ X) is None
+    X[:, 5] = 0.0                    # zero column
+    assert F.cholesky_upper(X.T @ X) is None
+    assert F.orth(X) is None
+
+
+@pytest.mark.parametrize("kind,p", KINDS_P)
+@pytest.mark.parametrize("P", [0, 1, 2])
+def test_loop_identities(kind, p, P):
+    m, n, b, eps = 300, 200, 10, 3e-2
+    A = low_rank_matrix(m, n, "poly1.5", 7)
+    zeta = 4 if kind == om.SPARSE_SIGN else 0
+    r = F.farpca(A, eps, P=P, b=b, kind=kind, seed=4, zeta=zeta, p=p, keep_y=True)
+    Q, B, l = r["Q"], r["B"], r["rank"]
+    assert r["status"] == F.OK and l % b == 0 and l > 0
+    normA2 = float(np.sum(A * A))
+    assert r["normA2"] == pytest.approx(normA2, rel=1e-14)
+    # orthonormal basis
+    assert np.abs(Q.T @ Q - np.eye(l)).max() < 1e-12 * math.sqrt(l)
+    # B = Q^T A and the indicator identity ||A - QB||^2 = ||A||^2 - ||B||^2
+    assert np.abs(B - Q.T @ A).max() < 1e-13 * math.sqrt(normA2)
+    direct = float(np.sum((A - Q @ B) ** 2))
+    assert abs(r["E"] - direct) < 1e-11 * normA2
+    assert r["E"] < eps ** 2 * normA2
+    if l > b:
+        assert r["E_trace"][-2] >= eps ** 2 * normA2
+    # Eckart-Young: no rank-l approximation beats the SVD tail
+    s = np.linalg.svd(A, compute_uv=False)
+    assert direct >= float(np.sum(s[l:] ** 2)) * (1 - 1e-10)
+    # span(Q) = span(Y): W Z^{-1} W^T = B^T B with W = A^T Y, Z = Y^T Y
+    Y = r["Y"]
+    W = A.T @ Y
+    lhs = W @ np.linalg.solve(Y.T @ Y, W.T)
+    assert np.abs(lhs - B.T @ B).max() < 1e-7 * normA2
+
+
+def test_p0_span_equals_raw_sketch_span():
+    # P = 0 is randQB_EI without power steps (Sec. 2.1): span(Q) = span([A Omega_1 ... A Omega_j]).
+    A = low_rank_matrix(250, 180, "poly1", 9)
+    r = F.farpca(A, 5e-2, P=0, b=8, kind=om.SPARSE_GAUSSIAN, seed=2, p=0.05)
+    l = r["rank"]
+    S = np.hstack([A @ om.omega_dense(om.SPARSE_GAUSSIAN, j, 180, 8, 2, p=0.05) for j in range(l // 8)])
+    Qs = qr_pos(S)
+    sv = np.linalg.svd(Qs.T @ r["Q"], compute_uv=False)   # cosines of principal angles
+    assert sv.min() > 1 - 1e-10
+
+
+@pytest.mark.parametrize("P", [1, 2])
+def test_exact_rank(P):
+    # rank-r input with r = 2b: the range is captured after two blocks (E ~ 0).
+    b = 8
+    A = exact_rank_matrix(200, 150, 2 * b, 3)
+    r = F.farpca(A, 1e-6, P=P, b=b, kind=om.SPARSE_SIGN, seed=1, zeta=4)
+    assert r["status"] == F.OK and r["blocks"] == 2
+    assert abs(r["E"]) < 1e-24 * 1e10 * r["normA2"]
+
+
+def test_error_bound_eq_4_9():
+    # Fixed rank l = k + h: E||(I - QQ^T)A||_F <= (1 + k/(h-1))^{1/2} (sum_{j>k} sigma_j^2)^{1/2}, averaged.
+    A = low_rank_matrix(300, 200, "poly1", 11)
+    s = np.linalg.svd(A, compute_uv=False)
+    b, kk, h = 10, 20, 10
+    for kind, p in [(om.GAUSSIAN, 0.0), (om.SPARSE_SIGN, 0.0), (om.STD_BERNOULLI, 0.5), (om.SPARSE_GAUSSIAN, 0.1)]:
+        errs = []
+        for seed in range(8):
+            r = F.farpca(A, 0.0, P=0, b=b, kind=kind, seed=seed, zeta=8, p=p, k=kk + h)
+            assert r["rank"] == kk + h
+            errs.append(math.sqrt(np.sum((A - r["Q"] @ r["B"]) ** 2)))
+        bound = math.sqrt(1 + kk / (h - 1)) * math.sqrt(np.sum(s[kk:] ** 2))
+        assert np.mean(errs) <= bound
+        assert min(errs) >= math.sqrt(np.sum(s[kk + h:] ** 2))
+
+
+def test_rank_at_least_numerical_rank():
+    A = workload_matrix("dense2000x1000_poly1.5")
+    s = np.linalg.svd(A, compute_uv=False)
+    tail = np.sqrt(np.cumsum((s ** 2)[::-1])[::-1] / np.sum(s ** 2))
+    k_opt = int(np.argmax(tail < 1e-2))
+    r = F.farpca(A, 1e-2, P=1, b=20, kind=om.SPARSE_SIGN, seed=0, zeta=8)
+    assert r["status"] == F.OK and k_opt <= r["rank"] <= k_opt + 2 * 20
+
+
+@pytest.mark.parametrize("kind,p", KINDS_P)
+@pytest.mark.parametrize("P", [1, 2])
+def test_paper_form_agrees(kind, p, P):
+    A = low_rank_matrix(400, 300, "poly1.5", 5)
+    zeta = 4 if kind == om.SPARSE_SIGN else 0
+    a = FP.farpca_paper(A, 1e-2, P=P, b=10, kind=kind, seed=3, zeta=zeta, p=p)
+    b_ = F.farpca(A, 1e-2, P=P, b=10, kind=kind, seed=3, zeta=zeta, p=p)
+    assert a["status"] == b_["status"] == F.OK
+    assert a["rank"] == b_["rank"]
+    assert abs(a["E"] - b_["E"]) < 1e-8 * b_["E"]
+
+
+def test_paper_form_agrees_p0_rank():
+    A = low_rank_matrix(400, 300, "poly1.5", 5)
+    for kind in (om.SPARSE_SIGN, om.GAUSSIAN):
+        a = FP.farpca_paper(A, 1e-2, P=0, b=10, kind=kind, seed=3, zeta=4)
+        b_ = F.farpca(A, 1e-2, P=0, b=10, kind=kind, seed=3, zeta=4)
+        assert a["rank"] == b_["rank"]
+        assert abs(a["E"] - b_["E"]) < 1e-4 * b_["E"]
+
+
+def test_paper_svd_extraction():
+    A = low_rank_matrix(300, 200, "poly1.5", 5)
+    a = FP.farpca_paper(A, 1e-2, P=1, b=10, kind=om.SPARSE_SIGN, seed=3, zeta=4)
+    U, s, V = FP.svd_from_yw(a["Y"], a["W"], a["Z"], a["T"])
+    b_ = F.farpca(A, 1e-2, P=1, b=10, kind=om.SPARSE_SIGN, seed=3, zeta=4)
+    sB = np.linalg.svd(b_["B"], compute_uv=False)
+    assert np.allclose(np.sort(s)[::-1], sB, rtol=1e-8, atol=1e-12)
+    approx = (U * s[None, :]) @ V.T
+    assert np.abs(approx - b_["Q"] @ b_["B"]).max() < 1e-9
+
+
+def test_edge_cases():
+    A = np.zeros((50, 40))
+    r = F.farpca(A, 1e-2, P=1, b=5)
+    assert r["rank"] == 0 and r["status"] == F.OK and r["E"] == 0.0
+    # one nonzero column: a block of b >= 2 sketches is rank deficient -> breakdown, rank 0
+    A[:, 7] = np.arange(50) + 1.0
+    r = F.farpca(A, 1e-3, P=0, b=4, kind=om.SPARSE_SIGN, seed=0, zeta=1)
+    assert r["status"] == F.BREAKDOWN and r["rank"] == 0
+    # fixed rank: ceil(k/b) blocks
+    A = low_rank_matrix(120, 90, "poly1", 2)
+    r = F.farpca(A, 0.0, P=1, b=7, k=30, kind=om.SPARSE_GAUSSIAN, seed=5, p=0.1)
+    assert r["blocks"] == 5 and r["rank"] == 35 and r["status"] == F.OK
+    # block cap: ceil(min(m, n) / (2b)) blocks, then NOT_CONVERGED
+    r = F.farpca(A, 1e-12, P=0, b=7, kind=om.SPARSE_SIGN, seed=5, zeta=3)
+    assert r["status"] == F.NOT_CONVERGED and r["blocks"] == F.default_max_blocks(120, 90, 7) == 7
+    # b = min(m, n) in one block captures everything
+    r = F.farpca(A[:, :14], 1e-8, P=1, b=14, kind=om.GAUSSIAN, seed=1)
+    assert r["rank"] == 14 and abs(r["E"]) < 1e-14 * r["normA2"]
+    with pytest.raises(ValueError):
+        F.farpca(A, 0.0, P=1, b=7)
+    with pytest.raises(ValueError):
+        F.farpca(A, 1e-2, P=1, b=91)
+    with pytest.raises(ValueError):
+        F.farpca(np.full((5, 5), np.nan), 1e-2, P=1, b=2)
+
+
+def _planted(replacements):
+    src = open(F.__file__).read()
+    for a, b_ in replacements:
+        assert a in src
+        src = src.replace(a, b_)
+    mod = types.ModuleType("oracle.planted")
+    mod.__package__ = "oracle"
+    exec(compile(src, "planted", "exec"), mod.__dict__)
+    return mod
+
+
+@pytest.mark.parametrize("repl", [
+    [("W = A.T @ S0 - B.T @ BOm", "W = A.T @ S0"), ("W = A.T @ (A @ G) - B.T @ (B @ G)", "W = A.T @ (A @ G)")],
+    [("W = A.T @ S0 - B.T @ BOm", "W = A.T @ S0 + B.T @ BOm")],
+    [("S0 = A @ Bj - z[:, None]", "S0 = A @ Bj")],
+    [("BOm = B @ Bj - (B @ w)[:, None]", "BOm = B @ Bj")],
+])
+def test_planted_mistakes_are_caught(repl):
+    """A mistake planted in a copy of the oracle makes the paper-form cross-check fail."""
+    bad = _planted(repl)
+    A = low_rank_matrix(400, 300, "poly1.5", 5)
+    kind, p = (om.STD_BERNOULLI, 0.1) if "Bj" in repl[0][0] else (om.SPARSE_SIGN, 0.0)
+    ref = FP.farpca_paper(A, 1e-2, P=1, b=10, kind=kind, seed=3, zeta=4, p=p)
+    r = bad.farpca(A, 1e-2, P=1, b=10, kind=kind, seed=3, zeta=4, p=p)
+    assert r["rank"] != ref["rank"] or abs(r["E"] - ref["E"]) > 1e-8 * ref["E"]
+
+
+def test_planted_single_projection_is_caught():
+    # Dropping the second Gram-Schmidt pass loses orthogonality on a steep spectrum.
+    bad = _planted([("        F = Q.T @ Yp\n        Yp = Yp - Q @ F\n", "")])
+    A = low_rank_matrix(600, 400, "matrix2", 8)
+    r = bad.farpca(A, 1e-9, P=0, b=10, kind=om.SPARSE_SIGN, seed=1, zeta=4)
+    Q = r["Q"]
+    good = F.farpca(A, 1e-9, P=0, b=10, kind=om.SPARSE_SIGN, seed=1, zeta=4)
+    assert np.abs(good["Q"].T @ good["Q"] - np.eye(good["rank"])).max() < 1e-12 * math.sqrt(good["rank"])
+    assert np.abs(Q.T @ Q - np.eye(Q.shape[1])).max() > 1e-12 * math.sqrt(Q.shape[1])
+
+
+TABLE1 = os.path.join(os.path.dirname(__file__), "golden", "table1_n5000.txt")
+
+
+def _table1_rows():
+    rows = []
+    for line in open(TABLE1):
+        if line.strip() and not line.startswith("#"):
+            f = line.split()
+            rows.append((int(f[0]), float(f[1]), int(f[2]), [float(x) for x in f[3:]]))
+    return rows
+
+
+@pytest.fixture(scope="module")
+def table1_matrices():
+    return {1: workload_matrix("matrix1_5000"), 2: workload_matrix("matrix2_5000")}
+
+
+@pytest.mark.parametrize("row", _table1_rows(), ids=lambda r: "M%d_eps%g" % (r[0], r[1]))
+def test_table1_ranks(row, table1_matrices):
+    """Sec. 5.2 Table 1, n = 5000: every kind attains the printed rank l; the achieved
+    relative error is within 15% of the printed 20-trial mean (one trial here)."""
+    mat, eps, l_paper, eps_opt = row
+    A = table1_matrices[mat]
+    n = 5000
+    b = min(max(20, n // 100), 50)
+    cases = [(om.GAUSSIAN, 0.0, 0), (om.STD_BERNOULLI, 0.0, 0), (om.SPARSE_SIGN_IID, 0.0, 0),
+             (om.SPARSE_GAUSSIAN, 0.0, 0), (om.BERNOULLI, 0.0, 0), (om.SPARSE_SIGN, 0.0, 10)]
+    col = {om.GAUSSIAN: 0, om.STD_BERNOULLI: 1, om.SPARSE_SIGN_IID: 2, om.SPARSE_GAUSSIAN: 3,
+           om.BERNOULLI: 4, om.SPARSE_SIGN: 2}
+    for kind, p, zeta in cases:
+        r = F.farpca(A, eps, P=1, b=b, kind=kind, seed=0, zeta=zeta, p=p)
+        assert r["status"] == F.OK
+        assert r["rank"] == l_paper, (om.KIND_NAMES[kind], r["rank"])
+        rel = math.sqrt(max(r["E"], 0.0) / r["normA2"])
+        assert abs(rel - eps_opt[col[kind]]) < 0.15 * eps_opt[col[kind]], (om.KIND_NAMES[kind], rel)
