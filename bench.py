@@ -1,0 +1,354 @@
+#!/usr/bin/env python3
+"""Time-to-eps of the fixed-precision farPCA loop on GB300 (arxiv 2506.03859).
+
+One step = one lra_farpca_run on a device-resident A: Omega generation, the
+sketch, the deflated power steps, the projections and CholQR2, and the error
+indicator, block by block until E < eps^2 ||A||_F^2.  Inputs are synthetic
+(seeded Haar U, V and the stated spectrum; lra_inputs), larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) each rank solves its own
+replica (no collective on the data path); value = solves of all ranks / max time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SPARSE_SIGN = 2
+WORKLOADS = {
+    # 20000 x 10000 FP64, sigma_i = 10^(-i/100) + 1e-6 N(0,1) noise; farPCASS zeta = 8, b = 50, P = 1
+    "farpcass_20000x10000_exp100_zeta8_b50_P1_eps1e-2": dict(
+        matrix="dense20000x10000_exp100", kind=SPARSE_SIGN, zeta=8, p=0.0, b=50, P=1, eps=1e-2, seed=1),
+    # 2000 x 1000 FP64, sigma_i = i^-1.5; farPCASS zeta = 8, b = 20, P = 1
+    "farpcass_2000x1000_poly1.5_zeta8_b20_P1_eps1e-2": dict(
+        matrix="dense2000x1000_poly1.5", kind=SPARSE_SIGN, zeta=8, p=0.0, b=20, P=1, eps=1e-2, seed=1),
+}
+DEFAULT_WORKLOAD = "farpcass_20000x10000_exp100_zeta8_b50_P1_eps1e-2"
+METRIC = "time-to-eps per matrix (fixed-precision farPCA), as solves/s"
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (152 SMs x ~2 FP64 FMA/clk x 2 flop x 2.07 GHz)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--sketch-blocks", type=int, default=64)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the timed farPCA steps (for launch-list profiling)")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def oracle_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n and n[0]:
+            return int(n[0])
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while timing."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def source_digest(names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2506_03859_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel, digest):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not t or t.get("source_digest") != digest:
+        return None
+    return t.get("dram_bytes_per_launch")
+
+
+def run_reference(args, cfg):
+    """The FP64 CPU oracle, as it stands, on the host cores: one full solve per step."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    from lra_inputs import workload_matrix
+    from oracle import farpca as F
+    A = workload_matrix(cfg["matrix"])
+    kw = dict(P=cfg["P"], b=cfg["b"], kind=cfg["kind"], seed=cfg["seed"], zeta=cfg["zeta"], p=cfg["p"])
+    for _ in range(args.warmup):
+        F.farpca(A, cfg["eps"], **kw)
+    times = []
+    r = None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = F.farpca(A, cfg["eps"], **kw)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps / total
+    cores = oracle_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "m": A.shape[0], "n": A.shape[1],
+                                        "rank": r["rank"], "rel_err": (max(r["E"], 0) / r["normA2"]) ** 0.5},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": "one full fixed-precision solve of the workload per step "
+                                   "(numpy/OpenBLAS FP64, QB form)"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    cfg = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from lra_inputs import workload_matrix
+    from paper_2506_03859_gb300 import lra
+    from paper_2506_03859_gb300.build import build
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    if local == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+    lra.load()
+    peaks, peak_src = measured_peaks()
+
+    A = workload_matrix(cfg["matrix"])
+    m, n = A.shape
+    Ad = lra.column_major(torch.from_numpy(A).cuda())
+    stream = torch.cuda.current_stream()
+    f = lra.Farpca(m, n, eps=cfg["eps"], b=cfg["b"], P=cfg["P"], kind=cfg["kind"], zeta=cfg["zeta"],
+                   p=cfg["p"], seed=cfg["seed"] + rank, profile=True, stream=stream)
+    for _ in range(max(args.warmup, 0)):
+        f.run(Ad)
+    torch.cuda.synchronize()
+    f.phase_times(reset=True)
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = lra.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        f.run(Ad)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = lra.kernel_launches() - launches0
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    res = f.result()
+    phases = f.phase_times(reset=True)
+    value = world * args.steps / (ms / 1e3)
+
+    # roofline of the dominant phase (the full passes over A: FP64 GEMM, FP64-pipe bound)
+    dense_ms, dense_calls = phases["dense"]
+    dense_avg_ms = dense_ms / max(dense_calls, 1)
+    flops = 2.0 * m * n * cfg["b"]
+    achieved_tf = flops / (dense_avg_ms * 1e-3) / 1e12 if dense_calls else 0.0
+    digest = source_digest(["dgemm_simt.cu"])
+    roofline = {"kernel": "k_dgemm (A^T X / A X, FP64 SIMT)", "bound": "alu", "achieved": achieved_tf,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
+                "traffic": traffic_for("k_dgemm", digest),
+                "algorithmic_per_launch": {"flops": flops, "bytes": 8.0 * m * n},
+                "avg_launch_ms": dense_avg_ms, "launches": dense_calls,
+                "peak_source": "nominal FP64 of the profiling recipe (no measured FP64 peak)"}
+    total_phase = sum(v[0] for v in phases.values()) or 1.0
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "m": m, "n": n, "b": cfg["b"], "P": cfg["P"],
+                   "eps": cfg["eps"], "omega": "sparse sign, zeta=%d" % cfg["zeta"],
+                   "rank": res["rank"], "blocks": res["blocks"], "rel_err": res["rel_err"],
+                   "status": lra.status_string(res["status"]),
+                   "l2": "inputs larger than L2 (A = %.2f GB)" % (8.0 * m * n / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "phase_share": {k: round(v[0] / total_phase, 4) for k, v in phases.items()},
+        "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+
+    if not args.no_extras:
+        line["sketch_pass"] = sketch_pass(lra, torch, f, Ad, cfg, args.sketch_blocks, peaks, peak_src)
+        line["e2e"] = e2e(lra, torch, np, f, A, args.steps)
+        if rank == 0 and world == 1:
+            line["cpu_baseline"] = cpu_baseline(A, cfg)
+    else:
+        line["e2e"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    f.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def sketch_pass(lra, torch, f, Ad, cfg, nblk, peaks, peak_src):
+    """lra_sketch over nblk consecutive blocks (one launch of the gather kernel)."""
+    m, n, b = f.m, f.n, f.b
+    Y = torch.empty_strided((m, nblk * b), (1, m), dtype=torch.float64, device="cuda")
+    distinct = 0
+    for j in range(nblk):
+        counts, rows, _ = f.copy_omega(j)
+        distinct += len(set(rows[:, :cfg["zeta"]].ravel().tolist()))
+    algo_bytes = 8.0 * m * (distinct + nblk * b)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        f.sketch(Ad, 0, nblk, Y)
+    torch.cuda.synchronize()
+    reps = 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for r in range(reps):
+        f.sketch(Ad, r * nblk, nblk, Y)   # a different Omega each repetition
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    gbs = algo_bytes / (ms * 1e-3) / 1e9
+    return {"kernel": "k_gather (sparse-sign sketch, Omega generated in the same call)",
+            "blocks": nblk, "ms": ms, "algorithmic_bytes": algo_bytes, "gbs": gbs,
+            "bound": "hbm", "peak": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
+            "frac_of_nominal_7900": gbs / 7900.0, "peak_source": peak_src}
+
+
+def e2e(lra, torch, np, f, A, steps):
+    """lra_farpca_host: A from pinned host memory, Q and B back to pinned host memory."""
+    m, n = A.shape
+    cap = f.capacity
+    Ah = torch.empty((n, m), dtype=torch.float64, pin_memory=True).numpy().T
+    Ah[...] = A
+    Qh = torch.empty((cap, m), dtype=torch.float64, pin_memory=True).numpy().T
+    Bh = torch.empty((n, cap), dtype=torch.float64, pin_memory=True).numpy().T
+    f.run_host(Ah, Qh, Bh)
+    k = max(3, min(steps, 5))
+    t0 = time.perf_counter()
+    r = None
+    for _ in range(k):
+        r = f.run_host(Ah, Qh, Bh)
+    dt = (time.perf_counter() - t0) / k
+    rank = r["rank"]
+    return {"value": 1.0 / dt, "unit": "solves/s", "h2d_bytes_per_step": 8 * m * n,
+            "d2h_bytes_per_step": 8 * (m * rank + rank * n), "ms_per_step": 1e3 * dt,
+            "api": "lra_farpca_host"}
+
+
+def cpu_baseline(A, cfg):
+    from oracle import farpca as F
+    t0 = time.perf_counter()
+    r = F.farpca(A, cfg["eps"], P=cfg["P"], b=cfg["b"], kind=cfg["kind"], seed=cfg["seed"],
+                 zeta=cfg["zeta"], p=cfg["p"])
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "solves/s", "cores": oracle_threads(), "kind": "oracle",
+            "sample": "one full fixed-precision solve of the same workload (rank %d, numpy/OpenBLAS "
+                      "FP64, QB form)" % r["rank"], "seconds": dt}
+
+
+if __name__ == "__main__":
+    main()

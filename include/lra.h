@@ -67,6 +67,21 @@ typedef enum { LRA_F64 = 0, LRA_F32 = 1 } lra_dtype;
 /* Flags for lra_params.flags. */
 #define LRA_FLAG_KEEP_Y 1u  /* keep every block's pre-projection sketch Y_j (the
                                paper's cumulative Y of Alg. 1); costs m x l_max FP64 */
+#define LRA_FLAG_PROFILE 2u /* time each phase of lra_farpca_run with CUDA events on
+                               the context's stream (read with lra_phase_times)   */
+
+/* Phases of one block, for lra_phase_times. */
+typedef enum {
+  LRA_PHASE_OMEGA = 0,      /* Omega_j generation (Philox)                         */
+  LRA_PHASE_SKETCH = 1,     /* S0 = A Omega_j                                      */
+  LRA_PHASE_DENSE = 2,      /* one full pass over A: A^T X or A X (power steps,
+                               Y_j = A G, B_j^T = A^T Q_j)                         */
+  LRA_PHASE_DEFLATE = 3,    /* B Omega_j, B G and B^T F (deflation)                */
+  LRA_PHASE_PROJECT = 4,    /* Q^T Y and Y - Q F, twice                            */
+  LRA_PHASE_ORTH = 5,       /* Gram, Cholesky, triangular apply, twice             */
+  LRA_PHASE_INDICATOR = 6,  /* ||A||_F^2, ||B_j||_F^2, append of B_j               */
+  LRA_NUM_PHASES = 7
+} lra_phase;
 
 /* A borrowed, read-only dense matrix. */
 typedef struct {
@@ -165,6 +180,12 @@ lra_status lra_farpca_host(lra_ctx* ctx, const double* A_host, int64_t lda_host,
    Errors: LRA_ERR_INVALID_ARG, LRA_ERR_CUDA. */
 lra_status lra_copy_omega(lra_ctx* ctx, int64_t j, int64_t cap, int32_t* counts,
                           int32_t* rows, double* vals);
+
+/* Accumulated device time (ms, CUDA events) and number of timed calls of each
+   phase since creation or the last reset, for a context created with
+   LRA_FLAG_PROFILE (zeros otherwise).  ms and calls are host arrays of nphases
+   (<= LRA_NUM_PHASES) entries; reset != 0 clears the counters after reading. */
+lra_status lra_phase_times(lra_ctx* ctx, double* ms, int64_t* calls, int32_t nphases, int32_t reset);
 
 /* Message for the last error on ctx ("" if none); never NULL. */
 const char* lra_last_error(const lra_ctx* ctx);

@@ -101,6 +101,8 @@ def check_args(m, n, eps, P, b, kind, zeta, p, k, max_blocks):
         raise ValueError("p must lie in (0, 1) (0 selects the default)")
     if max_blocks < 0:
         raise ValueError("max_blocks must be >= 0")
+    if max_blocks * b > min(m, n):
+        raise ValueError("max_blocks * b exceeds min(m, n)")
 
 
 def farpca(A, eps=0.0, P=1, b=20, kind=om.SPARSE_SIGN, seed=0, zeta=8, p=0.0,

@@ -1,0 +1,90 @@
+// Internal declarations shared by the library's translation units.
+// Every kernel launch goes through a host wrapper declared here; wrappers bump
+// the process-wide launch counter and return the launch's cudaError_t.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "../../include/lra.h"
+
+namespace lra {
+
+extern std::atomic<uint64_t> g_launches;
+
+inline cudaError_t launched() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+// Device-side error bits (a single int in device memory, read once per block).
+enum : int {
+  FLAG_BREAKDOWN = 1,     // a Cholesky pivot failed the breakdown test
+  FLAG_OMEGA_CAP = 2,     // fixed-zeta generator ran out of draws
+};
+
+// Philox stream tags (counter word 3); see philox.cuh.
+enum : uint32_t { TAG_SPARSE_SIGN = 1, TAG_MASK = 2, TAG_GAUSS = 3 };
+
+// ---------------------------------------------------------------- omega.cu
+struct OmegaSpec {
+  int kind;            // lra_omega_kind
+  int64_t n;           // rows of Omega
+  int b;               // columns per block
+  int zeta;            // fixed-zeta kind
+  double p;            // Bernoulli probability (i.i.d. kinds)
+  uint64_t thr;        // floor(p * 2^32)
+  double inv_scale;    // 1/sqrt(zeta) or 1/sqrt(p)
+  uint32_t k0, k1;     // Philox key
+};
+
+// Sparse structure of Omega for blocks j0 .. j0 + nblk - 1 (nblk * b columns):
+// counts[g], rows[g * cap + t], vals[g * cap + t].  Fixed-zeta kind or i.i.d.
+// mask kinds (values: 1 for the Bernoulli / standardized Bernoulli kinds).
+cudaError_t omega_sparse(const OmegaSpec& s, int64_t j0, int64_t nblk, int cap, int* counts,
+                         int* rows, double* vals, int* flags, cudaStream_t st);
+// Dense Omega (n x (nblk*b), ld ldo): Gaussian; standardized Bernoulli as the
+// shifted Bernoulli matrix B - p (Alg. 2 with the scale dropped); other kinds
+// as their definition.
+cudaError_t omega_dense(const OmegaSpec& s, int64_t j0, int64_t nblk, double* Om, int64_t ldo,
+                        cudaStream_t st);
+
+// ---------------------------------------------------------------- sketch.cu
+// Y[i, g] = sum_t vals[g*cap+t] * X[i, rows[g*cap+t]] - (shift ? shift[i] : 0)
+// for i < rows_x, g < ncols; X column-major with ld ldx.
+cudaError_t gather_sketch(const double* X, int64_t ldx, int64_t rows_x, const int* counts,
+                          const int* rows, const double* vals, int cap, int64_t ncols, double* Y,
+                          int64_t ldy, const double* shift, cudaStream_t st);
+
+// ---------------------------------------------------------------- dgemm_simt.cu
+// C[p, c] = alpha * sum_k opX[p, k] Y[k, c] + beta * C[p, c], p < P, c < N <= 64.
+// trans: opX[p, k] = X[k + p*ldx] (X is K x P); else opX[p, k] = X[p + k*ldx].
+// C element (p, c) at C[p*csp + c*csc].  beta == 0 never reads C.
+// ws: split-K workspace of ws_elems doubles.
+struct GemmOut {
+  double* C;
+  int64_t csp, csc;
+};
+cudaError_t dgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, const double* X,
+                  int64_t ldx, const double* Y, int64_t ldy, double beta, GemmOut out, double* ws,
+                  int64_t ws_elems, cudaStream_t st);
+int64_t dgemm_ws_elems();
+
+// ---------------------------------------------------------------- orth.cu
+// Per-column sums of squares and/or sums of X (rows x cols, ld): one CTA per column.
+cudaError_t col_sums(const double* X, int64_t ld, int64_t rows, int64_t cols, double* sumsq,
+                     double* sum, cudaStream_t st);
+// out[0] = sum of v[0..count) in a fixed order (one CTA).
+cudaError_t total(const double* v, int64_t count, double* out, cudaStream_t st);
+// Cholesky S = R^T R (S: b x b, ld b), R^{-1} into Rinv (b x b, ld b); on a failed
+// pivot (d_c not > tau * S_cc or not finite) sets FLAG_BREAKDOWN in *flags.
+cudaError_t chol_inv(const double* S, int b, double tau, double* Rinv, int* flags, cudaStream_t st);
+// B[row0 + c, r] = Wt[r, c] (Wt: n x b, ld ldw); zB[row0 + c] = p * colsum[c] if zB.
+cudaError_t append_rows(const double* Wt, int64_t ldw, int64_t n, int b, double* B, int64_t ldb,
+                        int64_t row0, const double* colsum, double p, double* zB, cudaStream_t st);
+// X[i, c] = v for all i < rows, c < cols.
+cudaError_t fill(double* X, int64_t ld, int64_t rows, int64_t cols, double v, cudaStream_t st);
+
+}  // namespace lra

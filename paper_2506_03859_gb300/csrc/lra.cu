@@ -1,0 +1,703 @@
+// C ABI of the library (include/lra.h) and the host driver of the blocked
+// farPCA loop (arxiv 2506.03859 Alg. 1, Alg. 2 for the standardized Bernoulli
+// test matrix), written in its QB form (Sec. 2.1: farPCA equals randQB_EI plus
+// a direct SVD for P = 0, 1, 2):
+//
+//   E = ||A||_F^2                                        (Alg. 1 step 1)
+//   for j: Omega_j (Philox, device)                      (step 3 / Alg. 2 step 4)
+//          S0 = A Omega_j  (Alg. 2: A B_j - z)            (steps 5-7)
+//          P >= 1: W = A^T S0 - B^T (B Omega_j); G = orth(W);
+//                  P-1 times W = A^T (A G) - B^T (B G), G = orth(W);  Y_j = A G
+//                  (deflation W Z^{-1} W^T = B^T B, steps 5-6 / Alg. 2 steps 9-13)
+//          P = 0:  Y_j = S0
+//          Y' = (I - Q Q^T) Y_j twice; Q_j = orth(Y'); B_j = Q_j^T A  (step 9-10)
+//          E -= ||B_j||_F^2; stop when E < eps^2 ||A||_F^2         (steps 10-11)
+//
+// orth(X) = X R^{-1} with R = chol(X^T X), applied twice (CholQR2): the Q factor
+// of the QR factorisation with positive diag(R).  All device work is ordered on
+// the context's stream; the host reads one small record per block (||B_j||_F^2
+// and the error flags) for the stop test.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "internal.cuh"
+
+namespace lra {
+std::atomic<uint64_t> g_launches{0};
+}
+
+using namespace lra;
+
+namespace {
+
+constexpr double PIVOT_TAU = 1e-13;
+constexpr int64_t SPARSE_MAX_NNZ_PER_COL = 256;   // above this expected nnz, Omega is dense
+constexpr int64_t SKETCH_SCRATCH_ENTRIES = 8 << 20;
+
+struct Pinned {
+  double v[4];
+  int flags;
+};
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct lra_ctx {
+  int64_t m = 0, n = 0;
+  lra_params prm{};
+  cudaStream_t st = nullptr;
+  int b = 0, P = 0, kind = 0;
+  bool sparse = false, keep_y = false, sb_sparse = false;
+  int cap = 0;  // entries per Omega column in the sparse structure
+  OmegaSpec os{};
+  int64_t nblk_max = 0, lmax = 0, ldq = 0, ldb = 0, lds = 0, ldf = 0, ldod = 0;
+
+  double *Q = nullptr, *B = nullptr, *Yk = nullptr;
+  double *S0 = nullptr, *Yb = nullptr, *T1 = nullptr, *Tmp = nullptr;
+  double *W = nullptr, *G = nullptr, *Wt = nullptr;
+  double *F = nullptr, *BOm = nullptr;
+  double *z = nullptr, *zB = nullptr, *wvec = nullptr;
+  double* ws = nullptr;
+  int64_t ws_elems = 0;
+  double *gram = nullptr, *Rinv = nullptr;
+  double *colsq = nullptr, *colsum = nullptr, *scal = nullptr;
+  int* flags = nullptr;
+  int *om_counts = nullptr, *om_rows = nullptr;
+  double *om_vals = nullptr, *om_dense = nullptr;
+  // lra_sketch / lra_copy_omega scratch (grown on demand)
+  int *sk_counts = nullptr, *sk_rows = nullptr;
+  double* sk_vals = nullptr;
+  int64_t sk_entries = 0, sk_cols = 0;
+  double* A_host_copy = nullptr;  // device copy of A for lra_farpca_host
+  Pinned* hp = nullptr;
+
+  // phase timing (LRA_FLAG_PROFILE)
+  static constexpr int NEV = 96;
+  bool prof = false;
+  cudaEvent_t ev0[NEV] = {}, ev1[NEV] = {};
+  int ev_phase[NEV] = {};
+  int nev = 0, cur_phase = 0;
+  double phase_ms[LRA_NUM_PHASES] = {};
+  int64_t phase_calls[LRA_NUM_PHASES] = {};
+
+  int32_t status = LRA_OK;
+  int64_t rank = 0, blocks = 0;
+  double E = 0.0, normA2 = 0.0;
+  std::string err;
+};
+
+namespace {
+
+lra_status fail(lra_ctx* c, lra_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define CK(expr)                                                                               \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? LRA_ERR_OOM : LRA_ERR_CUDA,           \
+                  "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+#define TRY(expr)                         \
+  do {                                    \
+    lra_status s_ = (expr);               \
+    if (s_ < 0) return s_;                \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, int64_t count) {
+  *p = nullptr;
+  if (count <= 0) return cudaSuccess;
+  return cudaMalloc((void**)p, (size_t)count * sizeof(T));
+}
+
+double default_p(int kind, int64_t n, int zeta) {
+  if (kind == LRA_OMEGA_SPARSE_GAUSSIAN && zeta > 0) return (double)zeta / (double)n;
+  if (kind == LRA_OMEGA_STD_BERNOULLI) return std::max(1e-3, log((double)n) / (double)n);
+  return std::max(1e-3, 10.0 / (double)n);
+}
+
+lra_status check_params(lra_ctx* ctx, int64_t m, int64_t n, const lra_params* p) {
+  if (m < 1 || n < 1 || m > INT32_MAX || n > INT32_MAX)
+    return fail(ctx, LRA_ERR_INVALID_ARG, "m and n must lie in [1, 2^31)");
+  const int64_t mn = std::min(m, n);
+  if (p->b < 1 || p->b > LRA_MAX_B || p->b > mn)
+    return fail(ctx, LRA_ERR_INVALID_ARG, "b must lie in [1, min(m, n, %d)]", LRA_MAX_B);
+  if (p->P < 0 || p->P > LRA_MAX_P)
+    return fail(ctx, LRA_ERR_INVALID_ARG, "P must lie in [0, %d]", LRA_MAX_P);
+  if (p->kind < 0 || p->kind > LRA_OMEGA_BERNOULLI)
+    return fail(ctx, LRA_ERR_INVALID_ARG, "unknown Omega kind %d", p->kind);
+  if (p->k < 0 || p->k > mn) return fail(ctx, LRA_ERR_INVALID_ARG, "k must lie in [0, min(m, n)]");
+  if (p->k == 0 && !(p->eps > 0.0 && isfinite(p->eps)))
+    return fail(ctx, LRA_ERR_INVALID_ARG, "eps must be finite and > 0 when k == 0");
+  if (p->k > 0 && (p->k + p->b - 1) / p->b * p->b > mn)
+    return fail(ctx, LRA_ERR_INVALID_ARG, "ceil(k/b) b exceeds min(m, n)");
+  if (p->kind == LRA_OMEGA_SPARSE_SIGN && (p->zeta < 1 || p->zeta > n || p->zeta > LRA_MAX_ZETA))
+    return fail(ctx, LRA_ERR_INVALID_ARG, "zeta must lie in [1, min(n, %d)]", LRA_MAX_ZETA);
+  if (p->kind != LRA_OMEGA_SPARSE_SIGN && p->zeta < 0)
+    return fail(ctx, LRA_ERR_INVALID_ARG, "zeta must be >= 0");
+  if (!(p->p >= 0.0 && p->p < 1.0)) return fail(ctx, LRA_ERR_INVALID_ARG, "p must lie in [0, 1)");
+  if (p->max_blocks < 0) return fail(ctx, LRA_ERR_INVALID_ARG, "max_blocks must be >= 0");
+  if ((int64_t)p->max_blocks * p->b > mn)
+    return fail(ctx, LRA_ERR_INVALID_ARG, "max_blocks * b exceeds min(m, n)");
+  if (p->flags & ~(LRA_FLAG_KEEP_Y | LRA_FLAG_PROFILE))
+    return fail(ctx, LRA_ERR_INVALID_ARG, "unknown flags");
+  return LRA_OK;
+}
+
+lra_status check_matrix(lra_ctx* ctx, const lra_matrix* A) {
+  if (!A || !A->data) return fail(ctx, LRA_ERR_INVALID_ARG, "A is NULL");
+  if (A->m != ctx->m || A->n != ctx->n)
+    return fail(ctx, LRA_ERR_INVALID_ARG, "A is %lld x %lld, context expects %lld x %lld",
+                (long long)A->m, (long long)A->n, (long long)ctx->m, (long long)ctx->n);
+  if (A->lda < A->m) return fail(ctx, LRA_ERR_INVALID_ARG, "lda < m");
+  if (A->dtype != LRA_F64)
+    return fail(ctx, LRA_ERR_UNSUPPORTED, "only LRA_F64 matrices are implemented");
+  return LRA_OK;
+}
+
+// ---- device steps ---------------------------------------------------------
+
+lra_status gemm(lra_ctx* ctx, bool trans, int64_t P, int64_t N, int64_t K, double alpha,
+                const double* X, int64_t ldx, const double* Y, int64_t ldy, double beta, double* C,
+                int64_t csp, int64_t csc) {
+  CK(dgemm(trans, P, N, K, alpha, X, ldx, Y, ldy, beta, GemmOut{C, csp, csc}, ctx->ws,
+           ctx->ws_elems, ctx->st));
+  return LRA_OK;
+}
+
+// out (rows x b, ld ldo) = Q factor of X (rows x b, ld ldx), CholQR2.
+lra_status orth(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows, double* out,
+                int64_t ldo) {
+  const int b = ctx->b;
+  TRY(gemm(ctx, true, b, b, rows, 1.0, X, ldx, X, ldx, 0.0, ctx->gram, 1, b));
+  CK(chol_inv(ctx->gram, b, PIVOT_TAU, ctx->Rinv, ctx->flags, ctx->st));
+  TRY(gemm(ctx, false, rows, b, b, 1.0, X, ldx, ctx->Rinv, b, 0.0, ctx->Tmp, 1, ctx->lds));
+  TRY(gemm(ctx, true, b, b, rows, 1.0, ctx->Tmp, ctx->lds, ctx->Tmp, ctx->lds, 0.0, ctx->gram, 1, b));
+  CK(chol_inv(ctx->gram, b, PIVOT_TAU, ctx->Rinv, ctx->flags, ctx->st));
+  TRY(gemm(ctx, false, rows, b, b, 1.0, ctx->Tmp, ctx->lds, ctx->Rinv, b, 0.0, out, 1, ldo));
+  return LRA_OK;
+}
+
+lra_status make_omega(lra_ctx* ctx, int64_t j) {
+  if (ctx->sparse)
+    CK(omega_sparse(ctx->os, j, 1, ctx->cap, ctx->om_counts, ctx->om_rows, ctx->om_vals, ctx->flags,
+                    ctx->st));
+  else
+    CK(omega_dense(ctx->os, j, 1, ctx->om_dense, ctx->ldod, ctx->st));
+  return LRA_OK;
+}
+
+// out (rows_x x b) = X Omega_j (minus the standardized-Bernoulli shift when sparse).
+lra_status apply_omega(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows_x, double* out,
+                       int64_t ldo, const double* shift) {
+  if (ctx->sparse) {
+    CK(gather_sketch(X, ldx, rows_x, ctx->om_counts, ctx->om_rows, ctx->om_vals, ctx->cap, ctx->b,
+                     out, ldo, shift, ctx->st));
+    return LRA_OK;
+  }
+  return gemm(ctx, false, rows_x, ctx->b, ctx->n, 1.0, X, ldx, ctx->om_dense, ctx->ldod, 0.0, out, 1,
+              ldo);
+}
+
+lra_status compute_z(lra_ctx* ctx, const double* A, int64_t lda) {
+  // z = A w, w = p 1 (Alg. 2 step 2)
+  CK(fill(ctx->wvec, ctx->n, ctx->n, 1, ctx->os.p, ctx->st));
+  return gemm(ctx, false, ctx->m, 1, ctx->n, 1.0, A, lda, ctx->wvec, ctx->n, 0.0, ctx->z, 1, ctx->m);
+}
+
+// Phase timing: events recorded on the context's stream around each phase,
+// read back at the per-block synchronisation point.
+lra_status prof_flush(lra_ctx* ctx) {
+  if (!ctx->prof || ctx->nev == 0) return LRA_OK;
+  CK(cudaStreamSynchronize(ctx->st));
+  for (int i = 0; i < ctx->nev; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0[i], ctx->ev1[i]));
+    ctx->phase_ms[ctx->ev_phase[i]] += ms;
+    ctx->phase_calls[ctx->ev_phase[i]] += 1;
+  }
+  ctx->nev = 0;
+  return LRA_OK;
+}
+
+lra_status prof_begin(lra_ctx* ctx, int phase) {
+  if (!ctx->prof) return LRA_OK;
+  if (ctx->nev == lra_ctx::NEV) TRY(prof_flush(ctx));
+  CK(cudaEventRecord(ctx->ev0[ctx->nev], ctx->st));
+  ctx->cur_phase = phase;
+  return LRA_OK;
+}
+
+lra_status prof_end(lra_ctx* ctx) {
+  if (!ctx->prof) return LRA_OK;
+  CK(cudaEventRecord(ctx->ev1[ctx->nev], ctx->st));
+  ctx->ev_phase[ctx->nev] = ctx->cur_phase;
+  ctx->nev += 1;
+  return LRA_OK;
+}
+
+#define PHASE(ph, body)            \
+  do {                             \
+    TRY(prof_begin(ctx, (ph)));    \
+    body;                          \
+    TRY(prof_end(ctx));            \
+  } while (0)
+
+lra_status read_record(lra_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->hp->v, ctx->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(&ctx->hp->flags, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return prof_flush(ctx);
+}
+
+lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
+  const int64_t m = ctx->m, n = ctx->n, lds = ctx->lds, ldq = ctx->ldq, ldb = ctx->ldb,
+                ldf = ctx->ldf;
+  const int b = ctx->b, P = ctx->P;
+  ctx->status = LRA_OK;
+  ctx->rank = ctx->blocks = 0;
+  ctx->E = ctx->normA2 = 0.0;
+  CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int), ctx->st));
+  // ||A||_F^2 (Alg. 1 step 1)
+  PHASE(LRA_PHASE_INDICATOR, {
+    CK(col_sums(A, lda, m, n, ctx->colsq, nullptr, ctx->st));
+    CK(total(ctx->colsq, n, ctx->scal, ctx->st));
+  });
+  TRY(read_record(ctx));
+  const double normA2 = ctx->hp->v[0];
+  if (!isfinite(normA2)) return fail(ctx, LRA_ERR_INVALID_ARG, "A has non-finite entries");
+  ctx->normA2 = ctx->E = normA2;
+  if (normA2 == 0.0) {
+    ctx->E = 0.0;
+    return LRA_OK;
+  }
+  if (ctx->sb_sparse) PHASE(LRA_PHASE_SKETCH, TRY(compute_z(ctx, A, lda)));
+  const double thr = ctx->prm.eps * ctx->prm.eps * normA2;
+  const bool fixed_rank = ctx->prm.k > 0;
+  double E = normA2;
+  int32_t status = fixed_rank ? LRA_OK : LRA_NOT_CONVERGED;
+  for (int64_t j = 0; j < ctx->nblk_max; ++j) {
+    const int64_t l = j * b;
+    PHASE(LRA_PHASE_OMEGA, TRY(make_omega(ctx, j)));
+    PHASE(LRA_PHASE_SKETCH,
+          TRY(apply_omega(ctx, A, lda, m, ctx->S0, lds, ctx->sb_sparse ? ctx->z : nullptr)));
+    double* Y = ctx->S0;
+    if (P >= 1) {
+      PHASE(LRA_PHASE_DENSE,
+            TRY(gemm(ctx, true, n, b, m, 1.0, A, lda, ctx->S0, lds, 0.0, ctx->W, 1, lds)));
+      if (l > 0) {
+        PHASE(LRA_PHASE_DEFLATE, {
+          TRY(apply_omega(ctx, ctx->B, ldb, l, ctx->BOm, ldf, ctx->sb_sparse ? ctx->zB : nullptr));
+          TRY(gemm(ctx, true, n, b, l, -1.0, ctx->B, ldb, ctx->BOm, ldf, 1.0, ctx->W, 1, lds));
+        });
+      }
+      PHASE(LRA_PHASE_ORTH, TRY(orth(ctx, ctx->W, lds, n, ctx->G, lds)));
+      for (int s = 1; s < P; ++s) {
+        PHASE(LRA_PHASE_DENSE,
+              TRY(gemm(ctx, false, m, b, n, 1.0, A, lda, ctx->G, lds, 0.0, ctx->T1, 1, lds)));
+        PHASE(LRA_PHASE_DENSE,
+              TRY(gemm(ctx, true, n, b, m, 1.0, A, lda, ctx->T1, lds, 0.0, ctx->W, 1, lds)));
+        if (l > 0) {
+          PHASE(LRA_PHASE_DEFLATE, {
+            TRY(gemm(ctx, false, l, b, n, 1.0, ctx->B, ldb, ctx->G, lds, 0.0, ctx->BOm, 1, ldf));
+            TRY(gemm(ctx, true, n, b, l, -1.0, ctx->B, ldb, ctx->BOm, ldf, 1.0, ctx->W, 1, lds));
+          });
+        }
+        PHASE(LRA_PHASE_ORTH, TRY(orth(ctx, ctx->W, lds, n, ctx->G, lds)));
+      }
+      PHASE(LRA_PHASE_DENSE,
+            TRY(gemm(ctx, false, m, b, n, 1.0, A, lda, ctx->G, lds, 0.0, ctx->Yb, 1, lds)));
+      Y = ctx->Yb;
+    }
+    if (ctx->keep_y)
+      CK(cudaMemcpy2DAsync(ctx->Yk + l * ldq, ldq * sizeof(double), Y, lds * sizeof(double),
+                           m * sizeof(double), b, cudaMemcpyDeviceToDevice, ctx->st));
+    if (l > 0) {
+      PHASE(LRA_PHASE_PROJECT, {
+        for (int pass = 0; pass < 2; ++pass) {
+          TRY(gemm(ctx, true, l, b, m, 1.0, ctx->Q, ldq, Y, lds, 0.0, ctx->F, 1, ldf));
+          TRY(gemm(ctx, false, m, b, l, -1.0, ctx->Q, ldq, ctx->F, ldf, 1.0, Y, 1, lds));
+        }
+      });
+    }
+    double* Qj = ctx->Q + l * ldq;
+    PHASE(LRA_PHASE_ORTH, TRY(orth(ctx, Y, lds, m, Qj, ldq)));
+    PHASE(LRA_PHASE_DENSE,
+          TRY(gemm(ctx, true, n, b, m, 1.0, A, lda, Qj, ldq, 0.0, ctx->Wt, 1, lds)));
+    PHASE(LRA_PHASE_INDICATOR, {
+      CK(col_sums(ctx->Wt, lds, n, b, ctx->colsq, ctx->sb_sparse ? ctx->colsum : nullptr, ctx->st));
+      CK(total(ctx->colsq, b, ctx->scal + 1, ctx->st));
+      CK(append_rows(ctx->Wt, lds, n, b, ctx->B, ldb, l, ctx->colsum, ctx->os.p,
+                     ctx->sb_sparse ? ctx->zB : nullptr, ctx->st));
+    });
+    TRY(read_record(ctx));
+    const int fl = ctx->hp->flags;
+    if (fl & FLAG_OMEGA_CAP)
+      return fail(ctx, LRA_ERR_INVALID_ARG, "fixed-zeta draws exhausted (zeta too close to n)");
+    if (fl & FLAG_BREAKDOWN) {
+      status = LRA_BREAKDOWN;
+      break;
+    }
+    E -= ctx->hp->v[1];
+    ctx->blocks = j + 1;
+    ctx->rank = (j + 1) * b;
+    ctx->E = E;
+    if (!fixed_rank && E < thr) {
+      status = LRA_OK;
+      break;
+    }
+  }
+  ctx->status = status;
+  return (lra_status)status;
+}
+
+lra_status ensure_sketch_scratch(lra_ctx* ctx, int64_t cols, int cap) {
+  const int64_t entries = cols * cap;
+  if (cols <= ctx->sk_cols && entries <= ctx->sk_entries) return LRA_OK;
+  cudaFree(ctx->sk_counts);
+  cudaFree(ctx->sk_rows);
+  cudaFree(ctx->sk_vals);
+  ctx->sk_counts = nullptr;
+  ctx->sk_rows = nullptr;
+  ctx->sk_vals = nullptr;
+  ctx->sk_cols = ctx->sk_entries = 0;
+  CK(dalloc(&ctx->sk_counts, cols));
+  CK(dalloc(&ctx->sk_rows, entries));
+  CK(dalloc(&ctx->sk_vals, entries));
+  ctx->sk_cols = cols;
+  ctx->sk_entries = entries;
+  return LRA_OK;
+}
+
+void free_all(lra_ctx* c) {
+  void* ptrs[] = {c->Q,      c->B,        c->Yk,     c->S0,       c->Yb,        c->T1,
+                  c->Tmp,    c->W,        c->G,      c->Wt,       c->F,         c->BOm,
+                  c->z,      c->zB,       c->wvec,   c->ws,       c->gram,      c->Rinv,
+                  c->colsq,  c->colsum,   c->scal,   c->flags,    c->om_counts, c->om_rows,
+                  c->om_vals, c->om_dense, c->sk_counts, c->sk_rows, c->sk_vals, c->A_host_copy};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->hp) cudaFreeHost(c->hp);
+  for (int i = 0; i < lra_ctx::NEV; ++i) {
+    if (c->ev0[i]) cudaEventDestroy(c->ev0[i]);
+    if (c->ev1[i]) cudaEventDestroy(c->ev1[i]);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t lra_version(void) { return LRA_VERSION; }
+
+uint64_t lra_kernel_launches(void) { return g_launches.load(); }
+
+const char* lra_status_string(int32_t s) {
+  switch (s) {
+    case LRA_OK: return "LRA_OK";
+    case LRA_NOT_CONVERGED: return "LRA_NOT_CONVERGED";
+    case LRA_BREAKDOWN: return "LRA_BREAKDOWN";
+    case LRA_ERR_INVALID_ARG: return "LRA_ERR_INVALID_ARG";
+    case LRA_ERR_OOM: return "LRA_ERR_OOM";
+    case LRA_ERR_CUDA: return "LRA_ERR_CUDA";
+    case LRA_ERR_TIMEOUT: return "LRA_ERR_TIMEOUT";
+    case LRA_ERR_UNSUPPORTED: return "LRA_ERR_UNSUPPORTED";
+    default: return "unknown status";
+  }
+}
+
+const char* lra_last_error(const lra_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int64_t lra_capacity(const lra_ctx* ctx) { return ctx ? ctx->lmax : -1; }
+
+lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* params,
+                      void* cuda_stream) {
+  if (!out || !params) return LRA_ERR_INVALID_ARG;
+  *out = nullptr;
+  lra_ctx* ctx = new lra_ctx();
+  lra_status s = check_params(ctx, m, n, params);
+  if (s != LRA_OK) {
+    delete ctx;
+    return s;
+  }
+  ctx->m = m;
+  ctx->n = n;
+  ctx->prm = *params;
+  ctx->st = (cudaStream_t)cuda_stream;
+  ctx->b = params->b;
+  ctx->P = params->P;
+  ctx->kind = params->kind;
+  ctx->keep_y = (params->flags & LRA_FLAG_KEEP_Y) != 0;
+  const int64_t mn = std::min(m, n);
+  ctx->nblk_max = params->k > 0 ? (params->k + ctx->b - 1) / ctx->b
+                  : params->max_blocks > 0 ? params->max_blocks
+                                           : (mn + 2 * ctx->b - 1) / (2 * ctx->b);
+  ctx->lmax = ctx->nblk_max * ctx->b;
+
+  OmegaSpec& os = ctx->os;
+  os.kind = params->kind;
+  os.n = n;
+  os.b = params->b;
+  os.zeta = params->zeta;
+  os.k0 = (uint32_t)(params->seed & 0xFFFFFFFFull);
+  os.k1 = (uint32_t)(params->seed >> 32);
+  os.p = 0.0;
+  os.thr = 0;
+  os.inv_scale = 1.0;
+  if (params->kind == LRA_OMEGA_SPARSE_SIGN) {
+    os.inv_scale = 1.0 / sqrt((double)params->zeta);
+    ctx->sparse = true;
+    ctx->cap = params->zeta;
+  } else if (params->kind == LRA_OMEGA_GAUSSIAN) {
+    ctx->sparse = false;
+  } else {
+    os.p = params->p > 0.0 ? params->p : default_p(params->kind, n, params->zeta);
+    os.thr = (uint64_t)floor(os.p * 4294967296.0);
+    if (params->kind == LRA_OMEGA_SPARSE_SIGN_IID || params->kind == LRA_OMEGA_SPARSE_GAUSSIAN)
+      os.inv_scale = 1.0 / sqrt(os.p);
+    ctx->sparse = (double)n * os.p <= (double)SPARSE_MAX_NNZ_PER_COL;
+    ctx->cap = (int)n;
+  }
+  ctx->sb_sparse = ctx->sparse && params->kind == LRA_OMEGA_STD_BERNOULLI;
+
+  ctx->ldq = round_up(m, 2);
+  ctx->ldb = round_up(std::max<int64_t>(ctx->lmax, 1), 2);
+  ctx->lds = round_up(std::max(m, n), 2);
+  ctx->ldf = round_up(std::max<int64_t>(ctx->lmax, 1), 2);
+  ctx->ldod = round_up(n, 2);
+  ctx->ws_elems = dgemm_ws_elems();
+  const int b = ctx->b;
+#define ALLOC(ptr, count)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = dalloc(&ctx->ptr, (count));                                           \
+    if (e_ != cudaSuccess) {                                                               \
+      lra_status r_ = fail(ctx, e_ == cudaErrorMemoryAllocation ? LRA_ERR_OOM : LRA_ERR_CUDA, \
+                           "allocating %s: %s", #ptr, cudaGetErrorString(e_));             \
+      free_all(ctx);                                                                       \
+      delete ctx;                                                                          \
+      cudaGetLastError();                                                                  \
+      return r_;                                                                           \
+    }                                                                                      \
+  } while (0)
+  ALLOC(Q, ctx->ldq * ctx->lmax);
+  ALLOC(B, ctx->ldb * n);
+  if (ctx->keep_y) ALLOC(Yk, ctx->ldq * ctx->lmax);
+  ALLOC(S0, ctx->lds * b);
+  ALLOC(Yb, ctx->lds * b);
+  ALLOC(T1, ctx->lds * b);
+  ALLOC(Tmp, ctx->lds * b);
+  ALLOC(W, ctx->lds * b);
+  ALLOC(G, ctx->lds * b);
+  ALLOC(Wt, ctx->lds * b);
+  ALLOC(F, ctx->ldf * b);
+  ALLOC(BOm, ctx->ldf * b);
+  ALLOC(z, m);
+  ALLOC(zB, ctx->ldb);
+  ALLOC(wvec, n);
+  ALLOC(ws, ctx->ws_elems);
+  ALLOC(gram, LRA_MAX_B * LRA_MAX_B);
+  ALLOC(Rinv, LRA_MAX_B * LRA_MAX_B);
+  ALLOC(colsq, std::max<int64_t>(n, LRA_MAX_B));
+  ALLOC(colsum, std::max<int64_t>(n, LRA_MAX_B));
+  ALLOC(scal, 8);
+  ALLOC(flags, 4);
+  if (ctx->sparse) {
+    ALLOC(om_counts, b);
+    ALLOC(om_rows, (int64_t)b * ctx->cap);
+    ALLOC(om_vals, (int64_t)b * ctx->cap);
+  } else {
+    ALLOC(om_dense, ctx->ldod * b);
+  }
+#undef ALLOC
+  cudaError_t e = cudaMallocHost((void**)&ctx->hp, sizeof(Pinned));
+  if (e != cudaSuccess) {
+    free_all(ctx);
+    delete ctx;
+    cudaGetLastError();
+    return LRA_ERR_OOM;
+  }
+  if (params->flags & LRA_FLAG_PROFILE) {
+    ctx->prof = true;
+    for (int i = 0; i < lra_ctx::NEV && e == cudaSuccess; ++i) {
+      e = cudaEventCreate(&ctx->ev0[i]);
+      if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1[i]);
+    }
+    if (e != cudaSuccess) {
+      free_all(ctx);
+      delete ctx;
+      return LRA_ERR_CUDA;
+    }
+  }
+  // zB must start at zero: rows are written as blocks are appended.
+  e = cudaMemsetAsync(ctx->zB, 0, ctx->ldb * sizeof(double), ctx->st);
+  if (e != cudaSuccess) {
+    free_all(ctx);
+    delete ctx;
+    return LRA_ERR_CUDA;
+  }
+  *out = ctx;
+  return LRA_OK;
+}
+
+void lra_destroy(lra_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  else cudaDeviceSynchronize();
+  free_all(ctx);
+  delete ctx;
+}
+
+lra_status lra_farpca_run(lra_ctx* ctx, const lra_matrix* A) {
+  if (!ctx) return LRA_ERR_INVALID_ARG;
+  ctx->err.clear();
+  TRY(check_matrix(ctx, A));
+  return run(ctx, (const double*)A->data, A->lda);
+}
+
+lra_status lra_phase_times(lra_ctx* ctx, double* ms, int64_t* calls, int32_t nphases,
+                           int32_t reset) {
+  if (!ctx || nphases < 0 || nphases > LRA_NUM_PHASES) return LRA_ERR_INVALID_ARG;
+  TRY(prof_flush(ctx));
+  for (int i = 0; i < nphases; ++i) {
+    if (ms) ms[i] = ctx->phase_ms[i];
+    if (calls) calls[i] = ctx->phase_calls[i];
+  }
+  if (reset)
+    for (int i = 0; i < LRA_NUM_PHASES; ++i) {
+      ctx->phase_ms[i] = 0.0;
+      ctx->phase_calls[i] = 0;
+    }
+  return LRA_OK;
+}
+
+lra_status lra_result(const lra_ctx* ctx, lra_result_t* out) {
+  if (!ctx || !out) return LRA_ERR_INVALID_ARG;
+  memset(out, 0, sizeof *out);
+  out->status = ctx->status;
+  out->rank = ctx->rank;
+  out->blocks = ctx->blocks;
+  out->E = ctx->E;
+  out->normA2 = ctx->normA2;
+  out->rel_err = ctx->normA2 > 0.0 ? sqrt(std::max(ctx->E, 0.0) / ctx->normA2) : 0.0;
+  out->Q = ctx->Q;
+  out->ldq = ctx->ldq;
+  out->B = ctx->B;
+  out->ldb = ctx->ldb;
+  out->Y = ctx->keep_y ? ctx->Yk : nullptr;
+  out->ldy = ctx->keep_y ? ctx->ldq : 0;
+  return LRA_OK;
+}
+
+lra_status lra_sketch(lra_ctx* ctx, const lra_matrix* A, int64_t j0, int64_t nblk, double* Y,
+                      int64_t ldy) {
+  if (!ctx) return LRA_ERR_INVALID_ARG;
+  ctx->err.clear();
+  TRY(check_matrix(ctx, A));
+  if (j0 < 0 || nblk < 0 || j0 + nblk > (int64_t)UINT32_MAX)
+    return fail(ctx, LRA_ERR_INVALID_ARG, "block range out of [0, 2^32)");
+  if (nblk == 0) return LRA_OK;
+  if (!Y || ldy < ctx->m) return fail(ctx, LRA_ERR_INVALID_ARG, "Y is NULL or ldy < m");
+  const double* Ad = (const double*)A->data;
+  const int b = ctx->b;
+  if (!ctx->sparse) {
+    for (int64_t j = j0; j < j0 + nblk; ++j) {
+      CK(omega_dense(ctx->os, j, 1, ctx->om_dense, ctx->ldod, ctx->st));
+      TRY(gemm(ctx, false, ctx->m, b, ctx->n, 1.0, Ad, A->lda, ctx->om_dense, ctx->ldod, 0.0,
+               Y + (j - j0) * b * ldy, 1, ldy));
+    }
+    return LRA_OK;
+  }
+  if (ctx->sb_sparse) TRY(compute_z(ctx, Ad, A->lda));
+  int64_t chunk = std::max<int64_t>(1, SKETCH_SCRATCH_ENTRIES / ((int64_t)b * ctx->cap));
+  chunk = std::min(chunk, nblk);
+  TRY(ensure_sketch_scratch(ctx, chunk * b, ctx->cap));
+  CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int), ctx->st));
+  for (int64_t j = j0; j < j0 + nblk; j += chunk) {
+    const int64_t nb = std::min(chunk, j0 + nblk - j);
+    CK(omega_sparse(ctx->os, j, nb, ctx->cap, ctx->sk_counts, ctx->sk_rows, ctx->sk_vals,
+                    ctx->flags, ctx->st));
+    CK(gather_sketch(Ad, A->lda, ctx->m, ctx->sk_counts, ctx->sk_rows, ctx->sk_vals, ctx->cap,
+                     nb * b, Y + (j - j0) * b * ldy, ldy, ctx->sb_sparse ? ctx->z : nullptr,
+                     ctx->st));
+  }
+  return LRA_OK;
+}
+
+lra_status lra_copy_omega(lra_ctx* ctx, int64_t j, int64_t cap, int32_t* counts, int32_t* rows,
+                          double* vals) {
+  if (!ctx || !counts || !rows || !vals) return LRA_ERR_INVALID_ARG;
+  ctx->err.clear();
+  const int b = ctx->b;
+  const int64_t n = ctx->n;
+  if (j < 0 || j > (int64_t)UINT32_MAX) return fail(ctx, LRA_ERR_INVALID_ARG, "j out of range");
+  if (ctx->kind == LRA_OMEGA_GAUSSIAN) {
+    if (cap < n) return fail(ctx, LRA_ERR_INVALID_ARG, "cap must be >= n");
+    CK(omega_dense(ctx->os, j, 1, ctx->om_dense, ctx->ldod, ctx->st));
+    CK(cudaMemcpy2DAsync(vals, cap * sizeof(double), ctx->om_dense, ctx->ldod * sizeof(double),
+                         n * sizeof(double), b, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    for (int c = 0; c < b; ++c) {
+      counts[c] = (int32_t)n;
+      for (int64_t t = 0; t < n; ++t) rows[c * cap + t] = (int32_t)t;
+    }
+    return LRA_OK;
+  }
+  const int dcap = ctx->kind == LRA_OMEGA_SPARSE_SIGN ? ctx->prm.zeta : (int)n;
+  if (cap < dcap) return fail(ctx, LRA_ERR_INVALID_ARG, "cap must be >= %d", dcap);
+  TRY(ensure_sketch_scratch(ctx, b, dcap));
+  CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int), ctx->st));
+  CK(omega_sparse(ctx->os, j, 1, dcap, ctx->sk_counts, ctx->sk_rows, ctx->sk_vals, ctx->flags,
+                  ctx->st));
+  CK(cudaMemcpyAsync(counts, ctx->sk_counts, b * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpy2DAsync(rows, cap * sizeof(int32_t), ctx->sk_rows, dcap * sizeof(int32_t),
+                       dcap * sizeof(int32_t), b, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpy2DAsync(vals, cap * sizeof(double), ctx->sk_vals, dcap * sizeof(double),
+                       dcap * sizeof(double), b, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(&ctx->hp->flags, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (ctx->hp->flags & FLAG_OMEGA_CAP)
+    return fail(ctx, LRA_ERR_INVALID_ARG, "fixed-zeta draws exhausted");
+  return LRA_OK;
+}
+
+lra_status lra_farpca_host(lra_ctx* ctx, const double* A_host, int64_t lda_host, double* Q_host,
+                           int64_t ldq_host, double* B_host, int64_t ldb_host, lra_result_t* out) {
+  if (!ctx || !A_host) return LRA_ERR_INVALID_ARG;
+  ctx->err.clear();
+  const int64_t m = ctx->m, n = ctx->n;
+  if (lda_host < m) return fail(ctx, LRA_ERR_INVALID_ARG, "lda_host < m");
+  if (Q_host && ldq_host < m) return fail(ctx, LRA_ERR_INVALID_ARG, "ldq_host < m");
+  if (B_host && ldb_host < ctx->lmax) return fail(ctx, LRA_ERR_INVALID_ARG, "ldb_host < capacity");
+  if (!ctx->A_host_copy) CK(dalloc(&ctx->A_host_copy, ctx->ldq * n));
+  CK(cudaMemcpy2DAsync(ctx->A_host_copy, ctx->ldq * sizeof(double), A_host,
+                       lda_host * sizeof(double), m * sizeof(double), n, cudaMemcpyHostToDevice,
+                       ctx->st));
+  lra_status s = run(ctx, ctx->A_host_copy, ctx->ldq);
+  if (s < 0) return s;
+  if (Q_host && ctx->rank > 0)
+    CK(cudaMemcpy2DAsync(Q_host, ldq_host * sizeof(double), ctx->Q, ctx->ldq * sizeof(double),
+                         m * sizeof(double), ctx->rank, cudaMemcpyDeviceToHost, ctx->st));
+  if (B_host && ctx->rank > 0)
+    CK(cudaMemcpy2DAsync(B_host, ldb_host * sizeof(double), ctx->B, ctx->ldb * sizeof(double),
+                         ctx->rank * sizeof(double), n, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (out) lra_result(ctx, out);
+  return s;
+}
+
+}  // extern "C"

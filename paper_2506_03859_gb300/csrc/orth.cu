@@ -1,0 +1,163 @@
+// Orthonormalisation and reduction kernels of the farPCA block (arxiv
+// 2506.03859): the b x b Cholesky factor of a Gram matrix and its inverse (the
+// basis Q_j = Y' R^{-1}, the role of Z^{-1} in Alg. 1 step 10), the Frobenius
+// norms behind the error indicator (E = ||A||_F^2 - sum_j ||B_j||_F^2, Sec. 2.1),
+// and the row append of B_j.  All reductions use a fixed order so repeated runs
+// give identical bits.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace lra {
+
+__device__ __forceinline__ double block_sum_256(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
+  __syncthreads();
+  return s;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256) k_col_sums(const double* __restrict__ X, int64_t ld,
+                                                  int64_t rows, double* __restrict__ sumsq,
+                                                  double* __restrict__ sum) {
+  __shared__ double red[8];
+  const int64_t c = blockIdx.x;
+  const double* col = X + c * ld;
+  double sq = 0.0, s = 0.0;
+  for (int64_t i = threadIdx.x; i < rows; i += 256) {
+    const double x = __ldg(col + i);
+    sq = fma(x, x, sq);
+    s += x;
+  }
+  if (sumsq) {
+    const double t = block_sum_256(sq, red);
+    if (threadIdx.x == 0) sumsq[c] = t;
+  }
+  if (sum) {
+    const double t = block_sum_256(s, red);
+    if (threadIdx.x == 0) sum[c] = t;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_total(const double* __restrict__ v, int64_t count,
+                                                double* __restrict__ out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < count; i += 1024) s += v[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 32; ++q) t += red[q];
+    out[0] = t;
+  }
+}
+
+// Upper Cholesky R of S (b <= 64) computed row by row, as R[c, c] = sqrt(S_cc -
+// sum_k R_kc^2) and R[c, c'] = (S_cc' - sum_k R_kc R_kc') / R_cc, then R^{-1} by
+// back substitution, one column per thread.
+__global__ void __launch_bounds__(64) k_chol_inv(const double* __restrict__ S, int b, double tau,
+                                                 double* __restrict__ Rinv, int* __restrict__ flags) {
+  __shared__ double R[64][65];
+  __shared__ double X[64][65];
+  __shared__ double Sd[64];
+  __shared__ int bad;
+  const int t = threadIdx.x;
+  for (int i = 0; i < b; ++i)
+    if (t < b) R[i][t] = S[i + t * b];
+  if (t < b) Sd[t] = S[t + t * b];
+  if (t == 0) bad = 0;
+  __syncthreads();
+  for (int c = 0; c < b; ++c) {
+    if (t == 0) {
+      double d = R[c][c];
+      for (int k = 0; k < c; ++k) d -= R[k][c] * R[k][c];
+      if (!(isfinite(d) && d > tau * Sd[c]))
+        bad = 1;
+      else
+        R[c][c] = sqrt(d);
+    }
+    __syncthreads();
+    if (bad) break;
+    if (t > c && t < b) {
+      double v = R[c][t];
+      for (int k = 0; k < c; ++k) v -= R[k][c] * R[k][t];
+      R[c][t] = v / R[c][c];
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (t == 0) atomicOr(flags, FLAG_BREAKDOWN);
+    for (int i = 0; i < b; ++i)
+      if (t < b) Rinv[i + t * b] = 0.0;
+    return;
+  }
+  if (t < b) {
+    const int jc = t;
+    for (int i = 0; i < b; ++i) X[i][jc] = 0.0;
+    X[jc][jc] = 1.0 / R[jc][jc];
+    for (int i = jc - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int k = i + 1; k <= jc; ++k) s += R[i][k] * X[k][jc];
+      X[i][jc] = -s / R[i][i];
+    }
+    for (int i = 0; i < b; ++i) Rinv[i + jc * b] = X[i][jc];
+  }
+}
+
+__global__ void k_append_rows(const double* __restrict__ Wt, int64_t ldw, int64_t n, int b,
+                              double* __restrict__ B, int64_t ldb, int64_t row0,
+                              const double* __restrict__ colsum, double p, double* __restrict__ zB) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * b) return;
+  const int c = (int)(idx % b);
+  const int64_t r = idx / b;
+  B[row0 + c + r * ldb] = Wt[r + (int64_t)c * ldw];
+  if (zB && r == 0) zB[row0 + c] = p * colsum[c];
+}
+
+__global__ void k_fill(double* __restrict__ X, int64_t ld, int64_t rows, int64_t cols, double v) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * cols) return;
+  X[(idx % rows) + (idx / rows) * ld] = v;
+}
+
+cudaError_t col_sums(const double* X, int64_t ld, int64_t rows, int64_t cols, double* sumsq,
+                     double* sum, cudaStream_t st) {
+  if (cols <= 0) return cudaSuccess;
+  k_col_sums<<<(unsigned)cols, 256, 0, st>>>(X, ld, rows, sumsq, sum);
+  return launched();
+}
+
+cudaError_t total(const double* v, int64_t count, double* out, cudaStream_t st) {
+  k_total<<<1, 1024, 0, st>>>(v, count, out);
+  return launched();
+}
+
+cudaError_t chol_inv(const double* S, int b, double tau, double* Rinv, int* flags, cudaStream_t st) {
+  k_chol_inv<<<1, 64, 0, st>>>(S, b, tau, Rinv, flags);
+  return launched();
+}
+
+cudaError_t append_rows(const double* Wt, int64_t ldw, int64_t n, int b, double* B, int64_t ldb,
+                        int64_t row0, const double* colsum, double p, double* zB, cudaStream_t st) {
+  const int64_t total_ = n * b;
+  k_append_rows<<<(unsigned)((total_ + 255) / 256), 256, 0, st>>>(Wt, ldw, n, b, B, ldb, row0,
+                                                                  colsum, p, zB);
+  return launched();
+}
+
+cudaError_t fill(double* X, int64_t ld, int64_t rows, int64_t cols, double v, cudaStream_t st) {
+  const int64_t total_ = rows * cols;
+  if (total_ <= 0) return cudaSuccess;
+  k_fill<<<(unsigned)((total_ + 255) / 256), 256, 0, st>>>(X, ld, rows, cols, v);
+  return launched();
+}
+
+}  // namespace lra

@@ -1,0 +1,243 @@
+"""ctypes binding of liblra.so (include/lra.h): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels; PyTorch
+supplies device memory and the stream.  Importing this module does not load the
+library; the first call does, and fails with an error when it was not built
+(no CPU fallback).
+
+Names follow the C ABI: lra_create / lra_sketch / lra_farpca_run / lra_result /
+lra_copy_omega / lra_farpca_host / lra_last_error, wrapped by ``Farpca``.
+"""
+import ctypes
+import os
+from ctypes import POINTER, Structure, byref, c_char_p, c_double, c_int32, c_int64, c_uint32, c_uint64, c_void_p
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblra.so")
+
+OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
+ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5
+GAUSSIAN, STD_BERNOULLI, SPARSE_SIGN, SPARSE_SIGN_IID, SPARSE_GAUSSIAN, BERNOULLI = range(6)
+F64, F32 = 0, 1
+FLAG_KEEP_Y = 1
+FLAG_PROFILE = 2
+PHASES = ("omega", "sketch", "dense", "deflate", "project", "orth", "indicator")
+MAX_B, MAX_P, MAX_ZETA = 64, 8, 256
+
+EXPORTS = ("lra_create", "lra_destroy", "lra_capacity", "lra_sketch", "lra_farpca_run", "lra_result",
+           "lra_farpca_host", "lra_copy_omega", "lra_last_error", "lra_status_string",
+           "lra_kernel_launches", "lra_version", "lra_phase_times")
+
+
+class Matrix(Structure):
+    _fields_ = [("m", c_int64), ("n", c_int64), ("lda", c_int64), ("dtype", c_int32),
+                ("reserved", c_int32), ("data", c_void_p)]
+
+
+class Params(Structure):
+    _fields_ = [("eps", c_double), ("k", c_int64), ("b", c_int32), ("P", c_int32), ("kind", c_int32),
+                ("zeta", c_int32), ("p", c_double), ("seed", c_uint64), ("max_blocks", c_int32),
+                ("flags", c_uint32)]
+
+
+class Result(Structure):
+    _fields_ = [("status", c_int32), ("reserved", c_int32), ("rank", c_int64), ("blocks", c_int64),
+                ("E", c_double), ("normA2", c_double), ("rel_err", c_double), ("Q", c_void_p),
+                ("ldq", c_int64), ("B", c_void_p), ("ldb", c_int64), ("Y", c_void_p), ("ldy", c_int64)]
+
+
+class LraError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (status_string(status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load liblra.so once; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError("liblra.so not built at %s: run __graft_entry__.build() or "
+                                "python -m paper_2506_03859_gb300.build" % path)
+    lib = ctypes.CDLL(path)
+    vp = c_void_p
+    lib.lra_create.argtypes = [POINTER(vp), c_int64, c_int64, POINTER(Params), vp]
+    lib.lra_create.restype = c_int32
+    lib.lra_destroy.argtypes = [vp]
+    lib.lra_destroy.restype = None
+    lib.lra_capacity.argtypes = [vp]
+    lib.lra_capacity.restype = c_int64
+    lib.lra_sketch.argtypes = [vp, POINTER(Matrix), c_int64, c_int64, vp, c_int64]
+    lib.lra_sketch.restype = c_int32
+    lib.lra_farpca_run.argtypes = [vp, POINTER(Matrix)]
+    lib.lra_farpca_run.restype = c_int32
+    lib.lra_result.argtypes = [vp, POINTER(Result)]
+    lib.lra_result.restype = c_int32
+    lib.lra_farpca_host.argtypes = [vp, vp, c_int64, vp, c_int64, vp, c_int64, POINTER(Result)]
+    lib.lra_farpca_host.restype = c_int32
+    lib.lra_copy_omega.argtypes = [vp, c_int64, c_int64, vp, vp, vp]
+    lib.lra_copy_omega.restype = c_int32
+    lib.lra_last_error.argtypes = [vp]
+    lib.lra_last_error.restype = c_char_p
+    lib.lra_status_string.argtypes = [c_int32]
+    lib.lra_status_string.restype = c_char_p
+    lib.lra_kernel_launches.argtypes = []
+    lib.lra_kernel_launches.restype = c_uint64
+    lib.lra_version.argtypes = []
+    lib.lra_version.restype = c_int32
+    lib.lra_phase_times.argtypes = [vp, vp, vp, c_int32, c_int32]
+    lib.lra_phase_times.restype = c_int32
+    _lib = lib
+    return lib
+
+
+def status_string(s):
+    return load().lra_status_string(int(s)).decode()
+
+
+def kernel_launches():
+    return int(load().lra_kernel_launches())
+
+
+class _DeviceView:
+    """A __cuda_array_interface__ over library-owned device memory (no copy)."""
+
+    def __init__(self, ptr, shape, strides_elems, owner):
+        self._owner = owner
+        self.__cuda_array_interface__ = {
+            "shape": tuple(shape), "typestr": "<f8", "data": (int(ptr), False),
+            "strides": tuple(8 * s for s in strides_elems), "version": 3, "stream": None}
+
+
+def _device_matrix(A, torch):
+    if not (A.is_cuda and A.dtype == torch.float64 and A.dim() == 2):
+        raise TypeError("A must be a 2-D float64 CUDA tensor")
+    m, n = A.shape
+    if A.stride(0) != 1 or (n > 1 and A.stride(1) < m):
+        raise ValueError("A must be column-major (stride(0) == 1, stride(1) >= m)")
+    return Matrix(m, n, max(A.stride(1), m), F64, 0, A.data_ptr())
+
+
+def column_major(t):
+    """Copy a 2-D tensor into a fresh column-major tensor on the same device."""
+    import torch
+    out = torch.empty_strided(tuple(t.shape), (1, t.shape[0]), dtype=t.dtype, device=t.device)
+    out.copy_(t)
+    return out
+
+
+class Farpca:
+    """One library context (lra_create) for m x n inputs and fixed parameters."""
+
+    def __init__(self, m, n, eps=0.0, k=0, b=20, P=1, kind=SPARSE_SIGN, zeta=8, p=0.0, seed=0,
+                 max_blocks=0, keep_y=False, profile=False, stream=None):
+        import torch
+        self._torch = torch
+        self._lib = load()
+        self.m, self.n, self.b = m, n, b
+        flags = (FLAG_KEEP_Y if keep_y else 0) | (FLAG_PROFILE if profile else 0)
+        self.params = Params(eps, k, b, P, kind, zeta, p, seed & 0xFFFFFFFFFFFFFFFF, max_blocks, flags)
+        self._ctx = c_void_p()
+        if stream is None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        sptr = c_void_p(stream.cuda_stream if stream is not None else 0)
+        s = self._lib.lra_create(byref(self._ctx), m, n, byref(self.params), sptr)
+        if s != OK:
+            raise LraError(s, "lra_create failed (invalid parameters or no device memory)")
+
+    def close(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            self._lib.lra_destroy(self._ctx)
+            self._ctx = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, s):
+        if s < 0:
+            raise LraError(s, self._lib.lra_last_error(self._ctx).decode())
+        return s
+
+    @property
+    def capacity(self):
+        return int(self._lib.lra_capacity(self._ctx))
+
+    def run(self, A):
+        """lra_farpca_run on a column-major float64 CUDA tensor; returns the status."""
+        mat = _device_matrix(A, self._torch)
+        return self._check(self._lib.lra_farpca_run(self._ctx, byref(mat)))
+
+    def result(self):
+        """lra_result: a dict with status, rank, blocks, E, normA2, rel_err and
+        zero-copy torch views Q (m x rank), B (rank x n) and, if kept, Y."""
+        r = Result()
+        self._check(self._lib.lra_result(self._ctx, byref(r)))
+        torch = self._torch
+        out = dict(status=r.status, rank=r.rank, blocks=r.blocks, E=r.E, normA2=r.normA2,
+                   rel_err=r.rel_err)
+        l = r.rank
+        if l > 0:
+            out["Q"] = torch.as_tensor(_DeviceView(r.Q, (self.m, l), (1, r.ldq), self), device="cuda")
+            out["B"] = torch.as_tensor(_DeviceView(r.B, (l, self.n), (1, r.ldb), self), device="cuda")
+            if r.Y:
+                out["Y"] = torch.as_tensor(_DeviceView(r.Y, (self.m, l), (1, r.ldy), self), device="cuda")
+        return out
+
+    def phase_times(self, reset=True):
+        """lra_phase_times: {phase: (ms, calls)} accumulated since the last reset."""
+        import numpy as np
+        ms = np.zeros(len(PHASES))
+        calls = np.zeros(len(PHASES), dtype=np.int64)
+        self._check(self._lib.lra_phase_times(self._ctx, ms.ctypes.data, calls.ctypes.data, len(PHASES),
+                                              1 if reset else 0))
+        return {name: (float(ms[i]), int(calls[i])) for i, name in enumerate(PHASES)}
+
+    def sketch(self, A, j0, nblk, Y=None):
+        """lra_sketch: Y = A [Omega_j0 .. Omega_{j0+nblk-1}] into a column-major m x nblk*b tensor."""
+        torch = self._torch
+        mat = _device_matrix(A, torch)
+        if Y is None:
+            Y = torch.empty_strided((self.m, nblk * self.b), (1, self.m), dtype=torch.float64,
+                                    device=A.device)
+        if Y.stride(0) != 1 or Y.shape[0] != self.m or Y.shape[1] < nblk * self.b:
+            raise ValueError("Y must be column-major m x (nblk*b)")
+        ldy = max(Y.stride(1), self.m)
+        self._check(self._lib.lra_sketch(self._ctx, byref(mat), j0, nblk, c_void_p(Y.data_ptr()), ldy))
+        return Y
+
+    def copy_omega(self, j, cap=None):
+        """lra_copy_omega: (counts[b], rows[b, cap], vals[b, cap]) as numpy arrays."""
+        import numpy as np
+        kind = self.params.kind
+        if cap is None:
+            cap = self.params.zeta if kind == SPARSE_SIGN else self.n
+        counts = np.zeros(self.b, dtype=np.int32)
+        rows = np.zeros((self.b, cap), dtype=np.int32)
+        vals = np.zeros((self.b, cap), dtype=np.float64)
+        self._check(self._lib.lra_copy_omega(self._ctx, j, cap, counts.ctypes.data, rows.ctypes.data,
+                                             vals.ctypes.data))
+        return counts, rows, vals
+
+    def run_host(self, A_host, Q_host=None, B_host=None):
+        """lra_farpca_host: A, Q, B in host memory (numpy, column-major; ideally
+        pinned).  Returns the result dict (without device views)."""
+        import numpy as np
+        if A_host.dtype != np.float64 or not A_host.flags.f_contiguous:
+            raise ValueError("A_host must be a Fortran-ordered float64 array")
+        r = Result()
+        qp = c_void_p(Q_host.ctypes.data) if Q_host is not None else c_void_p(0)
+        bp = c_void_p(B_host.ctypes.data) if B_host is not None else c_void_p(0)
+        ldq = Q_host.shape[0] if Q_host is not None else 0
+        ldb = B_host.shape[0] if B_host is not None else 0
+        s = self._lib.lra_farpca_host(self._ctx, c_void_p(A_host.ctypes.data), A_host.shape[0], qp, ldq,
+                                      bp, ldb, byref(r))
+        self._check(s)
+        return dict(status=r.status, rank=r.rank, blocks=r.blocks, E=r.E, normA2=r.normA2,
+                    rel_err=r.rel_err)

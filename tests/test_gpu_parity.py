@@ -1,0 +1,200 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Bar (from the method's arithmetic, FP64 on both sides):
+  * Omega: row indices bit-exact; values bit-exact except the Gaussian ones
+    (Box-Muller through the device's log/cospi vs the host libm: |diff| <= 1e-14 |v|);
+  * sketch and the pre-projection Y_j: max |diff| <= 1e-12 / 1e-10 of max |ref|;
+  * attained rank and status equal; E within 1e-10 relative; Q within 1e-10
+    absolute (entries are O(m^-1/2)); B within 1e-10 of max |B|.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from lra_inputs import low_rank_matrix, workload_matrix  # noqa: E402
+from oracle import farpca as F  # noqa: E402
+from oracle import omega as om  # noqa: E402
+from paper_2506_03859_gb300 import lra  # noqa: E402
+from paper_2506_03859_gb300.build import build  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+KIND_CASES = [(om.GAUSSIAN, 0.0, 0), (om.STD_BERNOULLI, 0.5, 0), (om.STD_BERNOULLI, 0.0, 0),
+              (om.SPARSE_SIGN, 0.0, 8), (om.SPARSE_SIGN_IID, 0.0, 0), (om.SPARSE_GAUSSIAN, 0.0, 0),
+              (om.BERNOULLI, 0.0, 0)]
+IDS = ["gauss", "sb_half", "sb_p1", "ss8", "ss_iid", "sg", "bern"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def library():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    build()
+    lra.load()
+
+
+def dev(A, pad=0):
+    m, n = A.shape
+    buf = torch.empty_strided((m + pad, n), (1, m + pad), dtype=torch.float64, device="cuda")
+    view = buf[:m]
+    view.copy_(torch.from_numpy(np.ascontiguousarray(A)))
+    return view
+
+
+def maxrel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def test_kind_numbers_agree():
+    assert (lra.GAUSSIAN, lra.STD_BERNOULLI, lra.SPARSE_SIGN, lra.SPARSE_SIGN_IID, lra.SPARSE_GAUSSIAN,
+            lra.BERNOULLI) == (om.GAUSSIAN, om.STD_BERNOULLI, om.SPARSE_SIGN, om.SPARSE_SIGN_IID,
+                               om.SPARSE_GAUSSIAN, om.BERNOULLI)
+
+
+@pytest.mark.parametrize("kind,p,zeta", KIND_CASES + [(om.SPARSE_SIGN, 0.0, 1), (om.SPARSE_SIGN, 0.0, 16),
+                                                      (om.SPARSE_SIGN, 0.0, 777)], ids=IDS + ["ss1", "ss16", "ss_full"])
+@pytest.mark.parametrize("n", [1000, 777])
+def test_omega_bit_exact(kind, p, zeta, n):
+    b, seed = 20, 12345678901
+    if zeta > n:
+        zeta = n
+    f = lra.Farpca(50, n, eps=1e-2, b=b, P=1, kind=kind, zeta=zeta, p=p, seed=seed)
+    for j in (0, 3, 1000):
+        counts, rows, vals = f.copy_omega(j)
+        ref = om.omega_entries(kind, j, n, b, seed, zeta=zeta, p=p)
+        for c in range(b):
+            r_ref, v_ref = ref[c]
+            k = int(counts[c])
+            assert k == len(r_ref)
+            assert np.array_equal(rows[c, :k].astype(np.int64), r_ref)
+            if kind in (om.GAUSSIAN, om.SPARSE_GAUSSIAN):
+                assert np.all(np.abs(vals[c, :k] - v_ref) <= 1e-14 * np.maximum(1.0, np.abs(v_ref)))
+            else:
+                assert np.array_equal(vals[c, :k], v_ref)
+    f.close()
+
+
+@pytest.mark.parametrize("kind,p,zeta", KIND_CASES, ids=IDS)
+@pytest.mark.parametrize("m,n,pad", [(1001, 700, 0), (640, 513, 3)])
+def test_sketch_parity(kind, p, zeta, m, n, pad):
+    b, seed = 12, 99
+    A = low_rank_matrix(m, n, "poly1", 5) + 1e-3 * np.random.default_rng(0).standard_normal((m, n))
+    f = lra.Farpca(m, n, eps=1e-2, b=b, P=1, kind=kind, zeta=zeta, p=p, seed=seed)
+    Y = f.sketch(dev(A, pad), 2, 3).cpu().numpy()
+    ref = F.sketch(A, kind, 2, 3, b, seed, zeta=zeta, p=p)
+    assert Y.shape == ref.shape
+    assert maxrel(Y, ref) <= 1e-12
+    f.close()
+
+
+def _compare(A, eps, P, b, kind, p, zeta, seed, k=0, max_blocks=0, pad=0):
+    m, n = A.shape
+    f = lra.Farpca(m, n, eps=eps, k=k, b=b, P=P, kind=kind, zeta=zeta, p=p, seed=seed,
+                   max_blocks=max_blocks, keep_y=True)
+    status = f.run(dev(A, pad))
+    r = f.result()
+    ref = F.farpca(A, eps, P=P, b=b, kind=kind, seed=seed, zeta=zeta, p=p, k=k, max_blocks=max_blocks,
+                   keep_y=True)
+    assert status == ref["status"] == r["status"]
+    assert r["rank"] == ref["rank"] and r["blocks"] == ref["blocks"]
+    assert abs(r["normA2"] - ref["normA2"]) <= 1e-13 * ref["normA2"]
+    if ref["rank"] > 0:
+        assert abs(r["E"] - ref["E"]) <= 1e-10 * abs(ref["E"]) + 1e-15 * ref["normA2"]
+        Q = r["Q"].cpu().numpy()
+        B = r["B"].cpu().numpy()
+        Y = r["Y"].cpu().numpy()
+        assert maxrel(Y, ref["Y"]) <= 1e-10
+        assert float(np.abs(Q - ref["Q"]).max()) <= 1e-10
+        assert maxrel(B, ref["B"]) <= 1e-10
+    f.close()
+    return r, ref
+
+
+@pytest.mark.parametrize("kind,p,zeta", KIND_CASES, ids=IDS)
+@pytest.mark.parametrize("P", [0, 1, 2])
+def test_farpca_parity(kind, p, zeta, P):
+    A = low_rank_matrix(700, 450, "poly1.5", 77)
+    _compare(A, 2e-2, P, 16, kind, p, zeta, seed=9)
+
+
+@pytest.mark.parametrize("kind,p,zeta", KIND_CASES, ids=IDS)
+def test_farpca_parity_2000x1000(kind, p, zeta):
+    # sigma_i = i^-1.5, b = 20, P = 1, eps = 1e-2, zeta = 8 (the 2000 x 1000 workload)
+    A = workload_matrix("dense2000x1000_poly1.5")
+    r, ref = _compare(A, 1e-2, 1, 20, kind, p, zeta, seed=2024)
+    assert r["status"] == 0 and r["rel_err"] < 1e-2
+
+
+def test_edge_cases():
+    m, n = 300, 200
+    # zero matrix: rank 0, OK
+    Z = np.zeros((m, n))
+    f = lra.Farpca(m, n, eps=1e-2, b=8, P=1, kind=lra.SPARSE_SIGN, zeta=4)
+    assert f.run(dev(Z)) == lra.OK
+    r = f.result()
+    assert r["rank"] == 0 and r["E"] == 0.0
+    # one nonzero column: the first block is rank deficient -> BREAKDOWN, rank 0
+    Z[:, 7] = np.arange(m) + 1.0
+    f2 = lra.Farpca(m, n, eps=1e-3, b=4, P=0, kind=lra.SPARSE_SIGN, zeta=1)
+    assert f2.run(dev(Z)) == lra.BREAKDOWN
+    assert f2.result()["rank"] == 0
+    # non-finite input is an error
+    Z[3, 3] = np.nan
+    with pytest.raises(lra.LraError):
+        f.run(dev(Z))
+    # wrong shape is an error
+    with pytest.raises(lra.LraError):
+        f.run(dev(np.ones((m + 1, n))))
+    A = low_rank_matrix(m, n, "poly1", 3)
+    # fixed rank, cap, b = 1, b = 64, padded lda, wide matrix
+    _compare(A, 0.0, 1, 7, lra.SPARSE_GAUSSIAN, 0.1, 0, seed=5, k=30)
+    r, _ = _compare(A, 1e-12, 0, 7, lra.SPARSE_SIGN, 0.0, 3, seed=5)
+    assert r["status"] == lra.NOT_CONVERGED and r["blocks"] == F.default_max_blocks(m, n, 7)
+    _compare(A, 5e-2, 1, 1, lra.SPARSE_SIGN, 0.0, 2, seed=1)
+    _compare(A, 1e-3, 1, 64, lra.GAUSSIAN, 0.0, 0, seed=1, pad=5)
+    _compare(np.asfortranarray(A.T), 2e-2, 2, 10, lra.SPARSE_SIGN, 0.0, 4, seed=3)
+
+
+def test_deterministic_and_host_path():
+    m, n = 900, 500
+    A = low_rank_matrix(m, n, "poly1.5", 8)
+    f = lra.Farpca(m, n, eps=1e-2, b=20, P=1, kind=lra.SPARSE_SIGN, zeta=8, seed=4)
+    Ad = dev(A)
+    f.run(Ad)
+    r1 = f.result()
+    Q1, B1 = r1["Q"].cpu().numpy().copy(), r1["B"].cpu().numpy().copy()
+    f.run(Ad)
+    r2 = f.result()
+    assert r2["E"] == r1["E"] and np.array_equal(r2["Q"].cpu().numpy(), Q1)
+    cap = f.capacity
+    Qh = np.zeros((m, cap), order="F")
+    Bh = np.zeros((cap, n), order="F")
+    rh = f.run_host(np.asfortranarray(A), Qh, Bh)
+    assert rh["rank"] == r1["rank"] and rh["E"] == r1["E"]
+    assert np.array_equal(Qh[:, :rh["rank"]], Q1) and np.array_equal(Bh[:rh["rank"]], B1)
+
+
+def test_full_size_bench_config():
+    """20000 x 10000, sigma_i = 10^(-i/100) + 1e-6 noise, sparse sign zeta = 8, b = 50,
+    P = 1, eps = 1e-2: the configuration bench.py times, against the oracle at full size."""
+    A = workload_matrix("dense20000x10000_exp100")
+    m, n = A.shape
+    Ad = dev(A)
+    r, ref = None, None
+    f = lra.Farpca(m, n, eps=1e-2, b=50, P=1, kind=lra.SPARSE_SIGN, zeta=8, seed=1, keep_y=True)
+    assert f.run(Ad) == lra.OK
+    r = f.result()
+    ref = F.farpca(A, 1e-2, P=1, b=50, kind=om.SPARSE_SIGN, seed=1, zeta=8, keep_y=True)
+    assert r["rank"] == ref["rank"] and r["status"] == ref["status"] == 0
+    assert abs(r["E"] - ref["E"]) <= 1e-10 * ref["E"]
+    assert maxrel(r["Y"].cpu().numpy(), ref["Y"]) <= 1e-10
+    assert float(np.abs(r["Q"].cpu().numpy() - ref["Q"]).max()) <= 1e-10
+    # many-block sketch pass (the sketch bandwidth measurement), sampled blocks
+    Y = f.sketch(Ad, 0, 64)
+    for j in (0, 17, 63):
+        cols = Y[:, j * 50:(j + 1) * 50].cpu().numpy()
+        refc = A @ om.omega_dense(om.SPARSE_SIGN, j, n, 50, 1, zeta=8)
+        assert maxrel(cols, refc) <= 1e-12
+    f.close()
