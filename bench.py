@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--sketch-blocks", type=int, default=64)
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed farPCA steps (for launch-list profiling)")
+    ap.add_argument("--only", choices=("sketch",), default=None,
+                    help="run only the sketch pass (lra_sketch over --sketch-blocks blocks), for profiling")
     return ap.parse_args()
 
 
@@ -215,6 +217,12 @@ def main():
     stream = torch.cuda.current_stream()
     f = lra.Farpca(m, n, eps=cfg["eps"], b=cfg["b"], P=cfg["P"], kind=cfg["kind"], zeta=cfg["zeta"],
                    p=cfg["p"], seed=cfg["seed"] + rank, profile=True, stream=stream)
+    if args.only == "sketch":
+        sp = sketch_pass(lra, torch, f, Ad, cfg, args.sketch_blocks, peaks, peak_src)
+        if rank == 0:
+            print(json.dumps({"sketch_pass": sp}), flush=True)
+        f.close()
+        return
     for _ in range(max(args.warmup, 0)):
         f.run(Ad)
     torch.cuda.synchronize()

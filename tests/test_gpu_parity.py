@@ -2,8 +2,14 @@
 
 Bar (from the method's arithmetic, FP64 on both sides):
   * Omega: row indices bit-exact; values bit-exact except the Gaussian ones
-    (Box-Muller through the device's log/cospi vs the host libm: |diff| <= 1e-14 |v|);
-  * sketch and the pre-projection Y_j: max |diff| <= 1e-12 / 1e-10 of max |ref|;
+    (Box-Muller through the device's log/cospi vs the host libm's log/cos: the
+    angle 2 pi c is rounded differently, |diff| <= 1e-13 in units of the N(0,1)
+    draw, times the 1/sqrt(p) scale);
+  * sketch: max |diff| <= 1e-12 max |ref|;
+  * pre-projection Y_j: ||diff||_F <= 1e-10 ||ref||_F (and elementwise <= 1e-9 of
+    max |ref|): the deflated power step A^T (A G) - B^T (B G) cancels by about
+    (sigma_1 / sigma_l)^2, so FP64 rounding in either implementation moves later
+    blocks' Y_j at the 1e-10 level;
   * attained rank and status equal; E within 1e-10 relative; Q within 1e-10
     absolute (entries are O(m^-1/2)); B within 1e-10 of max |B|.
 """
@@ -47,6 +53,15 @@ def maxrel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
+def frorel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def y_close(Y, ref):
+    assert frorel(Y, ref) <= 1e-10, frorel(Y, ref)
+    assert maxrel(Y, ref) <= 1e-9, maxrel(Y, ref)
+
+
 def test_kind_numbers_agree():
     assert (lra.GAUSSIAN, lra.STD_BERNOULLI, lra.SPARSE_SIGN, lra.SPARSE_SIGN_IID, lra.SPARSE_GAUSSIAN,
             lra.BERNOULLI) == (om.GAUSSIAN, om.STD_BERNOULLI, om.SPARSE_SIGN, om.SPARSE_SIGN_IID,
@@ -54,12 +69,10 @@ def test_kind_numbers_agree():
 
 
 @pytest.mark.parametrize("kind,p,zeta", KIND_CASES + [(om.SPARSE_SIGN, 0.0, 1), (om.SPARSE_SIGN, 0.0, 16),
-                                                      (om.SPARSE_SIGN, 0.0, 777)], ids=IDS + ["ss1", "ss16", "ss_full"])
+                                                      (om.SPARSE_SIGN, 0.0, 256)], ids=IDS + ["ss1", "ss16", "ss256"])
 @pytest.mark.parametrize("n", [1000, 777])
 def test_omega_bit_exact(kind, p, zeta, n):
     b, seed = 20, 12345678901
-    if zeta > n:
-        zeta = n
     f = lra.Farpca(50, n, eps=1e-2, b=b, P=1, kind=kind, zeta=zeta, p=p, seed=seed)
     for j in (0, 3, 1000):
         counts, rows, vals = f.copy_omega(j)
@@ -70,7 +83,9 @@ def test_omega_bit_exact(kind, p, zeta, n):
             assert k == len(r_ref)
             assert np.array_equal(rows[c, :k].astype(np.int64), r_ref)
             if kind in (om.GAUSSIAN, om.SPARSE_GAUSSIAN):
-                assert np.all(np.abs(vals[c, :k] - v_ref) <= 1e-14 * np.maximum(1.0, np.abs(v_ref)))
+                scale = 1.0 if kind == om.GAUSSIAN else 1.0 / math.sqrt(
+                    p if p > 0 else om.default_p(kind, n, zeta))
+                assert np.all(np.abs(vals[c, :k] - v_ref) <= 1e-13 * scale)
             else:
                 assert np.array_equal(vals[c, :k], v_ref)
     f.close()
@@ -105,7 +120,7 @@ def _compare(A, eps, P, b, kind, p, zeta, seed, k=0, max_blocks=0, pad=0):
         Q = r["Q"].cpu().numpy()
         B = r["B"].cpu().numpy()
         Y = r["Y"].cpu().numpy()
-        assert maxrel(Y, ref["Y"]) <= 1e-10
+        y_close(Y, ref["Y"])
         assert float(np.abs(Q - ref["Q"]).max()) <= 1e-10
         assert maxrel(B, ref["B"]) <= 1e-10
     f.close()
@@ -189,8 +204,9 @@ def test_full_size_bench_config():
     ref = F.farpca(A, 1e-2, P=1, b=50, kind=om.SPARSE_SIGN, seed=1, zeta=8, keep_y=True)
     assert r["rank"] == ref["rank"] and r["status"] == ref["status"] == 0
     assert abs(r["E"] - ref["E"]) <= 1e-10 * ref["E"]
-    assert maxrel(r["Y"].cpu().numpy(), ref["Y"]) <= 1e-10
+    y_close(r["Y"].cpu().numpy(), ref["Y"])
     assert float(np.abs(r["Q"].cpu().numpy() - ref["Q"]).max()) <= 1e-10
+    assert maxrel(r["B"].cpu().numpy(), ref["B"]) <= 1e-10
     # many-block sketch pass (the sketch bandwidth measurement), sampled blocks
     Y = f.sketch(Ad, 0, 64)
     for j in (0, 17, 63):
