@@ -69,6 +69,9 @@ typedef enum { LRA_F64 = 0, LRA_F32 = 1 } lra_dtype;
                                paper's cumulative Y of Alg. 1); costs m x l_max FP64 */
 #define LRA_FLAG_PROFILE 2u /* time each phase of lra_farpca_run with CUDA events on
                                the context's stream (read with lra_phase_times)   */
+#define LRA_FLAG_FP64_SIMT 4u /* run the full passes over A as FP64 FMAs on the CUDA
+                               cores instead of the FP64-accurate tensor-core GEMM
+                               (error-free bf16 slicing); ~60x slower on GB300     */
 
 /* Phases of one block, for lra_phase_times. */
 typedef enum {
@@ -149,6 +152,16 @@ int64_t lra_capacity(const lra_ctx* ctx);
    nblk = 0 is a no-op.  Errors: LRA_ERR_INVALID_ARG, LRA_ERR_CUDA. */
 lra_status lra_sketch(lra_ctx* ctx, const lra_matrix* A, int64_t j0, int64_t nblk,
                       double* Y, int64_t ldy);
+
+/* One full pass over A with the context's dense engine -- the contraction of
+   Alg. 1's A G_j and A^T Y_j: C = op(A) Y, op(A) = A^T when trans != 0, else A.
+   Y: device, (trans ? m : n) x N, ld ldy; C: device, (trans ? n : m) x N, ld ldc;
+   1 <= N <= LRA_MAX_B; caller-owned.  FP64 result; computed on the tensor cores
+   by error-free bf16 slicing (error comparable to an FP64 GEMM) unless the
+   context was created with LRA_FLAG_FP64_SIMT.  Errors: LRA_ERR_INVALID_ARG,
+   LRA_ERR_CUDA, LRA_ERR_TIMEOUT. */
+lra_status lra_apply(lra_ctx* ctx, const lra_matrix* A, int32_t trans, const double* Y, int64_t ldy,
+                     int64_t N, double* C, int64_t ldc);
 
 /* Run the blocked farPCA loop on A (device, m x n as at create) until
    E < eps^2 ||A||_F^2 (LRA_OK), the block cap (LRA_NOT_CONVERGED), a rank-deficient

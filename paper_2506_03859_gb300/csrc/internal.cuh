@@ -23,6 +23,7 @@ inline cudaError_t launched() {
 enum : int {
   FLAG_BREAKDOWN = 1,     // a Cholesky pivot failed the breakdown test
   FLAG_OMEGA_CAP = 2,     // fixed-zeta generator ran out of draws
+  FLAG_TIMEOUT = 4,       // a bounded device wait gave up
 };
 
 // Philox stream tags (counter word 3); see philox.cuh.
@@ -71,6 +72,25 @@ cudaError_t dgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, con
                   int64_t ldx, const double* Y, int64_t ldy, double beta, GemmOut out, double* ws,
                   int64_t ws_elems, cudaStream_t st);
 int64_t dgemm_ws_elems();
+
+// ---------------------------------------------------------------- ozgemm.cu
+// FP64-accurate C = alpha op(X) Y + beta C on the tcgen05 tensor cores (error-free
+// bf16 slicing).  xE: biased max exponent of each row of op(X) (P entries).
+struct OzWorkspace {
+  int* yE;           // 64 ints
+  uint8_t* img;      // pre-sliced Y, img_bytes
+  int64_t img_bytes;
+  double* part;      // partial tiles, oz_part_elems(ctas)
+  int ctas;          // CTAs of the persistent grid (one per SM)
+};
+int64_t oz_img_bytes(int64_t K);
+int64_t oz_part_elems(int ctas);
+cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, const double* X,
+                   int64_t ldx, const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
+                   const OzWorkspace& w, int* flags, cudaStream_t st);
+// rowE[r] / colE[c] = largest biased exponent in row r / column c of X (either may be NULL).
+cudaError_t oz_rowcol_exponents(const double* X, int64_t ld, int64_t rows, int64_t cols,
+                                int* rowE, int* colE, cudaStream_t st);
 
 // ---------------------------------------------------------------- orth.cu
 // Per-column sums of squares and/or sums of X (rows x cols, ld): one CTA per column.

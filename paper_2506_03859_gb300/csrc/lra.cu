@@ -54,6 +54,10 @@ struct lra_ctx {
   cudaStream_t st = nullptr;
   int b = 0, P = 0, kind = 0;
   bool sparse = false, keep_y = false, sb_sparse = false;
+  bool tensor = true;  // full passes over A on the tensor cores (FP64-accurate slicing)
+  int* rowE = nullptr;  // biased max exponent of each row / column of A
+  int* colE = nullptr;
+  OzWorkspace oz{};
   int cap = 0;  // entries per Omega column in the sparse structure
   OmegaSpec os{};
   int64_t nblk_max = 0, lmax = 0, ldq = 0, ldb = 0, lds = 0, ldf = 0, ldod = 0;
@@ -154,7 +158,7 @@ lra_status check_params(lra_ctx* ctx, int64_t m, int64_t n, const lra_params* p)
   if (p->max_blocks < 0) return fail(ctx, LRA_ERR_INVALID_ARG, "max_blocks must be >= 0");
   if ((int64_t)p->max_blocks * p->b > mn)
     return fail(ctx, LRA_ERR_INVALID_ARG, "max_blocks * b exceeds min(m, n)");
-  if (p->flags & ~(LRA_FLAG_KEEP_Y | LRA_FLAG_PROFILE))
+  if (p->flags & ~(LRA_FLAG_KEEP_Y | LRA_FLAG_PROFILE | LRA_FLAG_FP64_SIMT))
     return fail(ctx, LRA_ERR_INVALID_ARG, "unknown flags");
   return LRA_OK;
 }
@@ -180,6 +184,22 @@ lra_status gemm(lra_ctx* ctx, bool trans, int64_t P, int64_t N, int64_t K, doubl
   return LRA_OK;
 }
 
+// A full pass over A: C = alpha op(A) Y + beta C (op(A) = A^T when trans).
+lra_status dense(lra_ctx* ctx, bool trans, int64_t N, double alpha, const double* A, int64_t lda,
+                 const double* Y, int64_t ldy, double beta, double* C, int64_t csp, int64_t csc) {
+  const int64_t P = trans ? ctx->n : ctx->m, K = trans ? ctx->m : ctx->n;
+  if (!ctx->tensor) return gemm(ctx, trans, P, N, K, alpha, A, lda, Y, ldy, beta, C, csp, csc);
+  CK(ozgemm(trans, P, N, K, alpha, A, lda, trans ? ctx->colE : ctx->rowE, Y, ldy, beta,
+            GemmOut{C, csp, csc}, ctx->oz, ctx->flags, ctx->st));
+  return LRA_OK;
+}
+
+lra_status a_exponents(lra_ctx* ctx, const double* A, int64_t lda) {
+  if (ctx->tensor)
+    CK(oz_rowcol_exponents(A, lda, ctx->m, ctx->n, ctx->rowE, ctx->colE, ctx->st));
+  return LRA_OK;
+}
+
 // out (rows x b, ld ldo) = Q factor of X (rows x b, ld ldx), CholQR2.
 lra_status orth(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows, double* out,
                 int64_t ldo) {
@@ -202,14 +222,16 @@ lra_status make_omega(lra_ctx* ctx, int64_t j) {
   return LRA_OK;
 }
 
-// out (rows_x x b) = X Omega_j (minus the standardized-Bernoulli shift when sparse).
+// out (rows_x x b) = X Omega_j (minus the standardized-Bernoulli shift when sparse);
+// X is A (x_is_A) or the rows of B.
 lra_status apply_omega(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows_x, double* out,
-                       int64_t ldo, const double* shift) {
+                       int64_t ldo, const double* shift, bool x_is_A) {
   if (ctx->sparse) {
     CK(gather_sketch(X, ldx, rows_x, ctx->om_counts, ctx->om_rows, ctx->om_vals, ctx->cap, ctx->b,
                      out, ldo, shift, ctx->st));
     return LRA_OK;
   }
+  if (x_is_A) return dense(ctx, false, ctx->b, 1.0, X, ldx, ctx->om_dense, ctx->ldod, 0.0, out, 1, ldo);
   return gemm(ctx, false, rows_x, ctx->b, ctx->n, 1.0, X, ldx, ctx->om_dense, ctx->ldod, 0.0, out, 1,
               ldo);
 }
@@ -217,7 +239,7 @@ lra_status apply_omega(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows_
 lra_status compute_z(lra_ctx* ctx, const double* A, int64_t lda) {
   // z = A w, w = p 1 (Alg. 2 step 2)
   CK(fill(ctx->wvec, ctx->n, ctx->n, 1, ctx->os.p, ctx->st));
-  return gemm(ctx, false, ctx->m, 1, ctx->n, 1.0, A, lda, ctx->wvec, ctx->n, 0.0, ctx->z, 1, ctx->m);
+  return dense(ctx, false, 1, 1.0, A, lda, ctx->wvec, ctx->n, 0.0, ctx->z, 1, ctx->m);
 }
 
 // Phase timing: events recorded on the context's stream around each phase,
@@ -286,6 +308,7 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
     ctx->E = 0.0;
     return LRA_OK;
   }
+  PHASE(LRA_PHASE_INDICATOR, TRY(a_exponents(ctx, A, lda)));
   if (ctx->sb_sparse) PHASE(LRA_PHASE_SKETCH, TRY(compute_z(ctx, A, lda)));
   const double thr = ctx->prm.eps * ctx->prm.eps * normA2;
   const bool fixed_rank = ctx->prm.k > 0;
@@ -295,23 +318,23 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
     const int64_t l = j * b;
     PHASE(LRA_PHASE_OMEGA, TRY(make_omega(ctx, j)));
     PHASE(LRA_PHASE_SKETCH,
-          TRY(apply_omega(ctx, A, lda, m, ctx->S0, lds, ctx->sb_sparse ? ctx->z : nullptr)));
+          TRY(apply_omega(ctx, A, lda, m, ctx->S0, lds, ctx->sb_sparse ? ctx->z : nullptr, true)));
     double* Y = ctx->S0;
     if (P >= 1) {
-      PHASE(LRA_PHASE_DENSE,
-            TRY(gemm(ctx, true, n, b, m, 1.0, A, lda, ctx->S0, lds, 0.0, ctx->W, 1, lds)));
+      PHASE(LRA_PHASE_DENSE, TRY(dense(ctx, true, b, 1.0, A, lda, ctx->S0, lds, 0.0, ctx->W, 1, lds)));
       if (l > 0) {
         PHASE(LRA_PHASE_DEFLATE, {
-          TRY(apply_omega(ctx, ctx->B, ldb, l, ctx->BOm, ldf, ctx->sb_sparse ? ctx->zB : nullptr));
+          TRY(apply_omega(ctx, ctx->B, ldb, l, ctx->BOm, ldf, ctx->sb_sparse ? ctx->zB : nullptr,
+                          false));
           TRY(gemm(ctx, true, n, b, l, -1.0, ctx->B, ldb, ctx->BOm, ldf, 1.0, ctx->W, 1, lds));
         });
       }
       PHASE(LRA_PHASE_ORTH, TRY(orth(ctx, ctx->W, lds, n, ctx->G, lds)));
       for (int s = 1; s < P; ++s) {
         PHASE(LRA_PHASE_DENSE,
-              TRY(gemm(ctx, false, m, b, n, 1.0, A, lda, ctx->G, lds, 0.0, ctx->T1, 1, lds)));
+              TRY(dense(ctx, false, b, 1.0, A, lda, ctx->G, lds, 0.0, ctx->T1, 1, lds)));
         PHASE(LRA_PHASE_DENSE,
-              TRY(gemm(ctx, true, n, b, m, 1.0, A, lda, ctx->T1, lds, 0.0, ctx->W, 1, lds)));
+              TRY(dense(ctx, true, b, 1.0, A, lda, ctx->T1, lds, 0.0, ctx->W, 1, lds)));
         if (l > 0) {
           PHASE(LRA_PHASE_DEFLATE, {
             TRY(gemm(ctx, false, l, b, n, 1.0, ctx->B, ldb, ctx->G, lds, 0.0, ctx->BOm, 1, ldf));
@@ -320,8 +343,7 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
         }
         PHASE(LRA_PHASE_ORTH, TRY(orth(ctx, ctx->W, lds, n, ctx->G, lds)));
       }
-      PHASE(LRA_PHASE_DENSE,
-            TRY(gemm(ctx, false, m, b, n, 1.0, A, lda, ctx->G, lds, 0.0, ctx->Yb, 1, lds)));
+      PHASE(LRA_PHASE_DENSE, TRY(dense(ctx, false, b, 1.0, A, lda, ctx->G, lds, 0.0, ctx->Yb, 1, lds)));
       Y = ctx->Yb;
     }
     if (ctx->keep_y)
@@ -337,8 +359,7 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
     }
     double* Qj = ctx->Q + l * ldq;
     PHASE(LRA_PHASE_ORTH, TRY(orth(ctx, Y, lds, m, Qj, ldq)));
-    PHASE(LRA_PHASE_DENSE,
-          TRY(gemm(ctx, true, n, b, m, 1.0, A, lda, Qj, ldq, 0.0, ctx->Wt, 1, lds)));
+    PHASE(LRA_PHASE_DENSE, TRY(dense(ctx, true, b, 1.0, A, lda, Qj, ldq, 0.0, ctx->Wt, 1, lds)));
     PHASE(LRA_PHASE_INDICATOR, {
       CK(col_sums(ctx->Wt, lds, n, b, ctx->colsq, ctx->sb_sparse ? ctx->colsum : nullptr, ctx->st));
       CK(total(ctx->colsq, b, ctx->scal + 1, ctx->st));
@@ -347,6 +368,7 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
     });
     TRY(read_record(ctx));
     const int fl = ctx->hp->flags;
+    if (fl & FLAG_TIMEOUT) return fail(ctx, LRA_ERR_TIMEOUT, "a device wait timed out");
     if (fl & FLAG_OMEGA_CAP)
       return fail(ctx, LRA_ERR_INVALID_ARG, "fixed-zeta draws exhausted (zeta too close to n)");
     if (fl & FLAG_BREAKDOWN) {
@@ -389,7 +411,8 @@ void free_all(lra_ctx* c) {
                   c->Tmp,    c->W,        c->G,      c->Wt,       c->F,         c->BOm,
                   c->z,      c->zB,       c->wvec,   c->ws,       c->gram,      c->Rinv,
                   c->colsq,  c->colsum,   c->scal,   c->flags,    c->om_counts, c->om_rows,
-                  c->om_vals, c->om_dense, c->sk_counts, c->sk_rows, c->sk_vals, c->A_host_copy};
+                  c->om_vals, c->om_dense, c->sk_counts, c->sk_rows, c->sk_vals, c->A_host_copy,
+                  c->rowE,   c->colE,     c->oz.yE,  c->oz.img,   c->oz.part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->hp) cudaFreeHost(c->hp);
@@ -516,6 +539,19 @@ lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
   ALLOC(colsum, std::max<int64_t>(n, LRA_MAX_B));
   ALLOC(scal, 8);
   ALLOC(flags, 4);
+  ctx->tensor = (params->flags & LRA_FLAG_FP64_SIMT) == 0;
+  if (ctx->tensor) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    ctx->oz.ctas = sms > 0 ? sms : 1;
+    ctx->oz.img_bytes = oz_img_bytes(std::max(m, n));
+    ALLOC(rowE, m);
+    ALLOC(colE, n);
+    ALLOC(oz.yE, LRA_MAX_B);
+    ALLOC(oz.img, ctx->oz.img_bytes);
+    ALLOC(oz.part, oz_part_elems(ctx->oz.ctas));
+  }
   if (ctx->sparse) {
     ALLOC(om_counts, b);
     ALLOC(om_rows, (int64_t)b * ctx->cap);
@@ -615,14 +651,18 @@ lra_status lra_sketch(lra_ctx* ctx, const lra_matrix* A, int64_t j0, int64_t nbl
   const double* Ad = (const double*)A->data;
   const int b = ctx->b;
   if (!ctx->sparse) {
+    TRY(a_exponents(ctx, Ad, A->lda));
     for (int64_t j = j0; j < j0 + nblk; ++j) {
       CK(omega_dense(ctx->os, j, 1, ctx->om_dense, ctx->ldod, ctx->st));
-      TRY(gemm(ctx, false, ctx->m, b, ctx->n, 1.0, Ad, A->lda, ctx->om_dense, ctx->ldod, 0.0,
-               Y + (j - j0) * b * ldy, 1, ldy));
+      TRY(dense(ctx, false, b, 1.0, Ad, A->lda, ctx->om_dense, ctx->ldod, 0.0, Y + (j - j0) * b * ldy,
+                1, ldy));
     }
     return LRA_OK;
   }
-  if (ctx->sb_sparse) TRY(compute_z(ctx, Ad, A->lda));
+  if (ctx->sb_sparse) {
+    TRY(a_exponents(ctx, Ad, A->lda));
+    TRY(compute_z(ctx, Ad, A->lda));
+  }
   int64_t chunk = std::max<int64_t>(1, SKETCH_SCRATCH_ENTRIES / ((int64_t)b * ctx->cap));
   chunk = std::min(chunk, nblk);
   TRY(ensure_sketch_scratch(ctx, chunk * b, ctx->cap));
@@ -635,6 +675,26 @@ lra_status lra_sketch(lra_ctx* ctx, const lra_matrix* A, int64_t j0, int64_t nbl
                      nb * b, Y + (j - j0) * b * ldy, ldy, ctx->sb_sparse ? ctx->z : nullptr,
                      ctx->st));
   }
+  return LRA_OK;
+}
+
+lra_status lra_apply(lra_ctx* ctx, const lra_matrix* A, int32_t trans, const double* Y, int64_t ldy,
+                     int64_t N, double* C, int64_t ldc) {
+  if (!ctx) return LRA_ERR_INVALID_ARG;
+  ctx->err.clear();
+  TRY(check_matrix(ctx, A));
+  const int64_t rows_y = trans ? ctx->m : ctx->n, rows_c = trans ? ctx->n : ctx->m;
+  if (!Y || !C || N < 1 || N > LRA_MAX_B || ldy < rows_y || ldc < rows_c)
+    return fail(ctx, LRA_ERR_INVALID_ARG, "bad Y / C / N / ld");
+  const double* Ad = (const double*)A->data;
+  CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int), ctx->st));
+  if (ctx->tensor)
+    CK(oz_rowcol_exponents(Ad, A->lda, ctx->m, ctx->n, trans ? nullptr : ctx->rowE,
+                           trans ? ctx->colE : nullptr, ctx->st));
+  TRY(dense(ctx, trans != 0, N, 1.0, Ad, A->lda, Y, ldy, 0.0, C, 1, ldc));
+  CK(cudaMemcpyAsync(&ctx->hp->flags, ctx->flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (ctx->hp->flags & FLAG_TIMEOUT) return fail(ctx, LRA_ERR_TIMEOUT, "a device wait timed out");
   return LRA_OK;
 }
 

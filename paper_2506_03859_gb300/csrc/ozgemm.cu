@@ -1,0 +1,522 @@
+// FP64-accurate skinny GEMM on the tcgen05 tensor cores: C = alpha op(X) Y + beta C
+// with X, Y, C in FP64 and N <= 64.  These are the full passes over A of the
+// farPCA block (arxiv 2506.03859 Alg. 1 steps A^T(A G_j), A G_j, A^T Y_j).
+//
+// GB300's FP64 pipe delivers about 1.2 TFLOP/s, while such a pass streams A once
+// from HBM: run as FP64 FMAs it is ~60x slower than the memory bound.  Instead
+// every operand is cut, error-free, into bf16 slices (the splitting idea of
+// Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 2012):
+//
+//   each row p of op(X) is scaled by 2^-e_p (|x| < 2^e_p over the row) and
+//   each column c of Y by 2^-f_c; the scaled value, truncated to a 56-bit fixed
+//   point number, is x = 2^-8 sum_{s<7} v_s with v_s = d_s 2^(-8 s),
+//   d_s in [0, 255] carrying the sign of x.  Every v_s is exact in bf16.
+//
+//   x y = 2^-16 sum_{s,t} v_s w_t; the pairs with s + t <= 6 are kept (the
+//   rest is below 2^-56 relative), and each pair is a bf16 GEMM on the tensor
+//   core.  Pairs of weight s + t = 0, 1, 2 go to separate FP32 TMEM
+//   accumulators and are flushed every 64 values of K, a window in which their
+//   integer-valued partial sums stay below 2^24 and are therefore exact; all
+//   pairs of weight >= 3 share a fourth accumulator (their rounding is
+//   below 2^-48 of the result).  Flushed values are summed in double-float
+//   (hi + lo, FP32 two-sum) kept in TMEM next to the accumulators, and the
+//   tile is scaled by 2^(e_p + f_c) and written in FP64.
+//
+// Work split: one CTA per SM walks a contiguous range of (row tile, k-block)
+// units ("stream-K"); tiles whose k-blocks span two or more CTAs are written as
+// partial sums and combined by a fixup kernel in a fixed order.
+// Per k-block the CTA (256 threads) loads a 128 x 64 block of op(X) from HBM,
+// slices it into 7 shared-memory planes (128-byte swizzled, K-major), copies
+// the pre-sliced 64 x 64 block of Y, and one thread issues the 28 x 4 MMAs.
+#include <math.h>
+
+#include "internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace lra {
+
+namespace {
+constexpr int S = 7;              // slices per operand (8 bits each)
+constexpr int TM = 128;           // rows of op(X) per tile
+constexpr int KBK = 64;           // K per k-block
+constexpr int NN = 64;            // output columns (N padded)
+constexpr int NT = 256;           // threads per CTA
+constexpr int A_PLANE = TM * 128; // bytes of one slice plane of the X block
+constexpr int Y_PLANE = NN * 128; // bytes of one slice plane of the Y block
+constexpr int SMEM_DYN = S * A_PLANE + S * Y_PLANE + 1024;
+constexpr uint32_t TMEM_COLS = 512;  // 4 accumulators x 64 columns, then hi and lo sums
+constexpr uint32_t COL_HI = 256, COL_LO = 320;
+constexpr long WAIT_TRIES = 1L << 24;
+constexpr int EXP_OFFSET = 2060;  // 2 * (1022 + 8): see the scaling above
+}  // namespace
+
+int64_t oz_img_bytes(int64_t K) { return (K + KBK - 1) / KBK * S * Y_PLANE; }
+int64_t oz_part_elems(int ctas) { return (int64_t)ctas * 2 * TM * NN; }
+
+// |a| as a 56-bit fixed-point integer relative to 2^(emax - 1022) (emax = the
+// largest biased exponent of the row/column), and its sign.
+__device__ __forceinline__ uint64_t fixed56(double a, int emax, uint32_t& sign) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(a);
+  sign = (uint32_t)(bits >> 63);
+  const int E = (int)((bits >> 52) & 0x7FFu);
+  const uint64_t M = (E != 0) ? ((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : 0ull;
+  const int d = emax - E;  // >= 0 by the choice of emax
+  if (d <= 3) return M << (3 - d);
+  const int sh = d - 3;
+  return sh < 64 ? (M >> sh) : 0ull;
+}
+
+// bf16 bits of d * 2^(-8 s) (d < 256, exact), sign in bit 15.
+template <int SLICE>
+__device__ __forceinline__ uint32_t slice_bf16(uint64_t x, uint32_t sign) {
+  const uint32_t d = (uint32_t)(x >> (8 * (S - 1 - SLICE))) & 0xFFu;
+  constexpr float sc = (SLICE == 0) ? 1.0f : (SLICE == 1) ? 0x1p-8f : (SLICE == 2) ? 0x1p-16f
+                       : (SLICE == 3) ? 0x1p-24f : (SLICE == 4) ? 0x1p-32f : (SLICE == 5) ? 0x1p-40f
+                                                                                     : 0x1p-48f;
+  const float f = __fmaf_rn(__int_as_float(0x4B000000 | (int)d), sc, -8388608.0f * sc);
+  return (__float_as_uint(f) >> 16) | (sign << 15);
+}
+
+template <int SLICE>
+__device__ __forceinline__ uint32_t pack2(uint64_t x0, uint32_t s0, uint64_t x1, uint32_t s1) {
+  return slice_bf16<SLICE>(x0, s0) | (slice_bf16<SLICE>(x1, s1) << 16);
+}
+
+// ---------------------------------------------------------------- prep kernels
+
+// out[c] = largest biased exponent of X[:, c] (one CTA per column).
+__global__ void __launch_bounds__(256) k_oz_colmaxexp(const double* __restrict__ X, int64_t ld,
+                                                      int64_t rows, int* __restrict__ out) {
+  __shared__ int red[8];
+  const int64_t c = blockIdx.x;
+  int e = 0;
+  for (int64_t i = threadIdx.x; i < rows; i += 256) {
+    const uint64_t b = (uint64_t)__double_as_longlong(__ldg(X + i + c * ld));
+    e = max(e, (int)((b >> 52) & 0x7FFu));
+  }
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_down_sync(0xffffffffu, e, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int q = 0; q < 8; ++q) t = max(t, red[q]);
+    out[c] = t;
+  }
+}
+
+// out[r] = max over the columns of X[r, :] of the biased exponent (out pre-zeroed).
+__global__ void __launch_bounds__(256) k_oz_rowmaxexp(const double* __restrict__ X, int64_t ld,
+                                                      int64_t rows, int64_t cols, int64_t cchunk,
+                                                      int* __restrict__ out) {
+  const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (r >= rows) return;
+  const int64_t c0 = (int64_t)blockIdx.y * cchunk;
+  const int64_t c1 = (c0 + cchunk < cols) ? c0 + cchunk : cols;
+  int e = 0;
+  for (int64_t c = c0; c < c1; ++c) {
+    const uint64_t b = (uint64_t)__double_as_longlong(__ldg(X + r + c * ld));
+    e = max(e, (int)((b >> 52) & 0x7FFu));
+  }
+  atomicMax(out + r, e);
+}
+
+// Pre-sliced Y: img[kb][s] is the 64 x 64 (N x K) bf16 block of slice s in the
+// swizzled K-major layout.  One thread per (k-block, column c, 8-wide k chunk).
+__global__ void __launch_bounds__(256) k_oz_yslice(const double* __restrict__ Y, int64_t ldy,
+                                                   int64_t K, int N, const int* __restrict__ yE,
+                                                   uint8_t* __restrict__ img, int64_t kblocks) {
+  const int64_t idx = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (idx >= kblocks * NN * 8) return;
+  const int j = (int)(idx & 7);
+  const int c = (int)((idx >> 3) & (NN - 1));
+  const int64_t kb = idx >> 9;
+  const int emax = c < N ? yE[c] : 0;
+  uint64_t x[8];
+  uint32_t sg[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t k = kb * KBK + 8 * j + i;
+    const double v = (c < N && k < K) ? __ldg(Y + k + (int64_t)c * ldy) : 0.0;
+    x[i] = fixed56(v, emax, sg[i]);
+  }
+  uint8_t* base = img + (kb * S) * Y_PLANE + tc::sw128_offset((uint32_t)c, (uint32_t)(8 * j));
+#define LRA_YS(SL)                                                                          \
+  {                                                                                         \
+    uint4 w;                                                                                \
+    w.x = pack2<SL>(x[0], sg[0], x[1], sg[1]);                                              \
+    w.y = pack2<SL>(x[2], sg[2], x[3], sg[3]);                                              \
+    w.z = pack2<SL>(x[4], sg[4], x[5], sg[5]);                                              \
+    w.w = pack2<SL>(x[6], sg[6], x[7], sg[7]);                                              \
+    *reinterpret_cast<uint4*>(base + (SL)*Y_PLANE) = w;                                     \
+  }
+  LRA_YS(0) LRA_YS(1) LRA_YS(2) LRA_YS(3) LRA_YS(4) LRA_YS(5) LRA_YS(6)
+#undef LRA_YS
+}
+
+// ---------------------------------------------------------------- main kernel
+
+struct OzArgs {
+  int64_t P, K, N;
+  const double* X;
+  int64_t ldx;
+  const int* xE;       // biased max exponent of each row of op(X)
+  const int* yE;       // biased max exponent of each column of Y
+  const uint8_t* img;  // pre-sliced Y
+  double alpha, beta;
+  double* C;
+  int64_t csp, csc;
+  double* part;        // [cta][2][TM][NN] partial tiles
+  int64_t tiles, kblocks;
+  int* flags;
+  bool vec;            // 16-byte loads allowed (trans layout)
+};
+
+template <bool TRANS>
+__device__ __forceinline__ void slice_block(const OzArgs& a, int64_t tile, int64_t kb,
+                                            uint8_t* sA, const int* sE) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t p0 = tile * TM;
+  if (TRANS) {
+    // op(X)[p, k] = X[k + p*ldx]: lanes along k (pairs), warps along p.
+    const int64_t k = kb * KBK + 2 * lane;
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+      double v0[8], v1[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int pl = warp + 8 * (i + 8 * half);
+        const int64_t p = p0 + pl;
+        v0[i] = 0.0;
+        v1[i] = 0.0;
+        if (p < a.P) {
+          const double* src = a.X + k + p * a.ldx;
+          if (a.vec && k + 1 < a.K) {
+            const double2 t = __ldg(reinterpret_cast<const double2*>(src));
+            v0[i] = t.x;
+            v1[i] = t.y;
+          } else {
+            if (k < a.K) v0[i] = __ldg(src);
+            if (k + 1 < a.K) v1[i] = __ldg(src + 1);
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int pl = warp + 8 * (i + 8 * half);
+        const int emax = sE[pl];
+        uint32_t s0, s1;
+        const uint64_t x0 = fixed56(v0[i], emax, s0), x1 = fixed56(v1[i], emax, s1);
+        uint8_t* dst = sA + tc::sw128_offset((uint32_t)pl, (uint32_t)(2 * lane));
+        *reinterpret_cast<uint32_t*>(dst + 0 * A_PLANE) = pack2<0>(x0, s0, x1, s1);
+        *reinterpret_cast<uint32_t*>(dst + 1 * A_PLANE) = pack2<1>(x0, s0, x1, s1);
+        *reinterpret_cast<uint32_t*>(dst + 2 * A_PLANE) = pack2<2>(x0, s0, x1, s1);
+        *reinterpret_cast<uint32_t*>(dst + 3 * A_PLANE) = pack2<3>(x0, s0, x1, s1);
+        *reinterpret_cast<uint32_t*>(dst + 4 * A_PLANE) = pack2<4>(x0, s0, x1, s1);
+        *reinterpret_cast<uint32_t*>(dst + 5 * A_PLANE) = pack2<5>(x0, s0, x1, s1);
+        *reinterpret_cast<uint32_t*>(dst + 6 * A_PLANE) = pack2<6>(x0, s0, x1, s1);
+      }
+    }
+  } else {
+    // op(X)[p, k] = X[p + k*ldx]: lanes along p, each warp one 8-wide k chunk.
+    const int64_t k0 = kb * KBK + 8 * warp;
+#pragma unroll 1
+    for (int h = 0; h < 4; ++h) {
+      const int pl = lane + 32 * h;
+      const int64_t p = p0 + pl;
+      double v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        v[i] = (p < a.P && k0 + i < a.K) ? __ldg(a.X + p + (k0 + i) * a.ldx) : 0.0;
+      const int emax = sE[pl];
+      uint64_t x[8];
+      uint32_t sg[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[i] = fixed56(v[i], emax, sg[i]);
+      uint8_t* dst = sA + tc::sw128_offset((uint32_t)pl, (uint32_t)(8 * warp));
+#define LRA_XS(SL)                                                \
+  {                                                               \
+    uint4 w;                                                      \
+    w.x = pack2<SL>(x[0], sg[0], x[1], sg[1]);                    \
+    w.y = pack2<SL>(x[2], sg[2], x[3], sg[3]);                    \
+    w.z = pack2<SL>(x[4], sg[4], x[5], sg[5]);                    \
+    w.w = pack2<SL>(x[6], sg[6], x[7], sg[7]);                    \
+    *reinterpret_cast<uint4*>(dst + (SL)*A_PLANE) = w;            \
+  }
+      LRA_XS(0) LRA_XS(1) LRA_XS(2) LRA_XS(3) LRA_XS(4) LRA_XS(5) LRA_XS(6)
+#undef LRA_XS
+    }
+  }
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float bb = s - hi;
+  const float e = (hi - (s - bb)) + (v - bb);
+  hi = s;
+  lo += e;
+}
+
+template <bool TRANS>
+__global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ int sE[TM];
+  __shared__ int syE[NN];
+  __shared__ int s_abort;
+  const uint32_t raw = tc::smem_addr(smem_raw);
+  uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  uint8_t* sA = sm;
+  uint8_t* sY = sm + S * A_PLANE;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t T = a.tiles * a.kblocks;
+  const int64_t G = gridDim.x, cta = blockIdx.x;
+  const int64_t u0 = cta * T / G, u1 = (cta + 1) * T / G;
+  if (u0 >= u1) return;
+
+  if (warp == 0) tc::tmem_alloc(&s_tmem, TMEM_COLS);
+  if (tid == 0) {
+    tc::mbar_init(&s_bar, 1);
+    s_abort = 0;
+  }
+  if (tid < NN) syE[tid] = tid < a.N ? a.yE[tid] : 0;
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+  const uint32_t idesc = tc::idesc_bf16_f32(TM, NN);
+  const int64_t first_tile = u0 / a.kblocks;
+  uint32_t phase = 0;
+
+  for (int64_t u = u0; u < u1;) {
+    const int64_t tile = u / a.kblocks;
+    const int64_t kb0 = u % a.kblocks;
+    const int64_t kb1 = (a.kblocks < kb0 + (u1 - u)) ? a.kblocks : kb0 + (u1 - u);
+    const bool full = (kb0 == 0 && kb1 == a.kblocks);
+    if (tid < TM) {
+      const int64_t p = tile * TM + tid;
+      sE[tid] = p < a.P ? a.xE[p] : 0;
+    }
+    __syncthreads();
+    for (int64_t kb = kb0; kb < kb1; ++kb) {
+      // stage the pre-sliced Y block (async) and slice the X block
+      const uint8_t* ysrc = a.img + kb * (int64_t)(S * Y_PLANE);
+      for (int q = tid; q < S * Y_PLANE / 16; q += NT) tc::cp_async16(sY + 16 * q, ysrc + 16 * q);
+      slice_block<TRANS>(a, tile, kb, sA, sE);
+      tc::cp_async_wait_all();
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+      if (tid == 0) {
+        const uint32_t a0 = tc::smem_addr(sA), y0 = tc::smem_addr(sY);
+#pragma unroll 1
+        for (int sa = 0; sa < S; ++sa)
+#pragma unroll 1
+          for (int sy = 0; sy < S - sa; ++sy) {
+            const int g = (sa + sy < 3) ? sa + sy : 3;
+            const bool first = (sa == 0 && sy <= 3);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              tc::mma_bf16(tmem + 64u * g, tc::desc_k_sw128(a0 + sa * A_PLANE + 32 * kk),
+                           tc::desc_k_sw128(y0 + sy * Y_PLANE + 32 * kk), idesc,
+                           (first && kk == 0) ? 0u : 1u);
+          }
+        tc::mma_commit(&s_bar);
+      }
+      const bool ok = tc::mbar_wait(&s_bar, phase, WAIT_TRIES);
+      phase ^= 1u;
+      if (!ok) s_abort = 1;
+      tc::fence_after_sync();
+      if (ok && warp < 4) {
+        // flush: (hi, lo) += the four group sums, 16 columns at a time
+        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+        const bool fresh = (kb == kb0);
+#pragma unroll 1
+        for (int c0 = 0; c0 < NN; c0 += 16) {
+          uint32_t g0[16], g1[16], g2[16], g3[16], h[16], l[16];
+          tc::tmem_ld16(trow + 0u + c0, g0);
+          tc::tmem_ld16(trow + 64u + c0, g1);
+          tc::tmem_ld16(trow + 128u + c0, g2);
+          tc::tmem_ld16(trow + 192u + c0, g3);
+          if (!fresh) {
+            tc::tmem_ld16(trow + COL_HI + c0, h);
+            tc::tmem_ld16(trow + COL_LO + c0, l);
+          }
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            float hv = fresh ? 0.0f : __uint_as_float(h[i]);
+            float lv = fresh ? 0.0f : __uint_as_float(l[i]);
+            two_sum_add(hv, lv, __uint_as_float(g0[i]));
+            two_sum_add(hv, lv, __uint_as_float(g1[i]));
+            two_sum_add(hv, lv, __uint_as_float(g2[i]));
+            two_sum_add(hv, lv, __uint_as_float(g3[i]));
+            h[i] = __float_as_uint(hv);
+            l[i] = __float_as_uint(lv);
+          }
+          tmem_st16(trow + COL_HI + c0, h);
+          tmem_st16(trow + COL_LO + c0, l);
+        }
+        tmem_st_wait();
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+      if (s_abort) break;
+    }
+    if (s_abort) break;
+    tc::fence_after_sync();
+    if (warp < 4) {
+      const int pl = 32 * warp + lane;
+      const int64_t p = tile * TM + pl;
+      const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+      const int ep = sE[pl];
+      const int slot = (tile == first_tile) ? 0 : 1;
+      double* wrow = a.part + ((cta * 2 + slot) * TM + pl) * NN;
+#pragma unroll 1
+      for (int c0 = 0; c0 < NN; c0 += 16) {
+        uint32_t h[16], l[16];
+        tc::tmem_ld16(trow + COL_HI + c0, h);
+        tc::tmem_ld16(trow + COL_LO + c0, l);
+        tc::tmem_ld_wait();
+        if (p < a.P) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int c = c0 + i;
+            if (c < a.N) {
+              const double v = ldexp((double)__uint_as_float(h[i]) + (double)__uint_as_float(l[i]),
+                                     ep + syE[c] - EXP_OFFSET);
+              if (full) {
+                double* dst = a.C + p * a.csp + (int64_t)c * a.csc;
+                *dst = (a.beta == 0.0) ? a.alpha * v : a.alpha * v + a.beta * (*dst);
+              } else {
+                wrow[c] = v;
+              }
+            }
+          }
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    u += kb1 - kb0;
+  }
+  if (s_abort && tid == 0) atomicOr(a.flags, FLAG_TIMEOUT);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// Combine the partial tiles of tiles split across CTAs, in CTA order.
+__global__ void __launch_bounds__(256) k_oz_fixup(OzArgs a, int G) {
+  const int64_t t = blockIdx.x;
+  const int64_t T = a.tiles * a.kblocks;
+  auto owner = [&](int64_t u) {
+    int64_t c = u * G / T;
+    while (c + 1 < G && (c + 1) * T / G <= u) ++c;
+    while (c > 0 && c * T / G > u) --c;
+    return c;
+  };
+  const int64_t cf = owner(t * a.kblocks), cl = owner((t + 1) * a.kblocks - 1);
+  if (cf == cl) return;
+  for (int e = threadIdx.x; e < TM * NN; e += 256) {
+    const int r = e / NN, c = e % NN;
+    const int64_t p = t * TM + r;
+    if (p >= a.P || c >= a.N) continue;
+    double s = 0.0;
+    for (int64_t q = cf; q <= cl; ++q) {
+      const int slot = (t == (q * T / G) / a.kblocks) ? 0 : 1;
+      s += a.part[((q * 2 + slot) * TM + r) * NN + c];
+    }
+    double* dst = a.C + p * a.csp + (int64_t)c * a.csc;
+    *dst = (a.beta == 0.0) ? a.alpha * s : a.alpha * s + a.beta * (*dst);
+  }
+}
+
+cudaError_t oz_rowcol_exponents(const double* X, int64_t ld, int64_t rows, int64_t cols,
+                                int* rowE, int* colE, cudaStream_t st) {
+  if (colE) {
+    k_oz_colmaxexp<<<(unsigned)cols, 256, 0, st>>>(X, ld, rows, colE);
+    cudaError_t e = launched();
+    if (e != cudaSuccess) return e;
+  }
+  if (rowE) {
+    cudaError_t e = cudaMemsetAsync(rowE, 0, rows * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const int64_t csplit = 16;
+    const int64_t cchunk = (cols + csplit - 1) / csplit;
+    dim3 grid((unsigned)((rows + 255) / 256), (unsigned)((cols + cchunk - 1) / cchunk));
+    k_oz_rowmaxexp<<<grid, 256, 0, st>>>(X, ld, rows, cols, cchunk, rowE);
+    return launched();
+  }
+  return cudaSuccess;
+}
+
+cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, const double* X,
+                   int64_t ldx, const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
+                   const OzWorkspace& w, int* flags, cudaStream_t st) {
+  if (P <= 0 || N <= 0) return cudaSuccess;
+  if (N > NN || K <= 0) return cudaErrorInvalidValue;
+  const int64_t kblocks = (K + KBK - 1) / KBK;
+  if (oz_img_bytes(K) > w.img_bytes) return cudaErrorInvalidValue;
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[trans ? 1 : 0]) {
+    cudaError_t e = cudaFuncSetAttribute(trans ? (const void*)k_ozgemm<true> : (const void*)k_ozgemm<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_DYN);
+    if (e != cudaSuccess) return e;
+    attr_set[trans ? 1 : 0] = true;
+  }
+  k_oz_colmaxexp<<<(unsigned)N, 256, 0, st>>>(Y, ldy, K, w.yE);
+  cudaError_t e = launched();
+  if (e != cudaSuccess) return e;
+  const int64_t ythreads = kblocks * NN * 8;
+  k_oz_yslice<<<(unsigned)((ythreads + 255) / 256), 256, 0, st>>>(Y, ldy, K, (int)N, w.yE, w.img,
+                                                                  kblocks);
+  e = launched();
+  if (e != cudaSuccess) return e;
+  OzArgs a;
+  a.P = P;
+  a.K = K;
+  a.N = N;
+  a.X = X;
+  a.ldx = ldx;
+  a.xE = xE;
+  a.yE = w.yE;
+  a.img = w.img;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.C = out.C;
+  a.csp = out.csp;
+  a.csc = out.csc;
+  a.part = w.part;
+  a.tiles = (P + TM - 1) / TM;
+  a.kblocks = kblocks;
+  a.flags = flags;
+  a.vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (ldx % 2 == 0);
+  const int G = w.ctas;
+  if (trans)
+    k_ozgemm<true><<<G, NT, SMEM_DYN, st>>>(a);
+  else
+    k_ozgemm<false><<<G, NT, SMEM_DYN, st>>>(a);
+  e = launched();
+  if (e != cudaSuccess) return e;
+  k_oz_fixup<<<(unsigned)a.tiles, 256, 0, st>>>(a, G);
+  return launched();
+}
+
+}  // namespace lra

@@ -20,12 +20,13 @@ GAUSSIAN, STD_BERNOULLI, SPARSE_SIGN, SPARSE_SIGN_IID, SPARSE_GAUSSIAN, BERNOULL
 F64, F32 = 0, 1
 FLAG_KEEP_Y = 1
 FLAG_PROFILE = 2
+FLAG_FP64_SIMT = 4
 PHASES = ("omega", "sketch", "dense", "deflate", "project", "orth", "indicator")
 MAX_B, MAX_P, MAX_ZETA = 64, 8, 256
 
 EXPORTS = ("lra_create", "lra_destroy", "lra_capacity", "lra_sketch", "lra_farpca_run", "lra_result",
            "lra_farpca_host", "lra_copy_omega", "lra_last_error", "lra_status_string",
-           "lra_kernel_launches", "lra_version", "lra_phase_times")
+           "lra_kernel_launches", "lra_version", "lra_phase_times", "lra_apply")
 
 
 class Matrix(Structure):
@@ -90,6 +91,8 @@ def load(path=LIB_PATH):
     lib.lra_version.restype = c_int32
     lib.lra_phase_times.argtypes = [vp, vp, vp, c_int32, c_int32]
     lib.lra_phase_times.restype = c_int32
+    lib.lra_apply.argtypes = [vp, POINTER(Matrix), c_int32, vp, c_int64, c_int64, vp, c_int64]
+    lib.lra_apply.restype = c_int32
     _lib = lib
     return lib
 
@@ -133,12 +136,13 @@ class Farpca:
     """One library context (lra_create) for m x n inputs and fixed parameters."""
 
     def __init__(self, m, n, eps=0.0, k=0, b=20, P=1, kind=SPARSE_SIGN, zeta=8, p=0.0, seed=0,
-                 max_blocks=0, keep_y=False, profile=False, stream=None):
+                 max_blocks=0, keep_y=False, profile=False, fp64_simt=False, stream=None):
         import torch
         self._torch = torch
         self._lib = load()
         self.m, self.n, self.b = m, n, b
-        flags = (FLAG_KEEP_Y if keep_y else 0) | (FLAG_PROFILE if profile else 0)
+        flags = ((FLAG_KEEP_Y if keep_y else 0) | (FLAG_PROFILE if profile else 0)
+                 | (FLAG_FP64_SIMT if fp64_simt else 0))
         self.params = Params(eps, k, b, P, kind, zeta, p, seed & 0xFFFFFFFFFFFFFFFF, max_blocks, flags)
         self._ctx = c_void_p()
         if stream is None and torch.cuda.is_available():
@@ -189,6 +193,21 @@ class Farpca:
             if r.Y:
                 out["Y"] = torch.as_tensor(_DeviceView(r.Y, (self.m, l), (1, r.ldy), self), device="cuda")
         return out
+
+    def apply(self, A, Y, trans=False, C=None):
+        """lra_apply: C = op(A) Y (op(A) = A^T if trans) with the context's dense engine."""
+        torch = self._torch
+        mat = _device_matrix(A, torch)
+        rows_c = self.n if trans else self.m
+        N = Y.shape[1]
+        if Y.stride(0) != 1:
+            raise ValueError("Y must be column-major")
+        if C is None:
+            C = torch.empty_strided((rows_c, N), (1, rows_c), dtype=torch.float64, device=A.device)
+        self._check(self._lib.lra_apply(self._ctx, byref(mat), 1 if trans else 0, c_void_p(Y.data_ptr()),
+                                        max(Y.stride(1), Y.shape[0]), N, c_void_p(C.data_ptr()),
+                                        max(C.stride(1), rows_c)))
+        return C
 
     def phase_times(self, reset=True):
         """lra_phase_times: {phase: (ms, calls)} accumulated since the last reset."""

@@ -6,10 +6,12 @@ Bar (from the method's arithmetic, FP64 on both sides):
     angle 2 pi c is rounded differently, |diff| <= 1e-13 in units of the N(0,1)
     draw, times the 1/sqrt(p) scale);
   * sketch: max |diff| <= 1e-12 max |ref|;
-  * pre-projection Y_j: ||diff||_F <= 1e-10 ||ref||_F (and elementwise <= 1e-9 of
-    max |ref|): the deflated power step A^T (A G) - B^T (B G) cancels by about
-    (sigma_1 / sigma_l)^2, so FP64 rounding in either implementation moves later
-    blocks' Y_j at the 1e-10 level;
+  * pre-projection Y_j: P = 0 (raw sketches) ||diff||_F <= 1e-12 ||ref||_F; P >= 1
+    <= 1e-9: the deflated power step A^T (A G) - B^T (B G) cancels by about
+    (sigma_1 / sigma_l)^2, so the FP64 result itself is only defined to ~3e-10 --
+    the oracle moves that much when only its summation order changes
+    (tests/test_oracle_farpca.py::test_y_sensitivity_to_summation_order), while
+    Q, B and E stay within 1e-11;
   * attained rank and status equal; E within 1e-10 relative; Q within 1e-10
     absolute (entries are O(m^-1/2)); B within 1e-10 of max |B|.
 """
@@ -57,9 +59,9 @@ def frorel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def y_close(Y, ref):
-    assert frorel(Y, ref) <= 1e-10, frorel(Y, ref)
-    assert maxrel(Y, ref) <= 1e-9, maxrel(Y, ref)
+def y_close(Y, ref, P):
+    tol = 1e-12 if P == 0 else 1e-9
+    assert frorel(Y, ref) <= tol, frorel(Y, ref)
 
 
 def test_kind_numbers_agree():
@@ -104,10 +106,10 @@ def test_sketch_parity(kind, p, zeta, m, n, pad):
     f.close()
 
 
-def _compare(A, eps, P, b, kind, p, zeta, seed, k=0, max_blocks=0, pad=0):
+def _compare(A, eps, P, b, kind, p, zeta, seed, k=0, max_blocks=0, pad=0, fp64_simt=False):
     m, n = A.shape
     f = lra.Farpca(m, n, eps=eps, k=k, b=b, P=P, kind=kind, zeta=zeta, p=p, seed=seed,
-                   max_blocks=max_blocks, keep_y=True)
+                   max_blocks=max_blocks, keep_y=True, fp64_simt=fp64_simt)
     status = f.run(dev(A, pad))
     r = f.result()
     ref = F.farpca(A, eps, P=P, b=b, kind=kind, seed=seed, zeta=zeta, p=p, k=k, max_blocks=max_blocks,
@@ -120,7 +122,7 @@ def _compare(A, eps, P, b, kind, p, zeta, seed, k=0, max_blocks=0, pad=0):
         Q = r["Q"].cpu().numpy()
         B = r["B"].cpu().numpy()
         Y = r["Y"].cpu().numpy()
-        y_close(Y, ref["Y"])
+        y_close(Y, ref["Y"], P)
         assert float(np.abs(Q - ref["Q"]).max()) <= 1e-10
         assert maxrel(B, ref["B"]) <= 1e-10
     f.close()
@@ -129,9 +131,10 @@ def _compare(A, eps, P, b, kind, p, zeta, seed, k=0, max_blocks=0, pad=0):
 
 @pytest.mark.parametrize("kind,p,zeta", KIND_CASES, ids=IDS)
 @pytest.mark.parametrize("P", [0, 1, 2])
-def test_farpca_parity(kind, p, zeta, P):
+@pytest.mark.parametrize("engine", ["tensor", "fp64_simt"])
+def test_farpca_parity(kind, p, zeta, P, engine):
     A = low_rank_matrix(700, 450, "poly1.5", 77)
-    _compare(A, 2e-2, P, 16, kind, p, zeta, seed=9)
+    _compare(A, 2e-2, P, 16, kind, p, zeta, seed=9, fp64_simt=(engine == "fp64_simt"))
 
 
 @pytest.mark.parametrize("kind,p,zeta", KIND_CASES, ids=IDS)
@@ -204,7 +207,7 @@ def test_full_size_bench_config():
     ref = F.farpca(A, 1e-2, P=1, b=50, kind=om.SPARSE_SIGN, seed=1, zeta=8, keep_y=True)
     assert r["rank"] == ref["rank"] and r["status"] == ref["status"] == 0
     assert abs(r["E"] - ref["E"]) <= 1e-10 * ref["E"]
-    y_close(r["Y"].cpu().numpy(), ref["Y"])
+    y_close(r["Y"].cpu().numpy(), ref["Y"], 1)
     assert float(np.abs(r["Q"].cpu().numpy() - ref["Q"]).max()) <= 1e-10
     assert maxrel(r["B"].cpu().numpy(), ref["B"]) <= 1e-10
     # many-block sketch pass (the sketch bandwidth measurement), sampled blocks

@@ -262,3 +262,28 @@ def test_table1_ranks(row, table1_matrices):
         assert r["rank"] == l_paper, (om.KIND_NAMES[kind], r["rank"])
         rel = math.sqrt(max(r["E"], 0.0) / r["normA2"])
         assert abs(rel - eps_opt[col[kind]]) < 0.15 * eps_opt[col[kind]], (om.KIND_NAMES[kind], rel)
+
+
+def test_y_sensitivity_to_summation_order():
+    """The power-iterated Y_j is ill conditioned in FP64, Q, B and E are not.
+
+    Feeding the oracle A with its rows permuted changes only the order of its
+    FP64 sums over m.  Y_j moves by ~1e-10 normwise (later blocks by up to
+    ~1e-8 of their norm: the deflated step cancels by (sigma_1/sigma_l)^2),
+    while Q, B and E move by < 1e-11.  This fixes the GPU parity bar for Y_j
+    with P >= 1 (1e-9) and for Q, B, E (1e-10)."""
+    A = workload_matrix("dense2000x1000_poly1.5")
+    perm = np.random.default_rng(0).permutation(A.shape[0])
+    inv = np.argsort(perm)
+    r1 = F.farpca(A, 1e-2, P=1, b=20, kind=om.SPARSE_SIGN, seed=2024, zeta=8, keep_y=True)
+    r2 = F.farpca(A[perm], 1e-2, P=1, b=20, kind=om.SPARSE_SIGN, seed=2024, zeta=8, keep_y=True)
+    assert r1["rank"] == r2["rank"]
+    dy = np.linalg.norm(r1["Y"] - r2["Y"][inv]) / np.linalg.norm(r1["Y"])
+    assert 1e-12 < dy < 1e-9
+    assert np.abs(r1["Q"] - r2["Q"][inv]).max() < 1e-11
+    assert np.abs(r1["B"] - r2["B"]).max() < 1e-11 * np.abs(r1["B"]).max()
+    assert abs(r1["E"] - r2["E"]) < 1e-10 * r1["E"]
+    # P = 0: the sketches themselves are well conditioned
+    s1 = F.farpca(A, 1e-2, P=0, b=20, kind=om.SPARSE_SIGN, seed=2024, zeta=8, keep_y=True)
+    s2 = F.farpca(A[perm], 1e-2, P=0, b=20, kind=om.SPARSE_SIGN, seed=2024, zeta=8, keep_y=True)
+    assert np.linalg.norm(s1["Y"] - s2["Y"][inv]) <= 1e-14 * np.linalg.norm(s1["Y"])
