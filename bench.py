@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--sketch-blocks", type=int, default=64)
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed farPCA steps (for launch-list profiling)")
+    ap.add_argument("--engine", choices=("tensor", "fp64_simt"), default="tensor",
+                    help="dense passes on the tensor cores (FP64-accurate slicing) or FP64 CUDA cores")
     ap.add_argument("--only", choices=("sketch",), default=None,
                     help="run only the sketch pass (lra_sketch over --sketch-blocks blocks), for profiling")
     return ap.parse_args()
@@ -216,7 +218,8 @@ def main():
     Ad = lra.column_major(torch.from_numpy(A).cuda())
     stream = torch.cuda.current_stream()
     f = lra.Farpca(m, n, eps=cfg["eps"], b=cfg["b"], P=cfg["P"], kind=cfg["kind"], zeta=cfg["zeta"],
-                   p=cfg["p"], seed=cfg["seed"] + rank, profile=True, stream=stream)
+                   p=cfg["p"], seed=cfg["seed"] + rank, profile=True, stream=stream,
+                   fp64_simt=(args.engine == "fp64_simt"))
     if args.only == "sketch":
         sp = sketch_pass(lra, torch, f, Ad, cfg, args.sketch_blocks, peaks, peak_src)
         if rank == 0:

@@ -54,10 +54,12 @@ cudaError_t omega_dense(const OmegaSpec& s, int64_t j0, int64_t nblk, double* Om
 
 // ---------------------------------------------------------------- sketch.cu
 // Y[i, g] = sum_t vals[g*cap+t] * X[i, rows[g*cap+t]] - (shift ? shift[i] : 0)
-// for i < rows_x, g < ncols; X column-major with ld ldx.
+// for i < rows_x, g < ncols; X column-major with ld ldx.  pm_scale > 0 declares
+// that every vals entry is +-pm_scale: columns of <= 16 entries are then summed
+// exactly in integer fixed point.
 cudaError_t gather_sketch(const double* X, int64_t ldx, int64_t rows_x, const int* counts,
                           const int* rows, const double* vals, int cap, int64_t ncols, double* Y,
-                          int64_t ldy, const double* shift, cudaStream_t st);
+                          int64_t ldy, const double* shift, double pm_scale, cudaStream_t st);
 
 // ---------------------------------------------------------------- dgemm_simt.cu
 // C[p, c] = alpha * sum_k opX[p, k] Y[k, c] + beta * C[p, c], p < P, c < N <= 64.

@@ -59,6 +59,7 @@ struct lra_ctx {
   int* colE = nullptr;
   OzWorkspace oz{};
   int cap = 0;  // entries per Omega column in the sparse structure
+  double pm_scale = 0.0;  // > 0: every sparse Omega entry is +-pm_scale
   OmegaSpec os{};
   int64_t nblk_max = 0, lmax = 0, ldq = 0, ldb = 0, lds = 0, ldf = 0, ldod = 0;
 
@@ -228,7 +229,7 @@ lra_status apply_omega(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows_
                        int64_t ldo, const double* shift, bool x_is_A) {
   if (ctx->sparse) {
     CK(gather_sketch(X, ldx, rows_x, ctx->om_counts, ctx->om_rows, ctx->om_vals, ctx->cap, ctx->b,
-                     out, ldo, shift, ctx->st));
+                     out, ldo, shift, ctx->pm_scale, ctx->st));
     return LRA_OK;
   }
   if (x_is_A) return dense(ctx, false, ctx->b, 1.0, X, ldx, ctx->om_dense, ctx->ldod, 0.0, out, 1, ldo);
@@ -497,6 +498,10 @@ lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
     ctx->cap = (int)n;
   }
   ctx->sb_sparse = ctx->sparse && params->kind == LRA_OMEGA_STD_BERNOULLI;
+  if (ctx->sparse && params->kind != LRA_OMEGA_SPARSE_GAUSSIAN)
+    ctx->pm_scale = (params->kind == LRA_OMEGA_SPARSE_SIGN || params->kind == LRA_OMEGA_SPARSE_SIGN_IID)
+                        ? os.inv_scale
+                        : 1.0;
 
   ctx->ldq = round_up(m, 2);
   ctx->ldb = round_up(std::max<int64_t>(ctx->lmax, 1), 2);
@@ -673,7 +678,7 @@ lra_status lra_sketch(lra_ctx* ctx, const lra_matrix* A, int64_t j0, int64_t nbl
                     ctx->flags, ctx->st));
     CK(gather_sketch(Ad, A->lda, ctx->m, ctx->sk_counts, ctx->sk_rows, ctx->sk_vals, ctx->cap,
                      nb * b, Y + (j - j0) * b * ldy, ldy, ctx->sb_sparse ? ctx->z : nullptr,
-                     ctx->st));
+                     ctx->pm_scale, ctx->st));
   }
   return LRA_OK;
 }

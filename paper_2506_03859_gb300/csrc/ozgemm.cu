@@ -440,7 +440,9 @@ __global__ void __launch_bounds__(256) k_oz_fixup(OzArgs a, int G) {
     if (p >= a.P || c >= a.N) continue;
     double s = 0.0;
     for (int64_t q = cf; q <= cl; ++q) {
-      const int slot = (t == (q * T / G) / a.kblocks) ? 0 : 1;
+      const int64_t q0 = q * T / G, q1 = (q + 1) * T / G;
+      if (q0 >= q1) continue;  // a CTA with an empty range wrote nothing
+      const int slot = (t == q0 / a.kblocks) ? 0 : 1;
       s += a.part[((q * 2 + slot) * TM + r) * NN + c];
     }
     double* dst = a.C + p * a.csp + (int64_t)c * a.csc;

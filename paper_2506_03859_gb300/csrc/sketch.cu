@@ -1,10 +1,10 @@
 // Sparse sketch Y = X Omega (Alg. 1 step "A G_j" with a sparse Omega_j; Alg. 2
 // steps 5-7, A B_j - z).  Each output column g gathers counts[g] columns of the
-// column-major X.  HBM-bound: a thread owns two consecutive rows and issues one
-// 16-byte load per gathered column (unrolled by 4 so several loads are in
-// flight); consecutive threads read consecutive 16-byte words of the same
-// column, so every warp touches whole 128-byte lines.  Duplicated column
-// indices across output columns of a block hit in L2.
+// column-major X.  A thread owns two consecutive rows and issues one 16-byte
+// load per gathered column, all of a column's loads before any arithmetic;
+// consecutive threads read consecutive 16-byte words of the same column, so
+// every warp touches whole 128-byte lines.  Duplicated column indices across
+// output columns of a block hit in L2.
 #include "internal.cuh"
 
 namespace lra {
@@ -69,14 +69,150 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Omega entries of one magnitude (+-v: the sparse sign kinds; v = 1: the
+// Bernoulli kinds).  On GB300 every FP64 add costs as much as a DFMA on a pipe
+// delivering ~0.6 Tops/s, so summing zeta FP64 terms per output would bound
+// the pass by the FP64 pipe, not by HBM.  Here the signed sum of the gathered
+// doubles is taken exactly in 64-bit integer fixed point, aligned to the
+// largest exponent among a row's terms (at most 16 terms: 5 bits of headroom),
+// converted back to FP64 with round-to-nearest-even by integer operations, and
+// multiplied by v once: one FP64 operation per output instead of zeta.
+constexpr int PM_MAX_TERMS = 16;
+
+__device__ __forceinline__ int exp_of(double a) {
+  return (int)(((uint64_t)__double_as_longlong(a) >> 52) & 0x7FFu);
+}
+
+// |a| significand shifted to the common scale 2^(emax - 1080) (exact unless the
+// term is more than 5 binades below the largest, then truncated below 2^-58 of it).
+__device__ __forceinline__ int64_t fixed_term(double a, int emax) {
+  const uint64_t b = (uint64_t)__double_as_longlong(a);
+  const int E = (int)((b >> 52) & 0x7FFu);
+  const uint64_t M = (E != 0) ? ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : 0ull;
+  const int d = emax - E;
+  const uint64_t T = d < 64 ? ((M << 5) >> d) : 0ull;
+  return (b >> 63) ? -(int64_t)T : (int64_t)T;
+}
+
+// S * 2^(emax - 1080) as an FP64 value, rounded to nearest even (integer ops).
+__device__ __forceinline__ double fixed_to_double(int64_t S, int emax) {
+  if (S == 0) return 0.0;
+  const uint64_t sign = S < 0 ? (1ull << 63) : 0ull;
+  uint64_t mag = S < 0 ? (uint64_t)(-S) : (uint64_t)S;
+  int nbits = 64 - __clzll((long long)mag);
+  uint64_t mant;
+  if (nbits <= 53) {
+    mant = mag << (53 - nbits);
+  } else {
+    const int sh = nbits - 53;
+    mant = mag >> sh;
+    const uint64_t rem = mag & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) ++mant;
+    if (mant == (1ull << 53)) {
+      mant >>= 1;
+      ++nbits;
+    }
+  }
+  const int eb = nbits + emax - 58;  // biased exponent of the result
+  if (eb <= 0) return __longlong_as_double((long long)sign);             // below the normal range
+  if (eb >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+  return __longlong_as_double((long long)(sign | ((uint64_t)eb << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+template <bool VEC2>
+__global__ void __launch_bounds__(256)
+    k_gather_pm(const double* __restrict__ X, int64_t ldx, int64_t rows_x,
+                const int* __restrict__ counts, const int* __restrict__ rows,
+                const double* __restrict__ vals, int cap, int64_t ncols, double* __restrict__ Y,
+                int64_t ldy, const double* __restrict__ shift, double v) {
+  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
+  if (i0 >= rows_x) return;
+  const bool two = (i0 + 1) < rows_x;
+  for (int64_t g = blockIdx.y; g < ncols; g += gridDim.y) {
+    const int cnt = __ldg(counts + g);
+    const int* rg = rows + g * cap;
+    const double* vg = vals + g * cap;
+    double y0, y1;
+    if (cnt <= PM_MAX_TERMS) {
+      double a0[PM_MAX_TERMS], a1[PM_MAX_TERMS];
+      bool neg[PM_MAX_TERMS];
+#pragma unroll
+      for (int t = 0; t < PM_MAX_TERMS; ++t) {
+        a0[t] = 0.0;
+        a1[t] = 0.0;
+        neg[t] = false;
+        if (t < cnt) {
+          const double* col = X + (int64_t)__ldg(rg + t) * ldx + i0;
+          neg[t] = __ldg(vg + t) < 0.0;
+          if (VEC2 && two) {
+            const double2 q = __ldg(reinterpret_cast<const double2*>(col));
+            a0[t] = q.x;
+            a1[t] = q.y;
+          } else {
+            a0[t] = __ldg(col);
+            if (two) a1[t] = __ldg(col + 1);
+          }
+        }
+      }
+      int e0 = 0, e1 = 0;
+#pragma unroll
+      for (int t = 0; t < PM_MAX_TERMS; ++t) {
+        e0 = max(e0, exp_of(a0[t]));
+        e1 = max(e1, exp_of(a1[t]));
+      }
+      int64_t s0 = 0, s1 = 0;
+#pragma unroll
+      for (int t = 0; t < PM_MAX_TERMS; ++t) {
+        const int64_t t0 = fixed_term(a0[t], e0), t1 = fixed_term(a1[t], e1);
+        s0 += neg[t] ? -t0 : t0;
+        s1 += neg[t] ? -t1 : t1;
+      }
+      const double qnan = __longlong_as_double(0x7FF8000000000000ll);
+      y0 = (e0 == 2047) ? qnan : fixed_to_double(s0, e0);
+      y1 = (e1 == 2047) ? qnan : fixed_to_double(s1, e1);
+      if (v != 1.0) {
+        y0 *= v;
+        y1 *= v;
+      }
+    } else {
+      // long columns (large Bernoulli probability): FP64 multiply-adds
+      y0 = 0.0;
+      y1 = 0.0;
+      for (int t = 0; t < cnt; ++t) {
+        const double* col = X + (int64_t)__ldg(rg + t) * ldx + i0;
+        const double w = __ldg(vg + t);
+        y0 = fma(w, __ldg(col), y0);
+        if (two) y1 = fma(w, __ldg(col + 1), y1);
+      }
+    }
+    if (shift) {
+      y0 -= __ldg(shift + i0);
+      if (two) y1 -= __ldg(shift + i0 + 1);
+    }
+    double* yg = Y + g * ldy + i0;
+    yg[0] = y0;
+    if (two) yg[1] = y1;
+  }
+}
+
 cudaError_t gather_sketch(const double* X, int64_t ldx, int64_t rows_x, const int* counts,
                           const int* rows, const double* vals, int cap, int64_t ncols, double* Y,
-                          int64_t ldy, const double* shift, cudaStream_t st) {
+                          int64_t ldy, const double* shift, double pm_scale, cudaStream_t st) {
   if (ncols <= 0 || rows_x <= 0) return cudaSuccess;
   const int threads = 256;
   const int64_t chunks = (rows_x + 2 * threads - 1) / (2 * threads);
   dim3 grid((unsigned)chunks, (unsigned)(ncols < 65535 ? ncols : 65535));
   const bool vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (ldx % 2 == 0);
+  if (pm_scale > 0.0) {
+    if (vec)
+      k_gather_pm<true><<<grid, threads, 0, st>>>(X, ldx, rows_x, counts, rows, vals, cap, ncols, Y,
+                                                  ldy, shift, pm_scale);
+    else
+      k_gather_pm<false><<<grid, threads, 0, st>>>(X, ldx, rows_x, counts, rows, vals, cap, ncols,
+                                                   Y, ldy, shift, pm_scale);
+    return launched();
+  }
   if (vec)
     k_gather<true><<<grid, threads, 0, st>>>(X, ldx, rows_x, counts, rows, vals, cap, ncols, Y,
                                              ldy, shift);
