@@ -11,25 +11,28 @@
 //
 //   each row p of op(X) is scaled by 2^-e_p (|x| < 2^e_p over the row) and
 //   each column c of Y by 2^-f_c; the scaled value, truncated to a 56-bit fixed
-//   point number, is x = 2^-8 sum_{s<7} v_s with v_s = d_s 2^(-8 s),
-//   d_s in [0, 255] carrying the sign of x.  Every v_s is exact in bf16.
+//   point number, is x = 2^-7 sum_{s<8} v_s with v_s = d_s 2^(-7 s),
+//   d_s in [0, 127] carrying the sign of x.  Every v_s is exact in bf16.
 //
-//   x y = 2^-16 sum_{s,t} v_s w_t; the pairs with s + t <= 6 are kept (the
-//   rest is below 2^-56 relative), and each pair is a bf16 GEMM on the tensor
-//   core.  Pairs of weight s + t = 0, 1, 2 go to separate FP32 TMEM
-//   accumulators and are flushed every 64 values of K, a window in which their
-//   integer-valued partial sums stay below 2^24 and are therefore exact; all
-//   pairs of weight >= 3 share a fourth accumulator (their rounding is
-//   below 2^-48 of the result).  Flushed values are summed in double-float
-//   (hi + lo, FP32 two-sum) kept in TMEM next to the accumulators, and the
-//   tile is scaled by 2^(e_p + f_c) and written in FP64.
+//   x y = 2^-14 sum_{s,t} v_s w_t; the 36 pairs with s + t <= 7 are kept (the
+//   rest is below 2^-56 relative), each a bf16 MMA on the tensor core with FP32
+//   accumulation in TMEM.  The pairs of weight w = s + t <= 4 are summed per
+//   weight over windows of 32 values of K: every such sum is an integer
+//   multiple of 2^(-7 w) below 2^22 units (at most 5 pairs x 32 x 127^2), so the
+//   FP32 accumulator holds it exactly and adding 1.5 * 2^23 turns it into an
+//   integer.  The five integers are combined into one int64 per output in units
+//   of 2^-28 (exact).  The pairs of weight >= 5 (at most 2^-35 of a product) run
+//   in one FP32 accumulator over all of K.  The tile is then (int64 * 2^-28 +
+//   fp32) * 2^(e_p + f_c - 2058), written in FP64.  Against exact dot products
+//   the error is that of an FP64 GEMM (2^-52 of |op(X)| |Y| on Gaussian data).
 //
 // Work split: one CTA per SM walks a contiguous range of (row tile, k-block)
 // units ("stream-K"); tiles whose k-blocks span two or more CTAs are written as
 // partial sums and combined by a fixup kernel in a fixed order.
-// Per k-block the CTA (256 threads) loads a 128 x 64 block of op(X) from HBM,
-// slices it into 7 shared-memory planes (128-byte swizzled, K-major), copies
-// the pre-sliced 64 x 64 block of Y, and one thread issues the 28 x 4 MMAs.
+// Per 64-deep k-block the CTA (256 threads) loads a 128 x 64 block of op(X)
+// from HBM, slices it into 8 shared-memory planes (128-byte swizzled, K-major),
+// copies the pre-sliced 64 x 64 block of Y, and one thread issues the MMAs of
+// each 32-deep window; four warps flush the window from TMEM.
 #include <math.h>
 
 #include "internal.cuh"
@@ -38,7 +41,8 @@
 namespace lra {
 
 namespace {
-constexpr int S = 7;              // slices per operand (8 bits each)
+constexpr int S = 8;              // slices per operand (7 bits each)
+constexpr int BETA = 7;           // bits per slice
 constexpr int TM = 128;           // rows of op(X) per tile
 constexpr int KBK = 64;           // K per k-block
 constexpr int NN = 64;            // output columns (N padded)
@@ -46,10 +50,12 @@ constexpr int NT = 256;           // threads per CTA
 constexpr int A_PLANE = TM * 128; // bytes of one slice plane of the X block
 constexpr int Y_PLANE = NN * 128; // bytes of one slice plane of the Y block
 constexpr int SMEM_DYN = S * A_PLANE + S * Y_PLANE + 1024;
-constexpr uint32_t TMEM_COLS = 512;  // 4 accumulators x 64 columns, then hi and lo sums
-constexpr uint32_t COL_HI = 256, COL_LO = 320;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t COL_G5 = 320;                  // FP32 sum of the pairs of weight >= 5
+constexpr uint32_t COL_ACC_LO = 384, COL_ACC_HI = 448;  // int64 exact sum, two words
+constexpr int EXACT_GROUPS = 5;                   // weights 0..4, TMEM columns 64 w
 constexpr long WAIT_TRIES = 1L << 24;
-constexpr int EXP_OFFSET = 2060;  // 2 * (1022 + 8): see the scaling above
+constexpr int EXP_OFFSET = 2058;  // 2 * 1022 + 2 * BETA: see the scaling above
 }  // namespace
 
 int64_t oz_img_bytes(int64_t K) { return (K + KBK - 1) / KBK * S * Y_PLANE; }
@@ -68,13 +74,13 @@ __device__ __forceinline__ uint64_t fixed56(double a, int emax, uint32_t& sign) 
   return sh < 64 ? (M >> sh) : 0ull;
 }
 
-// bf16 bits of d * 2^(-8 s) (d < 256, exact), sign in bit 15.
+// bf16 bits of d * 2^(-7 s) (d < 128, exact), sign in bit 15.
 template <int SLICE>
 __device__ __forceinline__ uint32_t slice_bf16(uint64_t x, uint32_t sign) {
-  const uint32_t d = (uint32_t)(x >> (8 * (S - 1 - SLICE))) & 0xFFu;
-  constexpr float sc = (SLICE == 0) ? 1.0f : (SLICE == 1) ? 0x1p-8f : (SLICE == 2) ? 0x1p-16f
-                       : (SLICE == 3) ? 0x1p-24f : (SLICE == 4) ? 0x1p-32f : (SLICE == 5) ? 0x1p-40f
-                                                                                     : 0x1p-48f;
+  const uint32_t d = (uint32_t)(x >> (BETA * (S - 1 - SLICE))) & 0x7Fu;
+  constexpr float sc = (SLICE == 0) ? 1.0f : (SLICE == 1) ? 0x1p-7f : (SLICE == 2) ? 0x1p-14f
+                       : (SLICE == 3) ? 0x1p-21f : (SLICE == 4) ? 0x1p-28f : (SLICE == 5) ? 0x1p-35f
+                       : (SLICE == 6) ? 0x1p-42f : 0x1p-49f;
   const float f = __fmaf_rn(__int_as_float(0x4B000000 | (int)d), sc, -8388608.0f * sc);
   return (__float_as_uint(f) >> 16) | (sign << 15);
 }
@@ -151,7 +157,7 @@ __global__ void __launch_bounds__(256) k_oz_yslice(const double* __restrict__ Y,
     w.w = pack2<SL>(x[6], sg[6], x[7], sg[7]);                                              \
     *reinterpret_cast<uint4*>(base + (SL)*Y_PLANE) = w;                                     \
   }
-  LRA_YS(0) LRA_YS(1) LRA_YS(2) LRA_YS(3) LRA_YS(4) LRA_YS(5) LRA_YS(6)
+  LRA_YS(0) LRA_YS(1) LRA_YS(2) LRA_YS(3) LRA_YS(4) LRA_YS(5) LRA_YS(6) LRA_YS(7)
 #undef LRA_YS
 }
 
@@ -216,6 +222,7 @@ __device__ __forceinline__ void slice_block(const OzArgs& a, int64_t tile, int64
         *reinterpret_cast<uint32_t*>(dst + 4 * A_PLANE) = pack2<4>(x0, s0, x1, s1);
         *reinterpret_cast<uint32_t*>(dst + 5 * A_PLANE) = pack2<5>(x0, s0, x1, s1);
         *reinterpret_cast<uint32_t*>(dst + 6 * A_PLANE) = pack2<6>(x0, s0, x1, s1);
+        *reinterpret_cast<uint32_t*>(dst + 7 * A_PLANE) = pack2<7>(x0, s0, x1, s1);
       }
     }
   } else {
@@ -244,7 +251,7 @@ __device__ __forceinline__ void slice_block(const OzArgs& a, int64_t tile, int64
     w.w = pack2<SL>(x[6], sg[6], x[7], sg[7]);                    \
     *reinterpret_cast<uint4*>(dst + (SL)*A_PLANE) = w;            \
   }
-      LRA_XS(0) LRA_XS(1) LRA_XS(2) LRA_XS(3) LRA_XS(4) LRA_XS(5) LRA_XS(6)
+      LRA_XS(0) LRA_XS(1) LRA_XS(2) LRA_XS(3) LRA_XS(4) LRA_XS(5) LRA_XS(6) LRA_XS(7)
 #undef LRA_XS
     }
   }
@@ -262,12 +269,10 @@ __device__ __forceinline__ void tmem_st_wait() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
-  const float s = hi + v;
-  const float bb = s - hi;
-  const float e = (hi - (s - bb)) + (v - bb);
-  hi = s;
-  lo += e;
+// An FP32 value that is an integer multiple n of 2^-k with |n| < 2^22, as n:
+// adding 1.5 * 2^23 after scaling by 2^k puts n in the low mantissa bits.
+__device__ __forceinline__ int exact_int(uint32_t bits, float scale) {
+  return __float_as_int(__fmaf_rn(__uint_as_float(bits), scale, 12582912.0f)) - 0x4B400000;
 }
 
 template <bool TRANS>
@@ -323,64 +328,76 @@ __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
       tc::fence_before_sync();
       __syncthreads();
       tc::fence_after_sync();
-      if (tid == 0) {
-        const uint32_t a0 = tc::smem_addr(sA), y0 = tc::smem_addr(sY);
 #pragma unroll 1
-        for (int sa = 0; sa < S; ++sa)
+      for (int win = 0; win < 2; ++win) {
+        const bool fresh = (kb == kb0 && win == 0);
+        if (tid == 0) {
+          const uint32_t a0 = tc::smem_addr(sA), y0 = tc::smem_addr(sY);
 #pragma unroll 1
-          for (int sy = 0; sy < S - sa; ++sy) {
-            const int g = (sa + sy < 3) ? sa + sy : 3;
-            const bool first = (sa == 0 && sy <= 3);
+          for (int sa = 0; sa < S; ++sa)
+#pragma unroll 1
+            for (int sy = 0; sy < S - sa; ++sy) {
+              const int w = sa + sy;
+              const uint32_t col = w < EXACT_GROUPS ? 64u * w : COL_G5;
+              // exact groups restart every window; the weight >= 5 sum once per tile range
+              const bool first = (sa == 0) && (w < EXACT_GROUPS || (w == EXACT_GROUPS && fresh));
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-              tc::mma_bf16(tmem + 64u * g, tc::desc_k_sw128(a0 + sa * A_PLANE + 32 * kk),
-                           tc::desc_k_sw128(y0 + sy * Y_PLANE + 32 * kk), idesc,
-                           (first && kk == 0) ? 0u : 1u);
-          }
-        tc::mma_commit(&s_bar);
-      }
-      const bool ok = tc::mbar_wait(&s_bar, phase, WAIT_TRIES);
-      phase ^= 1u;
-      if (!ok) s_abort = 1;
-      tc::fence_after_sync();
-      if (ok && warp < 4) {
-        // flush: (hi, lo) += the four group sums, 16 columns at a time
-        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-        const bool fresh = (kb == kb0);
-#pragma unroll 1
-        for (int c0 = 0; c0 < NN; c0 += 16) {
-          uint32_t g0[16], g1[16], g2[16], g3[16], h[16], l[16];
-          tc::tmem_ld16(trow + 0u + c0, g0);
-          tc::tmem_ld16(trow + 64u + c0, g1);
-          tc::tmem_ld16(trow + 128u + c0, g2);
-          tc::tmem_ld16(trow + 192u + c0, g3);
-          if (!fresh) {
-            tc::tmem_ld16(trow + COL_HI + c0, h);
-            tc::tmem_ld16(trow + COL_LO + c0, l);
-          }
-          tc::tmem_ld_wait();
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            float hv = fresh ? 0.0f : __uint_as_float(h[i]);
-            float lv = fresh ? 0.0f : __uint_as_float(l[i]);
-            two_sum_add(hv, lv, __uint_as_float(g0[i]));
-            two_sum_add(hv, lv, __uint_as_float(g1[i]));
-            two_sum_add(hv, lv, __uint_as_float(g2[i]));
-            two_sum_add(hv, lv, __uint_as_float(g3[i]));
-            h[i] = __float_as_uint(hv);
-            l[i] = __float_as_uint(lv);
-          }
-          tmem_st16(trow + COL_HI + c0, h);
-          tmem_st16(trow + COL_LO + c0, l);
+              for (int k2 = 0; k2 < 2; ++k2) {
+                const int kk = 2 * win + k2;
+                tc::mma_bf16(tmem + col, tc::desc_k_sw128(a0 + sa * A_PLANE + 32 * kk),
+                             tc::desc_k_sw128(y0 + sy * Y_PLANE + 32 * kk), idesc,
+                             (first && k2 == 0) ? 0u : 1u);
+              }
+            }
+          tc::mma_commit(&s_bar);
         }
-        tmem_st_wait();
+        const bool ok = tc::mbar_wait(&s_bar, phase, WAIT_TRIES);
+        phase ^= 1u;
+        if (!ok) s_abort = 1;
+        tc::fence_after_sync();
+        if (ok && warp < 4) {
+          // flush: acc += sum_w n_w 2^(7 (4 - w)), 16 columns at a time
+          const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll 1
+          for (int c0 = 0; c0 < NN; c0 += 16) {
+            uint32_t g0[16], g1[16], g2[16], g3[16], g4[16], lo[16], hi[16];
+            tc::tmem_ld16(trow + 0u + c0, g0);
+            tc::tmem_ld16(trow + 64u + c0, g1);
+            tc::tmem_ld16(trow + 128u + c0, g2);
+            tc::tmem_ld16(trow + 192u + c0, g3);
+            tc::tmem_ld16(trow + 256u + c0, g4);
+            if (!fresh) {
+              tc::tmem_ld16(trow + COL_ACC_LO + c0, lo);
+              tc::tmem_ld16(trow + COL_ACC_HI + c0, hi);
+            }
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int n0 = exact_int(g0[i], 1.0f);
+              const int n1 = exact_int(g1[i], 0x1p7f);
+              const int n2 = exact_int(g2[i], 0x1p14f);
+              const int n3 = exact_int(g3[i], 0x1p21f);
+              const int n4 = exact_int(g4[i], 0x1p28f);
+              const int64_t add = ((int64_t)n0 << 28) + ((int64_t)(n1 * 128 + n2) << 14) +
+                                  (int64_t)(n3 * 128 + n4);
+              int64_t acc = fresh ? 0 : (int64_t)(((uint64_t)hi[i] << 32) | (uint64_t)lo[i]);
+              acc += add;
+              lo[i] = (uint32_t)((uint64_t)acc & 0xFFFFFFFFull);
+              hi[i] = (uint32_t)((uint64_t)acc >> 32);
+            }
+            tmem_st16(trow + COL_ACC_LO + c0, lo);
+            tmem_st16(trow + COL_ACC_HI + c0, hi);
+          }
+          tmem_st_wait();
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (s_abort) break;
       }
-      tc::fence_before_sync();
-      __syncthreads();
       if (s_abort) break;
     }
     if (s_abort) break;
-    tc::fence_after_sync();
     if (warp < 4) {
       const int pl = 32 * warp + lane;
       const int64_t p = tile * TM + pl;
@@ -390,17 +407,19 @@ __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
       double* wrow = a.part + ((cta * 2 + slot) * TM + pl) * NN;
 #pragma unroll 1
       for (int c0 = 0; c0 < NN; c0 += 16) {
-        uint32_t h[16], l[16];
-        tc::tmem_ld16(trow + COL_HI + c0, h);
-        tc::tmem_ld16(trow + COL_LO + c0, l);
+        uint32_t lo[16], hi[16], g5[16];
+        tc::tmem_ld16(trow + COL_ACC_LO + c0, lo);
+        tc::tmem_ld16(trow + COL_ACC_HI + c0, hi);
+        tc::tmem_ld16(trow + COL_G5 + c0, g5);
         tc::tmem_ld_wait();
         if (p < a.P) {
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             const int c = c0 + i;
             if (c < a.N) {
-              const double v = ldexp((double)__uint_as_float(h[i]) + (double)__uint_as_float(l[i]),
-                                     ep + syE[c] - EXP_OFFSET);
+              const int64_t acc = (int64_t)(((uint64_t)hi[i] << 32) | (uint64_t)lo[i]);
+              const double sum = fma(__ll2double_rn(acc), 0x1p-28, (double)__uint_as_float(g5[i]));
+              const double v = ldexp(sum, ep + syE[c] - EXP_OFFSET);
               if (full) {
                 double* dst = a.C + p * a.csp + (int64_t)c * a.csc;
                 *dst = (a.beta == 0.0) ? a.alpha * v : a.alpha * v + a.beta * (*dst);

@@ -120,7 +120,7 @@ __device__ __forceinline__ double fixed_to_double(int64_t S, int emax) {
   return __longlong_as_double((long long)(sign | ((uint64_t)eb << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
-template <bool VEC2>
+template <bool VEC2, int MAXT>
 __global__ void __launch_bounds__(256)
     k_gather_pm(const double* __restrict__ X, int64_t ldx, int64_t rows_x,
                 const int* __restrict__ counts, const int* __restrict__ rows,
@@ -134,11 +134,11 @@ __global__ void __launch_bounds__(256)
     const int* rg = rows + g * cap;
     const double* vg = vals + g * cap;
     double y0, y1;
-    if (cnt <= PM_MAX_TERMS) {
-      double a0[PM_MAX_TERMS], a1[PM_MAX_TERMS];
-      bool neg[PM_MAX_TERMS];
+    if (cnt <= MAXT) {
+      double a0[MAXT], a1[MAXT];
+      bool neg[MAXT];
 #pragma unroll
-      for (int t = 0; t < PM_MAX_TERMS; ++t) {
+      for (int t = 0; t < MAXT; ++t) {
         a0[t] = 0.0;
         a1[t] = 0.0;
         neg[t] = false;
@@ -157,16 +157,16 @@ __global__ void __launch_bounds__(256)
       }
       int e0 = 0, e1 = 0;
 #pragma unroll
-      for (int t = 0; t < PM_MAX_TERMS; ++t) {
+      for (int t = 0; t < MAXT; ++t) {
         e0 = max(e0, exp_of(a0[t]));
         e1 = max(e1, exp_of(a1[t]));
       }
       int64_t s0 = 0, s1 = 0;
 #pragma unroll
-      for (int t = 0; t < PM_MAX_TERMS; ++t) {
+      for (int t = 0; t < MAXT; ++t) {
         const int64_t t0 = fixed_term(a0[t], e0), t1 = fixed_term(a1[t], e1);
-        s0 += neg[t] ? -t0 : t0;
-        s1 += neg[t] ? -t1 : t1;
+        s0 = neg[t] ? s0 - t0 : s0 + t0;
+        s1 = neg[t] ? s1 - t1 : s1 + t1;
       }
       const double qnan = __longlong_as_double(0x7FF8000000000000ll);
       y0 = (e0 == 2047) ? qnan : fixed_to_double(s0, e0);
@@ -205,12 +205,17 @@ cudaError_t gather_sketch(const double* X, int64_t ldx, int64_t rows_x, const in
   dim3 grid((unsigned)chunks, (unsigned)(ncols < 65535 ? ncols : 65535));
   const bool vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (ldx % 2 == 0);
   if (pm_scale > 0.0) {
-    if (vec)
-      k_gather_pm<true><<<grid, threads, 0, st>>>(X, ldx, rows_x, counts, rows, vals, cap, ncols, Y,
-                                                  ldy, shift, pm_scale);
-    else
-      k_gather_pm<false><<<grid, threads, 0, st>>>(X, ldx, rows_x, counts, rows, vals, cap, ncols,
-                                                   Y, ldy, shift, pm_scale);
+#define LRA_PM(V, T)                                                                            \
+  k_gather_pm<V, T><<<grid, threads, 0, st>>>(X, ldx, rows_x, counts, rows, vals, cap, ncols, Y, \
+                                              ldy, shift, pm_scale)
+    if (cap <= 4) {
+      if (vec) LRA_PM(true, 4); else LRA_PM(false, 4);
+    } else if (cap <= 8) {
+      if (vec) LRA_PM(true, 8); else LRA_PM(false, 8);
+    } else {
+      if (vec) LRA_PM(true, 16); else LRA_PM(false, 16);
+    }
+#undef LRA_PM
     return launched();
   }
   if (vec)
