@@ -12,8 +12,13 @@ Bar (from the method's arithmetic, FP64 on both sides):
     the oracle moves that much when only its summation order changes
     (tests/test_oracle_farpca.py::test_y_sensitivity_to_summation_order), while
     Q, B and E stay within 1e-11;
-  * attained rank and status equal; E within 1e-10 relative; Q within 1e-10
-    absolute (entries are O(m^-1/2)); B within 1e-10 of max |B|.
+  * attained rank and status equal; Q within 1e-10 absolute (entries are
+    O(m^-1/2)); B within 1e-10 of max |B|;
+  * the indicator E = ||A||_F^2 - sum_j ||B_j||_F^2 within 1e-12 ||A||_F^2
+    absolute: E is ~eps^2 ||A||_F^2, so the FP64 rounding of the two large sums
+    (~1e-14 ||A||_F^2; the device sums FMA-exact squares, numpy rounded ones) is
+    amplified by ||A||_F^2 / E in E's relative error -- the resolution limit of
+    the FP64 indicator that Sec. 2.1 quotes (eps > 2.1e-7 ||A||_F).
 """
 import math
 
@@ -118,7 +123,7 @@ def _compare(A, eps, P, b, kind, p, zeta, seed, k=0, max_blocks=0, pad=0, fp64_s
     assert r["rank"] == ref["rank"] and r["blocks"] == ref["blocks"]
     assert abs(r["normA2"] - ref["normA2"]) <= 1e-13 * ref["normA2"]
     if ref["rank"] > 0:
-        assert abs(r["E"] - ref["E"]) <= 1e-10 * abs(ref["E"]) + 1e-15 * ref["normA2"]
+        assert abs(r["E"] - ref["E"]) <= 1e-12 * ref["normA2"]
         Q = r["Q"].cpu().numpy()
         B = r["B"].cpu().numpy()
         Y = r["Y"].cpu().numpy()
@@ -206,7 +211,7 @@ def test_full_size_bench_config():
     r = f.result()
     ref = F.farpca(A, 1e-2, P=1, b=50, kind=om.SPARSE_SIGN, seed=1, zeta=8, keep_y=True)
     assert r["rank"] == ref["rank"] and r["status"] == ref["status"] == 0
-    assert abs(r["E"] - ref["E"]) <= 1e-10 * ref["E"]
+    assert abs(r["E"] - ref["E"]) <= 1e-12 * ref["normA2"]
     y_close(r["Y"].cpu().numpy(), ref["Y"], 1)
     assert float(np.abs(r["Q"].cpu().numpy() - ref["Q"]).max()) <= 1e-10
     assert maxrel(r["B"].cpu().numpy(), ref["B"]) <= 1e-10
