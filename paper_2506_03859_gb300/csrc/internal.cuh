@@ -90,9 +90,10 @@ int64_t oz_part_elems(int ctas);
 cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, const double* X,
                    int64_t ldx, const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
                    const OzWorkspace& w, int* flags, cudaStream_t st);
-// rowE[r] / colE[c] = largest biased exponent in row r / column c of X (either may be NULL).
+// rowE[r] / colE[c] = largest biased exponent in row r / column c of X (either may
+// be NULL).  accumulate_rows: rowE[r] = max(rowE[r], ...) instead of overwriting.
 cudaError_t oz_rowcol_exponents(const double* X, int64_t ld, int64_t rows, int64_t cols,
-                                int* rowE, int* colE, cudaStream_t st);
+                                int* rowE, int* colE, cudaStream_t st, bool accumulate_rows = false);
 
 // ---------------------------------------------------------------- orth.cu
 // Per-column sums of squares and/or sums of X (rows x cols, ld): one CTA per column.

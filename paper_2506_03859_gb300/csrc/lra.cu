@@ -57,6 +57,9 @@ struct lra_ctx {
   bool tensor = true;  // full passes over A on the tensor cores (FP64-accurate slicing)
   int* rowE = nullptr;  // biased max exponent of each row / column of A
   int* colE = nullptr;
+  int *qrowE = nullptr, *qcolE = nullptr;  // ... of Q (rows: m, columns: l_max)
+  int *browE = nullptr, *bcolE = nullptr;  // ... of B (rows: l_max, columns: n)
+  int *xrowE = nullptr, *xcolE = nullptr;  // scratch for the operand of orth()
   OzWorkspace oz{};
   int cap = 0;  // entries per Omega column in the sparse structure
   double pm_scale = 0.0;  // > 0: every sparse Omega entry is +-pm_scale
@@ -201,16 +204,52 @@ lra_status a_exponents(lra_ctx* ctx, const double* A, int64_t lda) {
   return LRA_OK;
 }
 
+// C = alpha op(X) Y + beta C with the context's engine.  xE: biased max exponent
+// of each row of op(X); the tensor engine needs it (NULL selects the FP64 cores).
+lra_status mm(lra_ctx* ctx, bool trans, int64_t P, int64_t N, int64_t K, double alpha,
+              const double* X, int64_t ldx, const int* xE, const double* Y, int64_t ldy,
+              double beta, double* C, int64_t csp, int64_t csc) {
+  if (!ctx->tensor || !xE) return gemm(ctx, trans, P, N, K, alpha, X, ldx, Y, ldy, beta, C, csp, csc);
+  if (P <= 0 || N <= 0) return LRA_OK;
+  if (K <= 0) return LRA_OK;
+  CK(ozgemm(trans, P, N, K, alpha, X, ldx, xE, Y, ldy, beta, GemmOut{C, csp, csc}, ctx->oz,
+            ctx->flags, ctx->st));
+  return LRA_OK;
+}
+
+// S = X^T X (b x b) and Tmp-style right multiplication X R^{-1}, both on the
+// context's engine; exponents of X computed on the fly.
+lra_status gram(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows) {
+  const int b = ctx->b;
+  const int* xE = nullptr;
+  if (ctx->tensor) {
+    CK(oz_rowcol_exponents(X, ldx, rows, b, nullptr, ctx->xcolE, ctx->st));
+    xE = ctx->xcolE;
+  }
+  return mm(ctx, true, b, b, rows, 1.0, X, ldx, xE, X, ldx, 0.0, ctx->gram, 1, b);
+}
+
+lra_status right_apply_rinv(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows, double* out,
+                            int64_t ldo) {
+  const int b = ctx->b;
+  const int* xE = nullptr;
+  if (ctx->tensor) {
+    CK(oz_rowcol_exponents(X, ldx, rows, b, ctx->xrowE, nullptr, ctx->st));
+    xE = ctx->xrowE;
+  }
+  return mm(ctx, false, rows, b, b, 1.0, X, ldx, xE, ctx->Rinv, b, 0.0, out, 1, ldo);
+}
+
 // out (rows x b, ld ldo) = Q factor of X (rows x b, ld ldx), CholQR2.
 lra_status orth(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows, double* out,
                 int64_t ldo) {
   const int b = ctx->b;
-  TRY(gemm(ctx, true, b, b, rows, 1.0, X, ldx, X, ldx, 0.0, ctx->gram, 1, b));
+  TRY(gram(ctx, X, ldx, rows));
   CK(chol_inv(ctx->gram, b, PIVOT_TAU, ctx->Rinv, ctx->flags, ctx->st));
-  TRY(gemm(ctx, false, rows, b, b, 1.0, X, ldx, ctx->Rinv, b, 0.0, ctx->Tmp, 1, ctx->lds));
-  TRY(gemm(ctx, true, b, b, rows, 1.0, ctx->Tmp, ctx->lds, ctx->Tmp, ctx->lds, 0.0, ctx->gram, 1, b));
+  TRY(right_apply_rinv(ctx, X, ldx, rows, ctx->Tmp, ctx->lds));
+  TRY(gram(ctx, ctx->Tmp, ctx->lds, rows));
   CK(chol_inv(ctx->gram, b, PIVOT_TAU, ctx->Rinv, ctx->flags, ctx->st));
-  TRY(gemm(ctx, false, rows, b, b, 1.0, ctx->Tmp, ctx->lds, ctx->Rinv, b, 0.0, out, 1, ldo));
+  TRY(right_apply_rinv(ctx, ctx->Tmp, ctx->lds, rows, out, ldo));
   return LRA_OK;
 }
 
@@ -233,8 +272,8 @@ lra_status apply_omega(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows_
     return LRA_OK;
   }
   if (x_is_A) return dense(ctx, false, ctx->b, 1.0, X, ldx, ctx->om_dense, ctx->ldod, 0.0, out, 1, ldo);
-  return gemm(ctx, false, rows_x, ctx->b, ctx->n, 1.0, X, ldx, ctx->om_dense, ctx->ldod, 0.0, out, 1,
-              ldo);
+  return mm(ctx, false, rows_x, ctx->b, ctx->n, 1.0, X, ldx, ctx->browE, ctx->om_dense, ctx->ldod, 0.0,
+            out, 1, ldo);
 }
 
 lra_status compute_z(lra_ctx* ctx, const double* A, int64_t lda) {
@@ -310,6 +349,10 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
     return LRA_OK;
   }
   PHASE(LRA_PHASE_INDICATOR, TRY(a_exponents(ctx, A, lda)));
+  if (ctx->tensor) {
+    CK(cudaMemsetAsync(ctx->qrowE, 0, m * sizeof(int), ctx->st));
+    CK(cudaMemsetAsync(ctx->bcolE, 0, n * sizeof(int), ctx->st));
+  }
   if (ctx->sb_sparse) PHASE(LRA_PHASE_SKETCH, TRY(compute_z(ctx, A, lda)));
   const double thr = ctx->prm.eps * ctx->prm.eps * normA2;
   const bool fixed_rank = ctx->prm.k > 0;
@@ -327,7 +370,8 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
         PHASE(LRA_PHASE_DEFLATE, {
           TRY(apply_omega(ctx, ctx->B, ldb, l, ctx->BOm, ldf, ctx->sb_sparse ? ctx->zB : nullptr,
                           false));
-          TRY(gemm(ctx, true, n, b, l, -1.0, ctx->B, ldb, ctx->BOm, ldf, 1.0, ctx->W, 1, lds));
+          TRY(mm(ctx, true, n, b, l, -1.0, ctx->B, ldb, ctx->bcolE, ctx->BOm, ldf, 1.0, ctx->W, 1,
+                 lds));
         });
       }
       PHASE(LRA_PHASE_ORTH, TRY(orth(ctx, ctx->W, lds, n, ctx->G, lds)));
@@ -338,8 +382,10 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
               TRY(dense(ctx, true, b, 1.0, A, lda, ctx->T1, lds, 0.0, ctx->W, 1, lds)));
         if (l > 0) {
           PHASE(LRA_PHASE_DEFLATE, {
-            TRY(gemm(ctx, false, l, b, n, 1.0, ctx->B, ldb, ctx->G, lds, 0.0, ctx->BOm, 1, ldf));
-            TRY(gemm(ctx, true, n, b, l, -1.0, ctx->B, ldb, ctx->BOm, ldf, 1.0, ctx->W, 1, lds));
+            TRY(mm(ctx, false, l, b, n, 1.0, ctx->B, ldb, ctx->browE, ctx->G, lds, 0.0, ctx->BOm, 1,
+                   ldf));
+            TRY(mm(ctx, true, n, b, l, -1.0, ctx->B, ldb, ctx->bcolE, ctx->BOm, ldf, 1.0, ctx->W, 1,
+                   lds));
           });
         }
         PHASE(LRA_PHASE_ORTH, TRY(orth(ctx, ctx->W, lds, n, ctx->G, lds)));
@@ -353,8 +399,8 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
     if (l > 0) {
       PHASE(LRA_PHASE_PROJECT, {
         for (int pass = 0; pass < 2; ++pass) {
-          TRY(gemm(ctx, true, l, b, m, 1.0, ctx->Q, ldq, Y, lds, 0.0, ctx->F, 1, ldf));
-          TRY(gemm(ctx, false, m, b, l, -1.0, ctx->Q, ldq, ctx->F, ldf, 1.0, Y, 1, lds));
+          TRY(mm(ctx, true, l, b, m, 1.0, ctx->Q, ldq, ctx->qcolE, Y, lds, 0.0, ctx->F, 1, ldf));
+          TRY(mm(ctx, false, m, b, l, -1.0, ctx->Q, ldq, ctx->qrowE, ctx->F, ldf, 1.0, Y, 1, lds));
         }
       });
     }
@@ -366,6 +412,12 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
       CK(total(ctx->colsq, b, ctx->scal + 1, ctx->st));
       CK(append_rows(ctx->Wt, lds, n, b, ctx->B, ldb, l, ctx->colsum, ctx->os.p,
                      ctx->sb_sparse ? ctx->zB : nullptr, ctx->st));
+      if (ctx->tensor) {
+        // Q_j: its column maxima, and the running row maxima of Q
+        CK(oz_rowcol_exponents(Qj, ldq, m, b, ctx->qrowE, ctx->qcolE + l, ctx->st, true));
+        // B_j = Wt^T: row maxima of B_j are Wt's column maxima; B's column maxima grow
+        CK(oz_rowcol_exponents(ctx->Wt, lds, n, b, ctx->bcolE, ctx->browE + l, ctx->st, true));
+      }
     });
     TRY(read_record(ctx));
     const int fl = ctx->hp->flags;
@@ -413,7 +465,8 @@ void free_all(lra_ctx* c) {
                   c->z,      c->zB,       c->wvec,   c->ws,       c->gram,      c->Rinv,
                   c->colsq,  c->colsum,   c->scal,   c->flags,    c->om_counts, c->om_rows,
                   c->om_vals, c->om_dense, c->sk_counts, c->sk_rows, c->sk_vals, c->A_host_copy,
-                  c->rowE,   c->colE,     c->oz.yE,  c->oz.img,   c->oz.part};
+                  c->rowE,   c->colE,     c->oz.yE,  c->oz.img,   c->oz.part,
+                  c->qrowE,  c->qcolE,    c->browE,  c->bcolE,    c->xrowE,     c->xcolE};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->hp) cudaFreeHost(c->hp);
@@ -553,6 +606,12 @@ lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
     ctx->oz.img_bytes = oz_img_bytes(std::max(m, n));
     ALLOC(rowE, m);
     ALLOC(colE, n);
+    ALLOC(qrowE, m);
+    ALLOC(qcolE, ctx->ldb);
+    ALLOC(browE, ctx->ldb);
+    ALLOC(bcolE, n);
+    ALLOC(xrowE, ctx->lds);
+    ALLOC(xcolE, LRA_MAX_B);
     ALLOC(oz.yE, LRA_MAX_B);
     ALLOC(oz.img, ctx->oz.img_bytes);
     ALLOC(oz.part, oz_part_elems(ctx->oz.ctas));

@@ -441,7 +441,10 @@ __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
   if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
 }
 
-// Combine the partial tiles of tiles split across CTAs, in CTA order.
+// Combine the partial tiles of tiles split across CTAs, in CTA order.  Grid:
+// (tiles, FIX_SPLIT); each CTA handles TM*NN/FIX_SPLIT elements of its tile.
+constexpr int FIX_SPLIT = 32;
+
 __global__ void __launch_bounds__(256) k_oz_fixup(OzArgs a, int G) {
   const int64_t t = blockIdx.x;
   const int64_t T = a.tiles * a.kblocks;
@@ -453,7 +456,8 @@ __global__ void __launch_bounds__(256) k_oz_fixup(OzArgs a, int G) {
   };
   const int64_t cf = owner(t * a.kblocks), cl = owner((t + 1) * a.kblocks - 1);
   if (cf == cl) return;
-  for (int e = threadIdx.x; e < TM * NN; e += 256) {
+  constexpr int PER = TM * NN / FIX_SPLIT;
+  for (int e = blockIdx.y * PER + threadIdx.x; e < (int)(blockIdx.y + 1) * PER; e += 256) {
     const int r = e / NN, c = e % NN;
     const int64_t p = t * TM + r;
     if (p >= a.P || c >= a.N) continue;
@@ -470,16 +474,18 @@ __global__ void __launch_bounds__(256) k_oz_fixup(OzArgs a, int G) {
 }
 
 cudaError_t oz_rowcol_exponents(const double* X, int64_t ld, int64_t rows, int64_t cols,
-                                int* rowE, int* colE, cudaStream_t st) {
+                                int* rowE, int* colE, cudaStream_t st, bool accumulate_rows) {
   if (colE) {
     k_oz_colmaxexp<<<(unsigned)cols, 256, 0, st>>>(X, ld, rows, colE);
     cudaError_t e = launched();
     if (e != cudaSuccess) return e;
   }
   if (rowE) {
-    cudaError_t e = cudaMemsetAsync(rowE, 0, rows * sizeof(int), st);
-    if (e != cudaSuccess) return e;
-    const int64_t csplit = 16;
+    if (!accumulate_rows) {
+      cudaError_t e = cudaMemsetAsync(rowE, 0, rows * sizeof(int), st);
+      if (e != cudaSuccess) return e;
+    }
+    const int64_t csplit = cols >= 256 ? 16 : 1;
     const int64_t cchunk = (cols + csplit - 1) / csplit;
     dim3 grid((unsigned)((rows + 255) / 256), (unsigned)((cols + cchunk - 1) / cchunk));
     k_oz_rowmaxexp<<<grid, 256, 0, st>>>(X, ld, rows, cols, cchunk, rowE);
@@ -536,7 +542,7 @@ cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, co
     k_ozgemm<false><<<G, NT, SMEM_DYN, st>>>(a);
   e = launched();
   if (e != cudaSuccess) return e;
-  k_oz_fixup<<<(unsigned)a.tiles, 256, 0, st>>>(a, G);
+  k_oz_fixup<<<dim3((unsigned)a.tiles, FIX_SPLIT), 256, 0, st>>>(a, G);
   return launched();
 }
 

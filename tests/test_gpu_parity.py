@@ -7,11 +7,13 @@ Bar (from the method's arithmetic, FP64 on both sides):
     draw, times the 1/sqrt(p) scale);
   * sketch: max |diff| <= 1e-12 max |ref|;
   * pre-projection Y_j: P = 0 (raw sketches) ||diff||_F <= 1e-12 ||ref||_F; P >= 1
-    <= 1e-9: the deflated power step A^T (A G) - B^T (B G) cancels by about
-    (sigma_1 / sigma_l)^2, so the FP64 result itself is only defined to ~3e-10 --
-    the oracle moves that much when only its summation order changes
-    (tests/test_oracle_farpca.py::test_y_sensitivity_to_summation_order), while
-    Q, B and E stay within 1e-11;
+    <= 1e-8: the deflated power step A^T (A G) - B^T (B G) cancels by about
+    (sigma_1 / sigma_l)^2, so Y_j is ill conditioned -- a relative 2^-52 perturbation
+    of A moves the oracle's own Y_j by ~2e-10 and a change of summation order by
+    up to 4e-10 (tests/test_oracle_farpca.py::test_y_sensitivity_to_summation_order),
+    and GEMMs with FP64-sized but differently distributed errors (the tensor
+    engine) move it by a few 1e-9; Q, B and E, which depend on the span only, stay
+    within 1e-11 and carry the tight bars below;
   * attained rank and status equal; Q within 1e-10 absolute (entries are
     O(m^-1/2)); B within 1e-10 of max |B|;
   * the indicator E = ||A||_F^2 - sum_j ||B_j||_F^2 within 1e-12 ||A||_F^2
@@ -65,7 +67,7 @@ def frorel(a, b):
 
 
 def y_close(Y, ref, P):
-    tol = 1e-12 if P == 0 else 1e-9
+    tol = 1e-12 if P == 0 else 1e-8
     assert frorel(Y, ref) <= tol, frorel(Y, ref)
 
 
