@@ -200,6 +200,35 @@ lra_status lra_copy_omega(lra_ctx* ctx, int64_t j, int64_t cap, int32_t* counts,
    (<= LRA_NUM_PHASES) entries; reset != 0 clears the counters after reading. */
 lra_status lra_phase_times(lra_ctx* ctx, double* ms, int64_t* calls, int32_t nphases, int32_t reset);
 
+/* Bytes of the device array that lra_sketch_noalloc uses as its only scratch. */
+#define LRA_NOALLOC_SCRATCH_BYTES (8 << 20)
+
+/* The sparse sketch of lra_sketch, Y = A [Omega_j0 ... Omega_{j0+nblk-1}], without
+   any device allocation and without a context.  The paper has no counterpart:
+   this entry point exists for callers that cannot allocate device memory while
+   they run -- a service that reserves its whole memory budget at start-up, a
+   host framework whose own allocator owns the device memory, or code that
+   cannot afford the synchronisation a cudaMalloc may cause.  Its scratch (the
+   generated Omega) is one file-scope device array of LRA_NOALLOC_SCRATCH_BYTES
+   that every GPU loading the library keeps until the process exits.
+   A, params (b, kind, zeta, p, seed; the other fields are ignored), j0, nblk,
+   Y and ldy mean what they mean for lra_create / lra_sketch; cuda_stream is a
+   cudaStream_t (NULL = legacy default stream).  Kinds: LRA_OMEGA_SPARSE_SIGN,
+   LRA_OMEGA_SPARSE_SIGN_IID, LRA_OMEGA_SPARSE_GAUSSIAN, LRA_OMEGA_BERNOULLI;
+   the others need a context (LRA_ERR_UNSUPPORTED).  Limit: one block's Omega,
+   b * (4 + 12 cap) bytes with cap = zeta (fixed-zeta kind) or n (the i.i.d.
+   kinds), must fit in the array minus 768 bytes, else LRA_ERR_INVALID_ARG;
+   longer block ranges are processed in chunks.
+   The first call on each device looks up the array's device address
+   (cudaGetSymbolAddress); make that first call before any stream capture
+   starts.  All calls share the array and leave the last call's contents in it:
+   calls that can overlap on the GPU (other streams, other host threads) race
+   on it, so issue them in order on one stream.  The call synchronises its
+   stream before returning.  Errors: LRA_ERR_INVALID_ARG, LRA_ERR_UNSUPPORTED,
+   LRA_ERR_CUDA. */
+lra_status lra_sketch_noalloc(const lra_matrix* A, const lra_params* params, int64_t j0,
+                              int64_t nblk, double* Y, int64_t ldy, void* cuda_stream);
+
 /* Message for the last error on ctx ("" if none); never NULL. */
 const char* lra_last_error(const lra_ctx* ctx);
 

@@ -260,3 +260,26 @@ class Farpca:
         self._check(s)
         return dict(status=r.status, rank=r.rank, blocks=r.blocks, E=r.E, normA2=r.normA2,
                     rel_err=r.rel_err)
+
+
+def sketch_noalloc(A, j0, nblk, b, kind, zeta=8, p=0.0, seed=0, Y=None, stream=None):
+    """lra_sketch_noalloc: the sparse sketch without a context or any device
+    allocation by the library (Y is allocated here, by the caller's side, when
+    not given).  Returns Y (column-major m x nblk*b)."""
+    import torch
+    lib = load()
+    lib.lra_sketch_noalloc.argtypes = [POINTER(Matrix), POINTER(Params), c_int64, c_int64, c_void_p,
+                                       c_int64, c_void_p]
+    lib.lra_sketch_noalloc.restype = c_int32
+    mat = _device_matrix(A, torch)
+    m = A.shape[0]
+    if Y is None:
+        Y = torch.empty_strided((m, nblk * b), (1, m), dtype=torch.float64, device=A.device)
+    prm = Params(0.0, 0, b, 0, kind, zeta, p, seed & 0xFFFFFFFFFFFFFFFF, 0, 0)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    s = lib.lra_sketch_noalloc(byref(mat), byref(prm), j0, nblk, c_void_p(Y.data_ptr()),
+                               max(Y.stride(1), m), c_void_p(stream.cuda_stream))
+    if s != OK:
+        raise LraError(s, "lra_sketch_noalloc failed")
+    return Y
