@@ -26,13 +26,15 @@
 //   fp32) * 2^(e_p + f_c - 2058), written in FP64.  Against exact dot products
 //   the error is that of an FP64 GEMM (2^-52 of |op(X)| |Y| on Gaussian data).
 //
-// Work split: one CTA per SM walks a contiguous range of (row tile, k-block)
-// units ("stream-K"); tiles whose k-blocks span two or more CTAs are written as
-// partial sums and combined by a fixup kernel in a fixed order.
-// Per 64-deep k-block the CTA (256 threads) loads a 128 x 64 block of op(X)
-// from HBM, slices it into 8 shared-memory planes (128-byte swizzled, K-major),
-// copies the pre-sliced 64 x 64 block of Y, and one thread issues the MMAs of
-// each 32-deep window; four warps flush the window from TMEM.
+// Work split: one CTA per SM walks a contiguous range of (row tile, 32-deep
+// window) units ("stream-K"); tiles whose windows span two or more CTAs are
+// written as partial sums and combined by a fixup kernel in a fixed order.
+// Inside a CTA the work is pipelined by warp role: eight producer warps load
+// a 128 x 32 block of op(X) from HBM, slice it into 8 bf16 planes of a shared
+// memory stage (two stages, K-major core-matrix layout) and copy the pre-sliced
+// 64 x 32 block of Y; one thread issues the window's 72 MMAs; four warps flush
+// the exact sums from TMEM and write the tile.  mbarriers hand stages and the
+// TMEM accumulators between the roles; every wait is bounded.
 #include <math.h>
 
 #include "internal.cuh"
@@ -41,25 +43,36 @@
 namespace lra {
 
 namespace {
-constexpr int S = 8;              // slices per operand (7 bits each)
-constexpr int BETA = 7;           // bits per slice
-constexpr int TM = 128;           // rows of op(X) per tile
-constexpr int KBK = 64;           // K per k-block
-constexpr int NN = 64;            // output columns (N padded)
-constexpr int NT = 256;           // threads per CTA
-constexpr int A_PLANE = TM * 128; // bytes of one slice plane of the X block
-constexpr int Y_PLANE = NN * 128; // bytes of one slice plane of the Y block
-constexpr int SMEM_DYN = S * A_PLANE + S * Y_PLANE + 1024;
+constexpr int S = 8;               // slices per operand (7 bits each)
+constexpr int BETA = 7;            // bits per slice
+constexpr int TM = 128;            // rows of op(X) per tile
+constexpr int KW = 32;             // K per window (one pipeline stage)
+constexpr int NN = 64;             // output columns (N padded)
+constexpr int NPROD = 256;         // producer threads (warps 4..11)
+constexpr int NFLUSH = 128;        // flush threads (warps 0..3)
+constexpr int NT = NFLUSH + NPROD + 32;  // + one MMA warp (warp 12)
+constexpr int A_PLANE = TM * KW * 2;     // bytes of one slice plane of the op(X) block
+constexpr int Y_PLANE = NN * KW * 2;     // bytes of one slice plane of the Y block
+constexpr int STAGE = S * (A_PLANE + Y_PLANE);
+constexpr int NSTAGE = 2;
+constexpr int SMEM_DYN = NSTAGE * STAGE + 1024;
+constexpr uint32_t LBO = 128, SBO = 512;         // core-matrix strides (K, rows)
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t COL_G5 = 320;                  // FP32 sum of the pairs of weight >= 5
 constexpr uint32_t COL_ACC_LO = 384, COL_ACC_HI = 448;  // int64 exact sum, two words
 constexpr int EXACT_GROUPS = 5;                   // weights 0..4, TMEM columns 64 w
-constexpr long WAIT_TRIES = 1L << 24;
+constexpr long WAIT_TRIES = 1L << 22;
 constexpr int EXP_OFFSET = 2058;  // 2 * 1022 + 2 * BETA: see the scaling above
 }  // namespace
 
-int64_t oz_img_bytes(int64_t K) { return (K + KBK - 1) / KBK * S * Y_PLANE; }
+int64_t oz_img_bytes(int64_t K) { return (K + KW - 1) / KW * S * Y_PLANE; }
 int64_t oz_part_elems(int ctas) { return (int64_t)ctas * 2 * TM * NN; }
+
+// Offset of element (row, k), k < 32, in the K-major core-matrix layout of a
+// stage plane: core (row/8, k/8) at ((row/8)*4 + k/8)*128, row-major inside.
+__host__ __device__ __forceinline__ uint32_t core_offset(uint32_t row, uint32_t k) {
+  return (((row >> 3) << 2) + (k >> 3)) * 128u + (row & 7u) * 16u + (k & 7u) * 2u;
+}
 
 // |a| as a 56-bit fixed-point integer relative to 2^(emax - 1022) (emax = the
 // largest biased exponent of the row/column), and its sign.
@@ -128,34 +141,35 @@ __global__ void __launch_bounds__(256) k_oz_rowmaxexp(const double* __restrict__
   atomicMax(out + r, e);
 }
 
-// Pre-sliced Y: img[kb][s] is the 64 x 64 (N x K) bf16 block of slice s in the
-// swizzled K-major layout.  One thread per (k-block, column c, 8-wide k chunk).
+// Pre-sliced Y: img[w][s] is the 64 x 32 (N x K) bf16 block of slice s of
+// window w in the core-matrix layout.  One thread per (window, column c, 8-wide
+// k chunk j).
 __global__ void __launch_bounds__(256) k_oz_yslice(const double* __restrict__ Y, int64_t ldy,
                                                    int64_t K, int N, const int* __restrict__ yE,
-                                                   uint8_t* __restrict__ img, int64_t kblocks) {
+                                                   uint8_t* __restrict__ img, int64_t kwins) {
   const int64_t idx = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  if (idx >= kblocks * NN * 8) return;
-  const int j = (int)(idx & 7);
-  const int c = (int)((idx >> 3) & (NN - 1));
-  const int64_t kb = idx >> 9;
+  if (idx >= kwins * NN * 4) return;
+  const int j = (int)(idx & 3);
+  const int c = (int)((idx >> 2) & (NN - 1));
+  const int64_t w = idx >> 8;
   const int emax = c < N ? yE[c] : 0;
   uint64_t x[8];
   uint32_t sg[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const int64_t k = kb * KBK + 8 * j + i;
+    const int64_t k = w * KW + 8 * j + i;
     const double v = (c < N && k < K) ? __ldg(Y + k + (int64_t)c * ldy) : 0.0;
     x[i] = fixed56(v, emax, sg[i]);
   }
-  uint8_t* base = img + (kb * S) * Y_PLANE + tc::sw128_offset((uint32_t)c, (uint32_t)(8 * j));
+  uint8_t* base = img + (w * S) * Y_PLANE + core_offset((uint32_t)c, (uint32_t)(8 * j));
 #define LRA_YS(SL)                                                                          \
   {                                                                                         \
-    uint4 w;                                                                                \
-    w.x = pack2<SL>(x[0], sg[0], x[1], sg[1]);                                              \
-    w.y = pack2<SL>(x[2], sg[2], x[3], sg[3]);                                              \
-    w.z = pack2<SL>(x[4], sg[4], x[5], sg[5]);                                              \
-    w.w = pack2<SL>(x[6], sg[6], x[7], sg[7]);                                              \
-    *reinterpret_cast<uint4*>(base + (SL)*Y_PLANE) = w;                                     \
+    uint4 q;                                                                                \
+    q.x = pack2<SL>(x[0], sg[0], x[1], sg[1]);                                              \
+    q.y = pack2<SL>(x[2], sg[2], x[3], sg[3]);                                              \
+    q.z = pack2<SL>(x[4], sg[4], x[5], sg[5]);                                              \
+    q.w = pack2<SL>(x[6], sg[6], x[7], sg[7]);                                              \
+    *reinterpret_cast<uint4*>(base + (SL)*Y_PLANE) = q;                                     \
   }
   LRA_YS(0) LRA_YS(1) LRA_YS(2) LRA_YS(3) LRA_YS(4) LRA_YS(5) LRA_YS(6) LRA_YS(7)
 #undef LRA_YS
@@ -174,82 +188,79 @@ struct OzArgs {
   double* C;
   int64_t csp, csc;
   double* part;        // [cta][2][TM][NN] partial tiles
-  int64_t tiles, kblocks;
+  int64_t tiles, kwins;
   int* flags;
   bool vec;            // 16-byte loads allowed (trans layout)
 };
 
+// Producer: slice the 128 x 32 block (tile, window w) of op(X) into the eight
+// planes of a stage.  pt = producer thread 0..255.
 template <bool TRANS>
-__device__ __forceinline__ void slice_block(const OzArgs& a, int64_t tile, int64_t kb,
-                                            uint8_t* sA, const int* sE) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t p0 = tile * TM;
+__device__ __forceinline__ void slice_window(const OzArgs& a, int64_t tile, int64_t w,
+                                             uint8_t* sA, const int* sE, int pt) {
+  const int lane = pt & 31, pw = pt >> 5;
+  const int64_t p0 = tile * TM, k0 = w * KW;
   if (TRANS) {
-    // op(X)[p, k] = X[k + p*ldx]: lanes along k (pairs), warps along p.
-    const int64_t k = kb * KBK + 2 * lane;
-#pragma unroll 1
-    for (int half = 0; half < 2; ++half) {
-      double v0[8], v1[8];
+    // op(X)[p, k] = X[k + p*ldx]: each warp instruction covers one core matrix
+    // (8 rows x 8 k): lane -> row r8 = lane & 7, k pair q = lane >> 3.
+    const int r8 = lane & 7, q = lane >> 3;
+    double v0[8], v1[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int pl = warp + 8 * (i + 8 * half);
-        const int64_t p = p0 + pl;
-        v0[i] = 0.0;
-        v1[i] = 0.0;
-        if (p < a.P) {
-          const double* src = a.X + k + p * a.ldx;
-          if (a.vec && k + 1 < a.K) {
-            const double2 t = __ldg(reinterpret_cast<const double2*>(src));
-            v0[i] = t.x;
-            v1[i] = t.y;
-          } else {
-            if (k < a.K) v0[i] = __ldg(src);
-            if (k + 1 < a.K) v1[i] = __ldg(src + 1);
-          }
+    for (int i = 0; i < 8; ++i) {
+      const int core = pw + 8 * i, rg = core >> 2, kc = core & 3;
+      const int64_t p = p0 + rg * 8 + r8, k = k0 + kc * 8 + 2 * q;
+      v0[i] = 0.0;
+      v1[i] = 0.0;
+      if (p < a.P) {
+        const double* src = a.X + k + p * a.ldx;
+        if (a.vec && k + 1 < a.K) {
+          const double2 t = __ldg(reinterpret_cast<const double2*>(src));
+          v0[i] = t.x;
+          v1[i] = t.y;
+        } else {
+          if (k < a.K) v0[i] = __ldg(src);
+          if (k + 1 < a.K) v1[i] = __ldg(src + 1);
         }
       }
+    }
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int pl = warp + 8 * (i + 8 * half);
-        const int emax = sE[pl];
-        uint32_t s0, s1;
-        const uint64_t x0 = fixed56(v0[i], emax, s0), x1 = fixed56(v1[i], emax, s1);
-        uint8_t* dst = sA + tc::sw128_offset((uint32_t)pl, (uint32_t)(2 * lane));
-        *reinterpret_cast<uint32_t*>(dst + 0 * A_PLANE) = pack2<0>(x0, s0, x1, s1);
-        *reinterpret_cast<uint32_t*>(dst + 1 * A_PLANE) = pack2<1>(x0, s0, x1, s1);
-        *reinterpret_cast<uint32_t*>(dst + 2 * A_PLANE) = pack2<2>(x0, s0, x1, s1);
-        *reinterpret_cast<uint32_t*>(dst + 3 * A_PLANE) = pack2<3>(x0, s0, x1, s1);
-        *reinterpret_cast<uint32_t*>(dst + 4 * A_PLANE) = pack2<4>(x0, s0, x1, s1);
-        *reinterpret_cast<uint32_t*>(dst + 5 * A_PLANE) = pack2<5>(x0, s0, x1, s1);
-        *reinterpret_cast<uint32_t*>(dst + 6 * A_PLANE) = pack2<6>(x0, s0, x1, s1);
-        *reinterpret_cast<uint32_t*>(dst + 7 * A_PLANE) = pack2<7>(x0, s0, x1, s1);
-      }
+    for (int i = 0; i < 8; ++i) {
+      const int core = pw + 8 * i, rg = core >> 2, kc = core & 3;
+      const int row = rg * 8 + r8;
+      const int emax = sE[row];
+      uint32_t s0, s1;
+      const uint64_t x0 = fixed56(v0[i], emax, s0), x1 = fixed56(v1[i], emax, s1);
+      uint8_t* dst = sA + core * 128 + r8 * 16 + q * 4;
+#define LRA_XT(SL) *reinterpret_cast<uint32_t*>(dst + (SL)*A_PLANE) = pack2<SL>(x0, s0, x1, s1);
+      LRA_XT(0) LRA_XT(1) LRA_XT(2) LRA_XT(3) LRA_XT(4) LRA_XT(5) LRA_XT(6) LRA_XT(7)
+#undef LRA_XT
+      (void)kc;
     }
   } else {
-    // op(X)[p, k] = X[p + k*ldx]: lanes along p, each warp one 8-wide k chunk.
-    const int64_t k0 = kb * KBK + 8 * warp;
+    // op(X)[p, k] = X[p + k*ldx]: lanes along rows, each thread 8 consecutive k.
+    const int rgrp = pw & 3, kc0 = (pw >> 2) * 2;
 #pragma unroll 1
-    for (int h = 0; h < 4; ++h) {
-      const int pl = lane + 32 * h;
-      const int64_t p = p0 + pl;
+    for (int h = 0; h < 2; ++h) {
+      const int row = rgrp * 32 + lane, kc = kc0 + h;
+      const int64_t p = p0 + row, kb = k0 + kc * 8;
       double v[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i)
-        v[i] = (p < a.P && k0 + i < a.K) ? __ldg(a.X + p + (k0 + i) * a.ldx) : 0.0;
-      const int emax = sE[pl];
+        v[i] = (p < a.P && kb + i < a.K) ? __ldg(a.X + p + (kb + i) * a.ldx) : 0.0;
+      const int emax = sE[row];
       uint64_t x[8];
       uint32_t sg[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) x[i] = fixed56(v[i], emax, sg[i]);
-      uint8_t* dst = sA + tc::sw128_offset((uint32_t)pl, (uint32_t)(8 * warp));
+      uint8_t* dst = sA + core_offset((uint32_t)row, (uint32_t)(kc * 8));
 #define LRA_XS(SL)                                                \
   {                                                               \
-    uint4 w;                                                      \
-    w.x = pack2<SL>(x[0], sg[0], x[1], sg[1]);                    \
-    w.y = pack2<SL>(x[2], sg[2], x[3], sg[3]);                    \
-    w.z = pack2<SL>(x[4], sg[4], x[5], sg[5]);                    \
-    w.w = pack2<SL>(x[6], sg[6], x[7], sg[7]);                    \
-    *reinterpret_cast<uint4*>(dst + (SL)*A_PLANE) = w;            \
+    uint4 q;                                                      \
+    q.x = pack2<SL>(x[0], sg[0], x[1], sg[1]);                    \
+    q.y = pack2<SL>(x[2], sg[2], x[3], sg[3]);                    \
+    q.z = pack2<SL>(x[4], sg[4], x[5], sg[5]);                    \
+    q.w = pack2<SL>(x[6], sg[6], x[7], sg[7]);                    \
+    *reinterpret_cast<uint4*>(dst + (SL)*A_PLANE) = q;            \
   }
       LRA_XS(0) LRA_XS(1) LRA_XS(2) LRA_XS(3) LRA_XS(4) LRA_XS(5) LRA_XS(6) LRA_XS(7)
 #undef LRA_XS
@@ -275,28 +286,41 @@ __device__ __forceinline__ int exact_int(uint32_t bits, float scale) {
   return __float_as_int(__fmaf_rn(__uint_as_float(bits), scale, 12582912.0f)) - 0x4B400000;
 }
 
+// The CTA's windows: a contiguous range [u0, u1) of (tile, window) units, tile-major.
+struct Walk {
+  int64_t u0, u1, kwins;
+  __device__ __forceinline__ int64_t tile(int64_t u) const { return u / kwins; }
+  __device__ __forceinline__ bool seg_first(int64_t u) const { return u == u0 || u % kwins == 0; }
+  __device__ __forceinline__ bool seg_last(int64_t u) const {
+    return u + 1 == u1 || (u + 1) % kwins == 0;
+  }
+};
+
 template <bool TRANS>
 __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t s_bar;
-  __shared__ int sE[TM];
+  __shared__ __align__(8) uint64_t bar_full[NSTAGE], bar_empty[NSTAGE], bar_accfull, bar_accempty;
+  __shared__ int sEp[TM];  // producers: row exponents of the current tile
   __shared__ int syE[NN];
-  __shared__ int s_abort;
+  __shared__ volatile int s_abort;
   const uint32_t raw = tc::smem_addr(smem_raw);
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-  uint8_t* sA = sm;
-  uint8_t* sY = sm + S * A_PLANE;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t T = a.tiles * a.kblocks;
+  const int64_t T = a.tiles * a.kwins;
   const int64_t G = gridDim.x, cta = blockIdx.x;
-  const int64_t u0 = cta * T / G, u1 = (cta + 1) * T / G;
-  if (u0 >= u1) return;
+  const Walk wk{cta * T / G, (cta + 1) * T / G, a.kwins};
+  if (wk.u0 >= wk.u1) return;
 
   if (warp == 0) tc::tmem_alloc(&s_tmem, TMEM_COLS);
   if (tid == 0) {
-    tc::mbar_init(&s_bar, 1);
+    for (int s = 0; s < NSTAGE; ++s) {
+      tc::mbar_init(&bar_full[s], NPROD);
+      tc::mbar_init(&bar_empty[s], 1);
+    }
+    tc::mbar_init(&bar_accfull, 1);
+    tc::mbar_init(&bar_accempty, NFLUSH);
     s_abort = 0;
   }
   if (tid < NN) syE[tid] = tid < a.N ? a.yE[tid] : 0;
@@ -304,140 +328,167 @@ __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = s_tmem;
-  const uint32_t idesc = tc::idesc_bf16_f32(TM, NN);
-  const int64_t first_tile = u0 / a.kblocks;
-  uint32_t phase = 0;
+  const int64_t first_tile = wk.tile(wk.u0);
 
-  for (int64_t u = u0; u < u1;) {
-    const int64_t tile = u / a.kblocks;
-    const int64_t kb0 = u % a.kblocks;
-    const int64_t kb1 = (a.kblocks < kb0 + (u1 - u)) ? a.kblocks : kb0 + (u1 - u);
-    const bool full = (kb0 == 0 && kb1 == a.kblocks);
-    if (tid < TM) {
-      const int64_t p = tile * TM + tid;
-      sE[tid] = p < a.P ? a.xE[p] : 0;
-    }
-    __syncthreads();
-    for (int64_t kb = kb0; kb < kb1; ++kb) {
-      // stage the pre-sliced Y block (async) and slice the X block
-      const uint8_t* ysrc = a.img + kb * (int64_t)(S * Y_PLANE);
-      for (int q = tid; q < S * Y_PLANE / 16; q += NT) tc::cp_async16(sY + 16 * q, ysrc + 16 * q);
-      slice_block<TRANS>(a, tile, kb, sA, sE);
+  if (warp >= 4 && warp < 12) {
+    // ---------------------------------------------------------- producers
+    const int pt = tid - NFLUSH;
+    uint32_t ph_empty[NSTAGE] = {0, 0};
+    int64_t cur_tile = -1;
+    for (int64_t u = wk.u0, i = 0; u < wk.u1; ++u, ++i) {
+      const int st = (int)(i & 1);
+      // one thread waits for the stage; the named barrier makes the decision uniform
+      if (i >= NSTAGE) {
+        if (pt == 0 && !tc::mbar_wait(&bar_empty[st], ph_empty[st], WAIT_TRIES)) s_abort = 1;
+        ph_empty[st] ^= 1u;
+      }
+      tc::named_sync(1, NPROD);
+      if (s_abort) break;
+      const int64_t tile = wk.tile(u);
+      if (tile != cur_tile) {
+        tc::named_sync(1, NPROD);
+        if (pt < TM) {
+          const int64_t p = tile * TM + pt;
+          sEp[pt] = p < a.P ? a.xE[p] : 0;
+        }
+        tc::named_sync(1, NPROD);
+        cur_tile = tile;
+      }
+      uint8_t* sA = sm + st * STAGE;
+      uint8_t* sY = sA + S * A_PLANE;
+      const uint8_t* ysrc = a.img + (u % a.kwins) * (int64_t)(S * Y_PLANE);
+      for (int q = pt; q < S * Y_PLANE / 16; q += NPROD) tc::cp_async16(sY + 16 * q, ysrc + 16 * q);
+      slice_window<TRANS>(a, tile, u % a.kwins, sA, sEp, pt);
       tc::cp_async_wait_all();
       tc::fence_async_smem();
-      tc::fence_before_sync();
-      __syncthreads();
-      tc::fence_after_sync();
-#pragma unroll 1
-      for (int win = 0; win < 2; ++win) {
-        const bool fresh = (kb == kb0 && win == 0);
-        if (tid == 0) {
-          const uint32_t a0 = tc::smem_addr(sA), y0 = tc::smem_addr(sY);
-#pragma unroll 1
-          for (int sa = 0; sa < S; ++sa)
-#pragma unroll 1
-            for (int sy = 0; sy < S - sa; ++sy) {
-              const int w = sa + sy;
-              const uint32_t col = w < EXACT_GROUPS ? 64u * w : COL_G5;
-              // exact groups restart every window; the weight >= 5 sum once per tile range
-              const bool first = (sa == 0) && (w < EXACT_GROUPS || (w == EXACT_GROUPS && fresh));
-#pragma unroll
-              for (int k2 = 0; k2 < 2; ++k2) {
-                const int kk = 2 * win + k2;
-                tc::mma_bf16(tmem + col, tc::desc_k_sw128(a0 + sa * A_PLANE + 32 * kk),
-                             tc::desc_k_sw128(y0 + sy * Y_PLANE + 32 * kk), idesc,
-                             (first && k2 == 0) ? 0u : 1u);
-              }
-            }
-          tc::mma_commit(&s_bar);
-        }
-        const bool ok = tc::mbar_wait(&s_bar, phase, WAIT_TRIES);
-        phase ^= 1u;
-        if (!ok) s_abort = 1;
-        tc::fence_after_sync();
-        if (ok && warp < 4) {
-          // flush: acc += sum_w n_w 2^(7 (4 - w)), 16 columns at a time
-          const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-#pragma unroll 1
-          for (int c0 = 0; c0 < NN; c0 += 16) {
-            uint32_t g0[16], g1[16], g2[16], g3[16], g4[16], lo[16], hi[16];
-            tc::tmem_ld16(trow + 0u + c0, g0);
-            tc::tmem_ld16(trow + 64u + c0, g1);
-            tc::tmem_ld16(trow + 128u + c0, g2);
-            tc::tmem_ld16(trow + 192u + c0, g3);
-            tc::tmem_ld16(trow + 256u + c0, g4);
-            if (!fresh) {
-              tc::tmem_ld16(trow + COL_ACC_LO + c0, lo);
-              tc::tmem_ld16(trow + COL_ACC_HI + c0, hi);
-            }
-            tc::tmem_ld_wait();
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const int n0 = exact_int(g0[i], 1.0f);
-              const int n1 = exact_int(g1[i], 0x1p7f);
-              const int n2 = exact_int(g2[i], 0x1p14f);
-              const int n3 = exact_int(g3[i], 0x1p21f);
-              const int n4 = exact_int(g4[i], 0x1p28f);
-              const int64_t add = ((int64_t)n0 << 28) + ((int64_t)(n1 * 128 + n2) << 14) +
-                                  (int64_t)(n3 * 128 + n4);
-              int64_t acc = fresh ? 0 : (int64_t)(((uint64_t)hi[i] << 32) | (uint64_t)lo[i]);
-              acc += add;
-              lo[i] = (uint32_t)((uint64_t)acc & 0xFFFFFFFFull);
-              hi[i] = (uint32_t)((uint64_t)acc >> 32);
-            }
-            tmem_st16(trow + COL_ACC_LO + c0, lo);
-            tmem_st16(trow + COL_ACC_HI + c0, hi);
-          }
-          tmem_st_wait();
-        }
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (s_abort) break;
-      }
-      if (s_abort) break;
+      tc::mbar_arrive(&bar_full[st]);
     }
-    if (s_abort) break;
-    if (warp < 4) {
-      const int pl = 32 * warp + lane;
-      const int64_t p = tile * TM + pl;
-      const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-      const int ep = sE[pl];
-      const int slot = (tile == first_tile) ? 0 : 1;
-      double* wrow = a.part + ((cta * 2 + slot) * TM + pl) * NN;
+  } else if (warp == 12) {
+    // ---------------------------------------------------------- MMA issuer
+    uint32_t ph_full[NSTAGE] = {0, 0}, ph_accempty = 0;
+    const uint32_t idesc = tc::idesc_bf16_f32(TM, NN);
+    for (int64_t u = wk.u0, i = 0; u < wk.u1; ++u, ++i) {
+      const int st = (int)(i & 1);
+      bool ok = true;
+      if (lane == 0) {
+        ok = tc::mbar_wait(&bar_full[st], ph_full[st], WAIT_TRIES);
+        if (ok && i > 0) ok = tc::mbar_wait(&bar_accempty, ph_accempty, WAIT_TRIES);
+      }
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      ph_full[st] ^= 1u;
+      if (i > 0) ph_accempty ^= 1u;
+      if (!ok) s_abort = 1;
+      if (s_abort) break;
+      tc::fence_after_sync();
+      if (lane == 0) {
+        const bool fresh = wk.seg_first(u);
+        const uint32_t a0 = tc::smem_addr(sm + st * STAGE);
+        const uint32_t y0 = a0 + S * A_PLANE;
+#pragma unroll 1
+        for (int sa = 0; sa < S; ++sa)
+#pragma unroll 1
+          for (int sy = 0; sy < S - sa; ++sy) {
+            const int w = sa + sy;
+            const uint32_t col = w < EXACT_GROUPS ? 64u * w : COL_G5;
+            // exact groups restart every window; the weight >= 5 sum once per segment
+            const bool first = (sa == 0) && (w < EXACT_GROUPS || (w == EXACT_GROUPS && fresh));
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk)
+              tc::mma_bf16(tmem + col, tc::desc_k_none(a0 + sa * A_PLANE + 256 * kk, LBO, SBO),
+                           tc::desc_k_none(y0 + sy * Y_PLANE + 256 * kk, LBO, SBO), idesc,
+                           (first && kk == 0) ? 0u : 1u);
+          }
+        tc::mma_commit(&bar_empty[st]);
+        tc::mma_commit(&bar_accfull);
+      }
+      __syncwarp();
+    }
+  } else if (warp < 4) {
+    // ---------------------------------------------------------- flush + epilogue
+    uint32_t ph_accfull = 0;
+    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    for (int64_t u = wk.u0; u < wk.u1; ++u) {
+      // lane 0 waits; the warp follows its decision (tcgen05.ld is warp-collective)
+      bool ok = true;
+      if (lane == 0) ok = tc::mbar_wait(&bar_accfull, ph_accfull, WAIT_TRIES);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      ph_accfull ^= 1u;
+      if (!ok) s_abort = 1;
+      if (!ok) break;
+      tc::fence_after_sync();
+      const bool fresh = wk.seg_first(u);
 #pragma unroll 1
       for (int c0 = 0; c0 < NN; c0 += 16) {
-        uint32_t lo[16], hi[16], g5[16];
-        tc::tmem_ld16(trow + COL_ACC_LO + c0, lo);
-        tc::tmem_ld16(trow + COL_ACC_HI + c0, hi);
-        tc::tmem_ld16(trow + COL_G5 + c0, g5);
+        uint32_t g0[16], g1[16], g2[16], g3[16], g4[16], lo[16], hi[16];
+        tc::tmem_ld16(trow + 0u + c0, g0);
+        tc::tmem_ld16(trow + 64u + c0, g1);
+        tc::tmem_ld16(trow + 128u + c0, g2);
+        tc::tmem_ld16(trow + 192u + c0, g3);
+        tc::tmem_ld16(trow + 256u + c0, g4);
+        if (!fresh) {
+          tc::tmem_ld16(trow + COL_ACC_LO + c0, lo);
+          tc::tmem_ld16(trow + COL_ACC_HI + c0, hi);
+        }
         tc::tmem_ld_wait();
-        if (p < a.P) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int c = c0 + i;
-            if (c < a.N) {
-              const int64_t acc = (int64_t)(((uint64_t)hi[i] << 32) | (uint64_t)lo[i]);
-              const double sum = fma(__ll2double_rn(acc), 0x1p-28, (double)__uint_as_float(g5[i]));
-              const double v = ldexp(sum, ep + syE[c] - EXP_OFFSET);
-              if (full) {
-                double* dst = a.C + p * a.csp + (int64_t)c * a.csc;
-                *dst = (a.beta == 0.0) ? a.alpha * v : a.alpha * v + a.beta * (*dst);
-              } else {
-                wrow[c] = v;
+        for (int i = 0; i < 16; ++i) {
+          const int n0 = exact_int(g0[i], 1.0f);
+          const int n1 = exact_int(g1[i], 0x1p7f);
+          const int n2 = exact_int(g2[i], 0x1p14f);
+          const int n3 = exact_int(g3[i], 0x1p21f);
+          const int n4 = exact_int(g4[i], 0x1p28f);
+          const int64_t add = ((int64_t)n0 << 28) + ((int64_t)(n1 * 128 + n2) << 14) +
+                              (int64_t)(n3 * 128 + n4);
+          int64_t acc = fresh ? 0 : (int64_t)(((uint64_t)hi[i] << 32) | (uint64_t)lo[i]);
+          acc += add;
+          lo[i] = (uint32_t)((uint64_t)acc & 0xFFFFFFFFull);
+          hi[i] = (uint32_t)((uint64_t)acc >> 32);
+        }
+        tmem_st16(trow + COL_ACC_LO + c0, lo);
+        tmem_st16(trow + COL_ACC_HI + c0, hi);
+      }
+      tmem_st_wait();
+      if (wk.seg_last(u)) {
+        const int64_t tile = wk.tile(u);
+        const bool full = (u - (a.kwins - 1) == tile * a.kwins) && (u - (a.kwins - 1) >= wk.u0);
+        const int pl = 32 * warp + lane;
+        const int64_t p = tile * TM + pl;
+        const int ep = p < a.P ? a.xE[p] : 0;
+        const int slot = (tile == first_tile) ? 0 : 1;
+        double* wrow = a.part + ((cta * 2 + slot) * TM + pl) * NN;
+#pragma unroll 1
+        for (int c0 = 0; c0 < NN; c0 += 16) {
+          uint32_t lo[16], hi[16], g5[16];
+          tc::tmem_ld16(trow + COL_ACC_LO + c0, lo);
+          tc::tmem_ld16(trow + COL_ACC_HI + c0, hi);
+          tc::tmem_ld16(trow + COL_G5 + c0, g5);
+          tc::tmem_ld_wait();
+          if (p < a.P) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int c = c0 + i;
+              if (c < a.N) {
+                const int64_t acc = (int64_t)(((uint64_t)hi[i] << 32) | (uint64_t)lo[i]);
+                const double sum = fma(__ll2double_rn(acc), 0x1p-28, (double)__uint_as_float(g5[i]));
+                const double v = ldexp(sum, ep + syE[c] - EXP_OFFSET);
+                if (full) {
+                  double* dst = a.C + p * a.csp + (int64_t)c * a.csc;
+                  *dst = (a.beta == 0.0) ? a.alpha * v : a.alpha * v + a.beta * (*dst);
+                } else {
+                  wrow[c] = v;
+                }
               }
             }
           }
         }
       }
+      tc::fence_before_sync();
+      tc::mbar_arrive(&bar_accempty);
     }
-    tc::fence_before_sync();
-    __syncthreads();
-    u += kb1 - kb0;
   }
-  if (s_abort && tid == 0) atomicOr(a.flags, FLAG_TIMEOUT);
   tc::fence_before_sync();
   __syncthreads();
+  if (s_abort && tid == 0) atomicOr(a.flags, FLAG_TIMEOUT);
   if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
 }
 
@@ -447,14 +498,14 @@ constexpr int FIX_SPLIT = 32;
 
 __global__ void __launch_bounds__(256) k_oz_fixup(OzArgs a, int G) {
   const int64_t t = blockIdx.x;
-  const int64_t T = a.tiles * a.kblocks;
+  const int64_t T = a.tiles * a.kwins;
   auto owner = [&](int64_t u) {
     int64_t c = u * G / T;
     while (c + 1 < G && (c + 1) * T / G <= u) ++c;
     while (c > 0 && c * T / G > u) --c;
     return c;
   };
-  const int64_t cf = owner(t * a.kblocks), cl = owner((t + 1) * a.kblocks - 1);
+  const int64_t cf = owner(t * a.kwins), cl = owner((t + 1) * a.kwins - 1);
   if (cf == cl) return;
   constexpr int PER = TM * NN / FIX_SPLIT;
   for (int e = blockIdx.y * PER + threadIdx.x; e < (int)(blockIdx.y + 1) * PER; e += 256) {
@@ -465,7 +516,7 @@ __global__ void __launch_bounds__(256) k_oz_fixup(OzArgs a, int G) {
     for (int64_t q = cf; q <= cl; ++q) {
       const int64_t q0 = q * T / G, q1 = (q + 1) * T / G;
       if (q0 >= q1) continue;  // a CTA with an empty range wrote nothing
-      const int slot = (t == q0 / a.kblocks) ? 0 : 1;
+      const int slot = (t == q0 / a.kwins) ? 0 : 1;
       s += a.part[((q * 2 + slot) * TM + r) * NN + c];
     }
     double* dst = a.C + p * a.csp + (int64_t)c * a.csc;
@@ -499,7 +550,7 @@ cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, co
                    const OzWorkspace& w, int* flags, cudaStream_t st) {
   if (P <= 0 || N <= 0) return cudaSuccess;
   if (N > NN || K <= 0) return cudaErrorInvalidValue;
-  const int64_t kblocks = (K + KBK - 1) / KBK;
+  const int64_t kwins = (K + KW - 1) / KW;
   if (oz_img_bytes(K) > w.img_bytes) return cudaErrorInvalidValue;
   static bool attr_set[2] = {false, false};
   if (!attr_set[trans ? 1 : 0]) {
@@ -511,9 +562,9 @@ cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, co
   k_oz_colmaxexp<<<(unsigned)N, 256, 0, st>>>(Y, ldy, K, w.yE);
   cudaError_t e = launched();
   if (e != cudaSuccess) return e;
-  const int64_t ythreads = kblocks * NN * 8;
+  const int64_t ythreads = kwins * NN * 4;
   k_oz_yslice<<<(unsigned)((ythreads + 255) / 256), 256, 0, st>>>(Y, ldy, K, (int)N, w.yE, w.img,
-                                                                  kblocks);
+                                                                  kwins);
   e = launched();
   if (e != cudaSuccess) return e;
   OzArgs a;
@@ -532,7 +583,7 @@ cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, co
   a.csc = out.csc;
   a.part = w.part;
   a.tiles = (P + TM - 1) / TM;
-  a.kblocks = kblocks;
+  a.kwins = kwins;
   a.flags = flags;
   a.vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (ldx % 2 == 0);
   const int G = w.ctas;

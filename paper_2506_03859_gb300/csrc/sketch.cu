@@ -78,46 +78,36 @@ __global__ void __launch_bounds__(256)
 // largest exponent among a row's terms (at most 16 terms: 5 bits of headroom),
 // converted back to FP64 with round-to-nearest-even by integer operations, and
 // multiplied by v once: one FP64 operation per output instead of zeta.
-constexpr int PM_MAX_TERMS = 16;
-
-__device__ __forceinline__ int exp_of(double a) {
-  return (int)(((uint64_t)__double_as_longlong(a) >> 52) & 0x7FFu);
-}
-
-// |a| significand shifted to the common scale 2^(emax - 1080) (exact unless the
-// term is more than 5 binades below the largest, then truncated below 2^-58 of it).
-__device__ __forceinline__ int64_t fixed_term(double a, int emax) {
-  const uint64_t b = (uint64_t)__double_as_longlong(a);
-  const int E = (int)((b >> 52) & 0x7FFu);
-  const uint64_t M = (E != 0) ? ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : 0ull;
-  const int d = emax - E;
-  const uint64_t T = d < 64 ? ((M << 5) >> d) : 0ull;
-  return (b >> 63) ? -(int64_t)T : (int64_t)T;
-}
-
-// S * 2^(emax - 1080) as an FP64 value, rounded to nearest even (integer ops).
-__device__ __forceinline__ double fixed_to_double(int64_t S, int emax) {
-  if (S == 0) return 0.0;
-  const uint64_t sign = S < 0 ? (1ull << 63) : 0ull;
-  uint64_t mag = S < 0 ? (uint64_t)(-S) : (uint64_t)S;
-  int nbits = 64 - __clzll((long long)mag);
-  uint64_t mant;
-  if (nbits <= 53) {
-    mant = mag << (53 - nbits);
+// The 53-bit significand M of a double (hi word h, lo word l), shifted to
+// M * 2^(5 - d) for d = emax - E, as the 64-bit word (th:tl); d + 6 >= 64 (or a
+// zero / subnormal input, which is given d = 127) yields 0.  Exact unless the
+// term is more than 5 binades below the largest, then truncated below 2^-58 of it.
+__device__ __forceinline__ void fixed_term32(uint32_t h, uint32_t l, int emax, uint32_t& th,
+                                             uint32_t& tl) {
+  const int E = (int)((h << 1) >> 21);
+  const int k = (E != 0 ? emax - E : 127) + 6;     // right shift of M << 11
+  const uint32_t mh = (h & 0x000FFFFFu) | 0x00100000u;
+  const uint32_t vh = __funnelshift_l(l, mh, 11);  // (M << 11) is a 64-bit word
+  const uint32_t vl = l << 11;
+  if (k < 32) {
+    tl = __funnelshift_r(vl, vh, k);
+    th = vh >> k;
   } else {
-    const int sh = nbits - 53;
-    mant = mag >> sh;
-    const uint64_t rem = mag & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-    if (rem > half || (rem == half && (mant & 1ull))) ++mant;
-    if (mant == (1ull << 53)) {
-      mant >>= 1;
-      ++nbits;
-    }
+    tl = k < 64 ? (vh >> (k - 32)) : 0u;
+    th = 0u;
   }
-  const int eb = nbits + emax - 58;  // biased exponent of the result
-  if (eb <= 0) return __longlong_as_double((long long)sign);             // below the normal range
-  if (eb >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
-  return __longlong_as_double((long long)(sign | ((uint64_t)eb << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+// S * 2^(emax - 1080) * v: one int64 -> FP64 conversion and one multiply; the
+// power of two goes into v's exponent field when that stays in the normal range.
+__device__ __forceinline__ double pm_finish(int64_t S, int emax, double v) {
+  if (emax == 2047) return __longlong_as_double(0x7FF8000000000000ll);  // Inf / NaN input
+  if (emax == 0 || S == 0) return 0.0;
+  const int64_t vb = __double_as_longlong(v);
+  const int eb = (int)((vb >> 52) & 0x7FF) + emax - 1080;
+  const double scale = (eb > 0 && eb < 2047) ? __longlong_as_double(vb + ((int64_t)(emax - 1080) << 52))
+                                             : ldexp(v, emax - 1080);
+  return __ll2double_rn(S) * scale;
 }
 
 template <bool VEC2, int MAXT>
@@ -135,46 +125,51 @@ __global__ void __launch_bounds__(256)
     const double* vg = vals + g * cap;
     double y0, y1;
     if (cnt <= MAXT) {
-      double a0[MAXT], a1[MAXT];
+      uint32_t h0[MAXT], l0[MAXT], h1[MAXT], l1[MAXT];
       bool neg[MAXT];
 #pragma unroll
       for (int t = 0; t < MAXT; ++t) {
-        a0[t] = 0.0;
-        a1[t] = 0.0;
+        h0[t] = l0[t] = h1[t] = l1[t] = 0u;
         neg[t] = false;
         if (t < cnt) {
           const double* col = X + (int64_t)__ldg(rg + t) * ldx + i0;
           neg[t] = __ldg(vg + t) < 0.0;
+          double a0, a1 = 0.0;
           if (VEC2 && two) {
             const double2 q = __ldg(reinterpret_cast<const double2*>(col));
-            a0[t] = q.x;
-            a1[t] = q.y;
+            a0 = q.x;
+            a1 = q.y;
           } else {
-            a0[t] = __ldg(col);
-            if (two) a1[t] = __ldg(col + 1);
+            a0 = __ldg(col);
+            if (two) a1 = __ldg(col + 1);
           }
+          h0[t] = (uint32_t)__double2hiint(a0);
+          l0[t] = (uint32_t)__double2loint(a0);
+          h1[t] = (uint32_t)__double2hiint(a1);
+          l1[t] = (uint32_t)__double2loint(a1);
         }
       }
       int e0 = 0, e1 = 0;
 #pragma unroll
       for (int t = 0; t < MAXT; ++t) {
-        e0 = max(e0, exp_of(a0[t]));
-        e1 = max(e1, exp_of(a1[t]));
+        e0 = max(e0, (int)((h0[t] << 1) >> 21));
+        e1 = max(e1, (int)((h1[t] << 1) >> 21));
       }
+      // signed sums: a term's sign is its own sign bit xor the Omega sign
       int64_t s0 = 0, s1 = 0;
 #pragma unroll
       for (int t = 0; t < MAXT; ++t) {
-        const int64_t t0 = fixed_term(a0[t], e0), t1 = fixed_term(a1[t], e1);
-        s0 = neg[t] ? s0 - t0 : s0 + t0;
-        s1 = neg[t] ? s1 - t1 : s1 + t1;
+        uint32_t th, tl;
+        fixed_term32(h0[t], l0[t], e0, th, tl);
+        const int64_t t0 = (int64_t)(((uint64_t)th << 32) | tl);
+        s0 = (neg[t] != (bool)(h0[t] >> 31)) ? s0 - t0 : s0 + t0;
+        fixed_term32(h1[t], l1[t], e1, th, tl);
+        const int64_t t1 = (int64_t)(((uint64_t)th << 32) | tl);
+        s1 = (neg[t] != (bool)(h1[t] >> 31)) ? s1 - t1 : s1 + t1;
       }
-      const double qnan = __longlong_as_double(0x7FF8000000000000ll);
-      y0 = (e0 == 2047) ? qnan : fixed_to_double(s0, e0);
-      y1 = (e1 == 2047) ? qnan : fixed_to_double(s1, e1);
-      if (v != 1.0) {
-        y0 *= v;
-        y1 *= v;
-      }
+      // value = S * 2^(emax - 1080) * v
+      y0 = pm_finish(s0, e0, v);
+      y1 = pm_finish(s1, e1, v);
     } else {
       // long columns (large Bernoulli probability): FP64 multiply-adds
       y0 = 0.0;
