@@ -256,18 +256,33 @@ def main():
     phases = f.phase_times(reset=True)
     value = world * args.steps / (ms / 1e3)
 
-    # roofline of the dominant phase (the full passes over A: FP64 GEMM, FP64-pipe bound)
+    # roofline of the dominant phase: the full passes over A (one lra dense pass = one
+    # k_ozgemm launch plus its small prep / fixup kernels)
     dense_ms, dense_calls = phases["dense"]
     dense_avg_ms = dense_ms / max(dense_calls, 1)
-    flops = 2.0 * m * n * cfg["b"]
-    achieved_tf = flops / (dense_avg_ms * 1e-3) / 1e12 if dense_calls else 0.0
-    digest = source_digest(["dgemm_simt.cu"])
-    roofline = {"kernel": "k_dgemm (A^T X / A X, FP64 SIMT)", "bound": "alu", "achieved": achieved_tf,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                "traffic": traffic_for("k_dgemm", digest),
-                "algorithmic_per_launch": {"flops": flops, "bytes": 8.0 * m * n},
-                "avg_launch_ms": dense_avg_ms, "launches": dense_calls,
-                "peak_source": "nominal FP64 of the profiling recipe (no measured FP64 peak)"}
+    b = cfg["b"]
+    algo_bytes = 8.0 * (m * n + (m + n) * b)       # A once, the skinny operand and result
+    algo_flops = 2.0 * m * n * b
+    if args.engine == "fp64_simt":
+        achieved = algo_flops / (dense_avg_ms * 1e-3) / 1e12 if dense_calls else 0.0
+        roofline = {"kernel": "k_dgemm (FP64 FMA on the CUDA cores)", "bound": "alu",
+                    "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "nominal FP64 of the profiling recipe (no measured FP64 peak)"}
+    else:
+        achieved = algo_bytes / (dense_avg_ms * 1e-3) / 1e9 if dense_calls else 0.0
+        pair_flops = 36 * 2.0 * m * n * 64           # bf16 MMA work of the 36 slice pairs (N padded to 64)
+        tflops = pair_flops / (dense_avg_ms * 1e-3) / 1e12 if dense_calls else 0.0
+        roofline = {"kernel": "k_ozgemm (FP64-accurate GEMM from bf16 slices on tcgen05)",
+                    "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"],
+                    "traffic": traffic_for("k_ozgemm", source_digest(["ozgemm.cu"])),
+                    "peak_source": peak_src + " HBM copy bandwidth",
+                    "tensor_pipe": {"bf16_tflops": tflops, "peak": peaks["bf16_tflops"],
+                                    "frac": tflops / peaks["bf16_tflops"],
+                                    "note": "36 bf16 slice-pair MMAs per FP64 product, N padded to 64"}}
+    roofline.update({"algorithmic_per_launch": {"bytes": algo_bytes, "flops_fp64": algo_flops},
+                     "avg_launch_ms": dense_avg_ms, "launches": dense_calls})
     total_phase = sum(v[0] for v in phases.values()) or 1.0
 
     line = {
