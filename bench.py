@@ -52,8 +52,9 @@ def parse():
                     help="only the timed farPCA steps (for launch-list profiling)")
     ap.add_argument("--engine", choices=("tensor", "fp64_simt"), default="tensor",
                     help="dense passes on the tensor cores (FP64-accurate slicing) or FP64 CUDA cores")
-    ap.add_argument("--only", choices=("sketch",), default=None,
-                    help="run only the sketch pass (lra_sketch over --sketch-blocks blocks), for profiling")
+    ap.add_argument("--only", choices=("sketch", "dense"), default=None,
+                    help="run only the sketch pass (lra_sketch over --sketch-blocks blocks) or only "
+                         "the two dense passes A Y and A^T Y (lra_apply), for profiling")
     return ap.parse_args()
 
 
@@ -134,6 +135,29 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(ms, world, device):
+    """The timed duration of the slowest rank (all ranks call this after the timed region)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(ms_max, world, steps):
+    """Solves per second of the whole job: every rank solves `steps` matrices."""
+    return world * steps / (ms_max / 1e3)
+
+
+def workload_config(args, cfg, m, n, world):
+    return {"workload": args.workload, "m": m, "n": n, "b": cfg["b"], "P": cfg["P"], "eps": cfg["eps"],
+            "omega": "sparse sign, zeta=%d" % cfg["zeta"],
+            "l2": "inputs larger than L2 (A = %.2f GB)" % (8.0 * m * n / 1e9),
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def source_digest(names):
     h = hashlib.sha256()
     for n in names:
@@ -179,8 +203,9 @@ def run_reference(args, cfg):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": args.workload, "m": A.shape[0], "n": A.shape[1],
-                                        "rank": r["rank"], "rel_err": (max(r["E"], 0) / r["normA2"]) ** 0.5},
+        "data": "synthetic",
+        "config": dict(workload_config(args, cfg, A.shape[0], A.shape[1], 1), rank=r["rank"],
+                       blocks=r["blocks"], rel_err=(max(r["E"], 0) / r["normA2"]) ** 0.5),
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
                          "sample": "one full fixed-precision solve of the workload per step "
                                    "(numpy/OpenBLAS FP64, QB form)"},
@@ -220,10 +245,13 @@ def main():
     f = lra.Farpca(m, n, eps=cfg["eps"], b=cfg["b"], P=cfg["P"], kind=cfg["kind"], zeta=cfg["zeta"],
                    p=cfg["p"], seed=cfg["seed"] + rank, profile=True, stream=stream,
                    fp64_simt=(args.engine == "fp64_simt"))
-    if args.only == "sketch":
-        sp = sketch_pass(lra, torch, f, Ad, cfg, args.sketch_blocks, peaks, peak_src)
+    if args.only in ("sketch", "dense"):
+        if args.only == "sketch":
+            out = {"sketch_pass": sketch_pass(lra, torch, f, Ad, cfg, args.sketch_blocks, peaks, peak_src)}
+        else:
+            out = {"dense_pass": dense_pass(lra, torch, f, Ad, cfg, args.steps, args.warmup, peaks, peak_src)}
         if rank == 0:
-            print(json.dumps({"sketch_pass": sp}), flush=True)
+            print(json.dumps(out), flush=True)
         f.close()
         return
     for _ in range(max(args.warmup, 0)):
@@ -247,14 +275,12 @@ def main():
     launches = lra.kernel_launches() - launches0
     ms = e0.elapsed_time(e1)
     clocks = sampler.stop()
+    ms = max_over_ranks(ms, world, "cuda")
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     res = f.result()
     phases = f.phase_times(reset=True)
-    value = world * args.steps / (ms / 1e3)
+    value = whole_job_value(ms, world, args.steps)
 
     # roofline of the dominant phase: the full passes over A (one lra dense pass = one
     # k_ozgemm launch plus its small prep / fixup kernels)
@@ -271,7 +297,7 @@ def main():
                     "peak_source": "nominal FP64 of the profiling recipe (no measured FP64 peak)"}
     else:
         achieved = algo_bytes / (dense_avg_ms * 1e-3) / 1e9 if dense_calls else 0.0
-        pair_flops = 36 * 2.0 * m * n * 64           # bf16 MMA work of the 36 slice pairs (N padded to 64)
+        pair_flops = 28 * 2.0 * m * n * 64           # bf16 MMA work of the 28 digit pairs (N padded to 64)
         tflops = pair_flops / (dense_avg_ms * 1e-3) / 1e12 if dense_calls else 0.0
         roofline = {"kernel": "k_ozgemm (FP64-accurate GEMM from bf16 slices on tcgen05)",
                     "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -280,7 +306,7 @@ def main():
                     "peak_source": peak_src + " HBM copy bandwidth",
                     "tensor_pipe": {"bf16_tflops": tflops, "peak": peaks["bf16_tflops"],
                                     "frac": tflops / peaks["bf16_tflops"],
-                                    "note": "36 bf16 slice-pair MMAs per FP64 product, N padded to 64"}}
+                                    "note": "28 bf16 digit-pair products per FP64 product, N padded to 64"}}
     roofline.update({"algorithmic_per_launch": {"bytes": algo_bytes, "flops_fp64": algo_flops},
                      "avg_launch_ms": dense_avg_ms, "launches": dense_calls})
     total_phase = sum(v[0] for v in phases.values()) or 1.0
@@ -289,12 +315,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "m": m, "n": n, "b": cfg["b"], "P": cfg["P"],
-                   "eps": cfg["eps"], "omega": "sparse sign, zeta=%d" % cfg["zeta"],
-                   "rank": res["rank"], "blocks": res["blocks"], "rel_err": res["rel_err"],
-                   "status": lra.status_string(res["status"]),
-                   "l2": "inputs larger than L2 (A = %.2f GB)" % (8.0 * m * n / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": dict(workload_config(args, cfg, m, n, world), rank=res["rank"], blocks=res["blocks"],
+                       rel_err=res["rel_err"], status=lra.status_string(res["status"])),
         "roofline": roofline,
         "phase_share": {k: round(v[0] / total_phase, 4) for k, v in phases.items()},
         "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
@@ -342,6 +364,35 @@ def sketch_pass(lra, torch, f, Ad, cfg, nblk, peaks, peak_src):
             "blocks": nblk, "ms": ms, "algorithmic_bytes": algo_bytes, "gbs": gbs,
             "bound": "hbm", "peak": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
             "frac_of_nominal_7900": gbs / 7900.0, "peak_source": peak_src}
+
+
+def dense_pass(lra, torch, f, Ad, cfg, steps, warmup, peaks, peak_src):
+    """lra_apply with N = b: C = A Y and C = A^T Y, each timed alone (row exponents of A,
+    the cut of Y, the tensor-core pass and its fixup)."""
+    m, n, b = f.m, f.n, f.b
+    g = torch.Generator(device="cuda").manual_seed(7)
+    out = {}
+    for trans in (False, True):
+        rows_y = m if trans else n
+        Y = torch.randn((b, rows_y), generator=g, dtype=torch.float64, device="cuda").t()
+        for _ in range(max(warmup, 1)):
+            C = f.apply(Ad, Y, trans=trans)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(steps, 1)
+        e0.record(stream)
+        for _ in range(reps):
+            f.apply(Ad, Y, trans=trans, C=C)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        algo_bytes = 8.0 * (m * n + (m + n) * b)
+        out["AT_Y" if trans else "A_Y"] = {"ms": ms, "gbs": algo_bytes / (ms * 1e-3) / 1e9,
+                                           "frac": algo_bytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+    out.update({"peak_gbs": peaks["hbm_gbs"], "peak_source": peak_src,
+                "note": "each includes one exponent pass over A (lra_apply recomputes them)"})
+    return out
 
 
 def e2e(lra, torch, np, f, A, steps):

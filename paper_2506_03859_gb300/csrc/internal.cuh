@@ -87,6 +87,8 @@ struct OzWorkspace {
 };
 int64_t oz_img_bytes(int64_t K);
 int64_t oz_part_elems(int ctas);
+// Largest K the tensor engine accepts (its exact int64 sums stay in range).
+int64_t oz_max_k();
 cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, const double* X,
                    int64_t ldx, const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
                    const OzWorkspace& w, int* flags, cudaStream_t st);

@@ -192,7 +192,8 @@ lra_status gemm(lra_ctx* ctx, bool trans, int64_t P, int64_t N, int64_t K, doubl
 lra_status dense(lra_ctx* ctx, bool trans, int64_t N, double alpha, const double* A, int64_t lda,
                  const double* Y, int64_t ldy, double beta, double* C, int64_t csp, int64_t csc) {
   const int64_t P = trans ? ctx->n : ctx->m, K = trans ? ctx->m : ctx->n;
-  if (!ctx->tensor) return gemm(ctx, trans, P, N, K, alpha, A, lda, Y, ldy, beta, C, csp, csc);
+  if (!ctx->tensor || K > oz_max_k())
+    return gemm(ctx, trans, P, N, K, alpha, A, lda, Y, ldy, beta, C, csp, csc);
   CK(ozgemm(trans, P, N, K, alpha, A, lda, trans ? ctx->colE : ctx->rowE, Y, ldy, beta,
             GemmOut{C, csp, csc}, ctx->oz, ctx->flags, ctx->st));
   return LRA_OK;
@@ -209,7 +210,8 @@ lra_status a_exponents(lra_ctx* ctx, const double* A, int64_t lda) {
 lra_status mm(lra_ctx* ctx, bool trans, int64_t P, int64_t N, int64_t K, double alpha,
               const double* X, int64_t ldx, const int* xE, const double* Y, int64_t ldy,
               double beta, double* C, int64_t csp, int64_t csc) {
-  if (!ctx->tensor || !xE) return gemm(ctx, trans, P, N, K, alpha, X, ldx, Y, ldy, beta, C, csp, csc);
+  if (!ctx->tensor || !xE || K > oz_max_k())
+    return gemm(ctx, trans, P, N, K, alpha, X, ldx, Y, ldy, beta, C, csp, csc);
   if (P <= 0 || N <= 0) return LRA_OK;
   if (K <= 0) return LRA_OK;
   CK(ozgemm(trans, P, N, K, alpha, X, ldx, xE, Y, ldy, beta, GemmOut{C, csp, csc}, ctx->oz,

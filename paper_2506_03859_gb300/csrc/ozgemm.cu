@@ -1,6 +1,7 @@
 // FP64-accurate skinny GEMM on the tcgen05 tensor cores: C = alpha op(X) Y + beta C
 // with X, Y, C in FP64 and N <= 64.  These are the full passes over A of the
-// farPCA block (arxiv 2506.03859 Alg. 1 steps A^T(A G_j), A G_j, A^T Y_j).
+// farPCA block (arxiv 2506.03859 Alg. 1 steps A^T(A G_j), A G_j, A^T Y_j) and the
+// smaller products of the projection and orthonormalisation steps.
 //
 // GB300's FP64 pipe delivers about 1.2 TFLOP/s, while such a pass streams A once
 // from HBM: run as FP64 FMAs it is ~60x slower than the memory bound.  Instead
@@ -9,32 +10,46 @@
 // multiplication by using fast routines of matrix multiplication and its
 // applications", Numer. Algorithms 2012):
 //
-//   each row p of op(X) is scaled by 2^-e_p (|x| < 2^e_p over the row) and
-//   each column c of Y by 2^-f_c; the scaled value, truncated to a 56-bit fixed
-//   point number, is x = 2^-7 sum_{s<8} v_s with v_s = d_s 2^(-7 s),
-//   d_s in [0, 127] carrying the sign of x.  Every v_s is exact in bf16.
+//   Scaling.  Row p of op(X) has largest biased exponent ex_p, column c of Y
+//   ey_c.  x is turned into the signed integer N = trunc(x 2^(1077 - ex_p)),
+//   |N| < 2^55, and written in base 256 with seven digits d_0..d_6 (d_0 the most
+//   significant): N = sum_s d_s 256^(6-s), d_0 in [-128, 128], d_1..6 in
+//   [-128, 127].  Every digit is an integer of at most 8 significant bits, exact
+//   in bf16.  Y is cut the same way into digits e_0..e_6.
 //
-//   x y = 2^-14 sum_{s,t} v_s w_t; the 36 pairs with s + t <= 7 are kept (the
-//   rest is below 2^-56 relative), each a bf16 MMA on the tensor core with FP32
-//   accumulation in TMEM.  The pairs of weight w = s + t <= 4 are summed per
-//   weight over windows of 32 values of K: every such sum is an integer
-//   multiple of 2^(-7 w) below 2^22 units (at most 5 pairs x 32 x 127^2), so the
-//   FP32 accumulator holds it exactly and adding 1.5 * 2^23 turns it into an
-//   integer.  The five integers are combined into one int64 per output in units
-//   of 2^-28 (exact).  The pairs of weight >= 5 (at most 2^-35 of a product) run
-//   in one FP32 accumulator over all of K.  The tile is then (int64 * 2^-28 +
-//   fp32) * 2^(e_p + f_c - 2058), written in FP64.  Against exact dot products
-//   the error is that of an FP64 GEMM (2^-52 of |op(X)| |Y| on Gaussian data).
+//   Products.  x y = 2^(ex + ey - 2058) sum_{s,t} d_s e_t 256^(-(s+t)).  The 28
+//   pairs of weight w = s + t <= 6 are kept (the dropped ones are below 2^-53 of
+//   max|x| max|y|).  For each weight w the tensor core sums G_w = sum_{s+t=w}
+//   sum_k d_s e_t in an FP32 accumulator in TMEM (columns 64 w .. 64 w + 63).
+//
+//   Exact part.  For w <= 3 and a window of at most 64 values of K, |G_w| <=
+//   4 * 64 * 128^2 = 2^22, so the FP32 accumulator holds it exactly.  The
+//   accumulator starts each window at 1.5 * 2^23; its bit pattern minus that of
+//   1.5 * 2^23 is then G_w as an integer, and the four are folded into one int64
+//   per output, T += G_0 2^24 + G_1 2^16 + G_2 2^8 + G_3, held by the flush
+//   warps (half in registers, half in spare TMEM columns; exact while K <= 2^24).
+//
+//   Rest.  G_4, G_5, G_6 (at most 2^-32 of the leading term) run in FP32 over
+//   the whole range of K of the tile.  The result is
+//   (T 2^-24 + G_4 2^-32 + G_5 2^-40 + G_6 2^-48) 2^(ex + ey - 2058), written in
+//   FP64; against exact dot products its error is that of an FP64 GEMM.
+//
+// Tensor-core schedule.  Digit planes of Y are stored one after another in shared
+// memory, so one MMA with X plane s and Y planes t..t+c-1 (N = 64 c <= 256)
+// produces the weights s+t .. s+t+c-1 into adjacent TMEM column ranges: the 28
+// pairs take 11 MMAs per 16 values of K (4 for w <= 3, 7 for w >= 4).
 //
 // Work split: one CTA per SM walks a contiguous range of (row tile, 32-deep
-// window) units ("stream-K"); tiles whose windows span two or more CTAs are
+// stage) units ("stream-K"); tiles whose stages span two or more CTAs are
 // written as partial sums and combined by a fixup kernel in a fixed order.
-// Inside a CTA the work is pipelined by warp role: eight producer warps load
-// a 128 x 32 block of op(X) from HBM, slice it into 8 bf16 planes of a shared
-// memory stage (two stages, K-major core-matrix layout) and copy the pre-sliced
-// 64 x 32 block of Y; one thread issues the window's 72 MMAs; four warps flush
-// the exact sums from TMEM and write the tile.  mbarriers hand stages and the
-// TMEM accumulators between the roles; every wait is bounded.
+// Inside a CTA the work is pipelined by warp role: eight producer warps load a
+// 128 x 32 block of op(X) one stage ahead into registers, cut it into the seven
+// digit planes of a shared-memory stage (two stages, K-major core-matrix layout),
+// while a bulk copy brings the pre-cut 64 x 32 block of Y; one thread issues
+// the MMAs; four warps read the exact sums from TMEM at the end of each 64-deep
+// window, re-arm them, and write the tile.  The MMAs of weight >= 4 of a window
+// are issued before the wait for that re-arming, so the flush overlaps them.
+// mbarriers hand stages and accumulators between the roles; every wait is bounded.
 #include <math.h>
 
 #include "internal.cuh"
@@ -43,30 +58,32 @@
 namespace lra {
 
 namespace {
-constexpr int S = 8;               // slices per operand (7 bits each)
-constexpr int BETA = 7;            // bits per slice
-constexpr int TM = 128;            // rows of op(X) per tile
-constexpr int KW = 32;             // K per window (one pipeline stage)
-constexpr int NN = 64;             // output columns (N padded)
-constexpr int NPROD = 256;         // producer threads (warps 4..11)
-constexpr int NFLUSH = 128;        // flush threads (warps 0..3)
-constexpr int NT = NFLUSH + NPROD + 32;  // + one MMA warp (warp 12)
-constexpr int A_PLANE = TM * KW * 2;     // bytes of one slice plane of the op(X) block
-constexpr int Y_PLANE = NN * KW * 2;     // bytes of one slice plane of the Y block
-constexpr int STAGE = S * (A_PLANE + Y_PLANE);
+constexpr int S = 7;                     // digits per operand
+constexpr int TM = 128;                  // rows of op(X) per tile
+constexpr int KS = 32;                   // K per pipeline stage
+constexpr int NN = 64;                   // output columns (N padded)
+constexpr int NFLUSH = 128;              // flush threads (warps 0..3)
+constexpr int NPROD = 256;               // producer threads (warps 4..11)
+constexpr int MMA_WARP = 12;
+constexpr int NT = NFLUSH + NPROD + 32;
+constexpr int A_PLANE = TM * KS * 2;     // bytes of one digit plane of the op(X) block
+constexpr int Y_PLANE = NN * KS * 2;     // bytes of one digit plane of the Y block
+constexpr int Y_STAGE = S * Y_PLANE;     // the Y part of a stage (one bulk copy)
+constexpr int STAGE = S * A_PLANE + Y_STAGE;
 constexpr int NSTAGE = 2;
 constexpr int SMEM_DYN = NSTAGE * STAGE + 1024;
-constexpr uint32_t LBO = 128, SBO = 512;         // core-matrix strides (K, rows)
-constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t COL_G5 = 320;                  // FP32 sum of the pairs of weight >= 5
-constexpr uint32_t COL_ACC_LO = 384, COL_ACC_HI = 448;  // int64 exact sum, two words
-constexpr int EXACT_GROUPS = 5;                   // weights 0..4, TMEM columns 64 w
+constexpr uint32_t LBO = 128, SBO = 512;  // core-matrix strides (K, rows)
+constexpr uint32_t TMEM_COLS = 512;       // weights 0..6: columns 0..447
+constexpr uint32_t COL_ACC_LO = 448, COL_ACC_HI = 480;  // int64 sums of output columns 32..63
+constexpr uint32_t MAGIC = 0x4B400000u;   // bits of 1.5 * 2^23
 constexpr long WAIT_TRIES = 1L << 22;
-constexpr int EXP_OFFSET = 2058;  // 2 * 1022 + 2 * BETA: see the scaling above
+constexpr int EXP_OFFSET = 2058;          // 2 * 1077 - 96: see the scaling above
+constexpr int64_t MAX_K = int64_t(1) << 24;
 }  // namespace
 
-int64_t oz_img_bytes(int64_t K) { return (K + KW - 1) / KW * S * Y_PLANE; }
+int64_t oz_img_bytes(int64_t K) { return (K + KS - 1) / KS * Y_STAGE; }
 int64_t oz_part_elems(int ctas) { return (int64_t)ctas * 2 * TM * NN; }
+int64_t oz_max_k() { return MAX_K; }
 
 // Offset of element (row, k), k < 32, in the K-major core-matrix layout of a
 // stage plane: core (row/8, k/8) at ((row/8)*4 + k/8)*128, row-major inside.
@@ -74,33 +91,64 @@ __host__ __device__ __forceinline__ uint32_t core_offset(uint32_t row, uint32_t 
   return (((row >> 3) << 2) + (k >> 3)) * 128u + (row & 7u) * 16u + (k & 7u) * 2u;
 }
 
-// |a| as a 56-bit fixed-point integer relative to 2^(emax - 1022) (emax = the
-// largest biased exponent of the row/column), and its sign.
-__device__ __forceinline__ uint64_t fixed56(double a, int emax, uint32_t& sign) {
-  const uint64_t bits = (uint64_t)__double_as_longlong(a);
-  sign = (uint32_t)(bits >> 63);
-  const int E = (int)((bits >> 52) & 0x7FFu);
-  const uint64_t M = (E != 0) ? ((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : 0ull;
-  const int d = emax - E;  // >= 0 by the choice of emax
-  if (d <= 3) return M << (3 - d);
-  const int sh = d - 3;
-  return sh < 64 ? (M >> sh) : 0ull;
+// N + BIAS as two 32-bit words, N = trunc(x 2^(1077 - emax)) (emax >= the
+// biased exponent of x; zero and subnormal x give 0) and BIAS = 128 in each of
+// the six low bytes: the bytes of N + BIAS, minus 128, are the base-256 digits
+// of N below the top one, and its bits 48.. (signed) are the top digit.
+__device__ __forceinline__ void biased_fixed(double x, int emax, uint32_t& nh, uint32_t& nl) {
+  const uint32_t h = (uint32_t)__double2hiint(x), l = (uint32_t)__double2loint(x);
+  const int E = (int)((h >> 20) & 0x7FFu);
+  const uint32_t mh = (h & 0x000FFFFFu) | 0x00100000u;  // significand M = mh:l
+  const uint32_t vh = __funnelshift_l(l, mh, 10);      // M << 10, high word
+  const uint32_t vl = l << 10;
+  const int k = (E != 0 ? emax - E : 64) + 8;          // |N| = (M << 10) >> k
+  uint32_t rh, rl;
+  if (k < 32) {
+    rl = __funnelshift_r(vl, vh, k);
+    rh = vh >> k;
+  } else {
+    rl = k < 64 ? vh >> (k - 32) : 0u;
+    rh = 0u;
+  }
+  const uint32_t s = (uint32_t)((int)h >> 31);  // 0, or all ones for negative x
+  uint64_t v = ((uint64_t)(rh ^ s) << 32) | (uint64_t)(rl ^ s);
+  v += 0x0000808080808080ull + (uint64_t)(s & 1u);  // two's complement, plus BIAS
+  nh = (uint32_t)(v >> 32);
+  nl = (uint32_t)v;
 }
 
-// bf16 bits of d * 2^(-7 s) (d < 128, exact), sign in bit 15.
-template <int SLICE>
-__device__ __forceinline__ uint32_t slice_bf16(uint64_t x, uint32_t sign) {
-  const uint32_t d = (uint32_t)(x >> (BETA * (S - 1 - SLICE))) & 0x7Fu;
-  constexpr float sc = (SLICE == 0) ? 1.0f : (SLICE == 1) ? 0x1p-7f : (SLICE == 2) ? 0x1p-14f
-                       : (SLICE == 3) ? 0x1p-21f : (SLICE == 4) ? 0x1p-28f : (SLICE == 5) ? 0x1p-35f
-                       : (SLICE == 6) ? 0x1p-42f : 0x1p-49f;
-  const float f = __fmaf_rn(__int_as_float(0x4B000000 | (int)d), sc, -8388608.0f * sc);
-  return (__float_as_uint(f) >> 16) | (sign << 15);
+// Digit SL (0 = most significant) of (nh, nl) as a float: the byte is dropped
+// into the mantissa of 2^23 and 2^23 + 128 subtracted, exactly.
+template <int SL>
+__device__ __forceinline__ float digit_f(uint32_t nh, uint32_t nl) {
+  if (SL == 0) return __int_as_float(0x4B000080 + ((int)nh >> 16)) - 8388736.0f;
+  const uint32_t w = (SL <= 2) ? nh : nl;
+  constexpr uint32_t byte = (SL <= 2) ? (2 - SL) : (6 - SL);
+  return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7650u | byte)) - 8388736.0f;
 }
 
-template <int SLICE>
-__device__ __forceinline__ uint32_t pack2(uint64_t x0, uint32_t s0, uint64_t x1, uint32_t s1) {
-  return slice_bf16<SLICE>(x0, s0) | (slice_bf16<SLICE>(x1, s1) << 16);
+// Two floats holding bf16-exact values -> packed bf16 pair (lo in the low half).
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632u);
+}
+
+// Eight consecutive K values of one row (or column) -> one 16-byte chunk in each
+// of the seven digit planes at dst, dst + plane, ...
+__device__ __forceinline__ void cut8(const double* v, int emax, uint8_t* dst, int plane) {
+  uint32_t h[8], l[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) biased_fixed(v[i], emax, h[i], l[i]);
+#define LRA_CUT(SL)                                                                   \
+  {                                                                                   \
+    uint4 q;                                                                          \
+    q.x = pack_bf16(digit_f<SL>(h[0], l[0]), digit_f<SL>(h[1], l[1]));                \
+    q.y = pack_bf16(digit_f<SL>(h[2], l[2]), digit_f<SL>(h[3], l[3]));                \
+    q.z = pack_bf16(digit_f<SL>(h[4], l[4]), digit_f<SL>(h[5], l[5]));                \
+    q.w = pack_bf16(digit_f<SL>(h[6], l[6]), digit_f<SL>(h[7], l[7]));                \
+    *reinterpret_cast<uint4*>(dst + (SL) * plane) = q;                                \
+  }
+  LRA_CUT(0) LRA_CUT(1) LRA_CUT(2) LRA_CUT(3) LRA_CUT(4) LRA_CUT(5) LRA_CUT(6)
+#undef LRA_CUT
 }
 
 // ---------------------------------------------------------------- prep kernels
@@ -141,38 +189,25 @@ __global__ void __launch_bounds__(256) k_oz_rowmaxexp(const double* __restrict__
   atomicMax(out + r, e);
 }
 
-// Pre-sliced Y: img[w][s] is the 64 x 32 (N x K) bf16 block of slice s of
-// window w in the core-matrix layout.  One thread per (window, column c, 8-wide
-// k chunk j).
-__global__ void __launch_bounds__(256) k_oz_yslice(const double* __restrict__ Y, int64_t ldy,
-                                                   int64_t K, int N, const int* __restrict__ yE,
-                                                   uint8_t* __restrict__ img, int64_t kwins) {
+// Pre-cut Y: stage u of the image holds the seven 64 x 32 (N x K) digit planes
+// of K values 32u .. 32u + 31 in the core-matrix layout.  One thread per
+// (stage, column c, 8-wide k chunk j).
+__global__ void __launch_bounds__(256) k_oz_ycut(const double* __restrict__ Y, int64_t ldy,
+                                                 int64_t K, int N, const int* __restrict__ yE,
+                                                 uint8_t* __restrict__ img, int64_t kst) {
   const int64_t idx = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  if (idx >= kwins * NN * 4) return;
+  if (idx >= kst * NN * 4) return;
   const int j = (int)(idx & 3);
   const int c = (int)((idx >> 2) & (NN - 1));
-  const int64_t w = idx >> 8;
+  const int64_t u = idx >> 8;
   const int emax = c < N ? yE[c] : 0;
-  uint64_t x[8];
-  uint32_t sg[8];
+  double v[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const int64_t k = w * KW + 8 * j + i;
-    const double v = (c < N && k < K) ? __ldg(Y + k + (int64_t)c * ldy) : 0.0;
-    x[i] = fixed56(v, emax, sg[i]);
+    const int64_t k = u * KS + 8 * j + i;
+    v[i] = (c < N && k < K) ? __ldg(Y + k + (int64_t)c * ldy) : 0.0;
   }
-  uint8_t* base = img + (w * S) * Y_PLANE + core_offset((uint32_t)c, (uint32_t)(8 * j));
-#define LRA_YS(SL)                                                                          \
-  {                                                                                         \
-    uint4 q;                                                                                \
-    q.x = pack2<SL>(x[0], sg[0], x[1], sg[1]);                                              \
-    q.y = pack2<SL>(x[2], sg[2], x[3], sg[3]);                                              \
-    q.z = pack2<SL>(x[4], sg[4], x[5], sg[5]);                                              \
-    q.w = pack2<SL>(x[6], sg[6], x[7], sg[7]);                                              \
-    *reinterpret_cast<uint4*>(base + (SL)*Y_PLANE) = q;                                     \
-  }
-  LRA_YS(0) LRA_YS(1) LRA_YS(2) LRA_YS(3) LRA_YS(4) LRA_YS(5) LRA_YS(6) LRA_YS(7)
-#undef LRA_YS
+  cut8(v, emax, img + u * Y_STAGE + core_offset((uint32_t)c, (uint32_t)(8 * j)), Y_PLANE);
 }
 
 // ---------------------------------------------------------------- main kernel
@@ -183,140 +218,130 @@ struct OzArgs {
   int64_t ldx;
   const int* xE;       // biased max exponent of each row of op(X)
   const int* yE;       // biased max exponent of each column of Y
-  const uint8_t* img;  // pre-sliced Y
+  const uint8_t* img;  // pre-cut Y
   double alpha, beta;
   double* C;
   int64_t csp, csc;
-  double* part;        // [cta][2][TM][NN] partial tiles
-  int64_t tiles, kwins;
+  double* part;        // [cta][2][NN][TM] partial tiles
+  int64_t tiles, kst;  // row tiles; 32-deep stages per tile
   int* flags;
   bool vec;            // 16-byte loads allowed (trans layout)
 };
 
-// Producer: slice the 128 x 32 block (tile, window w) of op(X) into the eight
-// planes of a stage.  pt = producer thread 0..255.
+// The CTA's stages: a contiguous range [u0, u1) of (tile, stage) units,
+// tile-major.  A segment is the part of the range inside one tile; a window is
+// one or two consecutive stages of a segment, aligned to even stage indices.
+struct Walk {
+  int64_t u0, u1, kst;
+  __device__ __forceinline__ int64_t tile(int64_t u) const { return u / kst; }
+  __device__ __forceinline__ bool seg_first(int64_t u) const { return u == u0 || u % kst == 0; }
+  __device__ __forceinline__ bool seg_last(int64_t u) const {
+    return u + 1 == u1 || (u + 1) % kst == 0;
+  }
+  __device__ __forceinline__ bool win_first(int64_t u) const {
+    return seg_first(u) || ((u % kst) & 1) == 0;
+  }
+  __device__ __forceinline__ bool win_last(int64_t u) const {
+    return seg_last(u) || ((u % kst) & 1) == 1;
+  }
+};
+
+// A producer thread's share of one stage: 16 values of op(X).  TRANS == false:
+// op(X)[p, k] = X[p + k*ldx], the thread takes row 32 (pw % 4) + lane and 16
+// consecutive k (coalesced across the warp).  TRANS == true: op(X)[p, k] =
+// X[k + p*ldx]; each warp instruction covers one 8 x 8 core matrix, lane ->
+// (row r8 = lane % 8, k pair lane / 8).
 template <bool TRANS>
-__device__ __forceinline__ void slice_window(const OzArgs& a, int64_t tile, int64_t w,
-                                             uint8_t* sA, const int* sE, int pt) {
-  const int lane = pt & 31, pw = pt >> 5;
-  const int64_t p0 = tile * TM, k0 = w * KW;
-  if (TRANS) {
-    // op(X)[p, k] = X[k + p*ldx]: each warp instruction covers one core matrix
-    // (8 rows x 8 k): lane -> row r8 = lane & 7, k pair q = lane >> 3.
+__device__ __forceinline__ void fetch(const OzArgs& a, int64_t u, int pw, int lane, double (&v)[16]) {
+  const int64_t tile = u / a.kst, k0 = (u % a.kst) * KS;
+  if (!TRANS) {
+    const int64_t p = tile * TM + 32 * (pw & 3) + lane, kb = k0 + 16 * (pw >> 2);
+    const bool in = p < a.P;
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      v[i] = (in && kb + i < a.K) ? __ldg(a.X + p + (kb + i) * a.ldx) : 0.0;
+  } else {
     const int r8 = lane & 7, q = lane >> 3;
-    double v0[8], v1[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int core = pw + 8 * i, rg = core >> 2, kc = core & 3;
-      const int64_t p = p0 + rg * 8 + r8, k = k0 + kc * 8 + 2 * q;
-      v0[i] = 0.0;
-      v1[i] = 0.0;
+      const int64_t p = tile * TM + rg * 8 + r8, k = k0 + kc * 8 + 2 * q;
+      v[2 * i] = 0.0;
+      v[2 * i + 1] = 0.0;
       if (p < a.P) {
         const double* src = a.X + k + p * a.ldx;
         if (a.vec && k + 1 < a.K) {
           const double2 t = __ldg(reinterpret_cast<const double2*>(src));
-          v0[i] = t.x;
-          v1[i] = t.y;
+          v[2 * i] = t.x;
+          v[2 * i + 1] = t.y;
         } else {
-          if (k < a.K) v0[i] = __ldg(src);
-          if (k + 1 < a.K) v1[i] = __ldg(src + 1);
+          if (k < a.K) v[2 * i] = __ldg(src);
+          if (k + 1 < a.K) v[2 * i + 1] = __ldg(src + 1);
         }
       }
     }
+  }
+}
+
+// Cut the thread's 16 values into the stage; sE = row exponents of the tile.
+template <bool TRANS>
+__device__ __forceinline__ void cut_stage(const double (&v)[16], const int* sE, uint8_t* sA, int pw,
+                                          int lane) {
+  if (!TRANS) {
+    const uint32_t row = 32 * (pw & 3) + lane, kb = 16 * (pw >> 2);
+    const int e = sE[row];
+    cut8(v, e, sA + core_offset(row, kb), A_PLANE);
+    cut8(v + 8, e, sA + core_offset(row, kb + 8), A_PLANE);
+  } else {
+    const int r8 = lane & 7, q = lane >> 3;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int core = pw + 8 * i, rg = core >> 2, kc = core & 3;
-      const int row = rg * 8 + r8;
-      const int emax = sE[row];
-      uint32_t s0, s1;
-      const uint64_t x0 = fixed56(v0[i], emax, s0), x1 = fixed56(v1[i], emax, s1);
+      const int core = pw + 8 * i;
+      const int e = sE[(core >> 2) * 8 + r8];
       uint8_t* dst = sA + core * 128 + r8 * 16 + q * 4;
-#define LRA_XT(SL) *reinterpret_cast<uint32_t*>(dst + (SL)*A_PLANE) = pack2<SL>(x0, s0, x1, s1);
-      LRA_XT(0) LRA_XT(1) LRA_XT(2) LRA_XT(3) LRA_XT(4) LRA_XT(5) LRA_XT(6) LRA_XT(7)
-#undef LRA_XT
-      (void)kc;
-    }
-  } else {
-    // op(X)[p, k] = X[p + k*ldx]: lanes along rows, each thread 8 consecutive k.
-    const int rgrp = pw & 3, kc0 = (pw >> 2) * 2;
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-      const int row = rgrp * 32 + lane, kc = kc0 + h;
-      const int64_t p = p0 + row, kb = k0 + kc * 8;
-      double v[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-        v[i] = (p < a.P && kb + i < a.K) ? __ldg(a.X + p + (kb + i) * a.ldx) : 0.0;
-      const int emax = sE[row];
-      uint64_t x[8];
-      uint32_t sg[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) x[i] = fixed56(v[i], emax, sg[i]);
-      uint8_t* dst = sA + core_offset((uint32_t)row, (uint32_t)(kc * 8));
-#define LRA_XS(SL)                                                \
-  {                                                               \
-    uint4 q;                                                      \
-    q.x = pack2<SL>(x[0], sg[0], x[1], sg[1]);                    \
-    q.y = pack2<SL>(x[2], sg[2], x[3], sg[3]);                    \
-    q.z = pack2<SL>(x[4], sg[4], x[5], sg[5]);                    \
-    q.w = pack2<SL>(x[6], sg[6], x[7], sg[7]);                    \
-    *reinterpret_cast<uint4*>(dst + (SL)*A_PLANE) = q;            \
-  }
-      LRA_XS(0) LRA_XS(1) LRA_XS(2) LRA_XS(3) LRA_XS(4) LRA_XS(5) LRA_XS(6) LRA_XS(7)
-#undef LRA_XS
+      uint32_t h0, l0, h1, l1;
+      biased_fixed(v[2 * i], e, h0, l0);
+      biased_fixed(v[2 * i + 1], e, h1, l1);
+#define LRA_CUT2(SL) \
+  *reinterpret_cast<uint32_t*>(dst + (SL) * A_PLANE) = pack_bf16(digit_f<SL>(h0, l0), digit_f<SL>(h1, l1));
+      LRA_CUT2(0) LRA_CUT2(1) LRA_CUT2(2) LRA_CUT2(3) LRA_CUT2(4) LRA_CUT2(5) LRA_CUT2(6)
+#undef LRA_CUT2
     }
   }
 }
 
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
-      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
-      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
-      : "memory");
+// One MMA of X digit plane s against Y planes t0 .. t0+c-1 into the weight
+// columns 64 (s + t0) .. ; kk selects the 16-deep half of the stage.
+__device__ __forceinline__ void mma_group(uint32_t tmem, uint32_t a0, uint32_t y0, int s, int t0,
+                                          int c, int kk, uint32_t accumulate) {
+  const uint32_t idesc = tc::idesc_bf16_f32(TM, 64u * (uint32_t)c);
+  tc::mma_bf16(tmem + 64u * (uint32_t)(s + t0),
+               tc::desc_k_none(a0 + (uint32_t)s * A_PLANE + 256u * kk, LBO, SBO),
+               tc::desc_k_none(y0 + (uint32_t)t0 * Y_PLANE + 256u * kk, LBO, SBO), idesc, accumulate);
 }
-__device__ __forceinline__ void tmem_st_wait() {
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
-
-// An FP32 value that is an integer multiple n of 2^-k with |n| < 2^22, as n:
-// adding 1.5 * 2^23 after scaling by 2^k puts n in the low mantissa bits.
-__device__ __forceinline__ int exact_int(uint32_t bits, float scale) {
-  return __float_as_int(__fmaf_rn(__uint_as_float(bits), scale, 12582912.0f)) - 0x4B400000;
-}
-
-// The CTA's windows: a contiguous range [u0, u1) of (tile, window) units, tile-major.
-struct Walk {
-  int64_t u0, u1, kwins;
-  __device__ __forceinline__ int64_t tile(int64_t u) const { return u / kwins; }
-  __device__ __forceinline__ bool seg_first(int64_t u) const { return u == u0 || u % kwins == 0; }
-  __device__ __forceinline__ bool seg_last(int64_t u) const {
-    return u + 1 == u1 || (u + 1) % kwins == 0;
-  }
-};
 
 template <bool TRANS>
 __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t bar_full[NSTAGE], bar_empty[NSTAGE], bar_accfull, bar_accempty;
-  __shared__ int sEp[TM];  // producers: row exponents of the current tile
   __shared__ int syE[NN];
+  __shared__ int sEx[2][TM];  // producers: row exponents of tiles (by tile parity)
   __shared__ volatile int s_abort;
+  __shared__ volatile int s_pgo[2];  // producers: go on with iteration i (slot i % 2)
   const uint32_t raw = tc::smem_addr(smem_raw);
   uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t T = a.tiles * a.kwins;
+  const int64_t T = a.tiles * a.kst;
   const int64_t G = gridDim.x, cta = blockIdx.x;
-  const Walk wk{cta * T / G, (cta + 1) * T / G, a.kwins};
+  const Walk wk{cta * T / G, (cta + 1) * T / G, a.kst};
   if (wk.u0 >= wk.u1) return;
 
   if (warp == 0) tc::tmem_alloc(&s_tmem, TMEM_COLS);
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
-      tc::mbar_init(&bar_full[s], NPROD);
+      tc::mbar_init(&bar_full[s], NPROD + 1);  // + the arrival that carries the Y bytes
       tc::mbar_init(&bar_empty[s], 1);
     }
     tc::mbar_init(&bar_accfull, 1);
@@ -330,157 +355,235 @@ __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
   const uint32_t tmem = s_tmem;
   const int64_t first_tile = wk.tile(wk.u0);
 
-  if (warp >= 4 && warp < 12) {
+  if (warp >= 4 && warp < MMA_WARP) {
     // ---------------------------------------------------------- producers
-    const int pt = tid - NFLUSH;
+    const int pt = tid - NFLUSH, pw = pt >> 5;
     uint32_t ph_empty[NSTAGE] = {0, 0};
-    int64_t cur_tile = -1;
+    // row exponents of a tile in sEx[tile % 2], written while the first stage of
+    // the tile is fetched (one iteration ahead of its use, behind a named barrier)
+    auto load_exps = [&](int64_t tile) {
+      if (pt < TM) {
+        const int64_t p = tile * TM + pt;
+        sEx[tile & 1][pt] = p < a.P ? __ldg(a.xE + p) : 0;
+      }
+    };
+    double v[16];
+    load_exps(wk.tile(wk.u0));
+    fetch<TRANS>(a, wk.u0, pw, lane, v);
     for (int64_t u = wk.u0, i = 0; u < wk.u1; ++u, ++i) {
       const int st = (int)(i & 1);
-      // one thread waits for the stage; the named barrier makes the decision uniform
-      if (i >= NSTAGE) {
-        if (pt == 0 && !tc::mbar_wait(&bar_empty[st], ph_empty[st], WAIT_TRIES)) s_abort = 1;
-        ph_empty[st] ^= 1u;
+      // Thread 0 waits for the stage and decides whether to go on; the decision is
+      // published in slot i % 2 before the named barrier and read after it, so all
+      // producers leave the loop in the same iteration (slot i % 2 is next written
+      // in iteration i + 2, after every producer has passed barrier i + 1).
+      if (pt == 0) {
+        bool go = s_abort == 0;
+        if (go && i >= NSTAGE) go = tc::mbar_wait(&bar_empty[st], ph_empty[st], WAIT_TRIES);
+        if (!go) s_abort = 1;
+        s_pgo[i & 1] = go ? 1 : 0;
       }
+      if (i >= NSTAGE) ph_empty[st] ^= 1u;
       tc::named_sync(1, NPROD);
-      if (s_abort) break;
-      const int64_t tile = wk.tile(u);
-      if (tile != cur_tile) {
-        tc::named_sync(1, NPROD);
-        if (pt < TM) {
-          const int64_t p = tile * TM + pt;
-          sEp[pt] = p < a.P ? a.xE[p] : 0;
-        }
-        tc::named_sync(1, NPROD);
-        cur_tile = tile;
-      }
+      if (!s_pgo[i & 1]) break;
       uint8_t* sA = sm + st * STAGE;
-      uint8_t* sY = sA + S * A_PLANE;
-      const uint8_t* ysrc = a.img + (u % a.kwins) * (int64_t)(S * Y_PLANE);
-      for (int q = pt; q < S * Y_PLANE / 16; q += NPROD) tc::cp_async16(sY + 16 * q, ysrc + 16 * q);
-      slice_window<TRANS>(a, tile, u % a.kwins, sA, sEp, pt);
-      tc::cp_async_wait_all();
+      if (pt == 0) {
+        tc::mbar_arrive_expect_tx(&bar_full[st], Y_STAGE);
+        tc::bulk_g2s(sA + S * A_PLANE, a.img + (u % a.kst) * (int64_t)Y_STAGE, Y_STAGE,
+                     &bar_full[st]);
+      }
+      // next stage's values are in flight while this one is cut
+      double vn[16];
+      if (u + 1 < wk.u1) {
+        if (wk.tile(u + 1) != wk.tile(u)) load_exps(wk.tile(u + 1));
+        fetch<TRANS>(a, u + 1, pw, lane, vn);
+      }
+      cut_stage<TRANS>(v, sEx[wk.tile(u) & 1], sA, pw, lane);
       tc::fence_async_smem();
       tc::mbar_arrive(&bar_full[st]);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = vn[q];
     }
-  } else if (warp == 12) {
-    // ---------------------------------------------------------- MMA issuer
-    uint32_t ph_full[NSTAGE] = {0, 0}, ph_accempty = 0;
-    const uint32_t idesc = tc::idesc_bf16_f32(TM, NN);
-    for (int64_t u = wk.u0, i = 0; u < wk.u1; ++u, ++i) {
-      const int st = (int)(i & 1);
-      bool ok = true;
-      if (lane == 0) {
-        ok = tc::mbar_wait(&bar_full[st], ph_full[st], WAIT_TRIES);
-        if (ok && i > 0) ok = tc::mbar_wait(&bar_accempty, ph_accempty, WAIT_TRIES);
-      }
-      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-      ph_full[st] ^= 1u;
-      if (i > 0) ph_accempty ^= 1u;
-      if (!ok) s_abort = 1;
-      if (s_abort) break;
-      tc::fence_after_sync();
-      if (lane == 0) {
-        const bool fresh = wk.seg_first(u);
+  } else if (warp == MMA_WARP) {
+    // ---------------------------------------------------------- MMA issuer (one thread)
+    if (lane == 0) {
+      uint32_t ph_full[NSTAGE] = {0, 0}, ph_ae = 0;
+      for (int64_t u = wk.u0, i = 0; u < wk.u1; ++u, ++i) {
+        const int st = (int)(i & 1);
+        if (!tc::mbar_wait(&bar_full[st], ph_full[st], WAIT_TRIES)) {
+          s_abort = 1;
+          break;
+        }
+        ph_full[st] ^= 1u;
+        tc::fence_after_sync();
+        const bool sf = wk.seg_first(u);
+        // a new segment: the flush must have read the previous one's FP32 sums
+        if (sf) {
+          if (!tc::mbar_wait(&bar_accempty, ph_ae, WAIT_TRIES)) {
+            s_abort = 1;
+            break;
+          }
+          ph_ae ^= 1u;
+          tc::fence_after_sync();
+        }
         const uint32_t a0 = tc::smem_addr(sm + st * STAGE);
         const uint32_t y0 = a0 + S * A_PLANE;
-#pragma unroll 1
-        for (int sa = 0; sa < S; ++sa)
-#pragma unroll 1
-          for (int sy = 0; sy < S - sa; ++sy) {
-            const int w = sa + sy;
-            const uint32_t col = w < EXACT_GROUPS ? 64u * w : COL_G5;
-            // exact groups restart every window; the weight >= 5 sum once per segment
-            const bool first = (sa == 0) && (w < EXACT_GROUPS || (w == EXACT_GROUPS && fresh));
+        // weights 4..6 (FP32 over the segment); the first MMA of a segment starts them
 #pragma unroll
-            for (int kk = 0; kk < 2; ++kk)
-              tc::mma_bf16(tmem + col, tc::desc_k_none(a0 + sa * A_PLANE + 256 * kk, LBO, SBO),
-                           tc::desc_k_none(y0 + sy * Y_PLANE + 256 * kk, LBO, SBO), idesc,
-                           (first && kk == 0) ? 0u : 1u);
+        for (int kk = 0; kk < 2; ++kk) {
+          mma_group(tmem, a0, y0, 0, 4, 3, kk, (sf && kk == 0) ? 0u : 1u);
+          mma_group(tmem, a0, y0, 1, 3, 3, kk, 1u);
+          mma_group(tmem, a0, y0, 2, 2, 3, kk, 1u);
+          mma_group(tmem, a0, y0, 3, 1, 3, kk, 1u);
+          mma_group(tmem, a0, y0, 4, 0, 3, kk, 1u);
+          mma_group(tmem, a0, y0, 5, 0, 2, kk, 1u);
+          mma_group(tmem, a0, y0, 6, 0, 1, kk, 1u);
+        }
+        // weights 0..3 (exact per window): wait until the flush has re-armed them
+        if (wk.win_first(u) && !sf) {
+          if (!tc::mbar_wait(&bar_accempty, ph_ae, WAIT_TRIES)) {
+            s_abort = 1;
+            break;
           }
+          ph_ae ^= 1u;
+          tc::fence_after_sync();
+        }
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          mma_group(tmem, a0, y0, 0, 0, 4, kk, 1u);
+          mma_group(tmem, a0, y0, 1, 0, 3, kk, 1u);
+          mma_group(tmem, a0, y0, 2, 0, 2, kk, 1u);
+          mma_group(tmem, a0, y0, 3, 0, 1, kk, 1u);
+        }
         tc::mma_commit(&bar_empty[st]);
-        tc::mma_commit(&bar_accfull);
+        if (wk.win_last(u)) tc::mma_commit(&bar_accfull);
       }
-      __syncwarp();
     }
+    __syncwarp();
   } else if (warp < 4) {
     // ---------------------------------------------------------- flush + epilogue
-    uint32_t ph_accfull = 0;
-    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    // warp w owns TMEM lanes / tile rows 32 w .. 32 w + 31 (one row per thread) and
+    // all 64 output columns: the int64 sums of columns 0..31 live in registers,
+    // those of columns 32..63 in TMEM columns COL_ACC_LO / COL_ACC_HI.
+    const uint32_t tb = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) tc::tmem_st8_splat(tb + 64u * w + 8u * j, MAGIC);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      tc::tmem_st8_splat(tb + COL_ACC_LO + 8u * j, 0u);
+      tc::tmem_st8_splat(tb + COL_ACC_HI + 8u * j, 0u);
+    }
+    tc::tmem_st_wait();
+    tc::fence_before_sync();
+    tc::mbar_arrive(&bar_accempty);
+
+    int64_t acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0;
+    uint32_t ph_af = 0;
     for (int64_t u = wk.u0; u < wk.u1; ++u) {
+      if (!wk.win_last(u)) continue;
       // lane 0 waits; the warp follows its decision (tcgen05.ld is warp-collective)
       bool ok = true;
-      if (lane == 0) ok = tc::mbar_wait(&bar_accfull, ph_accfull, WAIT_TRIES);
+      if (lane == 0) ok = tc::mbar_wait(&bar_accfull, ph_af, WAIT_TRIES);
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-      ph_accfull ^= 1u;
-      if (!ok) s_abort = 1;
-      if (!ok) break;
-      tc::fence_after_sync();
-      const bool fresh = wk.seg_first(u);
-#pragma unroll 1
-      for (int c0 = 0; c0 < NN; c0 += 16) {
-        uint32_t g0[16], g1[16], g2[16], g3[16], g4[16], lo[16], hi[16];
-        tc::tmem_ld16(trow + 0u + c0, g0);
-        tc::tmem_ld16(trow + 64u + c0, g1);
-        tc::tmem_ld16(trow + 128u + c0, g2);
-        tc::tmem_ld16(trow + 192u + c0, g3);
-        tc::tmem_ld16(trow + 256u + c0, g4);
-        if (!fresh) {
-          tc::tmem_ld16(trow + COL_ACC_LO + c0, lo);
-          tc::tmem_ld16(trow + COL_ACC_HI + c0, hi);
-        }
-        tc::tmem_ld_wait();
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int n0 = exact_int(g0[i], 1.0f);
-          const int n1 = exact_int(g1[i], 0x1p7f);
-          const int n2 = exact_int(g2[i], 0x1p14f);
-          const int n3 = exact_int(g3[i], 0x1p21f);
-          const int n4 = exact_int(g4[i], 0x1p28f);
-          const int64_t add = ((int64_t)n0 << 28) + ((int64_t)(n1 * 128 + n2) << 14) +
-                              (int64_t)(n3 * 128 + n4);
-          int64_t acc = fresh ? 0 : (int64_t)(((uint64_t)hi[i] << 32) | (uint64_t)lo[i]);
-          acc += add;
-          lo[i] = (uint32_t)((uint64_t)acc & 0xFFFFFFFFull);
-          hi[i] = (uint32_t)((uint64_t)acc >> 32);
-        }
-        tmem_st16(trow + COL_ACC_LO + c0, lo);
-        tmem_st16(trow + COL_ACC_HI + c0, hi);
+      ph_af ^= 1u;
+      if (!ok) {
+        s_abort = 1;
+        break;
       }
-      tmem_st_wait();
+      tc::fence_after_sync();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {  // 4 output columns at a time
+        const uint32_t c4 = 4u * j;
+        uint32_t g0[4], g1[4], g2[4], g3[4];
+        tc::tmem_ld4(tb + c4, g0);
+        tc::tmem_ld4(tb + 64u + c4, g1);
+        tc::tmem_ld4(tb + 128u + c4, g2);
+        tc::tmem_ld4(tb + 192u + c4, g3);
+        tc::tmem_ld_wait();
+        int64_t add[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          // (G_0 * 256 + G_1) and (G_2 * 256 + G_3), each exact in 32 bits
+          const int hi = (int)(g0[i] * 256u + g1[i] - 257u * MAGIC);
+          const int lo = (int)(g2[i] * 256u + g3[i] - 257u * MAGIC);
+          add[i] = ((int64_t)hi << 16) + (int64_t)lo;
+        }
+        tc::tmem_st4_splat(tb + c4, MAGIC);
+        tc::tmem_st4_splat(tb + 64u + c4, MAGIC);
+        tc::tmem_st4_splat(tb + 128u + c4, MAGIC);
+        tc::tmem_st4_splat(tb + 192u + c4, MAGIC);
+        if (j < 8) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[4 * j + i] += add[i];
+        } else {
+          uint32_t lo[4], hi[4];
+          tc::tmem_ld4(tb + COL_ACC_LO + c4 - 32u, lo);
+          tc::tmem_ld4(tb + COL_ACC_HI + c4 - 32u, hi);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const uint64_t t = (((uint64_t)hi[i] << 32) | lo[i]) + (uint64_t)add[i];
+            lo[i] = (uint32_t)t;
+            hi[i] = (uint32_t)(t >> 32);
+          }
+          tc::tmem_st4(tb + COL_ACC_LO + c4 - 32u, lo);
+          tc::tmem_st4(tb + COL_ACC_HI + c4 - 32u, hi);
+        }
+      }
+      tc::tmem_st_wait();
       if (wk.seg_last(u)) {
         const int64_t tile = wk.tile(u);
-        const bool full = (u - (a.kwins - 1) == tile * a.kwins) && (u - (a.kwins - 1) >= wk.u0);
-        const int pl = 32 * warp + lane;
-        const int64_t p = tile * TM + pl;
-        const int ep = p < a.P ? a.xE[p] : 0;
+        const bool full = (u + 1 - a.kst == tile * a.kst) && (tile * a.kst >= wk.u0);
+        const int r = 32 * warp + lane;
+        const int64_t p = tile * TM + r;
+        const int ep = p < a.P ? __ldg(a.xE + p) : 0;
         const int slot = (tile == first_tile) ? 0 : 1;
-        double* wrow = a.part + ((cta * 2 + slot) * TM + pl) * NN;
-#pragma unroll 1
-        for (int c0 = 0; c0 < NN; c0 += 16) {
-          uint32_t lo[16], hi[16], g5[16];
-          tc::tmem_ld16(trow + COL_ACC_LO + c0, lo);
-          tc::tmem_ld16(trow + COL_ACC_HI + c0, hi);
-          tc::tmem_ld16(trow + COL_G5 + c0, g5);
-          tc::tmem_ld_wait();
-          if (p < a.P) {
+        double* wp = a.part + (cta * 2 + slot) * (int64_t)(NN * TM) + r;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const int c = c0 + i;
-              if (c < a.N) {
-                const int64_t acc = (int64_t)(((uint64_t)hi[i] << 32) | (uint64_t)lo[i]);
-                const double sum = fma(__ll2double_rn(acc), 0x1p-28, (double)__uint_as_float(g5[i]));
-                const double v = ldexp(sum, ep + syE[c] - EXP_OFFSET);
-                if (full) {
-                  double* dst = a.C + p * a.csp + (int64_t)c * a.csc;
-                  *dst = (a.beta == 0.0) ? a.alpha * v : a.alpha * v + a.beta * (*dst);
-                } else {
-                  wrow[c] = v;
-                }
+        for (int j = 0; j < 16; ++j) {
+          const uint32_t c4 = 4u * j;
+          uint32_t g4[4], g5[4], g6[4], lo[4], hi[4];
+          tc::tmem_ld4(tb + 256u + c4, g4);
+          tc::tmem_ld4(tb + 320u + c4, g5);
+          tc::tmem_ld4(tb + 384u + c4, g6);
+          if (j >= 8) {
+            tc::tmem_ld4(tb + COL_ACC_LO + c4 - 32u, lo);
+            tc::tmem_ld4(tb + COL_ACC_HI + c4 - 32u, hi);
+          }
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int c = 4 * j + i;
+            int64_t T;
+            if (j < 8) {
+              T = acc[c];
+              acc[c] = 0;
+            } else {
+              T = (int64_t)(((uint64_t)hi[i] << 32) | lo[i]);
+            }
+            const double rest = (double)__uint_as_float(g4[i]) * 0x1p-32 +
+                                (double)__uint_as_float(g5[i]) * 0x1p-40 +
+                                (double)__uint_as_float(g6[i]) * 0x1p-48;
+            const double sum = fma(__ll2double_rn(T), 0x1p-24, rest);
+            if (p < a.P && c < a.N) {
+              const double val = ldexp(sum, ep + syE[c] - EXP_OFFSET);
+              if (full) {
+                double* dst = a.C + p * a.csp + (int64_t)c * a.csc;
+                *dst = (a.beta == 0.0) ? a.alpha * val : a.alpha * val + a.beta * (*dst);
+              } else {
+                wp[(int64_t)c * TM] = val;
               }
             }
           }
+          if (j >= 8) {
+            tc::tmem_st4_splat(tb + COL_ACC_LO + c4 - 32u, 0u);
+            tc::tmem_st4_splat(tb + COL_ACC_HI + c4 - 32u, 0u);
+          }
         }
+        tc::tmem_st_wait();
       }
       tc::fence_before_sync();
       tc::mbar_arrive(&bar_accempty);
@@ -498,26 +601,26 @@ constexpr int FIX_SPLIT = 32;
 
 __global__ void __launch_bounds__(256) k_oz_fixup(OzArgs a, int G) {
   const int64_t t = blockIdx.x;
-  const int64_t T = a.tiles * a.kwins;
+  const int64_t T = a.tiles * a.kst;
   auto owner = [&](int64_t u) {
     int64_t c = u * G / T;
     while (c + 1 < G && (c + 1) * T / G <= u) ++c;
     while (c > 0 && c * T / G > u) --c;
     return c;
   };
-  const int64_t cf = owner(t * a.kwins), cl = owner((t + 1) * a.kwins - 1);
+  const int64_t cf = owner(t * a.kst), cl = owner((t + 1) * a.kst - 1);
   if (cf == cl) return;
   constexpr int PER = TM * NN / FIX_SPLIT;
   for (int e = blockIdx.y * PER + threadIdx.x; e < (int)(blockIdx.y + 1) * PER; e += 256) {
-    const int r = e / NN, c = e % NN;
+    const int r = e % TM, c = e / TM;
     const int64_t p = t * TM + r;
     if (p >= a.P || c >= a.N) continue;
     double s = 0.0;
     for (int64_t q = cf; q <= cl; ++q) {
       const int64_t q0 = q * T / G, q1 = (q + 1) * T / G;
       if (q0 >= q1) continue;  // a CTA with an empty range wrote nothing
-      const int slot = (t == q0 / a.kwins) ? 0 : 1;
-      s += a.part[((q * 2 + slot) * TM + r) * NN + c];
+      const int slot = (t == q0 / a.kst) ? 0 : 1;
+      s += a.part[((q * 2 + slot) * NN + c) * TM + r];
     }
     double* dst = a.C + p * a.csp + (int64_t)c * a.csc;
     *dst = (a.beta == 0.0) ? a.alpha * s : a.alpha * s + a.beta * (*dst);
@@ -549,8 +652,8 @@ cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, co
                    int64_t ldx, const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
                    const OzWorkspace& w, int* flags, cudaStream_t st) {
   if (P <= 0 || N <= 0) return cudaSuccess;
-  if (N > NN || K <= 0) return cudaErrorInvalidValue;
-  const int64_t kwins = (K + KW - 1) / KW;
+  if (N > NN || K <= 0 || K > MAX_K) return cudaErrorInvalidValue;
+  const int64_t kst = (K + KS - 1) / KS;
   if (oz_img_bytes(K) > w.img_bytes) return cudaErrorInvalidValue;
   static bool attr_set[2] = {false, false};
   if (!attr_set[trans ? 1 : 0]) {
@@ -562,9 +665,8 @@ cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, co
   k_oz_colmaxexp<<<(unsigned)N, 256, 0, st>>>(Y, ldy, K, w.yE);
   cudaError_t e = launched();
   if (e != cudaSuccess) return e;
-  const int64_t ythreads = kwins * NN * 4;
-  k_oz_yslice<<<(unsigned)((ythreads + 255) / 256), 256, 0, st>>>(Y, ldy, K, (int)N, w.yE, w.img,
-                                                                  kwins);
+  const int64_t ythreads = kst * NN * 4;
+  k_oz_ycut<<<(unsigned)((ythreads + 255) / 256), 256, 0, st>>>(Y, ldy, K, (int)N, w.yE, w.img, kst);
   e = launched();
   if (e != cudaSuccess) return e;
   OzArgs a;
@@ -583,7 +685,7 @@ cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, co
   a.csc = out.csc;
   a.part = w.part;
   a.tiles = (P + TM - 1) / TM;
-  a.kwins = kwins;
+  a.kst = kst;
   a.flags = flags;
   a.vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (ldx % 2 == 0);
   const int G = w.ctas;

@@ -224,3 +224,21 @@ def test_full_size_bench_config():
         refc = A @ om.omega_dense(om.SPARSE_SIGN, j, n, 50, 1, zeta=8)
         assert maxrel(cols, refc) <= 1e-12
     f.close()
+
+
+@pytest.mark.parametrize("kind,p,zeta,P", [(om.SPARSE_SIGN, 0.0, 8, 0), (om.SPARSE_SIGN, 0.0, 8, 1),
+                                           (om.SPARSE_SIGN, 0.0, 8, 2), (om.GAUSSIAN, 0.0, 0, 1)],
+                         ids=["ss8_P0", "ss8_P1", "ss8_P2", "gauss_P1"])
+def test_full_passes_per_block(kind, p, zeta, P):
+    """Sec. 3 (cost model, Remark 3.4): past the sketch, a block streams A 2P + 1 times
+    (P power steps of two passes, then B_j); the sketch adds one more full pass only
+    for a dense Omega.  The phase profile counts the dense passes."""
+    A = low_rank_matrix(600, 400, "poly1.5", seed=31)
+    f = lra.Farpca(600, 400, eps=1e-2, b=16, P=P, kind=kind, zeta=zeta, p=p, seed=3, profile=True)
+    f.run(dev(A))
+    r = f.result()
+    ph = f.phase_times(reset=True)
+    assert r["blocks"] >= 2
+    assert ph["dense"][1] == r["blocks"] * (2 * P + 1)
+    assert ph["sketch"][1] == r["blocks"]
+    f.close()
