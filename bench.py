@@ -31,6 +31,11 @@ WORKLOADS = {
     # 20000 x 10000 FP64, sigma_i = 10^(-i/100) + 1e-6 N(0,1) noise; farPCASS zeta = 8, b = 50, P = 1
     "farpcass_20000x10000_exp100_zeta8_b50_P1_eps1e-2": dict(
         matrix="dense20000x10000_exp100", kind=SPARSE_SIGN, zeta=8, p=0.0, b=50, P=1, eps=1e-2, seed=1),
+    # 5000 x 5000 FP64, Matrix 1 of Sec. 5 (sigma_j = 1/j^2); farPCASS zeta = 8, b = 50, P = 1;
+    # Table 1's eps = 1e-4 (rank 350).  A (200 MB) is larger than L2 yet small enough for
+    # full ncu captures.
+    "farpcass_5000x5000_matrix1_zeta8_b50_P1_eps1e-4": dict(
+        matrix="matrix1_5000", kind=SPARSE_SIGN, zeta=8, p=0.0, b=50, P=1, eps=1e-4, seed=1),
     # 2000 x 1000 FP64, sigma_i = i^-1.5; farPCASS zeta = 8, b = 20, P = 1
     "farpcass_2000x1000_poly1.5_zeta8_b20_P1_eps1e-2": dict(
         matrix="dense2000x1000_poly1.5", kind=SPARSE_SIGN, zeta=8, p=0.0, b=20, P=1, eps=1e-2, seed=1),

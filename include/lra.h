@@ -71,7 +71,17 @@ typedef enum { LRA_F64 = 0, LRA_F32 = 1 } lra_dtype;
                                the context's stream (read with lra_phase_times)   */
 #define LRA_FLAG_FP64_SIMT 4u /* run the full passes over A as FP64 FMAs on the CUDA
                                cores instead of the FP64-accurate tensor-core GEMM
-                               (error-free bf16 slicing); ~60x slower on GB300     */
+                               (error-free 8-bit digit split); an order of
+                               magnitude slower on GB300                           */
+#define LRA_FLAG_NO_A_DIGITS 8u /* tensor-core engine: do not keep A's digit images.
+                               By default lra_create also allocates two images of A
+                               cut into seven f16 digits (row- and column-scaled,
+                               14 bytes per element each, 28 m n bytes in all) when
+                               the device has room; lra_farpca_run cuts A once into
+                               them (phase LRA_PHASE_CUT) and every full pass then
+                               streams the digits instead of cutting A again.  With
+                               this flag, or when the images do not fit, each pass
+                               cuts A on the fly (same results, bit for bit).     */
 
 /* Phases of one block, for lra_phase_times. */
 typedef enum {
@@ -83,7 +93,9 @@ typedef enum {
   LRA_PHASE_PROJECT = 4,    /* Q^T Y and Y - Q F, twice                            */
   LRA_PHASE_ORTH = 5,       /* Gram, Cholesky, triangular apply, twice             */
   LRA_PHASE_INDICATOR = 6,  /* ||A||_F^2, ||B_j||_F^2, append of B_j               */
-  LRA_NUM_PHASES = 7
+  LRA_PHASE_CUT = 7,        /* A cut into its digit images (once per run; see
+                               LRA_FLAG_NO_A_DIGITS)                              */
+  LRA_NUM_PHASES = 8
 } lra_phase;
 
 /* A borrowed, read-only dense matrix. */

@@ -54,12 +54,11 @@ cudaError_t omega_dense(const OmegaSpec& s, int64_t j0, int64_t nblk, double* Om
 
 // ---------------------------------------------------------------- sketch.cu
 // Y[i, g] = sum_t vals[g*cap+t] * X[i, rows[g*cap+t]] - (shift ? shift[i] : 0)
-// for i < rows_x, g < ncols; X column-major with ld ldx.  pm_scale > 0 declares
-// that every vals entry is +-pm_scale: columns of <= 16 entries are then summed
-// exactly in integer fixed point.
+// for i < rows_x, g < ncols; X column-major with ld ldx.  A bounded device wait
+// that gives up sets FLAG_TIMEOUT in *flags.
 cudaError_t gather_sketch(const double* X, int64_t ldx, int64_t rows_x, const int* counts,
                           const int* rows, const double* vals, int cap, int64_t ncols, double* Y,
-                          int64_t ldy, const double* shift, double pm_scale, cudaStream_t st);
+                          int64_t ldy, const double* shift, int* flags, cudaStream_t st);
 
 // ---------------------------------------------------------------- dgemm_simt.cu
 // C[p, c] = alpha * sum_k opX[p, k] Y[k, c] + beta * C[p, c], p < P, c < N <= 64.
@@ -92,6 +91,14 @@ int64_t oz_max_k();
 cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, const double* X,
                    int64_t ldx, const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
                    const OzWorkspace& w, int* flags, cudaStream_t st);
+// The digit image of op(X) (P x K): every (128-row tile, 32-deep stage) as seven
+// f16 digit planes, cut once and reused by ozgemm_img.  xE as for ozgemm.
+int64_t oz_ximg_bytes(int64_t P, int64_t K);
+cudaError_t oz_cut_x(bool trans, int64_t P, int64_t K, const double* X, int64_t ldx, const int* xE,
+                     uint8_t* ximg, int ctas, cudaStream_t st);
+cudaError_t ozgemm_img(int64_t P, int64_t N, int64_t K, double alpha, const uint8_t* ximg,
+                       const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
+                       const OzWorkspace& w, int* flags, cudaStream_t st);
 // rowE[r] / colE[c] = largest biased exponent in row r / column c of X (either may
 // be NULL).  accumulate_rows: rowE[r] = max(rowE[r], ...) instead of overwriting.
 cudaError_t oz_rowcol_exponents(const double* X, int64_t ld, int64_t rows, int64_t cols,

@@ -61,8 +61,10 @@ struct lra_ctx {
   int *browE = nullptr, *bcolE = nullptr;  // ... of B (rows: l_max, columns: n)
   int *xrowE = nullptr, *xcolE = nullptr;  // scratch for the operand of orth()
   OzWorkspace oz{};
+  // A cut into digit images: [0] row-scaled (A X), [1] column-scaled (A^T X)
+  uint8_t* ximg[2] = {nullptr, nullptr};
+  bool ximg_ready = false;
   int cap = 0;  // entries per Omega column in the sparse structure
-  double pm_scale = 0.0;  // > 0: every sparse Omega entry is +-pm_scale
   OmegaSpec os{};
   int64_t nblk_max = 0, lmax = 0, ldq = 0, ldb = 0, lds = 0, ldf = 0, ldod = 0;
 
@@ -162,7 +164,7 @@ lra_status check_params(lra_ctx* ctx, int64_t m, int64_t n, const lra_params* p)
   if (p->max_blocks < 0) return fail(ctx, LRA_ERR_INVALID_ARG, "max_blocks must be >= 0");
   if ((int64_t)p->max_blocks * p->b > mn)
     return fail(ctx, LRA_ERR_INVALID_ARG, "max_blocks * b exceeds min(m, n)");
-  if (p->flags & ~(LRA_FLAG_KEEP_Y | LRA_FLAG_PROFILE | LRA_FLAG_FP64_SIMT))
+  if (p->flags & ~(LRA_FLAG_KEEP_Y | LRA_FLAG_PROFILE | LRA_FLAG_FP64_SIMT | LRA_FLAG_NO_A_DIGITS))
     return fail(ctx, LRA_ERR_INVALID_ARG, "unknown flags");
   return LRA_OK;
 }
@@ -188,12 +190,18 @@ lra_status gemm(lra_ctx* ctx, bool trans, int64_t P, int64_t N, int64_t K, doubl
   return LRA_OK;
 }
 
-// A full pass over A: C = alpha op(A) Y + beta C (op(A) = A^T when trans).
+// A full pass over A: C = alpha op(A) Y + beta C (op(A) = A^T when trans).  Inside
+// lra_farpca_run the digit images of A, once cut, replace A itself.
 lra_status dense(lra_ctx* ctx, bool trans, int64_t N, double alpha, const double* A, int64_t lda,
                  const double* Y, int64_t ldy, double beta, double* C, int64_t csp, int64_t csc) {
   const int64_t P = trans ? ctx->n : ctx->m, K = trans ? ctx->m : ctx->n;
   if (!ctx->tensor || K > oz_max_k())
     return gemm(ctx, trans, P, N, K, alpha, A, lda, Y, ldy, beta, C, csp, csc);
+  if (ctx->ximg_ready) {
+    CK(ozgemm_img(P, N, K, alpha, ctx->ximg[trans ? 1 : 0], trans ? ctx->colE : ctx->rowE, Y, ldy,
+                  beta, GemmOut{C, csp, csc}, ctx->oz, ctx->flags, ctx->st));
+    return LRA_OK;
+  }
   CK(ozgemm(trans, P, N, K, alpha, A, lda, trans ? ctx->colE : ctx->rowE, Y, ldy, beta,
             GemmOut{C, csp, csc}, ctx->oz, ctx->flags, ctx->st));
   return LRA_OK;
@@ -270,7 +278,7 @@ lra_status apply_omega(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows_
                        int64_t ldo, const double* shift, bool x_is_A) {
   if (ctx->sparse) {
     CK(gather_sketch(X, ldx, rows_x, ctx->om_counts, ctx->om_rows, ctx->om_vals, ctx->cap, ctx->b,
-                     out, ldo, shift, ctx->pm_scale, ctx->st));
+                     out, ldo, shift, ctx->flags, ctx->st));
     return LRA_OK;
   }
   if (x_is_A) return dense(ctx, false, ctx->b, 1.0, X, ldx, ctx->om_dense, ctx->ldod, 0.0, out, 1, ldo);
@@ -330,6 +338,11 @@ lra_status read_record(lra_ctx* ctx) {
 }
 
 lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
+  // the digit images describe this run's A only: invalid on every way out
+  struct ImageScope {
+    lra_ctx* c;
+    ~ImageScope() { c->ximg_ready = false; }
+  } image_scope{ctx};
   const int64_t m = ctx->m, n = ctx->n, lds = ctx->lds, ldq = ctx->ldq, ldb = ctx->ldb,
                 ldf = ctx->ldf;
   const int b = ctx->b, P = ctx->P;
@@ -351,6 +364,14 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
     return LRA_OK;
   }
   PHASE(LRA_PHASE_INDICATOR, TRY(a_exponents(ctx, A, lda)));
+  ctx->ximg_ready = false;
+  if (ctx->ximg[0] && ctx->ximg[1]) {
+    PHASE(LRA_PHASE_CUT, {
+      CK(oz_cut_x(false, m, n, A, lda, ctx->rowE, ctx->ximg[0], ctx->oz.ctas, ctx->st));
+      CK(oz_cut_x(true, n, m, A, lda, ctx->colE, ctx->ximg[1], ctx->oz.ctas, ctx->st));
+    });
+    ctx->ximg_ready = true;
+  }
   if (ctx->tensor) {
     CK(cudaMemsetAsync(ctx->qrowE, 0, m * sizeof(int), ctx->st));
     CK(cudaMemsetAsync(ctx->bcolE, 0, n * sizeof(int), ctx->st));
@@ -468,7 +489,8 @@ void free_all(lra_ctx* c) {
                   c->colsq,  c->colsum,   c->scal,   c->flags,    c->om_counts, c->om_rows,
                   c->om_vals, c->om_dense, c->sk_counts, c->sk_rows, c->sk_vals, c->A_host_copy,
                   c->rowE,   c->colE,     c->oz.yE,  c->oz.img,   c->oz.part,
-                  c->qrowE,  c->qcolE,    c->browE,  c->bcolE,    c->xrowE,     c->xcolE};
+                  c->qrowE,  c->qcolE,    c->browE,  c->bcolE,    c->xrowE,     c->xcolE,
+                  c->ximg[0], c->ximg[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->hp) cudaFreeHost(c->hp);
@@ -553,10 +575,6 @@ lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
     ctx->cap = (int)n;
   }
   ctx->sb_sparse = ctx->sparse && params->kind == LRA_OMEGA_STD_BERNOULLI;
-  if (ctx->sparse && params->kind != LRA_OMEGA_SPARSE_GAUSSIAN)
-    ctx->pm_scale = (params->kind == LRA_OMEGA_SPARSE_SIGN || params->kind == LRA_OMEGA_SPARSE_SIGN_IID)
-                        ? os.inv_scale
-                        : 1.0;
 
   ctx->ldq = round_up(m, 2);
   ctx->ldb = round_up(std::max<int64_t>(ctx->lmax, 1), 2);
@@ -617,6 +635,16 @@ lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
     ALLOC(oz.yE, LRA_MAX_B);
     ALLOC(oz.img, ctx->oz.img_bytes);
     ALLOC(oz.part, oz_part_elems(ctx->oz.ctas));
+    // A's digit images when the device has room (else every pass cuts A itself)
+    if (!(params->flags & LRA_FLAG_NO_A_DIGITS)) {
+      const int64_t b0 = oz_ximg_bytes(m, n), b1 = oz_ximg_bytes(n, m);
+      if (cudaMalloc((void**)&ctx->ximg[0], b0) != cudaSuccess ||
+          cudaMalloc((void**)&ctx->ximg[1], b1) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->ximg[0]) cudaFree(ctx->ximg[0]);
+        ctx->ximg[0] = ctx->ximg[1] = nullptr;
+      }
+    }
   }
   if (ctx->sparse) {
     ALLOC(om_counts, b);
@@ -739,7 +767,7 @@ lra_status lra_sketch(lra_ctx* ctx, const lra_matrix* A, int64_t j0, int64_t nbl
                     ctx->flags, ctx->st));
     CK(gather_sketch(Ad, A->lda, ctx->m, ctx->sk_counts, ctx->sk_rows, ctx->sk_vals, ctx->cap,
                      nb * b, Y + (j - j0) * b * ldy, ldy, ctx->sb_sparse ? ctx->z : nullptr,
-                     ctx->pm_scale, ctx->st));
+                     ctx->flags, ctx->st));
   }
   return LRA_OK;
 }

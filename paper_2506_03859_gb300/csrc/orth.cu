@@ -59,55 +59,90 @@ __global__ void __launch_bounds__(1024) k_total(const double* __restrict__ v, in
   }
 }
 
-// Upper Cholesky R of S (b <= 64) computed row by row, as R[c, c] = sqrt(S_cc -
-// sum_k R_kc^2) and R[c, c'] = (S_cc' - sum_k R_kc R_kc') / R_cc, then R^{-1} by
-// back substitution, one column per thread.
-__global__ void __launch_bounds__(64) k_chol_inv(const double* __restrict__ S, int b, double tau,
-                                                 double* __restrict__ Rinv, int* __restrict__ flags) {
-  __shared__ double R[64][65];
+// Upper Cholesky R of S (b <= 64) and R^{-1}, right-looking so that every step is
+// one parallel update over the CTA: at column c the pivot d = S_cc - sum_{k<c} R_kc^2
+// (the trailing block already holds the subtracted sum) must pass d > tau * S_cc
+// (original diagonal) and be finite; with r = 1/sqrt(d), R_cc = d r and row c of R
+// is the pivot row times r; the trailing block loses the outer product of that
+// row.  R^{-1} by back substitution over rows, bottom up: row k of X is final once
+// scaled by r_k = 1/R_kk, then it is subtracted, times R_ik, from every row i < k.
+//
+// The FP64 pipe is narrow (a warp instruction occupies it for many cycles), so no
+// lane may idle: the trailing-update pairs (i, j), c < i <= j, are read from a
+// table of all pairs i <= j sorted by i descending -- those of step c are its
+// first (b - c)(b - c + 1) / 2 entries -- and the back-substitution pairs
+// (i < k <= j) are numbered densely, i = e mod k, j = k + e div k.
+__global__ void __launch_bounds__(256) k_chol_inv(const double* __restrict__ S, int b, double tau,
+                                                  double* __restrict__ Rinv, int* __restrict__ flags) {
+  __shared__ double M[64][65];
   __shared__ double X[64][65];
   __shared__ double Sd[64];
+  __shared__ double dinv[64];
+  __shared__ uint16_t pairs[64 * 65 / 2];  // (i << 8) | j, i <= j, i descending
   __shared__ int bad;
   const int t = threadIdx.x;
-  for (int i = 0; i < b; ++i)
-    if (t < b) R[i][t] = S[i + t * b];
+  for (int e = t; e < b * b; e += 256) {
+    const int i = e % b, j = e / b;
+    M[i][j] = S[i + j * b];
+    X[i][j] = (i == j) ? 1.0 : 0.0;
+  }
+  // entry e of the pair table: rows b-1, b-2, ... in turn, row i holding j = i..b-1;
+  // the rows above i (i' > i) take sum_{i' > i} (b - i') = (b-1-i)(b-i)/2 entries
+  for (int i = t; i < b; i += 256) {
+    const int base = (b - 1 - i) * (b - i) / 2;
+    for (int j = i; j < b; ++j) pairs[base + (j - i)] = (uint16_t)((i << 8) | j);
+  }
   if (t < b) Sd[t] = S[t + t * b];
   if (t == 0) bad = 0;
   __syncthreads();
   for (int c = 0; c < b; ++c) {
     if (t == 0) {
-      double d = R[c][c];
-      for (int k = 0; k < c; ++k) d -= R[k][c] * R[k][c];
-      if (!(isfinite(d) && d > tau * Sd[c]))
+      const double d = M[c][c];
+      if (!(isfinite(d) && d > tau * Sd[c])) {
         bad = 1;
-      else
-        R[c][c] = sqrt(d);
+      } else {
+        const double r = rsqrt(d);
+        M[c][c] = d * r;
+        dinv[c] = r;
+      }
     }
     __syncthreads();
     if (bad) break;
-    if (t > c && t < b) {
-      double v = R[c][t];
-      for (int k = 0; k < c; ++k) v -= R[k][c] * R[k][t];
-      R[c][t] = v / R[c][c];
+    const double r = dinv[c];
+    for (int j = c + 1 + t; j < b; j += 256) M[c][j] *= r;
+    __syncthreads();
+    const int nt = b - c - 1;
+    const int count = nt * (nt + 1) / 2;
+    for (int e = t; e < count; e += 256) {
+      const int ij = pairs[e], i = ij >> 8, j = ij & 255;
+      M[i][j] -= M[c][i] * M[c][j];
     }
     __syncthreads();
   }
   if (bad) {
     if (t == 0) atomicOr(flags, FLAG_BREAKDOWN);
-    for (int i = 0; i < b; ++i)
-      if (t < b) Rinv[i + t * b] = 0.0;
+    for (int e = t; e < b * b; e += 256) Rinv[e] = 0.0;
     return;
   }
-  if (t < b) {
-    const int jc = t;
-    for (int i = 0; i < b; ++i) X[i][jc] = 0.0;
-    X[jc][jc] = 1.0 / R[jc][jc];
-    for (int i = jc - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int k = i + 1; k <= jc; ++k) s += R[i][k] * X[k][jc];
-      X[i][jc] = -s / R[i][i];
+  for (int k = b - 1; k >= 0; --k) {
+    const double r = dinv[k];
+    for (int j = k + t; j < b; j += 256) X[k][j] *= r;
+    __syncthreads();
+    const int count = k * (b - k);
+    if (count > 0) {
+      const float kinv = 1.0f / (float)k;
+      for (int e = t; e < count; e += 256) {
+        int q = (int)(((float)e + 0.5f) * kinv);  // e div k (e < 4096: the float is exact enough)
+        const int i = e - q * k;
+        const int j = k + q;
+        X[i][j] -= M[i][k] * X[k][j];
+      }
     }
-    for (int i = 0; i < b; ++i) Rinv[i + jc * b] = X[i][jc];
+    __syncthreads();
+  }
+  for (int e = t; e < b * b; e += 256) {
+    const int i = e % b, j = e / b;
+    Rinv[i + j * b] = X[i][j];
   }
 }
 
@@ -141,7 +176,7 @@ cudaError_t total(const double* v, int64_t count, double* out, cudaStream_t st) 
 }
 
 cudaError_t chol_inv(const double* S, int b, double tau, double* Rinv, int* flags, cudaStream_t st) {
-  k_chol_inv<<<1, 64, 0, st>>>(S, b, tau, Rinv, flags);
+  k_chol_inv<<<1, 256, 0, st>>>(S, b, tau, Rinv, flags);
   return launched();
 }
 

@@ -5,17 +5,16 @@
 //
 // GB300's FP64 pipe delivers about 1.2 TFLOP/s, while such a pass streams A once
 // from HBM: run as FP64 FMAs it is ~60x slower than the memory bound.  Instead
-// every operand is cut, error-free, into bf16 slices (the splitting idea of
-// Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix
-// multiplication by using fast routines of matrix multiplication and its
-// applications", Numer. Algorithms 2012):
+// every operand is cut, error-free, into small integer digits that the 16-bit
+// tensor-core formats hold exactly (the splitting idea of Ozaki, Ogita, Oishi,
+// Rump, "Error-free transformations of matrix multiplication by using fast
+// routines of matrix multiplication and its applications", Numer. Algorithms 2012):
 //
 //   Scaling.  Row p of op(X) has largest biased exponent ex_p, column c of Y
 //   ey_c.  x is turned into the signed integer N = trunc(x 2^(1077 - ex_p)),
 //   |N| < 2^55, and written in base 256 with seven digits d_0..d_6 (d_0 the most
 //   significant): N = sum_s d_s 256^(6-s), d_0 in [-128, 128], d_1..6 in
-//   [-128, 127].  Every digit is an integer of at most 8 significant bits, exact
-//   in bf16.  Y is cut the same way into digits e_0..e_6.
+//   [-128, 127], stored as f16 (exact).  Y is cut the same way into e_0..e_6.
 //
 //   Products.  x y = 2^(ex + ey - 2058) sum_{s,t} d_s e_t 256^(-(s+t)).  The 28
 //   pairs of weight w = s + t <= 6 are kept (the dropped ones are below 2^-53 of
@@ -37,20 +36,23 @@
 // Tensor-core schedule.  Digit planes of Y are stored one after another in shared
 // memory, so one MMA with X plane s and Y planes t..t+c-1 (N = 64 c <= 256)
 // produces the weights s+t .. s+t+c-1 into adjacent TMEM column ranges: the 28
-// pairs take 11 MMAs per 16 values of K (4 for w <= 3, 7 for w >= 4).
+// pairs take 11 MMAs per 16 values of K (4 for w <= 3, 7 for w >= 4), one stage.
 //
-// Work split: one CTA per SM walks a contiguous range of (row tile, 32-deep
+// Work split: one CTA per SM walks a contiguous range of (row tile, 16-deep
 // stage) units ("stream-K"); tiles whose stages span two or more CTAs are
 // written as partial sums and combined by a fixup kernel in a fixed order.
 // Inside a CTA the work is pipelined by warp role: eight producer warps load a
-// 128 x 32 block of op(X) one stage ahead into registers, cut it into the seven
-// digit planes of a shared-memory stage (two stages, K-major core-matrix layout),
-// while a bulk copy brings the pre-cut 64 x 32 block of Y; one thread issues
+// 128 x 16 block of op(X) one stage ahead into registers, cut it into the seven
+// digit planes of a shared-memory stage (four stages, K-major core-matrix layout),
+// while a bulk copy brings the pre-cut 64 x 16 block of Y; one thread issues
 // the MMAs; four warps read the exact sums from TMEM at the end of each 64-deep
 // window, re-arm them, and write the tile.  The MMAs of weight >= 4 of a window
 // are issued before the wait for that re-arming, so the flush overlaps them.
 // mbarriers hand stages and accumulators between the roles; every wait is bounded.
+#include <cuda_fp16.h>
 #include <math.h>
+
+#include <algorithm>
 
 #include "internal.cuh"
 #include "tc_ptx.cuh"
@@ -60,7 +62,7 @@ namespace lra {
 namespace {
 constexpr int S = 7;                     // digits per operand
 constexpr int TM = 128;                  // rows of op(X) per tile
-constexpr int KS = 32;                   // K per pipeline stage
+constexpr int KS = 16;                   // K per pipeline stage (one MMA k-step)
 constexpr int NN = 64;                   // output columns (N padded)
 constexpr int NFLUSH = 128;              // flush threads (warps 0..3)
 constexpr int NPROD = 256;               // producer threads (warps 4..11)
@@ -70,9 +72,9 @@ constexpr int A_PLANE = TM * KS * 2;     // bytes of one digit plane of the op(X
 constexpr int Y_PLANE = NN * KS * 2;     // bytes of one digit plane of the Y block
 constexpr int Y_STAGE = S * Y_PLANE;     // the Y part of a stage (one bulk copy)
 constexpr int STAGE = S * A_PLANE + Y_STAGE;
-constexpr int NSTAGE = 2;
+constexpr int NSTAGE = 4;
 constexpr int SMEM_DYN = NSTAGE * STAGE + 1024;
-constexpr uint32_t LBO = 128, SBO = 512;  // core-matrix strides (K, rows)
+constexpr uint32_t LBO = 128, SBO = 256;  // core-matrix strides (K, rows)
 constexpr uint32_t TMEM_COLS = 512;       // weights 0..6: columns 0..447
 constexpr uint32_t COL_ACC_LO = 448, COL_ACC_HI = 480;  // int64 sums of output columns 32..63
 constexpr uint32_t MAGIC = 0x4B400000u;   // bits of 1.5 * 2^23
@@ -85,51 +87,48 @@ int64_t oz_img_bytes(int64_t K) { return (K + KS - 1) / KS * Y_STAGE; }
 int64_t oz_part_elems(int ctas) { return (int64_t)ctas * 2 * TM * NN; }
 int64_t oz_max_k() { return MAX_K; }
 
-// Offset of element (row, k), k < 32, in the K-major core-matrix layout of a
-// stage plane: core (row/8, k/8) at ((row/8)*4 + k/8)*128, row-major inside.
+// Offset of element (row, k), k < 16, in the K-major core-matrix layout of a
+// stage plane: core (row/8, k/8) at ((row/8)*2 + k/8)*128, row-major inside.
 __host__ __device__ __forceinline__ uint32_t core_offset(uint32_t row, uint32_t k) {
-  return (((row >> 3) << 2) + (k >> 3)) * 128u + (row & 7u) * 16u + (k & 7u) * 2u;
+  return (((row >> 3) << 1) + (k >> 3)) * 128u + (row & 7u) * 16u + (k & 7u) * 2u;
 }
 
 // N + BIAS as two 32-bit words, N = trunc(x 2^(1077 - emax)) (emax >= the
 // biased exponent of x; zero and subnormal x give 0) and BIAS = 128 in each of
-// the six low bytes: the bytes of N + BIAS, minus 128, are the base-256 digits
-// of N below the top one, and its bits 48.. (signed) are the top digit.
+// the seven low bytes.  N + BIAS >= 0; its six low bytes u_1..u_6 and its bits
+// 48.. (u_0 <= 256) give the digits d_s = u_s - 128 of N.  Branch-free: the
+// significand M (53 bits) is shifted to M << 10 and right by min(k, 63), which
+// clears it for every k >= 63.
 __device__ __forceinline__ void biased_fixed(double x, int emax, uint32_t& nh, uint32_t& nl) {
-  const uint32_t h = (uint32_t)__double2hiint(x), l = (uint32_t)__double2loint(x);
+  const uint64_t bits = (uint64_t)__double_as_longlong(x);
+  const uint32_t h = (uint32_t)(bits >> 32);
   const int E = (int)((h >> 20) & 0x7FFu);
-  const uint32_t mh = (h & 0x000FFFFFu) | 0x00100000u;  // significand M = mh:l
-  const uint32_t vh = __funnelshift_l(l, mh, 10);      // M << 10, high word
-  const uint32_t vl = l << 10;
-  const int k = (E != 0 ? emax - E : 64) + 8;          // |N| = (M << 10) >> k
-  uint32_t rh, rl;
-  if (k < 32) {
-    rl = __funnelshift_r(vl, vh, k);
-    rh = vh >> k;
-  } else {
-    rl = k < 64 ? vh >> (k - 32) : 0u;
-    rh = 0u;
-  }
-  const uint32_t s = (uint32_t)((int)h >> 31);  // 0, or all ones for negative x
-  uint64_t v = ((uint64_t)(rh ^ s) << 32) | (uint64_t)(rl ^ s);
-  v += 0x0000808080808080ull + (uint64_t)(s & 1u);  // two's complement, plus BIAS
+  const uint64_t M = (bits & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  const int k = min(E != 0 ? emax - E + 8 : 63, 63);
+  const uint64_t a = (M << 10) >> k;                     // |N|
+  const uint64_t sgn = (uint64_t)((int64_t)(int)h >> 63);  // 0, or all ones for negative x
+  const uint64_t v = (a ^ sgn) + (0x0080808080808080ull + (sgn & 1u));
   nh = (uint32_t)(v >> 32);
   nl = (uint32_t)v;
 }
 
-// Digit SL (0 = most significant) of (nh, nl) as a float: the byte is dropped
-// into the mantissa of 2^23 and 2^23 + 128 subtracted, exactly.
+// Digit SL (0 = most significant) of two values a, b as a packed f16 pair (a in
+// the low half): the digit bytes (u + 1024 as f16 bits, i.e. 0x64uu) are built
+// by a byte permute and a mask, and one packed f16 subtract removes 1024 + 128;
+// every step is exact.
 template <int SL>
-__device__ __forceinline__ float digit_f(uint32_t nh, uint32_t nl) {
-  if (SL == 0) return __int_as_float(0x4B000080 + ((int)nh >> 16)) - 8388736.0f;
-  const uint32_t w = (SL <= 2) ? nh : nl;
-  constexpr uint32_t byte = (SL <= 2) ? (2 - SL) : (6 - SL);
-  return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7650u | byte)) - 8388736.0f;
-}
-
-// Two floats holding bf16-exact values -> packed bf16 pair (lo in the low half).
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632u);
+__device__ __forceinline__ uint32_t digit_pair(uint32_t ha, uint32_t la, uint32_t hb, uint32_t lb) {
+  uint32_t w;
+  if (SL == 0) {
+    w = __byte_perm(ha, hb, 0x7632u) + 0x64006400u;  // 16-bit top parts (<= 256) + 1024
+  } else {
+    constexpr uint32_t byte = (SL <= 2) ? (2 - SL) : (6 - SL);
+    const uint32_t xa = (SL <= 2) ? ha : la, xb = (SL <= 2) ? hb : lb;
+    w = (__byte_perm(xa, xb, byte | (byte << 4) | ((byte + 4) << 8) | ((byte + 4) << 12)) &
+         0x00FF00FFu) | 0x64006400u;
+  }
+  const __half2 r = __hsub2(*reinterpret_cast<const __half2*>(&w), __half2(__half(1152.0f), __half(1152.0f)));
+  return *reinterpret_cast<const uint32_t*>(&r);
 }
 
 // Eight consecutive K values of one row (or column) -> one 16-byte chunk in each
@@ -138,14 +137,14 @@ __device__ __forceinline__ void cut8(const double* v, int emax, uint8_t* dst, in
   uint32_t h[8], l[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) biased_fixed(v[i], emax, h[i], l[i]);
-#define LRA_CUT(SL)                                                                   \
-  {                                                                                   \
-    uint4 q;                                                                          \
-    q.x = pack_bf16(digit_f<SL>(h[0], l[0]), digit_f<SL>(h[1], l[1]));                \
-    q.y = pack_bf16(digit_f<SL>(h[2], l[2]), digit_f<SL>(h[3], l[3]));                \
-    q.z = pack_bf16(digit_f<SL>(h[4], l[4]), digit_f<SL>(h[5], l[5]));                \
-    q.w = pack_bf16(digit_f<SL>(h[6], l[6]), digit_f<SL>(h[7], l[7]));                \
-    *reinterpret_cast<uint4*>(dst + (SL) * plane) = q;                                \
+#define LRA_CUT(SL)                                                   \
+  {                                                                   \
+    uint4 q;                                                          \
+    q.x = digit_pair<SL>(h[0], l[0], h[1], l[1]);                     \
+    q.y = digit_pair<SL>(h[2], l[2], h[3], l[3]);                     \
+    q.z = digit_pair<SL>(h[4], l[4], h[5], l[5]);                     \
+    q.w = digit_pair<SL>(h[6], l[6], h[7], l[7]);                     \
+    *reinterpret_cast<uint4*>(dst + (SL) * plane) = q;                \
   }
   LRA_CUT(0) LRA_CUT(1) LRA_CUT(2) LRA_CUT(3) LRA_CUT(4) LRA_CUT(5) LRA_CUT(6)
 #undef LRA_CUT
@@ -153,13 +152,17 @@ __device__ __forceinline__ void cut8(const double* v, int emax, uint8_t* dst, in
 
 // ---------------------------------------------------------------- prep kernels
 
-// out[c] = largest biased exponent of X[:, c] (one CTA per column).
+// out[c] = largest biased exponent of X[:, c] (out pre-zeroed): CTA (c, y) scans
+// rows [y rchunk, (y + 1) rchunk) of column c.
 __global__ void __launch_bounds__(256) k_oz_colmaxexp(const double* __restrict__ X, int64_t ld,
-                                                      int64_t rows, int* __restrict__ out) {
+                                                      int64_t rows, int64_t rchunk,
+                                                      int* __restrict__ out) {
   __shared__ int red[8];
   const int64_t c = blockIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.y * rchunk;
+  const int64_t r1 = (r0 + rchunk < rows) ? r0 + rchunk : rows;
   int e = 0;
-  for (int64_t i = threadIdx.x; i < rows; i += 256) {
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += 256) {
     const uint64_t b = (uint64_t)__double_as_longlong(__ldg(X + i + c * ld));
     e = max(e, (int)((b >> 52) & 0x7FFu));
   }
@@ -169,8 +172,19 @@ __global__ void __launch_bounds__(256) k_oz_colmaxexp(const double* __restrict__
   if (threadIdx.x == 0) {
     int t = 0;
     for (int q = 0; q < 8; ++q) t = max(t, red[q]);
-    out[c] = t;
+    atomicMax(out + c, t);
   }
+}
+
+// Column exponents of X (rows x cols): zero out, then the split scan.
+cudaError_t colmaxexp(const double* X, int64_t ld, int64_t rows, int64_t cols, int* out,
+                      cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, cols * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const int64_t rchunk = 4096;
+  dim3 grid((unsigned)cols, (unsigned)((rows + rchunk - 1) / rchunk));
+  k_oz_colmaxexp<<<grid, 256, 0, st>>>(X, ld, rows, rchunk, out);
+  return launched();
 }
 
 // out[r] = max over the columns of X[r, :] of the biased exponent (out pre-zeroed).
@@ -189,17 +203,17 @@ __global__ void __launch_bounds__(256) k_oz_rowmaxexp(const double* __restrict__
   atomicMax(out + r, e);
 }
 
-// Pre-cut Y: stage u of the image holds the seven 64 x 32 (N x K) digit planes
-// of K values 32u .. 32u + 31 in the core-matrix layout.  One thread per
+// Pre-cut Y: stage u of the image holds the seven 64 x 16 (N x K) digit planes
+// of K values 16u .. 16u + 15 in the core-matrix layout.  One thread per
 // (stage, column c, 8-wide k chunk j).
 __global__ void __launch_bounds__(256) k_oz_ycut(const double* __restrict__ Y, int64_t ldy,
                                                  int64_t K, int N, const int* __restrict__ yE,
                                                  uint8_t* __restrict__ img, int64_t kst) {
   const int64_t idx = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  if (idx >= kst * NN * 4) return;
-  const int j = (int)(idx & 3);
-  const int c = (int)((idx >> 2) & (NN - 1));
-  const int64_t u = idx >> 8;
+  if (idx >= kst * NN * 2) return;
+  const int j = (int)(idx & 1);
+  const int c = (int)((idx >> 1) & (NN - 1));
+  const int64_t u = idx >> 7;
   const int emax = c < N ? yE[c] : 0;
   double v[8];
 #pragma unroll
@@ -226,240 +240,253 @@ struct OzArgs {
   int64_t tiles, kst;  // row tiles; 32-deep stages per tile
   int* flags;
   bool vec;            // 16-byte loads allowed (trans layout)
+  bool whole_tiles;    // ranges hold whole tiles: no tile is split, no fixup
 };
+
+// The range [u0, u1) of CTA cta of G: an even share of all units ("stream-K"),
+// or, with whole_tiles, an even share of whole tiles.
+__device__ __forceinline__ void cta_range(const OzArgs& a, int64_t cta, int64_t G, int64_t& u0,
+                                          int64_t& u1) {
+  if (a.whole_tiles) {
+    u0 = (cta * a.tiles / G) * a.kst;
+    u1 = ((cta + 1) * a.tiles / G) * a.kst;
+  } else {
+    const int64_t T = a.tiles * a.kst;
+    u0 = cta * T / G;
+    u1 = (cta + 1) * T / G;
+  }
+}
 
 // The CTA's stages: a contiguous range [u0, u1) of (tile, stage) units,
-// tile-major.  A segment is the part of the range inside one tile; a window is
-// one or two consecutive stages of a segment, aligned to even stage indices.
-struct Walk {
-  int64_t u0, u1, kst;
-  __device__ __forceinline__ int64_t tile(int64_t u) const { return u / kst; }
-  __device__ __forceinline__ bool seg_first(int64_t u) const { return u == u0 || u % kst == 0; }
-  __device__ __forceinline__ bool seg_last(int64_t u) const {
-    return u + 1 == u1 || (u + 1) % kst == 0;
+// tile-major, walked with a (tile, stage-in-tile) cursor.  A segment is the part
+// of the range inside one tile; a window is up to four consecutive stages (64
+// values of K) of a segment, aligned to stage indices divisible by four.
+struct Cursor {
+  int64_t tile;   // row tile of the current unit
+  int ks;         // its stage within the tile
+  int64_t i;      // its index within the CTA's range
+  int64_t n;      // units in the range
+  int kst;        // stages per tile
+  __device__ __forceinline__ void next() {
+    ++i;
+    if (++ks == kst) {
+      ks = 0;
+      ++tile;
+    }
   }
-  __device__ __forceinline__ bool win_first(int64_t u) const {
-    return seg_first(u) || ((u % kst) & 1) == 0;
-  }
-  __device__ __forceinline__ bool win_last(int64_t u) const {
-    return seg_last(u) || ((u % kst) & 1) == 1;
-  }
+  __device__ __forceinline__ bool seg_first() const { return i == 0 || ks == 0; }
+  __device__ __forceinline__ bool seg_last() const { return i + 1 == n || ks + 1 == kst; }
+  __device__ __forceinline__ bool win_first() const { return seg_first() || (ks & 3) == 0; }
+  __device__ __forceinline__ bool win_last() const { return seg_last() || (ks & 3) == 3; }
 };
 
-// A producer thread's share of one stage: 16 values of op(X).  TRANS == false:
-// op(X)[p, k] = X[p + k*ldx], the thread takes row 32 (pw % 4) + lane and 16
+// A producer thread's share of one stage: 8 values of op(X).  TRANS == false:
+// op(X)[p, k] = X[p + k*ldx], the thread takes row 32 (pw % 4) + lane and 8
 // consecutive k (coalesced across the warp).  TRANS == true: op(X)[p, k] =
 // X[k + p*ldx]; each warp instruction covers one 8 x 8 core matrix, lane ->
-// (row r8 = lane % 8, k pair lane / 8).
+// (row r8 = lane % 8, k pair lane / 8): values 2i, 2i+1 belong to row
+// 8 (pw / 2 + 4 i) + r8 and k 8 (pw % 2) + 2 (lane / 8) + {0, 1}.
+constexpr int VPT = TM * KS / NPROD;  // values per producer thread per stage
+
 template <bool TRANS>
-__device__ __forceinline__ void fetch(const OzArgs& a, int64_t u, int pw, int lane, double (&v)[16]) {
-  const int64_t tile = u / a.kst, k0 = (u % a.kst) * KS;
+__device__ __forceinline__ void fetch(const OzArgs& a, int64_t tile, int ks, int pw, int lane,
+                                      double (&v)[VPT]) {
   if (!TRANS) {
-    const int64_t p = tile * TM + 32 * (pw & 3) + lane, kb = k0 + 16 * (pw >> 2);
-    const bool in = p < a.P;
+    const int64_t p = tile * TM + 32 * (pw & 3) + lane, kb = (int64_t)ks * KS + 8 * (pw >> 2);
+    const double* src = a.X + p + kb * a.ldx;
+    if (p < a.P && kb + 8 <= a.K) {
 #pragma unroll
-    for (int i = 0; i < 16; ++i)
-      v[i] = (in && kb + i < a.K) ? __ldg(a.X + p + (kb + i) * a.ldx) : 0.0;
+      for (int i = 0; i < 8; ++i) {
+        v[i] = __ldg(src);
+        src += a.ldx;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        v[i] = (p < a.P && kb + i < a.K) ? __ldg(src + i * a.ldx) : 0.0;
+    }
   } else {
     const int r8 = lane & 7, q = lane >> 3;
+    const int64_t p0 = tile * TM + (pw >> 1) * 8 + r8, k = (int64_t)ks * KS + (pw & 1) * 8 + 2 * q;
+    const double* src = a.X + k + p0 * a.ldx;
+    if (a.vec && tile * TM + TM <= a.P && k + 2 <= a.K) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int core = pw + 8 * i, rg = core >> 2, kc = core & 3;
-      const int64_t p = tile * TM + rg * 8 + r8, k = k0 + kc * 8 + 2 * q;
-      v[2 * i] = 0.0;
-      v[2 * i + 1] = 0.0;
-      if (p < a.P) {
-        const double* src = a.X + k + p * a.ldx;
-        if (a.vec && k + 1 < a.K) {
-          const double2 t = __ldg(reinterpret_cast<const double2*>(src));
-          v[2 * i] = t.x;
-          v[2 * i + 1] = t.y;
-        } else {
-          if (k < a.K) v[2 * i] = __ldg(src);
-          if (k + 1 < a.K) v[2 * i + 1] = __ldg(src + 1);
-        }
+      for (int i = 0; i < 4; ++i) {
+        const double2 t = __ldg(reinterpret_cast<const double2*>(src));
+        v[2 * i] = t.x;
+        v[2 * i + 1] = t.y;
+        src += 32 * a.ldx;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const bool in = p0 + 32 * i < a.P;
+        const double* s2 = src + 32 * i * a.ldx;
+        v[2 * i] = (in && k < a.K) ? __ldg(s2) : 0.0;
+        v[2 * i + 1] = (in && k + 1 < a.K) ? __ldg(s2 + 1) : 0.0;
       }
     }
   }
 }
 
-// Cut the thread's 16 values into the stage; sE = row exponents of the tile.
+// Cut the thread's 8 values into the stage; sE = row exponents of the tile.
 template <bool TRANS>
-__device__ __forceinline__ void cut_stage(const double (&v)[16], const int* sE, uint8_t* sA, int pw,
+__device__ __forceinline__ void cut_stage(const double (&v)[VPT], const int* sE, uint8_t* sA, int pw,
                                           int lane) {
   if (!TRANS) {
-    const uint32_t row = 32 * (pw & 3) + lane, kb = 16 * (pw >> 2);
-    const int e = sE[row];
-    cut8(v, e, sA + core_offset(row, kb), A_PLANE);
-    cut8(v + 8, e, sA + core_offset(row, kb + 8), A_PLANE);
+    const uint32_t row = 32 * (pw & 3) + lane, kb = 8 * (pw >> 2);
+    cut8(v, sE[row], sA + core_offset(row, kb), A_PLANE);
   } else {
     const int r8 = lane & 7, q = lane >> 3;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int core = pw + 8 * i;
-      const int e = sE[(core >> 2) * 8 + r8];
+    for (int i = 0; i < 4; ++i) {
+      const int core = pw + 8 * i;  // row group core / 2 = pw / 2 + 4 i, k group pw % 2
+      const int e = sE[(core >> 1) * 8 + r8];
       uint8_t* dst = sA + core * 128 + r8 * 16 + q * 4;
       uint32_t h0, l0, h1, l1;
       biased_fixed(v[2 * i], e, h0, l0);
       biased_fixed(v[2 * i + 1], e, h1, l1);
 #define LRA_CUT2(SL) \
-  *reinterpret_cast<uint32_t*>(dst + (SL) * A_PLANE) = pack_bf16(digit_f<SL>(h0, l0), digit_f<SL>(h1, l1));
+  *reinterpret_cast<uint32_t*>(dst + (SL) * A_PLANE) = digit_pair<SL>(h0, l0, h1, l1);
       LRA_CUT2(0) LRA_CUT2(1) LRA_CUT2(2) LRA_CUT2(3) LRA_CUT2(4) LRA_CUT2(5) LRA_CUT2(6)
 #undef LRA_CUT2
     }
   }
 }
 
-// One MMA of X digit plane s against Y planes t0 .. t0+c-1 into the weight
-// columns 64 (s + t0) .. ; kk selects the 16-deep half of the stage.
+// One MMA of X digit plane s against Y planes t0 .. t0+c-1 (N = 64 c) into the
+// weight columns 64 (s + t0) .. 64 (s + t0 + c) - 1, over the stage's 16 values of K.
 __device__ __forceinline__ void mma_group(uint32_t tmem, uint32_t a0, uint32_t y0, int s, int t0,
-                                          int c, int kk, uint32_t accumulate) {
-  const uint32_t idesc = tc::idesc_bf16_f32(TM, 64u * (uint32_t)c);
-  tc::mma_bf16(tmem + 64u * (uint32_t)(s + t0),
-               tc::desc_k_none(a0 + (uint32_t)s * A_PLANE + 256u * kk, LBO, SBO),
-               tc::desc_k_none(y0 + (uint32_t)t0 * Y_PLANE + 256u * kk, LBO, SBO), idesc, accumulate);
+                                          int c, uint32_t accumulate) {
+  const uint32_t idesc = tc::idesc_f16_f32(TM, 64u * (uint32_t)c);
+  tc::mma_f16(tmem + 64u * (uint32_t)(s + t0), tc::desc_k_none(a0 + (uint32_t)s * A_PLANE, LBO, SBO),
+              tc::desc_k_none(y0 + (uint32_t)t0 * Y_PLANE, LBO, SBO), idesc, accumulate);
 }
 
-template <bool TRANS>
-__global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
-  extern __shared__ uint8_t smem_raw[];
-  __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t bar_full[NSTAGE], bar_empty[NSTAGE], bar_accfull, bar_accempty;
-  __shared__ int syE[NN];
-  __shared__ int sEx[2][TM];  // producers: row exponents of tiles (by tile parity)
-  __shared__ volatile int s_abort;
-  __shared__ volatile int s_pgo[2];  // producers: go on with iteration i (slot i % 2)
-  const uint32_t raw = tc::smem_addr(smem_raw);
-  uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+// Barriers, TMEM address and small tables a CTA's roles share.
+struct OzShared {
+  uint64_t full[NSTAGE], empty[NSTAGE], accfull, accempty;
+  uint32_t tmem;
+  int abort;
+  int yE[NN];
+};
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t T = a.tiles * a.kst;
-  const int64_t G = gridDim.x, cta = blockIdx.x;
-  const Walk wk{cta * T / G, (cta + 1) * T / G, a.kst};
-  if (wk.u0 >= wk.u1) return;
-
-  if (warp == 0) tc::tmem_alloc(&s_tmem, TMEM_COLS);
+// Set-up common to both kernels: TMEM (warp 0), barriers (thread 0), Y exponents.
+// full_count: arrivals that complete a stage.
+__device__ __forceinline__ void oz_setup(OzShared& sh, const OzArgs& a, int full_count) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) tc::tmem_alloc(&sh.tmem, TMEM_COLS);
   if (tid == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
-      tc::mbar_init(&bar_full[s], NPROD + 1);  // + the arrival that carries the Y bytes
-      tc::mbar_init(&bar_empty[s], 1);
+      tc::mbar_init(&sh.full[s], full_count);
+      tc::mbar_init(&sh.empty[s], 1);
     }
-    tc::mbar_init(&bar_accfull, 1);
-    tc::mbar_init(&bar_accempty, NFLUSH);
-    s_abort = 0;
+    tc::mbar_init(&sh.accfull, 1);
+    tc::mbar_init(&sh.accempty, NFLUSH);
+    sh.abort = 0;
   }
-  if (tid < NN) syE[tid] = tid < a.N ? a.yE[tid] : 0;
+  if (tid < NN) sh.yE[tid] = tid < a.N ? a.yE[tid] : 0;
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  const uint32_t tmem = s_tmem;
-  const int64_t first_tile = wk.tile(wk.u0);
+}
 
-  if (warp >= 4 && warp < MMA_WARP) {
-    // ---------------------------------------------------------- producers
-    const int pt = tid - NFLUSH, pw = pt >> 5;
-    uint32_t ph_empty[NSTAGE] = {0, 0};
-    // row exponents of a tile in sEx[tile % 2], written while the first stage of
-    // the tile is fetched (one iteration ahead of its use, behind a named barrier)
-    auto load_exps = [&](int64_t tile) {
-      if (pt < TM) {
-        const int64_t p = tile * TM + pt;
-        sEx[tile & 1][pt] = p < a.P ? __ldg(a.xE + p) : 0;
+__device__ __forceinline__ void oz_teardown(OzShared& sh, const OzArgs& a) {
+  tc::fence_before_sync();
+  __syncthreads();
+  if (sh.abort && threadIdx.x == 0) atomicOr(a.flags, FLAG_TIMEOUT);
+  if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(sh.tmem, TMEM_COLS);
+}
+
+// The MMA issuer (one thread).  Per stage: the weight >= 4 MMAs (FP32 over the
+// segment; the first MMA of a segment starts them), then the exact weights 0..3,
+// which at a window start must wait until the flush has read and re-armed them.
+// To hide that wait the first two stages of a window are issued together: both
+// stages' weight >= 4 MMAs, the wait, then both stages' exact MMAs.  A new
+// segment first waits for the flush to finish the previous one (its FP32 sums).
+__device__ __forceinline__ void oz_mma_role(OzShared& sh, const Cursor& start, uint8_t* sm) {
+  volatile int& s_abort = sh.abort;
+  const uint32_t tmem = sh.tmem;
+  uint32_t ph_full[NSTAGE] = {0, 0, 0, 0}, ph_ae = 0;
+  auto wait_full = [&](int st) -> bool {
+    if (!tc::mbar_wait(&sh.full[st], ph_full[st], WAIT_TRIES)) return false;
+    ph_full[st] ^= 1u;
+    tc::fence_after_sync();
+    return true;
+  };
+  auto wait_accempty = [&]() -> bool {
+    if (!tc::mbar_wait(&sh.accempty, ph_ae, WAIT_TRIES)) return false;
+    ph_ae ^= 1u;
+    tc::fence_after_sync();
+    return true;
+  };
+  auto high = [&](int st, bool fresh) {
+    const uint32_t a0 = tc::smem_addr(sm + st * STAGE), y0 = a0 + S * A_PLANE;
+    mma_group(tmem, a0, y0, 0, 4, 3, fresh ? 0u : 1u);
+    mma_group(tmem, a0, y0, 1, 3, 3, 1u);
+    mma_group(tmem, a0, y0, 2, 2, 3, 1u);
+    mma_group(tmem, a0, y0, 3, 1, 3, 1u);
+    mma_group(tmem, a0, y0, 4, 0, 3, 1u);
+    mma_group(tmem, a0, y0, 5, 0, 2, 1u);
+    mma_group(tmem, a0, y0, 6, 0, 1, 1u);
+  };
+  auto exact = [&](int st) {
+    const uint32_t a0 = tc::smem_addr(sm + st * STAGE), y0 = a0 + S * A_PLANE;
+    mma_group(tmem, a0, y0, 0, 0, 4, 1u);
+    mma_group(tmem, a0, y0, 1, 0, 3, 1u);
+    mma_group(tmem, a0, y0, 2, 0, 2, 1u);
+    mma_group(tmem, a0, y0, 3, 0, 1, 1u);
+    tc::mma_commit(&sh.empty[st]);
+  };
+  Cursor c = start;
+  while (c.i < c.n) {
+    const int st = (int)(c.i % NSTAGE);
+    if (!wait_full(st)) break;
+    const bool sf = c.seg_first();
+    if (sf && !wait_accempty()) break;
+    high(st, sf);
+    if (c.win_first() && !sf) {
+      if (!c.win_last()) {  // pair with the window's second stage
+        Cursor d = c;
+        d.next();
+        const int st2 = (int)(d.i % NSTAGE);
+        if (!wait_full(st2)) break;
+        high(st2, false);
+        if (!wait_accempty()) break;
+        exact(st);
+        exact(st2);
+        if (d.win_last()) tc::mma_commit(&sh.accfull);
+        c = d;
+        c.next();
+        continue;
       }
-    };
-    double v[16];
-    load_exps(wk.tile(wk.u0));
-    fetch<TRANS>(a, wk.u0, pw, lane, v);
-    for (int64_t u = wk.u0, i = 0; u < wk.u1; ++u, ++i) {
-      const int st = (int)(i & 1);
-      // Thread 0 waits for the stage and decides whether to go on; the decision is
-      // published in slot i % 2 before the named barrier and read after it, so all
-      // producers leave the loop in the same iteration (slot i % 2 is next written
-      // in iteration i + 2, after every producer has passed barrier i + 1).
-      if (pt == 0) {
-        bool go = s_abort == 0;
-        if (go && i >= NSTAGE) go = tc::mbar_wait(&bar_empty[st], ph_empty[st], WAIT_TRIES);
-        if (!go) s_abort = 1;
-        s_pgo[i & 1] = go ? 1 : 0;
-      }
-      if (i >= NSTAGE) ph_empty[st] ^= 1u;
-      tc::named_sync(1, NPROD);
-      if (!s_pgo[i & 1]) break;
-      uint8_t* sA = sm + st * STAGE;
-      if (pt == 0) {
-        tc::mbar_arrive_expect_tx(&bar_full[st], Y_STAGE);
-        tc::bulk_g2s(sA + S * A_PLANE, a.img + (u % a.kst) * (int64_t)Y_STAGE, Y_STAGE,
-                     &bar_full[st]);
-      }
-      // next stage's values are in flight while this one is cut
-      double vn[16];
-      if (u + 1 < wk.u1) {
-        if (wk.tile(u + 1) != wk.tile(u)) load_exps(wk.tile(u + 1));
-        fetch<TRANS>(a, u + 1, pw, lane, vn);
-      }
-      cut_stage<TRANS>(v, sEx[wk.tile(u) & 1], sA, pw, lane);
-      tc::fence_async_smem();
-      tc::mbar_arrive(&bar_full[st]);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = vn[q];
+      if (!wait_accempty()) break;
     }
-  } else if (warp == MMA_WARP) {
-    // ---------------------------------------------------------- MMA issuer (one thread)
-    if (lane == 0) {
-      uint32_t ph_full[NSTAGE] = {0, 0}, ph_ae = 0;
-      for (int64_t u = wk.u0, i = 0; u < wk.u1; ++u, ++i) {
-        const int st = (int)(i & 1);
-        if (!tc::mbar_wait(&bar_full[st], ph_full[st], WAIT_TRIES)) {
-          s_abort = 1;
-          break;
-        }
-        ph_full[st] ^= 1u;
-        tc::fence_after_sync();
-        const bool sf = wk.seg_first(u);
-        // a new segment: the flush must have read the previous one's FP32 sums
-        if (sf) {
-          if (!tc::mbar_wait(&bar_accempty, ph_ae, WAIT_TRIES)) {
-            s_abort = 1;
-            break;
-          }
-          ph_ae ^= 1u;
-          tc::fence_after_sync();
-        }
-        const uint32_t a0 = tc::smem_addr(sm + st * STAGE);
-        const uint32_t y0 = a0 + S * A_PLANE;
-        // weights 4..6 (FP32 over the segment); the first MMA of a segment starts them
-#pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
-          mma_group(tmem, a0, y0, 0, 4, 3, kk, (sf && kk == 0) ? 0u : 1u);
-          mma_group(tmem, a0, y0, 1, 3, 3, kk, 1u);
-          mma_group(tmem, a0, y0, 2, 2, 3, kk, 1u);
-          mma_group(tmem, a0, y0, 3, 1, 3, kk, 1u);
-          mma_group(tmem, a0, y0, 4, 0, 3, kk, 1u);
-          mma_group(tmem, a0, y0, 5, 0, 2, kk, 1u);
-          mma_group(tmem, a0, y0, 6, 0, 1, kk, 1u);
-        }
-        // weights 0..3 (exact per window): wait until the flush has re-armed them
-        if (wk.win_first(u) && !sf) {
-          if (!tc::mbar_wait(&bar_accempty, ph_ae, WAIT_TRIES)) {
-            s_abort = 1;
-            break;
-          }
-          ph_ae ^= 1u;
-          tc::fence_after_sync();
-        }
-#pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
-          mma_group(tmem, a0, y0, 0, 0, 4, kk, 1u);
-          mma_group(tmem, a0, y0, 1, 0, 3, kk, 1u);
-          mma_group(tmem, a0, y0, 2, 0, 2, kk, 1u);
-          mma_group(tmem, a0, y0, 3, 0, 1, kk, 1u);
-        }
-        tc::mma_commit(&bar_empty[st]);
-        if (wk.win_last(u)) tc::mma_commit(&bar_accfull);
-      }
-    }
-    __syncwarp();
-  } else if (warp < 4) {
+    exact(st);
+    if (c.win_last()) tc::mma_commit(&sh.accfull);
+    c.next();
+  }
+  if (c.i < c.n) s_abort = 1;
+}
+
+// v 2^e: the exponent field moves when the result stays normal, else ldexp.
+__device__ __forceinline__ double scale2(double v, int e) {
+  const int64_t bits = __double_as_longlong(v);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  if (ex != 0 && ex + e > 0 && ex + e < 2047) return __longlong_as_double(bits + ((int64_t)e << 52));
+  return ldexp(v, e);
+}
+
+// The flush (warps 0..3): at every window end fold the exact sums into the int64
+// totals and re-arm them; at a segment end also read weights 4..6 and write the
+// tile (to C when the segment is the whole tile, else to the CTA's partial slot).
+__device__ __forceinline__ void oz_flush_role(OzShared& sh, const OzArgs& a, const Cursor& start,
+                                              int64_t cta) {
+  volatile int& s_abort = sh.abort;
+  const int* syE = sh.yE;
+  const uint32_t tmem = sh.tmem;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t first_tile = start.tile;
     // ---------------------------------------------------------- flush + epilogue
     // warp w owns TMEM lanes / tile rows 32 w .. 32 w + 31 (one row per thread) and
     // all 64 output columns: the int64 sums of columns 0..31 live in registers,
@@ -476,17 +503,18 @@ __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
     }
     tc::tmem_st_wait();
     tc::fence_before_sync();
-    tc::mbar_arrive(&bar_accempty);
+    tc::mbar_arrive(&sh.accempty);
 
     int64_t acc[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) acc[i] = 0;
     uint32_t ph_af = 0;
-    for (int64_t u = wk.u0; u < wk.u1; ++u) {
-      if (!wk.win_last(u)) continue;
+    const int ncols = min((int)a.N, NN);  // output columns actually read
+    for (Cursor c = start; c.i < c.n; c.next()) {
+      if (!c.win_last()) continue;
       // lane 0 waits; the warp follows its decision (tcgen05.ld is warp-collective)
       bool ok = true;
-      if (lane == 0) ok = tc::mbar_wait(&bar_accfull, ph_af, WAIT_TRIES);
+      if (lane == 0) ok = tc::mbar_wait(&sh.accfull, ph_af, WAIT_TRIES);
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
       ph_af ^= 1u;
       if (!ok) {
@@ -496,6 +524,7 @@ __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
       tc::fence_after_sync();
 #pragma unroll
       for (int j = 0; j < 16; ++j) {  // 4 output columns at a time
+        if (4 * j >= ncols) continue;  // padding columns: never read, never re-armed
         const uint32_t c4 = 4u * j;
         uint32_t g0[4], g1[4], g2[4], g3[4];
         tc::tmem_ld4(tb + c4, g0);
@@ -534,9 +563,10 @@ __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
         }
       }
       tc::tmem_st_wait();
-      if (wk.seg_last(u)) {
-        const int64_t tile = wk.tile(u);
-        const bool full = (u + 1 - a.kst == tile * a.kst) && (tile * a.kst >= wk.u0);
+      if (c.seg_last()) {
+        const int64_t tile = c.tile;
+        // the segment is the whole tile: it started at stage 0 and ends at the last
+        const bool full = (c.ks + 1 == c.kst) && (c.i >= c.kst - 1);
         const int r = 32 * warp + lane;
         const int64_t p = tile * TM + r;
         const int ep = p < a.P ? __ldg(a.xE + p) : 0;
@@ -544,6 +574,7 @@ __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
         double* wp = a.part + (cta * 2 + slot) * (int64_t)(NN * TM) + r;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
+          if (4 * j >= ncols) continue;
           const uint32_t c4 = 4u * j;
           uint32_t g4[4], g5[4], g6[4], lo[4], hi[4];
           tc::tmem_ld4(tb + 256u + c4, g4);
@@ -556,25 +587,27 @@ __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
           tc::tmem_ld_wait();
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            const int c = 4 * j + i;
+            const int col = 4 * j + i;
             int64_t T;
             if (j < 8) {
-              T = acc[c];
-              acc[c] = 0;
+              T = acc[col];
+              acc[col] = 0;
             } else {
               T = (int64_t)(((uint64_t)hi[i] << 32) | lo[i]);
             }
-            const double rest = (double)__uint_as_float(g4[i]) * 0x1p-32 +
-                                (double)__uint_as_float(g5[i]) * 0x1p-40 +
-                                (double)__uint_as_float(g6[i]) * 0x1p-48;
-            const double sum = fma(__ll2double_rn(T), 0x1p-24, rest);
-            if (p < a.P && c < a.N) {
-              const double val = ldexp(sum, ep + syE[c] - EXP_OFFSET);
+            if (p < a.P && col < a.N) {
+              // weights 4..6 in the units of weight 4, in FP32 (their own FP32 sums
+              // carry more rounding than this), then one FP64 multiply-add onto T
+              const float rest = fmaf(__uint_as_float(g6[i]), 0x1p-16f,
+                                      fmaf(__uint_as_float(g5[i]), 0x1p-8f, __uint_as_float(g4[i])));
+              const double sum = fma((double)rest, 0x1p-8, __ll2double_rn(T));  // units of 2^-24
+              const double val = scale2(sum, ep + syE[col] - EXP_OFFSET - 24);
               if (full) {
-                double* dst = a.C + p * a.csp + (int64_t)c * a.csc;
-                *dst = (a.beta == 0.0) ? a.alpha * val : a.alpha * val + a.beta * (*dst);
+                double* dst = a.C + p * a.csp + (int64_t)col * a.csc;
+                const double av = (a.alpha == 1.0) ? val : (a.alpha == -1.0) ? -val : a.alpha * val;
+                *dst = (a.beta == 0.0) ? av : av + a.beta * (*dst);
               } else {
-                wp[(int64_t)c * TM] = val;
+                wp[(int64_t)col * TM] = val;
               }
             }
           }
@@ -586,42 +619,223 @@ __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
         tc::tmem_st_wait();
       }
       tc::fence_before_sync();
-      tc::mbar_arrive(&bar_accempty);
+      tc::mbar_arrive(&sh.accempty);
     }
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  if (s_abort && tid == 0) atomicOr(a.flags, FLAG_TIMEOUT);
-  if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
 }
 
-// Combine the partial tiles of tiles split across CTAs, in CTA order.  Grid:
-// (tiles, FIX_SPLIT); each CTA handles TM*NN/FIX_SPLIT elements of its tile.
-constexpr int FIX_SPLIT = 32;
+template <bool TRANS>
+__global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ OzShared sh;
+  __shared__ int sEx[2][TM];  // producers: row exponents of tiles (by tile parity)
+  __shared__ volatile int s_pgo[2];  // producers: go on with iteration i (slot i % 2)
+  const uint32_t raw = tc::smem_addr(smem_raw);
+  uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  volatile int& s_abort = sh.abort;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t G = gridDim.x, cta = blockIdx.x;
+  int64_t u0, u1;
+  cta_range(a, cta, G, u0, u1);
+  if (u0 >= u1) return;
+  const Cursor start{u0 / a.kst, (int)(u0 % a.kst), 0, u1 - u0, (int)a.kst};
+  oz_setup(sh, a, NPROD + 1);  // + the arrival that carries the Y bytes
+
+  if (warp >= 4 && warp < MMA_WARP) {
+    // ---------------------------------------------------------- producers
+    const int pt = tid - NFLUSH, pw = pt >> 5;
+    uint32_t ph_empty[NSTAGE] = {0, 0, 0, 0};
+    // row exponents of a tile in sEx[tile % 2], written while the first stage of
+    // the tile is fetched (one iteration ahead of its use, behind a named barrier)
+    auto load_exps = [&](int64_t tile) {
+      if (pt < TM) {
+        const int64_t p = tile * TM + pt;
+        sEx[tile & 1][pt] = p < a.P ? __ldg(a.xE + p) : 0;
+      }
+    };
+    // One stage: wait for its buffer, start the Y copy, prefetch the next stage's
+    // values into nxt, cut cur.  Returns false when the producers stop.
+    auto stage = [&](const Cursor& c, double (&cur)[VPT], double (&nxt)[VPT]) -> bool {
+      const int st = (int)(c.i % NSTAGE), slot = (int)(c.i & 1);
+      // Thread 0 waits for the stage and decides whether to go on; the decision is
+      // published in slot i % 2 before the named barrier and read after it, so all
+      // producers leave the loop in the same iteration (slot i % 2 is next written
+      // in iteration i + 2, after every producer has passed barrier i + 1).
+      if (pt == 0) {
+        bool go = s_abort == 0;
+        if (go && c.i >= NSTAGE) go = tc::mbar_wait(&sh.empty[st], ph_empty[st], WAIT_TRIES);
+        if (!go) s_abort = 1;
+        s_pgo[slot] = go ? 1 : 0;
+      }
+      if (c.i >= NSTAGE) ph_empty[st] ^= 1u;
+      tc::named_sync(1, NPROD);
+      if (!s_pgo[slot]) return false;
+      uint8_t* sA = sm + st * STAGE;
+      if (pt == 0) {
+        tc::mbar_arrive_expect_tx(&sh.full[st], Y_STAGE);
+        tc::bulk_g2s(sA + S * A_PLANE, a.img + (int64_t)c.ks * Y_STAGE, Y_STAGE, &sh.full[st]);
+      }
+      if (c.i + 1 < c.n) {
+        Cursor d = c;
+        d.next();
+        if (d.ks == 0) load_exps(d.tile);
+        fetch<TRANS>(a, d.tile, d.ks, pw, lane, nxt);
+      }
+      cut_stage<TRANS>(cur, sEx[c.tile & 1], sA, pw, lane);
+      tc::fence_async_smem();
+      tc::mbar_arrive(&sh.full[st]);
+      return true;
+    };
+    double va[VPT], vb[VPT];
+    Cursor c = start;
+    load_exps(c.tile);
+    fetch<TRANS>(a, c.tile, c.ks, pw, lane, va);
+    // two stages per trip, so that the two value buffers swap roles without copies
+    while (c.i < c.n) {
+      if (!stage(c, va, vb)) break;
+      c.next();
+      if (c.i >= c.n) break;
+      if (!stage(c, vb, va)) break;
+      c.next();
+    }
+  } else if (warp == MMA_WARP) {
+    if (lane == 0) oz_mma_role(sh, start, sm);
+    __syncwarp();
+  } else if (warp < 4) {
+    oz_flush_role(sh, a, start, cta);
+  }
+  oz_teardown(sh, a);
+}
+
+// The same product with op(X) already cut: img holds, per (tile, stage), the
+// seven digit planes in the stage layout (A_PLANE bytes each, contiguous), so a
+// stage is two bulk copies issued by one thread.  Warps 0..3 flush, warp 4
+// copies, warp 5 issues the MMAs.
+constexpr int NT_IMG = NFLUSH + 64;
+
+__global__ void __launch_bounds__(NT_IMG, 1) k_ozgemm_img(OzArgs a, const uint8_t* __restrict__ ximg) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ OzShared sh;
+  const uint32_t raw = tc::smem_addr(smem_raw);
+  uint8_t* sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  volatile int& s_abort = sh.abort;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t G = gridDim.x, cta = blockIdx.x;
+  int64_t u0, u1;
+  cta_range(a, cta, G, u0, u1);
+  if (u0 >= u1) return;
+  const Cursor start{u0 / a.kst, (int)(u0 % a.kst), 0, u1 - u0, (int)a.kst};
+  oz_setup(sh, a, 1);
+
+  if (warp == 4) {
+    if (lane == 0) {
+      uint32_t ph_empty[NSTAGE] = {0, 0, 0, 0};
+      for (Cursor c = start; c.i < c.n; c.next()) {
+        const int st = (int)(c.i % NSTAGE);
+        if (c.i >= NSTAGE) {
+          if (s_abort || !tc::mbar_wait(&sh.empty[st], ph_empty[st], WAIT_TRIES)) {
+            s_abort = 1;
+            break;
+          }
+          ph_empty[st] ^= 1u;
+        }
+        uint8_t* sA = sm + st * STAGE;
+        tc::mbar_arrive_expect_tx(&sh.full[st], STAGE);
+        tc::bulk_g2s(sA, ximg + (c.tile * a.kst + c.ks) * (int64_t)(S * A_PLANE), S * A_PLANE,
+                     &sh.full[st]);
+        tc::bulk_g2s(sA + S * A_PLANE, a.img + (int64_t)c.ks * Y_STAGE, Y_STAGE, &sh.full[st]);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 5) {
+    if (lane == 0) oz_mma_role(sh, start, sm);
+    __syncwarp();
+  } else {
+    oz_flush_role(sh, a, start, cta);
+  }
+  oz_teardown(sh, a);
+}
+
+// Cut op(X) into its digit image (the stage layout of k_ozgemm_img): one CTA of
+// NPROD threads per (tile, stage) unit, grid-stride.
+template <bool TRANS>
+__global__ void __launch_bounds__(NPROD) k_oz_xcut(OzArgs a, uint8_t* __restrict__ ximg) {
+  __shared__ int sE[TM];
+  const int pw = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t T = a.tiles * a.kst;
+  int64_t prev_tile = -1;
+  for (int64_t u = blockIdx.x; u < T; u += gridDim.x) {
+    const int64_t tile = u / a.kst;
+    const int ks = (int)(u % a.kst);
+    if (tile != prev_tile) {
+      __syncthreads();
+      if (threadIdx.x < TM) {
+        const int64_t p = tile * TM + threadIdx.x;
+        sE[threadIdx.x] = p < a.P ? __ldg(a.xE + p) : 0;
+      }
+      __syncthreads();
+      prev_tile = tile;
+    }
+    double v[VPT];
+    fetch<TRANS>(a, tile, ks, pw, lane, v);
+    cut_stage<TRANS>(v, sE, ximg + u * (int64_t)(S * A_PLANE), pw, lane);
+  }
+}
+
+// Combine the partial tiles of tiles split across CTAs, in a fixed order.  Grid:
+// (tiles, FIX_SPLIT); each CTA handles FIX_ELEMS elements of its tile with
+// FIX_LANES threads per element: thread l sums the partials of the contributing
+// CTAs cf + l, cf + l + FIX_LANES, ... in CTA order, and the FIX_LANES sums are
+// added in lane order.  Tile t is covered by CTAs cf..cl; every one of them but
+// cf starts its range inside t, so t is its first tile (slot 0); cf holds t in
+// slot 1 unless its range also starts inside t.  CTAs with an empty range (more
+// CTAs than units) wrote nothing and are skipped.
+constexpr int FIX_LANES = 4;
+constexpr int FIX_ELEMS = 256 / FIX_LANES;
+constexpr int FIX_SPLIT = TM * NN / FIX_ELEMS;
 
 __global__ void __launch_bounds__(256) k_oz_fixup(OzArgs a, int G) {
+  __shared__ int64_t s_cf, s_cl;
+  __shared__ int s_slot_f;
   const int64_t t = blockIdx.x;
   const int64_t T = a.tiles * a.kst;
-  auto owner = [&](int64_t u) {
-    int64_t c = u * G / T;
-    while (c + 1 < G && (c + 1) * T / G <= u) ++c;
-    while (c > 0 && c * T / G > u) --c;
-    return c;
-  };
-  const int64_t cf = owner(t * a.kst), cl = owner((t + 1) * a.kst - 1);
+  if (threadIdx.x == 0) {
+    auto owner = [&](int64_t u) {
+      int64_t c = u * G / T;
+      while (c + 1 < G && (c + 1) * T / G <= u) ++c;
+      while (c > 0 && c * T / G > u) --c;
+      return c;
+    };
+    s_cf = owner(t * a.kst);
+    s_cl = owner((t + 1) * a.kst - 1);
+    s_slot_f = ((s_cf * T / G) / a.kst == t) ? 0 : 1;
+  }
+  __syncthreads();
+  const int64_t cf = s_cf, cl = s_cl;
   if (cf == cl) return;
-  constexpr int PER = TM * NN / FIX_SPLIT;
-  for (int e = blockIdx.y * PER + threadIdx.x; e < (int)(blockIdx.y + 1) * PER; e += 256) {
-    const int r = e % TM, c = e / TM;
-    const int64_t p = t * TM + r;
-    if (p >= a.P || c >= a.N) continue;
-    double s = 0.0;
-    for (int64_t q = cf; q <= cl; ++q) {
-      const int64_t q0 = q * T / G, q1 = (q + 1) * T / G;
-      if (q0 >= q1) continue;  // a CTA with an empty range wrote nothing
-      const int slot = (t == q0 / a.kst) ? 0 : 1;
-      s += a.part[((q * 2 + slot) * NN + c) * TM + r];
+  const int slot_f = s_slot_f;
+  const int lane = threadIdx.x % FIX_LANES;
+  const int e = blockIdx.y * FIX_ELEMS + threadIdx.x / FIX_LANES;
+  const int r = e % TM, c = e / TM;
+  const int64_t p = t * TM + r;
+  const bool valid = p < a.P && c < a.N;
+  const double* src = a.part + (int64_t)c * TM + r;
+  const bool all_nonempty = T >= G;  // then every CTA's range holds a unit
+  double s = 0.0;
+  if (valid) {
+    for (int64_t q = cf + lane; q <= cl; q += FIX_LANES) {
+      const int slot = (q == cf) ? slot_f : 0;
+      if (all_nonempty || q * T / G < (q + 1) * T / G) s += src[(q * 2 + slot) * (int64_t)(NN * TM)];
     }
+  }
+  // lanes of one element are adjacent threads of one warp
+#pragma unroll
+  for (int o = 1; o < FIX_LANES; o <<= 1) {
+    const double other = __shfl_down_sync(0xffffffffu, s, o, FIX_LANES);
+    if ((lane & (2 * o - 1)) == 0) s += other;
+  }
+  if (lane == 0 && valid) {
     double* dst = a.C + p * a.csp + (int64_t)c * a.csc;
     *dst = (a.beta == 0.0) ? a.alpha * s : a.alpha * s + a.beta * (*dst);
   }
@@ -630,8 +844,7 @@ __global__ void __launch_bounds__(256) k_oz_fixup(OzArgs a, int G) {
 cudaError_t oz_rowcol_exponents(const double* X, int64_t ld, int64_t rows, int64_t cols,
                                 int* rowE, int* colE, cudaStream_t st, bool accumulate_rows) {
   if (colE) {
-    k_oz_colmaxexp<<<(unsigned)cols, 256, 0, st>>>(X, ld, rows, colE);
-    cudaError_t e = launched();
+    cudaError_t e = colmaxexp(X, ld, rows, cols, colE, st);
     if (e != cudaSuccess) return e;
   }
   if (rowE) {
@@ -648,27 +861,9 @@ cudaError_t oz_rowcol_exponents(const double* X, int64_t ld, int64_t rows, int64
   return cudaSuccess;
 }
 
-cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, const double* X,
-                   int64_t ldx, const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
-                   const OzWorkspace& w, int* flags, cudaStream_t st) {
-  if (P <= 0 || N <= 0) return cudaSuccess;
-  if (N > NN || K <= 0 || K > MAX_K) return cudaErrorInvalidValue;
-  const int64_t kst = (K + KS - 1) / KS;
-  if (oz_img_bytes(K) > w.img_bytes) return cudaErrorInvalidValue;
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[trans ? 1 : 0]) {
-    cudaError_t e = cudaFuncSetAttribute(trans ? (const void*)k_ozgemm<true> : (const void*)k_ozgemm<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_DYN);
-    if (e != cudaSuccess) return e;
-    attr_set[trans ? 1 : 0] = true;
-  }
-  k_oz_colmaxexp<<<(unsigned)N, 256, 0, st>>>(Y, ldy, K, w.yE);
-  cudaError_t e = launched();
-  if (e != cudaSuccess) return e;
-  const int64_t ythreads = kst * NN * 4;
-  k_oz_ycut<<<(unsigned)((ythreads + 255) / 256), 256, 0, st>>>(Y, ldy, K, (int)N, w.yE, w.img, kst);
-  e = launched();
-  if (e != cudaSuccess) return e;
+namespace {
+OzArgs make_args(int64_t P, int64_t N, int64_t K, double alpha, const double* X, int64_t ldx,
+                 const int* xE, double beta, GemmOut out, const OzWorkspace& w, int* flags) {
   OzArgs a;
   a.P = P;
   a.K = K;
@@ -685,16 +880,93 @@ cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, co
   a.csc = out.csc;
   a.part = w.part;
   a.tiles = (P + TM - 1) / TM;
-  a.kst = kst;
+  a.kst = (K + KS - 1) / KS;
   a.flags = flags;
-  a.vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (ldx % 2 == 0);
+  a.vec = X && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (ldx % 2 == 0);
+  // short tiles (K <= 64): whole tiles per CTA beat splitting plus a fixup; long
+  // tiles are split along K (stream-K), also when there are few of them
+  a.whole_tiles = a.kst <= 4;
+  return a;
+}
+
+// Y's exponents and digit image (shared by both GEMM kernels).
+cudaError_t prepare_y(const double* Y, int64_t ldy, int64_t K, int64_t N, const OzWorkspace& w,
+                      cudaStream_t st) {
+  const int64_t kst = (K + KS - 1) / KS;
+  cudaError_t e = colmaxexp(Y, ldy, K, N, w.yE, st);
+  if (e != cudaSuccess) return e;
+  const int64_t ythreads = kst * NN * 2;
+  k_oz_ycut<<<(unsigned)((ythreads + 255) / 256), 256, 0, st>>>(Y, ldy, K, (int)N, w.yE, w.img, kst);
+  return launched();
+}
+
+template <typename F>
+cudaError_t set_smem_once(F kernel, bool& done) {
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       SMEM_DYN);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+}  // namespace
+
+int64_t oz_ximg_bytes(int64_t P, int64_t K) {
+  return ((P + TM - 1) / TM) * ((K + KS - 1) / KS) * (int64_t)(S * A_PLANE);
+}
+
+cudaError_t oz_cut_x(bool trans, int64_t P, int64_t K, const double* X, int64_t ldx, const int* xE,
+                     uint8_t* ximg, int ctas, cudaStream_t st) {
+  if (P <= 0 || K <= 0) return cudaSuccess;
+  OzWorkspace none{};
+  OzArgs a = make_args(P, 1, K, 1.0, X, ldx, xE, 0.0, GemmOut{nullptr, 0, 0}, none, nullptr);
+  const int64_t units = a.tiles * a.kst;
+  const unsigned grid = (unsigned)std::min<int64_t>(units, (int64_t)ctas * 4);
+  if (trans)
+    k_oz_xcut<true><<<grid, NPROD, 0, st>>>(a, ximg);
+  else
+    k_oz_xcut<false><<<grid, NPROD, 0, st>>>(a, ximg);
+  return launched();
+}
+
+cudaError_t ozgemm_img(int64_t P, int64_t N, int64_t K, double alpha, const uint8_t* ximg,
+                       const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
+                       const OzWorkspace& w, int* flags, cudaStream_t st) {
+  if (P <= 0 || N <= 0) return cudaSuccess;
+  if (N > NN || K <= 0 || K > MAX_K) return cudaErrorInvalidValue;
+  if (oz_img_bytes(K) > w.img_bytes) return cudaErrorInvalidValue;
+  static bool attr = false;
+  cudaError_t e = set_smem_once(k_ozgemm_img, attr);
+  if (e != cudaSuccess) return e;
+  e = prepare_y(Y, ldy, K, N, w, st);
+  if (e != cudaSuccess) return e;
+  OzArgs a = make_args(P, N, K, alpha, nullptr, 0, xE, beta, out, w, flags);
+  const int G = w.ctas;
+  k_ozgemm_img<<<G, NT_IMG, SMEM_DYN, st>>>(a, ximg);
+  e = launched();
+  if (e != cudaSuccess || a.whole_tiles) return e;
+  k_oz_fixup<<<dim3((unsigned)a.tiles, FIX_SPLIT), 256, 0, st>>>(a, G);
+  return launched();
+}
+
+cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, const double* X,
+                   int64_t ldx, const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
+                   const OzWorkspace& w, int* flags, cudaStream_t st) {
+  if (P <= 0 || N <= 0) return cudaSuccess;
+  if (N > NN || K <= 0 || K > MAX_K) return cudaErrorInvalidValue;
+  if (oz_img_bytes(K) > w.img_bytes) return cudaErrorInvalidValue;
+  static bool attr[2] = {false, false};
+  cudaError_t e = trans ? set_smem_once(k_ozgemm<true>, attr[1]) : set_smem_once(k_ozgemm<false>, attr[0]);
+  if (e != cudaSuccess) return e;
+  e = prepare_y(Y, ldy, K, N, w, st);
+  if (e != cudaSuccess) return e;
+  OzArgs a = make_args(P, N, K, alpha, X, ldx, xE, beta, out, w, flags);
   const int G = w.ctas;
   if (trans)
     k_ozgemm<true><<<G, NT, SMEM_DYN, st>>>(a);
   else
     k_ozgemm<false><<<G, NT, SMEM_DYN, st>>>(a);
   e = launched();
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || a.whole_tiles) return e;
   k_oz_fixup<<<dim3((unsigned)a.tiles, FIX_SPLIT), 256, 0, st>>>(a, G);
   return launched();
 }

@@ -82,14 +82,12 @@ extern "C" lra_status lra_sketch_noalloc(const lra_matrix* A, const lra_params* 
   os.k1 = (uint32_t)(params->seed >> 32);
   os.inv_scale = 1.0;
   int cap = 0;
-  double pm_scale = 0.0;
   switch (params->kind) {
     case LRA_OMEGA_SPARSE_SIGN:
       if (params->zeta < 1 || params->zeta > n || params->zeta > LRA_MAX_ZETA)
         return LRA_ERR_INVALID_ARG;
       os.inv_scale = 1.0 / sqrt((double)params->zeta);
       cap = params->zeta;
-      pm_scale = os.inv_scale;
       break;
     case LRA_OMEGA_SPARSE_SIGN_IID:
     case LRA_OMEGA_SPARSE_GAUSSIAN:
@@ -99,9 +97,6 @@ extern "C" lra_status lra_sketch_noalloc(const lra_matrix* A, const lra_params* 
       os.thr = (uint64_t)floor(os.p * 4294967296.0);
       if (params->kind != LRA_OMEGA_BERNOULLI) os.inv_scale = 1.0 / sqrt(os.p);
       cap = (int)n;
-      pm_scale = params->kind == LRA_OMEGA_SPARSE_SIGN_IID ? os.inv_scale
-                 : params->kind == LRA_OMEGA_BERNOULLI     ? 1.0
-                                                           : 0.0;
       break;
     default:
       return LRA_ERR_UNSUPPORTED;  // Gaussian and standardized Bernoulli need a context
@@ -135,7 +130,7 @@ extern "C" lra_status lra_sketch_noalloc(const lra_matrix* A, const lra_params* 
     if (omega_sparse(os, j, nb, cap, counts, rows, vals, flags, st) != cudaSuccess)
       return LRA_ERR_CUDA;
     if (gather_sketch(Ad, A->lda, m, counts, rows, vals, cap, nb * b, Y + (j - j0) * b * ldy, ldy,
-                      nullptr, pm_scale, st) != cudaSuccess)
+                      nullptr, flags, st) != cudaSuccess)
       return LRA_ERR_CUDA;
   }
   int hflags = 0;
@@ -143,5 +138,6 @@ extern "C" lra_status lra_sketch_noalloc(const lra_matrix* A, const lra_params* 
     return LRA_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return LRA_ERR_CUDA;
   if (hflags & FLAG_OMEGA_CAP) return LRA_ERR_INVALID_ARG;
+  if (hflags & FLAG_TIMEOUT) return LRA_ERR_TIMEOUT;
   return LRA_OK;
 }

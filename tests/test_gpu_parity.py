@@ -242,3 +242,27 @@ def test_full_passes_per_block(kind, p, zeta, P):
     assert ph["dense"][1] == r["blocks"] * (2 * P + 1)
     assert ph["sketch"][1] == r["blocks"]
     f.close()
+
+
+@pytest.mark.parametrize("kind,p,zeta,P", [(om.SPARSE_SIGN, 0.0, 8, 1), (om.GAUSSIAN, 0.0, 0, 2),
+                                           (om.STD_BERNOULLI, 0.0, 0, 1)],
+                         ids=["ss8_P1", "gauss_P2", "sb_p1_P1"])
+def test_digit_images_change_nothing(kind, p, zeta, P):
+    """A cut once into its digit images (the default) and A cut on every pass
+    (LRA_FLAG_NO_A_DIGITS) feed the tensor cores the same digits in the same order:
+    the runs agree bit for bit.  Ragged sizes: neither m nor n is a multiple of the
+    128-row tile or the 32-deep stage."""
+    m, n = 1001, 643
+    A = low_rank_matrix(m, n, "poly1.5", seed=41)
+    Ad = dev(A)
+    out = []
+    for digits in (True, False):
+        f = lra.Farpca(m, n, eps=1e-2, b=24, P=P, kind=kind, zeta=zeta, p=p, seed=5, a_digits=digits)
+        f.run(Ad)
+        r = f.result()
+        out.append((r["status"], r["rank"], r["E"], r["Q"].cpu().numpy().copy(), r["B"].cpu().numpy().copy()))
+        f.close()
+    (s0, k0, e0, q0, b0), (s1, k1, e1, q1, b1) = out
+    assert (s0, k0) == (s1, k1) and k0 > 0
+    assert e0 == e1
+    assert np.array_equal(q0, q1) and np.array_equal(b0, b1)
