@@ -82,6 +82,11 @@ typedef enum { LRA_F64 = 0, LRA_F32 = 1 } lra_dtype;
                                streams the digits instead of cutting A again.  With
                                this flag, or when the images do not fit, each pass
                                cuts A on the fly (same results, bit for bit).     */
+#define LRA_FLAG_NO_GRAPHS 16u /* launch every kernel of lra_farpca_run directly.  By
+                               default the fixed kernel sequence of each block (and
+                               of the set-up after ||A||_F^2) is captured once into a
+                               CUDA graph, cached per block index and per A pointer,
+                               and replayed; results are the same bit for bit.     */
 
 /* Phases of one block, for lra_phase_times. */
 typedef enum {
@@ -146,7 +151,9 @@ typedef struct lra_ctx lra_ctx;
 
 /* Create a context for m x n inputs: validates *params, allocates the device
    workspace for the largest rank the run can reach (l_max = block cap * b), and
-   binds `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
+   binds `cuda_stream` (a cudaStream_t).  With NULL the context creates and owns
+   a blocking stream, which is ordered with the legacy default stream as NULL
+   would be (the legacy stream itself cannot be captured into CUDA graphs).
    Errors: LRA_ERR_INVALID_ARG, LRA_ERR_OOM, LRA_ERR_CUDA.  *out is NULL on error. */
 lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* params,
                       void* cuda_stream);

@@ -74,6 +74,8 @@ WORKLOADS = {
     "dense2000x1000_poly1.5": dict(m=2000, n=1000, spectrum="poly1.5", noise=0.0, seed=1001),
     # 20000 x 10000, sigma_i = 10^(-i/100) + 1e-6 N(0,1) noise, b = 50
     "dense20000x10000_exp100": dict(m=20000, n=10000, spectrum="exp100", noise=1e-6, seed=1002),
+    # the same family at a quarter of the size (profiling: A 400 MB, above L2)
+    "dense10000x5000_exp100": dict(m=10000, n=5000, spectrum="exp100", noise=1e-6, seed=1003),
     # Table 1, n = 5000
     "matrix1_5000": dict(m=5000, n=5000, spectrum="matrix1", noise=0.0, seed=2001),
     "matrix2_5000": dict(m=5000, n=5000, spectrum="matrix2", noise=0.0, seed=2002),

@@ -56,6 +56,9 @@ cudaError_t omega_dense(const OmegaSpec& s, int64_t j0, int64_t nblk, double* Om
 // Y[i, g] = sum_t vals[g*cap+t] * X[i, rows[g*cap+t]] - (shift ? shift[i] : 0)
 // for i < rows_x, g < ncols; X column-major with ld ldx.  A bounded device wait
 // that gives up sets FLAG_TIMEOUT in *flags.
+// Kernel attributes (dynamic shared memory) set once per process, before any
+// stream capture; the prepare functions are idempotent.
+cudaError_t gather_prepare();
 cudaError_t gather_sketch(const double* X, int64_t ldx, int64_t rows_x, const int* counts,
                           const int* rows, const double* vals, int cap, int64_t ncols, double* Y,
                           int64_t ldy, const double* shift, int* flags, cudaStream_t st);
@@ -85,12 +88,14 @@ struct OzWorkspace {
   int ctas;          // CTAs of the persistent grid (one per SM)
 };
 int64_t oz_img_bytes(int64_t K);
+cudaError_t oz_prepare();
 int64_t oz_part_elems(int ctas);
 // Largest K the tensor engine accepts (its exact int64 sums stay in range).
 int64_t oz_max_k();
+// yE_known: biased max exponents of Y's columns when the caller has them.
 cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, const double* X,
                    int64_t ldx, const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
-                   const OzWorkspace& w, int* flags, cudaStream_t st);
+                   const OzWorkspace& w, int* flags, cudaStream_t st, const int* yE_known = nullptr);
 // The digit image of op(X) (P x K): every (128-row tile, 32-deep stage) as seven
 // f16 digit planes, cut once and reused by ozgemm_img.  xE as for ozgemm.
 int64_t oz_ximg_bytes(int64_t P, int64_t K);
@@ -108,6 +113,12 @@ cudaError_t oz_rowcol_exponents(const double* X, int64_t ld, int64_t rows, int64
 // Per-column sums of squares and/or sums of X (rows x cols, ld): one CTA per column.
 cudaError_t col_sums(const double* X, int64_t ld, int64_t rows, int64_t cols, double* sumsq,
                      double* sum, cudaStream_t st);
+// One pass over A: colsq[c] = ||A[:, c]||^2 (summed over 512-row blocks through
+// part, a_stats_part_elems(m, n) doubles), colE / rowE = largest biased exponent
+// of each column / row.  Deterministic.
+int64_t a_stats_part_elems(int64_t m, int64_t n);
+cudaError_t a_stats(const double* A, int64_t lda, int64_t m, int64_t n, double* part, double* colsq,
+                    int* colE, int* rowE, cudaStream_t st);
 // out[0] = sum of v[0..count) in a fixed order (one CTA).
 cudaError_t total(const double* v, int64_t count, double* out, cudaStream_t st);
 // Cholesky S = R^T R (S: b x b, ld b), R^{-1} into Rinv (b x b, ld b); on a failed

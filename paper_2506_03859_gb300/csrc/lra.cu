@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -61,6 +62,20 @@ struct lra_ctx {
   int *browE = nullptr, *bcolE = nullptr;  // ... of B (rows: l_max, columns: n)
   int *xrowE = nullptr, *xcolE = nullptr;  // scratch for the operand of orth()
   OzWorkspace oz{};
+  // CUDA graphs of the set-up and of each block (index j), keyed on A and lda
+  struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    const double* A = nullptr;
+    int64_t lda = 0;
+    int nev0 = 0;            // first profiling event index it records
+    int nev = 0;             // profiling events the graph records
+    std::vector<int> phase;  // ... and their phases
+    uint64_t launches = 0;   // kernel launches it holds
+  };
+  bool graphs = true;
+  bool own_stream = false;  // st created by lra_create (the caller passed none)
+  GraphSlot gpre;
+  std::vector<GraphSlot> gblock;
   // A cut into digit images: [0] row-scaled (A X), [1] column-scaled (A^T X)
   uint8_t* ximg[2] = {nullptr, nullptr};
   bool ximg_ready = false;
@@ -75,6 +90,7 @@ struct lra_ctx {
   double *z = nullptr, *zB = nullptr, *wvec = nullptr;
   double* ws = nullptr;
   int64_t ws_elems = 0;
+  double* astat = nullptr;  // per-(512-row block, column) sums of squares of A
   double *gram = nullptr, *Rinv = nullptr;
   double *colsq = nullptr, *colsum = nullptr, *scal = nullptr;
   int* flags = nullptr;
@@ -164,7 +180,8 @@ lra_status check_params(lra_ctx* ctx, int64_t m, int64_t n, const lra_params* p)
   if (p->max_blocks < 0) return fail(ctx, LRA_ERR_INVALID_ARG, "max_blocks must be >= 0");
   if ((int64_t)p->max_blocks * p->b > mn)
     return fail(ctx, LRA_ERR_INVALID_ARG, "max_blocks * b exceeds min(m, n)");
-  if (p->flags & ~(LRA_FLAG_KEEP_Y | LRA_FLAG_PROFILE | LRA_FLAG_FP64_SIMT | LRA_FLAG_NO_A_DIGITS))
+  if (p->flags & ~(LRA_FLAG_KEEP_Y | LRA_FLAG_PROFILE | LRA_FLAG_FP64_SIMT | LRA_FLAG_NO_A_DIGITS |
+                   LRA_FLAG_NO_GRAPHS))
     return fail(ctx, LRA_ERR_INVALID_ARG, "unknown flags");
   return LRA_OK;
 }
@@ -217,13 +234,13 @@ lra_status a_exponents(lra_ctx* ctx, const double* A, int64_t lda) {
 // of each row of op(X); the tensor engine needs it (NULL selects the FP64 cores).
 lra_status mm(lra_ctx* ctx, bool trans, int64_t P, int64_t N, int64_t K, double alpha,
               const double* X, int64_t ldx, const int* xE, const double* Y, int64_t ldy,
-              double beta, double* C, int64_t csp, int64_t csc) {
+              double beta, double* C, int64_t csp, int64_t csc, const int* yE_known = nullptr) {
   if (!ctx->tensor || !xE || K > oz_max_k())
     return gemm(ctx, trans, P, N, K, alpha, X, ldx, Y, ldy, beta, C, csp, csc);
   if (P <= 0 || N <= 0) return LRA_OK;
   if (K <= 0) return LRA_OK;
   CK(ozgemm(trans, P, N, K, alpha, X, ldx, xE, Y, ldy, beta, GemmOut{C, csp, csc}, ctx->oz,
-            ctx->flags, ctx->st));
+            ctx->flags, ctx->st, yE_known));
   return LRA_OK;
 }
 
@@ -236,7 +253,8 @@ lra_status gram(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows) {
     CK(oz_rowcol_exponents(X, ldx, rows, b, nullptr, ctx->xcolE, ctx->st));
     xE = ctx->xcolE;
   }
-  return mm(ctx, true, b, b, rows, 1.0, X, ldx, xE, X, ldx, 0.0, ctx->gram, 1, b);
+  // X^T X: the right operand's column exponents are the left operand's row exponents
+  return mm(ctx, true, b, b, rows, 1.0, X, ldx, xE, X, ldx, 0.0, ctx->gram, 1, b, xE);
 }
 
 lra_status right_apply_rinv(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows, double* out,
@@ -307,17 +325,29 @@ lra_status prof_flush(lra_ctx* ctx) {
   return LRA_OK;
 }
 
+// Records ev on the context's stream.  Inside a graph capture the record must be
+// external, so that the graph records the event at every replay (a plain record
+// would only order the capture); outside a capture the flag is not accepted.
+cudaError_t record(lra_ctx* ctx, cudaEvent_t ev) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(ctx->st, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs == cudaStreamCaptureStatusActive)
+    return cudaEventRecordWithFlags(ev, ctx->st, cudaEventRecordExternal);
+  return cudaEventRecord(ev, ctx->st);
+}
+
 lra_status prof_begin(lra_ctx* ctx, int phase) {
   if (!ctx->prof) return LRA_OK;
   if (ctx->nev == lra_ctx::NEV) TRY(prof_flush(ctx));
-  CK(cudaEventRecord(ctx->ev0[ctx->nev], ctx->st));
+  CK(record(ctx, ctx->ev0[ctx->nev]));
   ctx->cur_phase = phase;
   return LRA_OK;
 }
 
 lra_status prof_end(lra_ctx* ctx) {
   if (!ctx->prof) return LRA_OK;
-  CK(cudaEventRecord(ctx->ev1[ctx->nev], ctx->st));
+  CK(record(ctx, ctx->ev1[ctx->nev]));
   ctx->ev_phase[ctx->nev] = ctx->cur_phase;
   ctx->nev += 1;
   return LRA_OK;
@@ -337,6 +367,61 @@ lra_status read_record(lra_ctx* ctx) {
   return prof_flush(ctx);
 }
 
+// Runs body on the context's stream as a CUDA graph: captured on first use (and
+// again when A or lda change), replayed afterwards.  The host-side counters that
+// body advances while it issues work (profiling events, kernel launches) advance
+// by the graph's amounts at every replay.  A capture always ends, also on error,
+// so the stream stays usable.
+template <typename F>
+lra_status captured(lra_ctx* ctx, lra_ctx::GraphSlot& gs, const double* A, int64_t lda, F&& body) {
+  if (!gs.exec || gs.A != A || gs.lda != lda || gs.nev0 != ctx->nev) {
+    if (gs.exec) {
+      cudaGraphExecDestroy(gs.exec);
+      gs.exec = nullptr;
+    }
+    const int nev0 = ctx->nev;
+    const uint64_t l0 = g_launches.load();
+    CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+    const lra_status s = body();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->st, &g);
+    const uint64_t launches = g_launches.load() - l0;
+    g_launches.fetch_sub(launches);
+    const int nev = ctx->nev - nev0;
+    ctx->nev = nev0;
+    if (s != LRA_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      if (s != LRA_OK) return s;
+      return fail(ctx, LRA_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&gs.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      gs.exec = nullptr;
+      return fail(ctx, LRA_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+    }
+    gs.A = A;
+    gs.lda = lda;
+    gs.nev0 = nev0;
+    gs.nev = nev;
+    gs.phase.assign(ctx->ev_phase + nev0, ctx->ev_phase + nev0 + nev);
+    gs.launches = launches;
+  }
+  CK(cudaGraphLaunch(gs.exec, ctx->st));
+  // the graph records events nev .. nev + gs.nev - 1 (the indices of its capture)
+  for (int i = 0; i < gs.nev; ++i) ctx->ev_phase[ctx->nev + i] = gs.phase[i];
+  ctx->nev += gs.nev;
+  g_launches.fetch_add(gs.launches);
+  return LRA_OK;
+}
+
+template <typename F>
+lra_status issue(lra_ctx* ctx, lra_ctx::GraphSlot& gs, const double* A, int64_t lda, F&& body) {
+  if (ctx->graphs) return captured(ctx, gs, A, lda, body);
+  return body();
+}
+
 lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
   // the digit images describe this run's A only: invalid on every way out
   struct ImageScope {
@@ -350,9 +435,13 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
   ctx->rank = ctx->blocks = 0;
   ctx->E = ctx->normA2 = 0.0;
   CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int), ctx->st));
-  // ||A||_F^2 (Alg. 1 step 1)
+  // ||A||_F^2 (Alg. 1 step 1); the tensor engine takes the exponents of A's rows
+  // and columns in the same pass
   PHASE(LRA_PHASE_INDICATOR, {
-    CK(col_sums(A, lda, m, n, ctx->colsq, nullptr, ctx->st));
+    if (ctx->tensor)
+      CK(a_stats(A, lda, m, n, ctx->astat, ctx->colsq, ctx->colE, ctx->rowE, ctx->st));
+    else
+      CK(col_sums(A, lda, m, n, ctx->colsq, nullptr, ctx->st));
     CK(total(ctx->colsq, n, ctx->scal, ctx->st));
   });
   TRY(read_record(ctx));
@@ -363,85 +452,92 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
     ctx->E = 0.0;
     return LRA_OK;
   }
-  PHASE(LRA_PHASE_INDICATOR, TRY(a_exponents(ctx, A, lda)));
-  ctx->ximg_ready = false;
-  if (ctx->ximg[0] && ctx->ximg[1]) {
-    PHASE(LRA_PHASE_CUT, {
-      CK(oz_cut_x(false, m, n, A, lda, ctx->rowE, ctx->ximg[0], ctx->oz.ctas, ctx->st));
-      CK(oz_cut_x(true, n, m, A, lda, ctx->colE, ctx->ximg[1], ctx->oz.ctas, ctx->st));
-    });
-    ctx->ximg_ready = true;
-  }
-  if (ctx->tensor) {
-    CK(cudaMemsetAsync(ctx->qrowE, 0, m * sizeof(int), ctx->st));
-    CK(cudaMemsetAsync(ctx->bcolE, 0, n * sizeof(int), ctx->st));
-  }
-  if (ctx->sb_sparse) PHASE(LRA_PHASE_SKETCH, TRY(compute_z(ctx, A, lda)));
+  // set-up: exponents of A, its digit images, z = A (p 1) for the shifted sketch
+  const bool images = ctx->ximg[0] && ctx->ximg[1];
+  ctx->ximg_ready = images;  // stream order puts the cut before every pass that reads it
+  TRY(issue(ctx, ctx->gpre, A, lda, [&]() -> lra_status {
+    if (images) {
+      PHASE(LRA_PHASE_CUT, {
+        CK(oz_cut_x(false, m, n, A, lda, ctx->rowE, ctx->ximg[0], ctx->oz.ctas, ctx->st));
+        CK(oz_cut_x(true, n, m, A, lda, ctx->colE, ctx->ximg[1], ctx->oz.ctas, ctx->st));
+      });
+    }
+    if (ctx->tensor) {
+      CK(cudaMemsetAsync(ctx->qrowE, 0, m * sizeof(int), ctx->st));
+      CK(cudaMemsetAsync(ctx->bcolE, 0, n * sizeof(int), ctx->st));
+    }
+    if (ctx->sb_sparse) PHASE(LRA_PHASE_SKETCH, TRY(compute_z(ctx, A, lda)));
+    return LRA_OK;
+  }));
   const double thr = ctx->prm.eps * ctx->prm.eps * normA2;
   const bool fixed_rank = ctx->prm.k > 0;
   double E = normA2;
   int32_t status = fixed_rank ? LRA_OK : LRA_NOT_CONVERGED;
   for (int64_t j = 0; j < ctx->nblk_max; ++j) {
-    const int64_t l = j * b;
-    PHASE(LRA_PHASE_OMEGA, TRY(make_omega(ctx, j)));
-    PHASE(LRA_PHASE_SKETCH,
-          TRY(apply_omega(ctx, A, lda, m, ctx->S0, lds, ctx->sb_sparse ? ctx->z : nullptr, true)));
-    double* Y = ctx->S0;
-    if (P >= 1) {
-      PHASE(LRA_PHASE_DENSE, TRY(dense(ctx, true, b, 1.0, A, lda, ctx->S0, lds, 0.0, ctx->W, 1, lds)));
-      if (l > 0) {
-        PHASE(LRA_PHASE_DEFLATE, {
-          TRY(apply_omega(ctx, ctx->B, ldb, l, ctx->BOm, ldf, ctx->sb_sparse ? ctx->zB : nullptr,
-                          false));
-          TRY(mm(ctx, true, n, b, l, -1.0, ctx->B, ldb, ctx->bcolE, ctx->BOm, ldf, 1.0, ctx->W, 1,
-                 lds));
-        });
-      }
-      PHASE(LRA_PHASE_ORTH, TRY(orth(ctx, ctx->W, lds, n, ctx->G, lds)));
-      for (int s = 1; s < P; ++s) {
-        PHASE(LRA_PHASE_DENSE,
-              TRY(dense(ctx, false, b, 1.0, A, lda, ctx->G, lds, 0.0, ctx->T1, 1, lds)));
-        PHASE(LRA_PHASE_DENSE,
-              TRY(dense(ctx, true, b, 1.0, A, lda, ctx->T1, lds, 0.0, ctx->W, 1, lds)));
+    if ((int64_t)ctx->gblock.size() <= j) ctx->gblock.resize(j + 1);
+    TRY(issue(ctx, ctx->gblock[j], A, lda, [&]() -> lra_status {
+      const int64_t l = j * b;
+      PHASE(LRA_PHASE_OMEGA, TRY(make_omega(ctx, j)));
+      PHASE(LRA_PHASE_SKETCH,
+            TRY(apply_omega(ctx, A, lda, m, ctx->S0, lds, ctx->sb_sparse ? ctx->z : nullptr, true)));
+      double* Y = ctx->S0;
+      if (P >= 1) {
+        PHASE(LRA_PHASE_DENSE, TRY(dense(ctx, true, b, 1.0, A, lda, ctx->S0, lds, 0.0, ctx->W, 1, lds)));
         if (l > 0) {
           PHASE(LRA_PHASE_DEFLATE, {
-            TRY(mm(ctx, false, l, b, n, 1.0, ctx->B, ldb, ctx->browE, ctx->G, lds, 0.0, ctx->BOm, 1,
-                   ldf));
+            TRY(apply_omega(ctx, ctx->B, ldb, l, ctx->BOm, ldf, ctx->sb_sparse ? ctx->zB : nullptr,
+                            false));
             TRY(mm(ctx, true, n, b, l, -1.0, ctx->B, ldb, ctx->bcolE, ctx->BOm, ldf, 1.0, ctx->W, 1,
                    lds));
           });
         }
         PHASE(LRA_PHASE_ORTH, TRY(orth(ctx, ctx->W, lds, n, ctx->G, lds)));
+        for (int s = 1; s < P; ++s) {
+          PHASE(LRA_PHASE_DENSE,
+                TRY(dense(ctx, false, b, 1.0, A, lda, ctx->G, lds, 0.0, ctx->T1, 1, lds)));
+          PHASE(LRA_PHASE_DENSE,
+                TRY(dense(ctx, true, b, 1.0, A, lda, ctx->T1, lds, 0.0, ctx->W, 1, lds)));
+          if (l > 0) {
+            PHASE(LRA_PHASE_DEFLATE, {
+              TRY(mm(ctx, false, l, b, n, 1.0, ctx->B, ldb, ctx->browE, ctx->G, lds, 0.0, ctx->BOm, 1,
+                     ldf));
+              TRY(mm(ctx, true, n, b, l, -1.0, ctx->B, ldb, ctx->bcolE, ctx->BOm, ldf, 1.0, ctx->W, 1,
+                     lds));
+            });
+          }
+          PHASE(LRA_PHASE_ORTH, TRY(orth(ctx, ctx->W, lds, n, ctx->G, lds)));
+        }
+        PHASE(LRA_PHASE_DENSE, TRY(dense(ctx, false, b, 1.0, A, lda, ctx->G, lds, 0.0, ctx->Yb, 1, lds)));
+        Y = ctx->Yb;
       }
-      PHASE(LRA_PHASE_DENSE, TRY(dense(ctx, false, b, 1.0, A, lda, ctx->G, lds, 0.0, ctx->Yb, 1, lds)));
-      Y = ctx->Yb;
-    }
-    if (ctx->keep_y)
-      CK(cudaMemcpy2DAsync(ctx->Yk + l * ldq, ldq * sizeof(double), Y, lds * sizeof(double),
-                           m * sizeof(double), b, cudaMemcpyDeviceToDevice, ctx->st));
-    if (l > 0) {
-      PHASE(LRA_PHASE_PROJECT, {
-        for (int pass = 0; pass < 2; ++pass) {
-          TRY(mm(ctx, true, l, b, m, 1.0, ctx->Q, ldq, ctx->qcolE, Y, lds, 0.0, ctx->F, 1, ldf));
-          TRY(mm(ctx, false, m, b, l, -1.0, ctx->Q, ldq, ctx->qrowE, ctx->F, ldf, 1.0, Y, 1, lds));
+      if (ctx->keep_y)
+        CK(cudaMemcpy2DAsync(ctx->Yk + l * ldq, ldq * sizeof(double), Y, lds * sizeof(double),
+                             m * sizeof(double), b, cudaMemcpyDeviceToDevice, ctx->st));
+      if (l > 0) {
+        PHASE(LRA_PHASE_PROJECT, {
+          for (int pass = 0; pass < 2; ++pass) {
+            TRY(mm(ctx, true, l, b, m, 1.0, ctx->Q, ldq, ctx->qcolE, Y, lds, 0.0, ctx->F, 1, ldf));
+            TRY(mm(ctx, false, m, b, l, -1.0, ctx->Q, ldq, ctx->qrowE, ctx->F, ldf, 1.0, Y, 1, lds));
+          }
+        });
+      }
+      double* Qj = ctx->Q + l * ldq;
+      PHASE(LRA_PHASE_ORTH, TRY(orth(ctx, Y, lds, m, Qj, ldq)));
+      PHASE(LRA_PHASE_DENSE, TRY(dense(ctx, true, b, 1.0, A, lda, Qj, ldq, 0.0, ctx->Wt, 1, lds)));
+      PHASE(LRA_PHASE_INDICATOR, {
+        CK(col_sums(ctx->Wt, lds, n, b, ctx->colsq, ctx->sb_sparse ? ctx->colsum : nullptr, ctx->st));
+        CK(total(ctx->colsq, b, ctx->scal + 1, ctx->st));
+        CK(append_rows(ctx->Wt, lds, n, b, ctx->B, ldb, l, ctx->colsum, ctx->os.p,
+                       ctx->sb_sparse ? ctx->zB : nullptr, ctx->st));
+        if (ctx->tensor) {
+          // Q_j: its column maxima, and the running row maxima of Q
+          CK(oz_rowcol_exponents(Qj, ldq, m, b, ctx->qrowE, ctx->qcolE + l, ctx->st, true));
+          // B_j = Wt^T: row maxima of B_j are Wt's column maxima; B's column maxima grow
+          CK(oz_rowcol_exponents(ctx->Wt, lds, n, b, ctx->bcolE, ctx->browE + l, ctx->st, true));
         }
       });
-    }
-    double* Qj = ctx->Q + l * ldq;
-    PHASE(LRA_PHASE_ORTH, TRY(orth(ctx, Y, lds, m, Qj, ldq)));
-    PHASE(LRA_PHASE_DENSE, TRY(dense(ctx, true, b, 1.0, A, lda, Qj, ldq, 0.0, ctx->Wt, 1, lds)));
-    PHASE(LRA_PHASE_INDICATOR, {
-      CK(col_sums(ctx->Wt, lds, n, b, ctx->colsq, ctx->sb_sparse ? ctx->colsum : nullptr, ctx->st));
-      CK(total(ctx->colsq, b, ctx->scal + 1, ctx->st));
-      CK(append_rows(ctx->Wt, lds, n, b, ctx->B, ldb, l, ctx->colsum, ctx->os.p,
-                     ctx->sb_sparse ? ctx->zB : nullptr, ctx->st));
-      if (ctx->tensor) {
-        // Q_j: its column maxima, and the running row maxima of Q
-        CK(oz_rowcol_exponents(Qj, ldq, m, b, ctx->qrowE, ctx->qcolE + l, ctx->st, true));
-        // B_j = Wt^T: row maxima of B_j are Wt's column maxima; B's column maxima grow
-        CK(oz_rowcol_exponents(ctx->Wt, lds, n, b, ctx->bcolE, ctx->browE + l, ctx->st, true));
-      }
-    });
+      return LRA_OK;
+    }));
     TRY(read_record(ctx));
     const int fl = ctx->hp->flags;
     if (fl & FLAG_TIMEOUT) return fail(ctx, LRA_ERR_TIMEOUT, "a device wait timed out");
@@ -490,9 +586,16 @@ void free_all(lra_ctx* c) {
                   c->om_vals, c->om_dense, c->sk_counts, c->sk_rows, c->sk_vals, c->A_host_copy,
                   c->rowE,   c->colE,     c->oz.yE,  c->oz.img,   c->oz.part,
                   c->qrowE,  c->qcolE,    c->browE,  c->bcolE,    c->xrowE,     c->xcolE,
-                  c->ximg[0], c->ximg[1]};
+                  c->ximg[0], c->ximg[1], c->astat};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (c->gpre.exec) cudaGraphExecDestroy(c->gpre.exec);
+  if (c->own_stream && c->st) {
+    cudaStreamDestroy(c->st);
+    c->st = nullptr;
+  }
+  for (auto& g : c->gblock)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (c->hp) cudaFreeHost(c->hp);
   for (int i = 0; i < lra_ctx::NEV; ++i) {
     if (c->ev0[i]) cudaEventDestroy(c->ev0[i]);
@@ -540,6 +643,16 @@ lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
   ctx->n = n;
   ctx->prm = *params;
   ctx->st = (cudaStream_t)cuda_stream;
+  if (!ctx->st) {
+    // a blocking stream of our own: ordered with the legacy default stream like
+    // NULL, but capturable into graphs
+    if (cudaStreamCreate(&ctx->st) != cudaSuccess) {
+      cudaGetLastError();
+      delete ctx;
+      return LRA_ERR_CUDA;
+    }
+    ctx->own_stream = true;
+  }
   ctx->b = params->b;
   ctx->P = params->P;
   ctx->kind = params->kind;
@@ -618,6 +731,18 @@ lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
   ALLOC(scal, 8);
   ALLOC(flags, 4);
   ctx->tensor = (params->flags & LRA_FLAG_FP64_SIMT) == 0;
+  ctx->graphs = (params->flags & LRA_FLAG_NO_GRAPHS) == 0;
+  {
+    // kernel attributes, before any stream capture
+    cudaError_t e = gather_prepare();
+    if (e == cudaSuccess && ctx->tensor) e = oz_prepare();
+    if (e != cudaSuccess) {
+      lra_status r = fail(ctx, LRA_ERR_CUDA, "kernel attributes: %s", cudaGetErrorString(e));
+      free_all(ctx);
+      delete ctx;
+      return r;
+    }
+  }
   if (ctx->tensor) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -635,6 +760,7 @@ lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
     ALLOC(oz.yE, LRA_MAX_B);
     ALLOC(oz.img, ctx->oz.img_bytes);
     ALLOC(oz.part, oz_part_elems(ctx->oz.ctas));
+    ALLOC(astat, a_stats_part_elems(m, n));
     // A's digit images when the device has room (else every pass cuts A itself)
     if (!(params->flags & LRA_FLAG_NO_A_DIGITS)) {
       const int64_t b0 = oz_ximg_bytes(m, n), b1 = oz_ximg_bytes(n, m);

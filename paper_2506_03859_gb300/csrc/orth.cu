@@ -44,6 +44,72 @@ __global__ void __launch_bounds__(256) k_col_sums(const double* __restrict__ X, 
   }
 }
 
+// One pass over A (m x n, column-major) for the set-up of a run: per-column sums of
+// squares (||A||_F^2 of Alg. 1 step 1, summed per column over 512-row blocks,
+// then over the blocks in order), and the largest biased exponent of every
+// column and every row (the scales of the tensor-core digits).  CTA (rb, cb):
+// rows 512 rb .., columns 32 cb ..; warp w takes 4 of the columns, lane l the
+// rows l, l + 32, ...; per column the warp reduces by shuffles; row maxima meet
+// in shared memory, one atomic per row and CTA.  colE and rowE start at zero.
+__global__ void __launch_bounds__(256) k_a_stats(const double* __restrict__ A, int64_t lda,
+                                                 int64_t m, int64_t n, double* __restrict__ part,
+                                                 int* __restrict__ colE, int* __restrict__ rowE) {
+  __shared__ int srow[8][512];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t r0 = (int64_t)blockIdx.x * 512, c0 = (int64_t)blockIdx.y * 32 + warp * 4;
+  int rmax[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) rmax[k] = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t c = c0 + q;
+    if (c >= n) break;  // warp-uniform
+    const double* col = A + c * lda + r0;
+    double s0 = 0.0, s1 = 0.0;
+    int e = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int64_t r = lane + 32 * k;
+      const double x = (r0 + r < m) ? __ldg(col + r) : 0.0;
+      const int ex = (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+      e = max(e, ex);
+      rmax[k] = max(rmax[k], ex);
+      if (k & 1)
+        s1 = fma(x, x, s1);
+      else
+        s0 = fma(x, x, s0);
+    }
+    double sq = s0 + s1;
+    for (int o = 16; o > 0; o >>= 1) {
+      sq += __shfl_down_sync(0xffffffffu, sq, o);
+      e = max(e, __shfl_down_sync(0xffffffffu, e, o));
+    }
+    if (lane == 0) {
+      part[(int64_t)blockIdx.x * n + c] = sq;
+      atomicMax(colE + c, e);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) srow[warp][lane + 32 * k] = rmax[k];
+  __syncthreads();
+  for (int r = threadIdx.x; r < 512; r += 256) {
+    int e = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) e = max(e, srow[w][r]);
+    if (r0 + r < m) atomicMax(rowE + r0 + r, e);
+  }
+}
+
+// colsq[c] = sum over the row blocks, in order, of part[rb * n + c].
+__global__ void __launch_bounds__(256) k_sum_blocks(const double* __restrict__ part, int64_t nrb,
+                                                    int64_t n, double* __restrict__ colsq) {
+  const int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (c >= n) return;
+  double s = 0.0;
+  for (int64_t rb = 0; rb < nrb; ++rb) s += part[rb * n + c];
+  colsq[c] = s;
+}
+
 __global__ void __launch_bounds__(1024) k_total(const double* __restrict__ v, int64_t count,
                                                 double* __restrict__ out) {
   __shared__ double red[32];
@@ -167,6 +233,22 @@ cudaError_t col_sums(const double* X, int64_t ld, int64_t rows, int64_t cols, do
                      double* sum, cudaStream_t st) {
   if (cols <= 0) return cudaSuccess;
   k_col_sums<<<(unsigned)cols, 256, 0, st>>>(X, ld, rows, sumsq, sum);
+  return launched();
+}
+
+int64_t a_stats_part_elems(int64_t m, int64_t n) { return (m + 511) / 512 * n; }
+
+cudaError_t a_stats(const double* A, int64_t lda, int64_t m, int64_t n, double* part, double* colsq,
+                    int* colE, int* rowE, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(colE, 0, n * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(rowE, 0, m * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const int64_t nrb = (m + 511) / 512;
+  k_a_stats<<<dim3((unsigned)nrb, (unsigned)((n + 31) / 32)), 256, 0, st>>>(A, lda, m, n, part, colE,
+                                                                            rowE);
+  e = launched();
+  if (e != cudaSuccess) return e;
+  k_sum_blocks<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, nrb, n, colsq);
   return launched();
 }
 

@@ -172,16 +172,21 @@ __global__ void __launch_bounds__(256) k_oz_colmaxexp(const double* __restrict__
   if (threadIdx.x == 0) {
     int t = 0;
     for (int q = 0; q < 8; ++q) t = max(t, red[q]);
-    atomicMax(out + c, t);
+    if (gridDim.y == 1)
+      out[c] = t;  // the only chunk: no zeroing, no atomics
+    else
+      atomicMax(out + c, t);
   }
 }
 
 // Column exponents of X (rows x cols): zero out, then the split scan.
 cudaError_t colmaxexp(const double* X, int64_t ld, int64_t rows, int64_t cols, int* out,
                       cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(out, 0, cols * sizeof(int), st);
-  if (e != cudaSuccess) return e;
   const int64_t rchunk = 4096;
+  if (rows > rchunk) {
+    cudaError_t e = cudaMemsetAsync(out, 0, cols * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+  }
   dim3 grid((unsigned)cols, (unsigned)((rows + rchunk - 1) / rchunk));
   k_oz_colmaxexp<<<grid, 256, 0, st>>>(X, ld, rows, rchunk, out);
   return launched();
@@ -190,7 +195,7 @@ cudaError_t colmaxexp(const double* X, int64_t ld, int64_t rows, int64_t cols, i
 // out[r] = max over the columns of X[r, :] of the biased exponent (out pre-zeroed).
 __global__ void __launch_bounds__(256) k_oz_rowmaxexp(const double* __restrict__ X, int64_t ld,
                                                       int64_t rows, int64_t cols, int64_t cchunk,
-                                                      int* __restrict__ out) {
+                                                      int* __restrict__ out, bool direct) {
   const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (r >= rows) return;
   const int64_t c0 = (int64_t)blockIdx.y * cchunk;
@@ -200,7 +205,10 @@ __global__ void __launch_bounds__(256) k_oz_rowmaxexp(const double* __restrict__
     const uint64_t b = (uint64_t)__double_as_longlong(__ldg(X + r + c * ld));
     e = max(e, (int)((b >> 52) & 0x7FFu));
   }
-  atomicMax(out + r, e);
+  if (direct)
+    out[r] = e;  // one column chunk and nothing to accumulate: plain store
+  else
+    atomicMax(out + r, e);
 }
 
 // Pre-cut Y: stage u of the image holds the seven 64 x 16 (N x K) digit planes
@@ -480,6 +488,9 @@ __device__ __forceinline__ double scale2(double v, int e) {
 // The flush (warps 0..3): at every window end fold the exact sums into the int64
 // totals and re-arm them; at a segment end also read weights 4..6 and write the
 // tile (to C when the segment is the whole tile, else to the CTA's partial slot).
+// PIPE: overlap the TMEM loads of the next 4-column chunk with the current one
+// (needs ~48 more registers; the on-the-fly kernel, capped at 128, goes without).
+template <bool PIPE>
 __device__ __forceinline__ void oz_flush_role(OzShared& sh, const OzArgs& a, const Cursor& start,
                                               int64_t cta) {
   volatile int& s_abort = sh.abort;
@@ -522,22 +533,29 @@ __device__ __forceinline__ void oz_flush_role(OzShared& sh, const OzArgs& a, con
         break;
       }
       tc::fence_after_sync();
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {  // 4 output columns at a time
-        if (4 * j >= ncols) continue;  // padding columns: never read, never re-armed
+      // 4 output columns at a time; chunk j + 1's TMEM loads are issued right after
+      // chunk j's wait, so their latency overlaps chunk j's integer work.  Padding
+      // columns (>= ncols) are never read and never re-armed.
+      uint32_t ra[6][4], rb[6][4];
+      auto load = [&](int j, uint32_t (&r)[6][4]) {
         const uint32_t c4 = 4u * j;
-        uint32_t g0[4], g1[4], g2[4], g3[4];
-        tc::tmem_ld4(tb + c4, g0);
-        tc::tmem_ld4(tb + 64u + c4, g1);
-        tc::tmem_ld4(tb + 128u + c4, g2);
-        tc::tmem_ld4(tb + 192u + c4, g3);
-        tc::tmem_ld_wait();
+        tc::tmem_ld4(tb + c4, r[0]);
+        tc::tmem_ld4(tb + 64u + c4, r[1]);
+        tc::tmem_ld4(tb + 128u + c4, r[2]);
+        tc::tmem_ld4(tb + 192u + c4, r[3]);
+        if (j >= 8) {
+          tc::tmem_ld4(tb + COL_ACC_LO + c4 - 32u, r[4]);
+          tc::tmem_ld4(tb + COL_ACC_HI + c4 - 32u, r[5]);
+        }
+      };
+      auto work = [&](int j, uint32_t (&r)[6][4]) {
+        const uint32_t c4 = 4u * j;
         int64_t add[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           // (G_0 * 256 + G_1) and (G_2 * 256 + G_3), each exact in 32 bits
-          const int hi = (int)(g0[i] * 256u + g1[i] - 257u * MAGIC);
-          const int lo = (int)(g2[i] * 256u + g3[i] - 257u * MAGIC);
+          const int hi = (int)(r[0][i] * 256u + r[1][i] - 257u * MAGIC);
+          const int lo = (int)(r[2][i] * 256u + r[3][i] - 257u * MAGIC);
           add[i] = ((int64_t)hi << 16) + (int64_t)lo;
         }
         tc::tmem_st4_splat(tb + c4, MAGIC);
@@ -549,17 +567,40 @@ __device__ __forceinline__ void oz_flush_role(OzShared& sh, const OzArgs& a, con
           for (int i = 0; i < 4; ++i) acc[4 * j + i] += add[i];
         } else {
           uint32_t lo[4], hi[4];
-          tc::tmem_ld4(tb + COL_ACC_LO + c4 - 32u, lo);
-          tc::tmem_ld4(tb + COL_ACC_HI + c4 - 32u, hi);
-          tc::tmem_ld_wait();
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            const uint64_t t = (((uint64_t)hi[i] << 32) | lo[i]) + (uint64_t)add[i];
+            const uint64_t t = (((uint64_t)r[5][i] << 32) | r[4][i]) + (uint64_t)add[i];
             lo[i] = (uint32_t)t;
             hi[i] = (uint32_t)(t >> 32);
           }
           tc::tmem_st4(tb + COL_ACC_LO + c4 - 32u, lo);
           tc::tmem_st4(tb + COL_ACC_HI + c4 - 32u, hi);
+        }
+      };
+      if (PIPE) {
+        load(0, ra);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          if (4 * j >= ncols) break;
+          tc::tmem_ld_wait();
+          if (j + 1 < 16 && 4 * (j + 1) < ncols) {
+            if (j & 1)
+              load(j + 1, ra);
+            else
+              load(j + 1, rb);
+          }
+          if (j & 1)
+            work(j, rb);
+          else
+            work(j, ra);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          if (4 * j >= ncols) break;
+          load(j, ra);
+          tc::tmem_ld_wait();
+          work(j, ra);
         }
       }
       tc::tmem_st_wait();
@@ -702,7 +743,7 @@ __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
     if (lane == 0) oz_mma_role(sh, start, sm);
     __syncwarp();
   } else if (warp < 4) {
-    oz_flush_role(sh, a, start, cta);
+    oz_flush_role<false>(sh, a, start, cta);
   }
   oz_teardown(sh, a);
 }
@@ -752,7 +793,7 @@ __global__ void __launch_bounds__(NT_IMG, 1) k_ozgemm_img(OzArgs a, const uint8_
     if (lane == 0) oz_mma_role(sh, start, sm);
     __syncwarp();
   } else {
-    oz_flush_role(sh, a, start, cta);
+    oz_flush_role<true>(sh, a, start, cta);
   }
   oz_teardown(sh, a);
 }
@@ -784,18 +825,16 @@ __global__ void __launch_bounds__(NPROD) k_oz_xcut(OzArgs a, uint8_t* __restrict
 }
 
 // Combine the partial tiles of tiles split across CTAs, in a fixed order.  Grid:
-// (tiles, FIX_SPLIT); each CTA handles FIX_ELEMS elements of its tile with
-// FIX_LANES threads per element: thread l sums the partials of the contributing
-// CTAs cf + l, cf + l + FIX_LANES, ... in CTA order, and the FIX_LANES sums are
-// added in lane order.  Tile t is covered by CTAs cf..cl; every one of them but
-// cf starts its range inside t, so t is its first tile (slot 0); cf holds t in
-// slot 1 unless its range also starts inside t.  CTAs with an empty range (more
-// CTAs than units) wrote nothing and are skipped.
-constexpr int FIX_LANES = 4;
-constexpr int FIX_ELEMS = 256 / FIX_LANES;
-constexpr int FIX_SPLIT = TM * NN / FIX_ELEMS;
-
+// (tiles, TM * NN * LANES / 256); each CTA handles 256 / LANES elements of its tile
+// with LANES threads per element: thread l sums the partials of the contributing
+// CTAs cf + l, cf + l + LANES, ... in CTA order, and the LANES sums are added in
+// lane order.  Tile t is covered by CTAs cf..cl; every one of them but cf starts
+// its range inside t, so t is its first tile (slot 0); cf holds t in slot 1
+// unless its range also starts inside t.  CTAs with an empty range (more CTAs
+// than units) wrote nothing and are skipped.
+template <int LANES>
 __global__ void __launch_bounds__(256) k_oz_fixup(OzArgs a, int G) {
+  constexpr int ELEMS = 256 / LANES;
   __shared__ int64_t s_cf, s_cl;
   __shared__ int s_slot_f;
   const int64_t t = blockIdx.x;
@@ -815,30 +854,55 @@ __global__ void __launch_bounds__(256) k_oz_fixup(OzArgs a, int G) {
   const int64_t cf = s_cf, cl = s_cl;
   if (cf == cl) return;
   const int slot_f = s_slot_f;
-  const int lane = threadIdx.x % FIX_LANES;
-  const int e = blockIdx.y * FIX_ELEMS + threadIdx.x / FIX_LANES;
+  const int lane = threadIdx.x % LANES;
+  const int e = blockIdx.y * ELEMS + threadIdx.x / LANES;
   const int r = e % TM, c = e / TM;
   const int64_t p = t * TM + r;
   const bool valid = p < a.P && c < a.N;
   const double* src = a.part + (int64_t)c * TM + r;
   const bool all_nonempty = T >= G;  // then every CTA's range holds a unit
-  double s = 0.0;
+  // four independent running sums over the lane's partials (the k-th takes every
+  // fourth), so that four loads are in flight; combined in a fixed order
+  auto part = [&](int64_t q) -> double {
+    const int slot = (q == cf) ? slot_f : 0;
+    return (all_nonempty || q * T / G < (q + 1) * T / G) ? src[(q * 2 + slot) * (int64_t)(NN * TM)]
+                                                          : 0.0;
+  };
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   if (valid) {
-    for (int64_t q = cf + lane; q <= cl; q += FIX_LANES) {
-      const int slot = (q == cf) ? slot_f : 0;
-      if (all_nonempty || q * T / G < (q + 1) * T / G) s += src[(q * 2 + slot) * (int64_t)(NN * TM)];
+    int64_t q = cf + lane;
+    for (; q + 3 * LANES <= cl; q += 4 * LANES) {
+      const double v0 = part(q), v1 = part(q + LANES), v2 = part(q + 2 * LANES), v3 = part(q + 3 * LANES);
+      s0 += v0;
+      s1 += v1;
+      s2 += v2;
+      s3 += v3;
     }
+    for (; q <= cl; q += LANES) s0 += part(q);
   }
+  double s = (s0 + s1) + (s2 + s3);
   // lanes of one element are adjacent threads of one warp
 #pragma unroll
-  for (int o = 1; o < FIX_LANES; o <<= 1) {
-    const double other = __shfl_down_sync(0xffffffffu, s, o, FIX_LANES);
+  for (int o = 1; o < LANES; o <<= 1) {
+    const double other = __shfl_down_sync(0xffffffffu, s, o, LANES);
     if ((lane & (2 * o - 1)) == 0) s += other;
   }
   if (lane == 0 && valid) {
     double* dst = a.C + p * a.csp + (int64_t)c * a.csc;
     *dst = (a.beta == 0.0) ? a.alpha * s : a.alpha * s + a.beta * (*dst);
   }
+}
+
+// The fixup launch: one lane per element when a CTA's range spans a tile or more
+// (a tile then has two or three parts), four when tiles span many CTAs.
+cudaError_t launch_fixup(const OzArgs& a, int G, cudaStream_t st) {
+  const int64_t T = a.tiles * a.kst;
+  if (T >= (int64_t)G * a.kst) {
+    k_oz_fixup<1><<<dim3((unsigned)a.tiles, TM * NN / 256), 256, 0, st>>>(a, G);
+  } else {
+    k_oz_fixup<4><<<dim3((unsigned)a.tiles, TM * NN * 4 / 256), 256, 0, st>>>(a, G);
+  }
+  return launched();
 }
 
 cudaError_t oz_rowcol_exponents(const double* X, int64_t ld, int64_t rows, int64_t cols,
@@ -848,14 +912,15 @@ cudaError_t oz_rowcol_exponents(const double* X, int64_t ld, int64_t rows, int64
     if (e != cudaSuccess) return e;
   }
   if (rowE) {
-    if (!accumulate_rows) {
+    const int64_t csplit = cols >= 256 ? 16 : 1;
+    const bool direct = csplit == 1 && !accumulate_rows;
+    if (!accumulate_rows && !direct) {
       cudaError_t e = cudaMemsetAsync(rowE, 0, rows * sizeof(int), st);
       if (e != cudaSuccess) return e;
     }
-    const int64_t csplit = cols >= 256 ? 16 : 1;
     const int64_t cchunk = (cols + csplit - 1) / csplit;
     dim3 grid((unsigned)((rows + 255) / 256), (unsigned)((cols + cchunk - 1) / cchunk));
-    k_oz_rowmaxexp<<<grid, 256, 0, st>>>(X, ld, rows, cols, cchunk, rowE);
+    k_oz_rowmaxexp<<<grid, 256, 0, st>>>(X, ld, rows, cols, cchunk, rowE, direct);
     return launched();
   }
   return cudaSuccess;
@@ -890,13 +955,18 @@ OzArgs make_args(int64_t P, int64_t N, int64_t K, double alpha, const double* X,
 }
 
 // Y's exponents and digit image (shared by both GEMM kernels).
+// yE_known: Y's column exponents when the caller has them (else computed into w.yE).
 cudaError_t prepare_y(const double* Y, int64_t ldy, int64_t K, int64_t N, const OzWorkspace& w,
-                      cudaStream_t st) {
+                      const int* yE_known, cudaStream_t st) {
   const int64_t kst = (K + KS - 1) / KS;
-  cudaError_t e = colmaxexp(Y, ldy, K, N, w.yE, st);
-  if (e != cudaSuccess) return e;
+  const int* yE = yE_known;
+  if (!yE) {
+    cudaError_t e = colmaxexp(Y, ldy, K, N, w.yE, st);
+    if (e != cudaSuccess) return e;
+    yE = w.yE;
+  }
   const int64_t ythreads = kst * NN * 2;
-  k_oz_ycut<<<(unsigned)((ythreads + 255) / 256), 256, 0, st>>>(Y, ldy, K, (int)N, w.yE, w.img, kst);
+  k_oz_ycut<<<(unsigned)((ythreads + 255) / 256), 256, 0, st>>>(Y, ldy, K, (int)N, yE, w.img, kst);
   return launched();
 }
 
@@ -909,6 +979,14 @@ cudaError_t set_smem_once(F kernel, bool& done) {
   return e;
 }
 }  // namespace
+
+cudaError_t oz_prepare() {
+  static bool a0 = false, a1 = false, a2 = false;
+  cudaError_t e = set_smem_once(k_ozgemm<false>, a0);
+  if (e == cudaSuccess) e = set_smem_once(k_ozgemm<true>, a1);
+  if (e == cudaSuccess) e = set_smem_once(k_ozgemm_img, a2);
+  return e;
+}
 
 int64_t oz_ximg_bytes(int64_t P, int64_t K) {
   return ((P + TM - 1) / TM) * ((K + KS - 1) / KS) * (int64_t)(S * A_PLANE);
@@ -934,32 +1012,30 @@ cudaError_t ozgemm_img(int64_t P, int64_t N, int64_t K, double alpha, const uint
   if (P <= 0 || N <= 0) return cudaSuccess;
   if (N > NN || K <= 0 || K > MAX_K) return cudaErrorInvalidValue;
   if (oz_img_bytes(K) > w.img_bytes) return cudaErrorInvalidValue;
-  static bool attr = false;
-  cudaError_t e = set_smem_once(k_ozgemm_img, attr);
+  cudaError_t e = oz_prepare();
   if (e != cudaSuccess) return e;
-  e = prepare_y(Y, ldy, K, N, w, st);
+  e = prepare_y(Y, ldy, K, N, w, nullptr, st);
   if (e != cudaSuccess) return e;
   OzArgs a = make_args(P, N, K, alpha, nullptr, 0, xE, beta, out, w, flags);
   const int G = w.ctas;
   k_ozgemm_img<<<G, NT_IMG, SMEM_DYN, st>>>(a, ximg);
   e = launched();
   if (e != cudaSuccess || a.whole_tiles) return e;
-  k_oz_fixup<<<dim3((unsigned)a.tiles, FIX_SPLIT), 256, 0, st>>>(a, G);
-  return launched();
+  return launch_fixup(a, G, st);
 }
 
 cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, const double* X,
                    int64_t ldx, const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
-                   const OzWorkspace& w, int* flags, cudaStream_t st) {
+                   const OzWorkspace& w, int* flags, cudaStream_t st, const int* yE_known) {
   if (P <= 0 || N <= 0) return cudaSuccess;
   if (N > NN || K <= 0 || K > MAX_K) return cudaErrorInvalidValue;
   if (oz_img_bytes(K) > w.img_bytes) return cudaErrorInvalidValue;
-  static bool attr[2] = {false, false};
-  cudaError_t e = trans ? set_smem_once(k_ozgemm<true>, attr[1]) : set_smem_once(k_ozgemm<false>, attr[0]);
+  cudaError_t e = oz_prepare();
   if (e != cudaSuccess) return e;
-  e = prepare_y(Y, ldy, K, N, w, st);
+  e = prepare_y(Y, ldy, K, N, w, yE_known, st);
   if (e != cudaSuccess) return e;
   OzArgs a = make_args(P, N, K, alpha, X, ldx, xE, beta, out, w, flags);
+  if (yE_known) a.yE = yE_known;
   const int G = w.ctas;
   if (trans)
     k_ozgemm<true><<<G, NT, SMEM_DYN, st>>>(a);
@@ -967,8 +1043,7 @@ cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, co
     k_ozgemm<false><<<G, NT, SMEM_DYN, st>>>(a);
   e = launched();
   if (e != cudaSuccess || a.whole_tiles) return e;
-  k_oz_fixup<<<dim3((unsigned)a.tiles, FIX_SPLIT), 256, 0, st>>>(a, G);
-  return launched();
+  return launch_fixup(a, G, st);
 }
 
 }  // namespace lra

@@ -95,17 +95,21 @@ __global__ void __launch_bounds__(256) k_gather_staged(
   }
 }
 
+cudaError_t gather_prepare() {
+  static bool attr = false;
+  if (attr) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute((const void*)k_gather_staged,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM);
+  if (e == cudaSuccess) attr = true;
+  return e;
+}
+
 cudaError_t gather_sketch(const double* X, int64_t ldx, int64_t rows_x, const int* counts,
                           const int* rows, const double* vals, int cap, int64_t ncols, double* Y,
                           int64_t ldy, const double* shift, int* flags, cudaStream_t st) {
   if (ncols <= 0 || rows_x <= 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute((const void*)k_gather_staged,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e0 = gather_prepare();
+  if (e0 != cudaSuccess) return e0;
   const int64_t chunks = (rows_x + GR - 1) / GR;
   dim3 grid((unsigned)chunks, (unsigned)std::min<int64_t>(ncols, 65535));
   const bool aligned = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (ldx % 2 == 0);

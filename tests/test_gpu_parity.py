@@ -266,3 +266,29 @@ def test_digit_images_change_nothing(kind, p, zeta, P):
     assert (s0, k0) == (s1, k1) and k0 > 0
     assert e0 == e1
     assert np.array_equal(q0, q1) and np.array_equal(b0, b1)
+
+
+@pytest.mark.parametrize("kind,p,zeta,P", [(om.SPARSE_SIGN, 0.0, 8, 1), (om.STD_BERNOULLI, 0.0, 0, 2)],
+                         ids=["ss8_P1", "sb_p1_P2"])
+def test_graphs_change_nothing(kind, p, zeta, P):
+    """Each block's kernels replayed from a captured CUDA graph (the default) and
+    launched one by one (LRA_FLAG_NO_GRAPHS) agree bit for bit, on the first run
+    (capture) and on a second run (replay), and count the same launches."""
+    m, n = 1201, 757
+    A = low_rank_matrix(m, n, "poly1.5", seed=43)
+    Ad = dev(A)
+    runs = []
+    for graphs in (True, False):
+        f = lra.Farpca(m, n, eps=1e-2, b=24, P=P, kind=kind, zeta=zeta, p=p, seed=9, graphs=graphs)
+        for _ in range(2):
+            k0 = lra.kernel_launches()
+            f.run(Ad)
+            r = f.result()
+            runs.append((r["status"], r["rank"], r["E"], lra.kernel_launches() - k0,
+                         r["Q"].cpu().numpy().copy(), r["B"].cpu().numpy().copy()))
+        f.close()
+    ref = runs[-1]  # no graphs, second run
+    assert ref[1] > 0
+    for got in runs:
+        assert got[:4] == ref[:4]
+        assert np.array_equal(got[4], ref[4]) and np.array_equal(got[5], ref[5])
