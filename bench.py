@@ -174,14 +174,15 @@ def source_digest(names):
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel, digest):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+def traffic_for(kernel, digest, workload):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged
+    and the figure is for this workload."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f).get(kernel)
     except (OSError, ValueError):
         return None
-    if not t or t.get("source_digest") != digest:
+    if not t or t.get("source_digest") != digest or t.get("workload") != workload:
         return None
     return t.get("dram_bytes_per_launch")
 
@@ -310,7 +311,7 @@ def main():
         roofline = {"kernel": "k_ozgemm_img (FP64-accurate GEMM on tcgen05 from the f16 digit images of A)",
                     "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"],
-                    "traffic": traffic_for("k_ozgemm_img", source_digest(["ozgemm.cu"])),
+                    "traffic": traffic_for("k_ozgemm_img", source_digest(["ozgemm.cu"]), args.workload),
                     "peak_source": peak_src + " HBM copy bandwidth",
                     "tensor_pipe": {"bf16_tflops": tflops, "peak": peaks["bf16_tflops"],
                                     "frac": tflops / peaks["bf16_tflops"],

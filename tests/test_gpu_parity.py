@@ -226,6 +226,42 @@ def test_full_size_bench_config():
     f.close()
 
 
+@pytest.fixture(scope="module")
+def big():
+    """The 20000 x 10000 benchmark matrix, on the host and on the device (built once)."""
+    A = workload_matrix("dense20000x10000_exp100")
+    return A, dev(A)
+
+
+# The other variants of the 20000 x 10000 configuration: every Omega kind, zeta in
+# {4, 16}, P in {0, 2}, eps in {1e-1, 1e-2}
+# (seed 2 of the sparse Gaussian kind draws an empty Omega column in block 0:
+# the Cholesky breakdown rule ends that run with rank 0, on both sides)
+BIG_CASES = [(om.GAUSSIAN, 0.0, 0, 1, 1e-2, 2), (om.STD_BERNOULLI, 0.5, 0, 1, 1e-2, 2),
+             (om.SPARSE_SIGN, 0.0, 4, 0, 1e-1, 2), (om.SPARSE_SIGN, 0.0, 16, 2, 1e-2, 2),
+             (om.SPARSE_GAUSSIAN, 0.0, 8, 1, 1e-2, 3), (om.SPARSE_GAUSSIAN, 0.0, 8, 1, 1e-2, 2)]
+
+
+@pytest.mark.parametrize("kind,p,zeta,P,eps,seed", BIG_CASES,
+                         ids=["gauss_P1", "sb_half_P1", "ss4_P0_eps1e-1", "ss16_P2", "sg8_P1",
+                              "sg8_breakdown"])
+def test_full_size_variants(big, kind, p, zeta, P, eps, seed):
+    """Full-size parity for the other Omega kinds and settings of the benchmark's
+    matrix family: attained rank and status equal, E, Q and B within the bars."""
+    A, Ad = big
+    m, n = A.shape
+    f = lra.Farpca(m, n, eps=eps, b=50, P=P, kind=kind, zeta=zeta, p=p, seed=seed)
+    f.run(Ad)
+    r = f.result()
+    ref = F.farpca(A, eps, P=P, b=50, kind=kind, seed=seed, zeta=zeta, p=p)
+    assert r["rank"] == ref["rank"] and r["status"] == ref["status"]
+    assert abs(r["E"] - ref["E"]) <= 1e-12 * ref["normA2"]
+    if ref["rank"] > 0:  # a breakdown in the first block (an empty Omega column) leaves none
+        assert float(np.abs(r["Q"].cpu().numpy() - ref["Q"]).max()) <= 1e-10
+        assert maxrel(r["B"].cpu().numpy(), ref["B"]) <= 1e-10
+    f.close()
+
+
 @pytest.mark.parametrize("kind,p,zeta,P", [(om.SPARSE_SIGN, 0.0, 8, 0), (om.SPARSE_SIGN, 0.0, 8, 1),
                                            (om.SPARSE_SIGN, 0.0, 8, 2), (om.GAUSSIAN, 0.0, 0, 1)],
                          ids=["ss8_P0", "ss8_P1", "ss8_P2", "gauss_P1"])
