@@ -101,6 +101,11 @@ struct lra_ctx {
   double* sk_vals = nullptr;
   int64_t sk_entries = 0, sk_cols = 0;
   double* A_host_copy = nullptr;  // device copy of A for lra_farpca_host
+  // lra_farpca_host copies A in column chunks on several streams (copy engines)
+  static constexpr int NCOPY = 4;
+  cudaStream_t cst[NCOPY] = {};
+  cudaEvent_t cev[NCOPY] = {};
+  cudaEvent_t cstart = nullptr;
   Pinned* hp = nullptr;
 
   // phase timing (LRA_FLAG_PROFILE)
@@ -590,6 +595,11 @@ void free_all(lra_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->gpre.exec) cudaGraphExecDestroy(c->gpre.exec);
+  for (int i = 0; i < lra_ctx::NCOPY; ++i) {
+    if (c->cst[i]) cudaStreamDestroy(c->cst[i]);
+    if (c->cev[i]) cudaEventDestroy(c->cev[i]);
+  }
+  if (c->cstart) cudaEventDestroy(c->cstart);
   if (c->own_stream && c->st) {
     cudaStreamDestroy(c->st);
     c->st = nullptr;
@@ -964,9 +974,26 @@ lra_status lra_farpca_host(lra_ctx* ctx, const double* A_host, int64_t lda_host,
   if (Q_host && ldq_host < m) return fail(ctx, LRA_ERR_INVALID_ARG, "ldq_host < m");
   if (B_host && ldb_host < ctx->lmax) return fail(ctx, LRA_ERR_INVALID_ARG, "ldb_host < capacity");
   if (!ctx->A_host_copy) CK(dalloc(&ctx->A_host_copy, ctx->ldq * n));
-  CK(cudaMemcpy2DAsync(ctx->A_host_copy, ctx->ldq * sizeof(double), A_host,
-                       lda_host * sizeof(double), m * sizeof(double), n, cudaMemcpyHostToDevice,
-                       ctx->st));
+  if (!ctx->cstart) {
+    CK(cudaEventCreateWithFlags(&ctx->cstart, cudaEventDisableTiming));
+    for (int i = 0; i < lra_ctx::NCOPY; ++i) {
+      CK(cudaStreamCreateWithFlags(&ctx->cst[i], cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&ctx->cev[i], cudaEventDisableTiming));
+    }
+  }
+  // A in NCOPY column chunks on as many streams (several copy engines at once), all
+  // after the work already on the context's stream and before the run
+  CK(cudaEventRecord(ctx->cstart, ctx->st));
+  for (int i = 0; i < lra_ctx::NCOPY; ++i) {
+    const int64_t c0 = i * n / lra_ctx::NCOPY, c1 = (i + 1) * n / lra_ctx::NCOPY;
+    CK(cudaStreamWaitEvent(ctx->cst[i], ctx->cstart, 0));
+    if (c1 > c0)
+      CK(cudaMemcpy2DAsync(ctx->A_host_copy + c0 * ctx->ldq, ctx->ldq * sizeof(double),
+                           A_host + c0 * lda_host, lda_host * sizeof(double), m * sizeof(double),
+                           c1 - c0, cudaMemcpyHostToDevice, ctx->cst[i]));
+    CK(cudaEventRecord(ctx->cev[i], ctx->cst[i]));
+    CK(cudaStreamWaitEvent(ctx->st, ctx->cev[i], 0));
+  }
   lra_status s = run(ctx, ctx->A_host_copy, ctx->ldq);
   if (s < 0) return s;
   if (Q_host && ctx->rank > 0)
