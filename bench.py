@@ -334,6 +334,7 @@ def main():
     }
 
     if not args.no_extras:
+        line["mixed"] = mixed_form(lra, torch, Ad, cfg, m, n, args.steps, res["rel_err"], stream)
         line["sketch_pass"] = sketch_pass(lra, torch, f, Ad, cfg, args.sketch_blocks, peaks, peak_src)
         line["e2e"] = e2e(lra, torch, np, f, A, args.steps)
         if rank == 0 and world == 1:
@@ -373,6 +374,29 @@ def sketch_pass(lra, torch, f, Ad, cfg, nblk, peaks, peak_src):
             "blocks": nblk, "ms": ms, "algorithmic_bytes": algo_bytes, "gbs": gbs,
             "bound": "hbm", "peak": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
             "frac_of_nominal_7900": gbs / 7900.0, "peak_source": peak_src}
+
+
+def mixed_form(lra, torch, Ad, cfg, m, n, steps, rel_err_fp64, stream):
+    """The mixed precision form (LRA_FLAG_MIXED) on the same workload: time-to-eps as
+    solves/s and its final relative error beside the FP64 form's."""
+    f = lra.Farpca(m, n, eps=cfg["eps"], b=cfg["b"], P=cfg["P"], kind=cfg["kind"], zeta=cfg["zeta"],
+                   p=cfg["p"], seed=cfg["seed"], mixed=True, stream=stream)
+    for _ in range(2):
+        f.run(Ad)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        f.run(Ad)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    r = f.result()
+    f.close()
+    return {"value": 1e3 / ms, "unit": "solves/s", "ms_per_step": ms, "rank": r["rank"],
+            "rel_err": r["rel_err"], "rel_err_fp64_form": rel_err_fp64,
+            "note": "sketch and power passes from 4 of the 7 digits; B_j, projections, "
+                    "Gram, Cholesky and indicator FP64-accurate"}
 
 
 def dense_pass(lra, torch, f, Ad, cfg, steps, warmup, peaks, peak_src):

@@ -87,6 +87,15 @@ typedef enum { LRA_F64 = 0, LRA_F32 = 1 } lra_dtype;
                                of the set-up after ||A||_F^2) is captured once into a
                                CUDA graph, cached per block index and per A pointer,
                                and replayed; results are the same bit for bit.     */
+#define LRA_FLAG_MIXED 32u /* mixed precision form (tensor-core engine with A's digit
+                               images): the sketch and power-step passes (dense
+                               Omega sketch, W_j, the extra power steps, Y_j) use
+                               the top four of the seven digits of A and of their
+                               right operand, ~2^-30 of max|x| max|y| per product;
+                               B_j = Q_j^T A, the projections, Gram, Cholesky and
+                               the indicator stay FP64-accurate, so E is exact for
+                               the basis found.  Without the images the flag has
+                               no effect.                                          */
 
 /* Phases of one block, for lra_phase_times. */
 typedef enum {

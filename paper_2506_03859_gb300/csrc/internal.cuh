@@ -101,9 +101,10 @@ cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, co
 int64_t oz_ximg_bytes(int64_t P, int64_t K);
 cudaError_t oz_cut_x(bool trans, int64_t P, int64_t K, const double* X, int64_t ldx, const int* xE,
                      uint8_t* ximg, int ctas, cudaStream_t st);
+// low: the reduced form (digits 0..3 of both operands; ~2^-30 of max|x| max|y|).
 cudaError_t ozgemm_img(int64_t P, int64_t N, int64_t K, double alpha, const uint8_t* ximg,
                        const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
-                       const OzWorkspace& w, int* flags, cudaStream_t st);
+                       const OzWorkspace& w, int* flags, cudaStream_t st, bool low = false);
 // rowE[r] / colE[c] = largest biased exponent in row r / column c of X (either may
 // be NULL).  accumulate_rows: rowE[r] = max(rowE[r], ...) instead of overwriting.
 cudaError_t oz_rowcol_exponents(const double* X, int64_t ld, int64_t rows, int64_t cols,

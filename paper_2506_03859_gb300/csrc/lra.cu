@@ -73,6 +73,7 @@ struct lra_ctx {
     uint64_t launches = 0;   // kernel launches it holds
   };
   bool graphs = true;
+  bool mixed = false;       // LRA_FLAG_MIXED: reduced digits in the sketch and power passes
   bool own_stream = false;  // st created by lra_create (the caller passed none)
   GraphSlot gpre;
   std::vector<GraphSlot> gblock;
@@ -186,7 +187,7 @@ lra_status check_params(lra_ctx* ctx, int64_t m, int64_t n, const lra_params* p)
   if ((int64_t)p->max_blocks * p->b > mn)
     return fail(ctx, LRA_ERR_INVALID_ARG, "max_blocks * b exceeds min(m, n)");
   if (p->flags & ~(LRA_FLAG_KEEP_Y | LRA_FLAG_PROFILE | LRA_FLAG_FP64_SIMT | LRA_FLAG_NO_A_DIGITS |
-                   LRA_FLAG_NO_GRAPHS))
+                   LRA_FLAG_NO_GRAPHS | LRA_FLAG_MIXED))
     return fail(ctx, LRA_ERR_INVALID_ARG, "unknown flags");
   return LRA_OK;
 }
@@ -214,14 +215,16 @@ lra_status gemm(lra_ctx* ctx, bool trans, int64_t P, int64_t N, int64_t K, doubl
 
 // A full pass over A: C = alpha op(A) Y + beta C (op(A) = A^T when trans).  Inside
 // lra_farpca_run the digit images of A, once cut, replace A itself.
+// power: a sketch or power-step pass, which the mixed precision form runs reduced.
 lra_status dense(lra_ctx* ctx, bool trans, int64_t N, double alpha, const double* A, int64_t lda,
-                 const double* Y, int64_t ldy, double beta, double* C, int64_t csp, int64_t csc) {
+                 const double* Y, int64_t ldy, double beta, double* C, int64_t csp, int64_t csc,
+                 bool power = false) {
   const int64_t P = trans ? ctx->n : ctx->m, K = trans ? ctx->m : ctx->n;
   if (!ctx->tensor || K > oz_max_k())
     return gemm(ctx, trans, P, N, K, alpha, A, lda, Y, ldy, beta, C, csp, csc);
   if (ctx->ximg_ready) {
     CK(ozgemm_img(P, N, K, alpha, ctx->ximg[trans ? 1 : 0], trans ? ctx->colE : ctx->rowE, Y, ldy,
-                  beta, GemmOut{C, csp, csc}, ctx->oz, ctx->flags, ctx->st));
+                  beta, GemmOut{C, csp, csc}, ctx->oz, ctx->flags, ctx->st, power && ctx->mixed));
     return LRA_OK;
   }
   CK(ozgemm(trans, P, N, K, alpha, A, lda, trans ? ctx->colE : ctx->rowE, Y, ldy, beta,
@@ -304,7 +307,8 @@ lra_status apply_omega(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows_
                      out, ldo, shift, ctx->flags, ctx->st));
     return LRA_OK;
   }
-  if (x_is_A) return dense(ctx, false, ctx->b, 1.0, X, ldx, ctx->om_dense, ctx->ldod, 0.0, out, 1, ldo);
+  if (x_is_A)
+    return dense(ctx, false, ctx->b, 1.0, X, ldx, ctx->om_dense, ctx->ldod, 0.0, out, 1, ldo, true);
   return mm(ctx, false, rows_x, ctx->b, ctx->n, 1.0, X, ldx, ctx->browE, ctx->om_dense, ctx->ldod, 0.0,
             out, 1, ldo);
 }
@@ -487,7 +491,8 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
             TRY(apply_omega(ctx, A, lda, m, ctx->S0, lds, ctx->sb_sparse ? ctx->z : nullptr, true)));
       double* Y = ctx->S0;
       if (P >= 1) {
-        PHASE(LRA_PHASE_DENSE, TRY(dense(ctx, true, b, 1.0, A, lda, ctx->S0, lds, 0.0, ctx->W, 1, lds)));
+        PHASE(LRA_PHASE_DENSE,
+            TRY(dense(ctx, true, b, 1.0, A, lda, ctx->S0, lds, 0.0, ctx->W, 1, lds, true)));
         if (l > 0) {
           PHASE(LRA_PHASE_DEFLATE, {
             TRY(apply_omega(ctx, ctx->B, ldb, l, ctx->BOm, ldf, ctx->sb_sparse ? ctx->zB : nullptr,
@@ -499,9 +504,9 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
         PHASE(LRA_PHASE_ORTH, TRY(orth(ctx, ctx->W, lds, n, ctx->G, lds)));
         for (int s = 1; s < P; ++s) {
           PHASE(LRA_PHASE_DENSE,
-                TRY(dense(ctx, false, b, 1.0, A, lda, ctx->G, lds, 0.0, ctx->T1, 1, lds)));
+                TRY(dense(ctx, false, b, 1.0, A, lda, ctx->G, lds, 0.0, ctx->T1, 1, lds, true)));
           PHASE(LRA_PHASE_DENSE,
-                TRY(dense(ctx, true, b, 1.0, A, lda, ctx->T1, lds, 0.0, ctx->W, 1, lds)));
+                TRY(dense(ctx, true, b, 1.0, A, lda, ctx->T1, lds, 0.0, ctx->W, 1, lds, true)));
           if (l > 0) {
             PHASE(LRA_PHASE_DEFLATE, {
               TRY(mm(ctx, false, l, b, n, 1.0, ctx->B, ldb, ctx->browE, ctx->G, lds, 0.0, ctx->BOm, 1,
@@ -512,7 +517,8 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
           }
           PHASE(LRA_PHASE_ORTH, TRY(orth(ctx, ctx->W, lds, n, ctx->G, lds)));
         }
-        PHASE(LRA_PHASE_DENSE, TRY(dense(ctx, false, b, 1.0, A, lda, ctx->G, lds, 0.0, ctx->Yb, 1, lds)));
+        PHASE(LRA_PHASE_DENSE,
+              TRY(dense(ctx, false, b, 1.0, A, lda, ctx->G, lds, 0.0, ctx->Yb, 1, lds, true)));
         Y = ctx->Yb;
       }
       if (ctx->keep_y)
@@ -742,6 +748,7 @@ lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
   ALLOC(flags, 4);
   ctx->tensor = (params->flags & LRA_FLAG_FP64_SIMT) == 0;
   ctx->graphs = (params->flags & LRA_FLAG_NO_GRAPHS) == 0;
+  ctx->mixed = (params->flags & LRA_FLAG_MIXED) != 0;
   {
     // kernel attributes, before any stream capture
     cudaError_t e = gather_prepare();

@@ -381,7 +381,8 @@ struct OzShared {
 
 // Set-up common to both kernels: TMEM (warp 0), barriers (thread 0), Y exponents.
 // full_count: arrivals that complete a stage.
-__device__ __forceinline__ void oz_setup(OzShared& sh, const OzArgs& a, int full_count) {
+__device__ __forceinline__ void oz_setup(OzShared& sh, const OzArgs& a, int full_count,
+                                         int flush_threads) {
   const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) tc::tmem_alloc(&sh.tmem, TMEM_COLS);
   if (tid == 0) {
@@ -390,7 +391,7 @@ __device__ __forceinline__ void oz_setup(OzShared& sh, const OzArgs& a, int full
       tc::mbar_init(&sh.empty[s], 1);
     }
     tc::mbar_init(&sh.accfull, 1);
-    tc::mbar_init(&sh.accempty, NFLUSH);
+    tc::mbar_init(&sh.accempty, flush_threads);
     sh.abort = 0;
   }
   if (tid < NN) sh.yE[tid] = tid < a.N ? a.yE[tid] : 0;
@@ -412,6 +413,8 @@ __device__ __forceinline__ void oz_teardown(OzShared& sh, const OzArgs& a) {
 // To hide that wait the first two stages of a window are issued together: both
 // stages' weight >= 4 MMAs, the wait, then both stages' exact MMAs.  A new
 // segment first waits for the flush to finish the previous one (its FP32 sums).
+// HIGH = false: the reduced form (digits 0..3 of both operands only), exact MMAs alone.
+template <bool HIGH>
 __device__ __forceinline__ void oz_mma_role(OzShared& sh, const Cursor& start, uint8_t* sm) {
   volatile int& s_abort = sh.abort;
   const uint32_t tmem = sh.tmem;
@@ -429,6 +432,7 @@ __device__ __forceinline__ void oz_mma_role(OzShared& sh, const Cursor& start, u
     return true;
   };
   auto high = [&](int st, bool fresh) {
+    if (!HIGH) return;
     const uint32_t a0 = tc::smem_addr(sm + st * STAGE), y0 = a0 + S * A_PLANE;
     mma_group(tmem, a0, y0, 0, 4, 3, fresh ? 0u : 1u);
     mma_group(tmem, a0, y0, 1, 3, 3, 1u);
@@ -488,180 +492,190 @@ __device__ __forceinline__ double scale2(double v, int e) {
 // The flush (warps 0..3): at every window end fold the exact sums into the int64
 // totals and re-arm them; at a segment end also read weights 4..6 and write the
 // tile (to C when the segment is the whole tile, else to the CTA's partial slot).
+// The flush (warps 0 .. NFW-1): at every window end fold the exact sums into the
+// int64 totals and re-arm them; at a segment end also read weights 4..6 and write
+// the tile (to C when the segment is the whole tile, else to the CTA's partial
+// slot).  Warp w owns TMEM lanes / tile rows 32 (w % 4) .. + 31 (one row per
+// thread).  NFW = 4: each warp takes all 64 output columns, the int64 sums of
+// columns 0..31 in registers and of 32..63 in TMEM (COL_ACC_LO / COL_ACC_HI);
+// NFW = 8: warps w and w + 4 split the columns, 32 each, all sums in registers.
 // PIPE: overlap the TMEM loads of the next 4-column chunk with the current one
 // (needs ~48 more registers; the on-the-fly kernel, capped at 128, goes without).
-template <bool PIPE>
+// HIGH = false: the reduced form, no weights 4..6.
+template <bool PIPE, bool HIGH, int NFW>
 __device__ __forceinline__ void oz_flush_role(OzShared& sh, const OzArgs& a, const Cursor& start,
                                               int64_t cta) {
+  constexpr int NCOL = NFW == 8 ? 32 : 64;  // output columns per thread
+  constexpr int NJ = NCOL / 4;              // 4-column chunks
   volatile int& s_abort = sh.abort;
   const int* syE = sh.yE;
-  const uint32_t tmem = sh.tmem;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quarter = warp & 3, col0 = NFW == 8 ? NCOL * (warp >> 2) : 0;
   const int64_t first_tile = start.tile;
-    // ---------------------------------------------------------- flush + epilogue
-    // warp w owns TMEM lanes / tile rows 32 w .. 32 w + 31 (one row per thread) and
-    // all 64 output columns: the int64 sums of columns 0..31 live in registers,
-    // those of columns 32..63 in TMEM columns COL_ACC_LO / COL_ACC_HI.
-    const uint32_t tb = tmem + ((uint32_t)(32 * warp) << 16);
+  const uint32_t tb = sh.tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)col0;
 #pragma unroll
-    for (int w = 0; w < 4; ++w)
+  for (int w = 0; w < 4; ++w)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) tc::tmem_st8_splat(tb + 64u * w + 8u * j, MAGIC);
+    for (int j = 0; j < NCOL / 8; ++j) tc::tmem_st8_splat(tb + 64u * w + 8u * j, MAGIC);
+  if (NCOL == 64) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       tc::tmem_st8_splat(tb + COL_ACC_LO + 8u * j, 0u);
       tc::tmem_st8_splat(tb + COL_ACC_HI + 8u * j, 0u);
     }
-    tc::tmem_st_wait();
-    tc::fence_before_sync();
-    tc::mbar_arrive(&sh.accempty);
+  }
+  tc::tmem_st_wait();
+  tc::fence_before_sync();
+  tc::mbar_arrive(&sh.accempty);
 
-    int64_t acc[32];
+  int64_t acc[32];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) acc[i] = 0;
-    uint32_t ph_af = 0;
-    const int ncols = min((int)a.N, NN);  // output columns actually read
-    for (Cursor c = start; c.i < c.n; c.next()) {
-      if (!c.win_last()) continue;
-      // lane 0 waits; the warp follows its decision (tcgen05.ld is warp-collective)
-      bool ok = true;
-      if (lane == 0) ok = tc::mbar_wait(&sh.accfull, ph_af, WAIT_TRIES);
-      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-      ph_af ^= 1u;
-      if (!ok) {
-        s_abort = 1;
-        break;
+  for (int i = 0; i < 32; ++i) acc[i] = 0;
+  uint32_t ph_af = 0;
+  const int ncols = min((int)a.N, NN);  // output columns actually read
+  for (Cursor c = start; c.i < c.n; c.next()) {
+    if (!c.win_last()) continue;
+    // lane 0 waits; the warp follows its decision (tcgen05.ld is warp-collective)
+    bool ok = true;
+    if (lane == 0) ok = tc::mbar_wait(&sh.accfull, ph_af, WAIT_TRIES);
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    ph_af ^= 1u;
+    if (!ok) {
+      s_abort = 1;
+      break;
+    }
+    tc::fence_after_sync();
+    // 4 output columns at a time.  Padding columns (>= ncols) are never read and
+    // never re-armed.
+    uint32_t ra[6][4], rb[6][4];
+    auto load = [&](int j, uint32_t (&r)[6][4]) {
+      const uint32_t c4 = 4u * j;
+      tc::tmem_ld4(tb + c4, r[0]);
+      tc::tmem_ld4(tb + 64u + c4, r[1]);
+      tc::tmem_ld4(tb + 128u + c4, r[2]);
+      tc::tmem_ld4(tb + 192u + c4, r[3]);
+      if (j >= 8) {
+        tc::tmem_ld4(tb + COL_ACC_LO + c4 - 32u, r[4]);
+        tc::tmem_ld4(tb + COL_ACC_HI + c4 - 32u, r[5]);
       }
-      tc::fence_after_sync();
-      // 4 output columns at a time; chunk j + 1's TMEM loads are issued right after
-      // chunk j's wait, so their latency overlaps chunk j's integer work.  Padding
-      // columns (>= ncols) are never read and never re-armed.
-      uint32_t ra[6][4], rb[6][4];
-      auto load = [&](int j, uint32_t (&r)[6][4]) {
-        const uint32_t c4 = 4u * j;
-        tc::tmem_ld4(tb + c4, r[0]);
-        tc::tmem_ld4(tb + 64u + c4, r[1]);
-        tc::tmem_ld4(tb + 128u + c4, r[2]);
-        tc::tmem_ld4(tb + 192u + c4, r[3]);
-        if (j >= 8) {
-          tc::tmem_ld4(tb + COL_ACC_LO + c4 - 32u, r[4]);
-          tc::tmem_ld4(tb + COL_ACC_HI + c4 - 32u, r[5]);
-        }
-      };
-      auto work = [&](int j, uint32_t (&r)[6][4]) {
-        const uint32_t c4 = 4u * j;
-        int64_t add[4];
+    };
+    auto work = [&](int j, uint32_t (&r)[6][4]) {
+      const uint32_t c4 = 4u * j;
+      int64_t add[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        // (G_0 * 256 + G_1) and (G_2 * 256 + G_3), each exact in 32 bits
+        const int hi = (int)(r[0][i] * 256u + r[1][i] - 257u * MAGIC);
+        const int lo = (int)(r[2][i] * 256u + r[3][i] - 257u * MAGIC);
+        add[i] = ((int64_t)hi << 16) + (int64_t)lo;
+      }
+      tc::tmem_st4_splat(tb + c4, MAGIC);
+      tc::tmem_st4_splat(tb + 64u + c4, MAGIC);
+      tc::tmem_st4_splat(tb + 128u + c4, MAGIC);
+      tc::tmem_st4_splat(tb + 192u + c4, MAGIC);
+      if (j < 8) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[4 * j + i] += add[i];
+      } else {
+        uint32_t lo[4], hi[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          // (G_0 * 256 + G_1) and (G_2 * 256 + G_3), each exact in 32 bits
-          const int hi = (int)(r[0][i] * 256u + r[1][i] - 257u * MAGIC);
-          const int lo = (int)(r[2][i] * 256u + r[3][i] - 257u * MAGIC);
-          add[i] = ((int64_t)hi << 16) + (int64_t)lo;
+          const uint64_t t = (((uint64_t)r[5][i] << 32) | r[4][i]) + (uint64_t)add[i];
+          lo[i] = (uint32_t)t;
+          hi[i] = (uint32_t)(t >> 32);
         }
-        tc::tmem_st4_splat(tb + c4, MAGIC);
-        tc::tmem_st4_splat(tb + 64u + c4, MAGIC);
-        tc::tmem_st4_splat(tb + 128u + c4, MAGIC);
-        tc::tmem_st4_splat(tb + 192u + c4, MAGIC);
-        if (j < 8) {
-#pragma unroll
-          for (int i = 0; i < 4; ++i) acc[4 * j + i] += add[i];
-        } else {
-          uint32_t lo[4], hi[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const uint64_t t = (((uint64_t)r[5][i] << 32) | r[4][i]) + (uint64_t)add[i];
-            lo[i] = (uint32_t)t;
-            hi[i] = (uint32_t)(t >> 32);
-          }
-          tc::tmem_st4(tb + COL_ACC_LO + c4 - 32u, lo);
-          tc::tmem_st4(tb + COL_ACC_HI + c4 - 32u, hi);
-        }
-      };
-      if (PIPE) {
-        load(0, ra);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          if (4 * j >= ncols) break;
-          tc::tmem_ld_wait();
-          if (j + 1 < 16 && 4 * (j + 1) < ncols) {
-            if (j & 1)
-              load(j + 1, ra);
-            else
-              load(j + 1, rb);
-          }
-          if (j & 1)
-            work(j, rb);
-          else
-            work(j, ra);
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          if (4 * j >= ncols) break;
-          load(j, ra);
-          tc::tmem_ld_wait();
-          work(j, ra);
-        }
+        tc::tmem_st4(tb + COL_ACC_LO + c4 - 32u, lo);
+        tc::tmem_st4(tb + COL_ACC_HI + c4 - 32u, hi);
       }
-      tc::tmem_st_wait();
-      if (c.seg_last()) {
-        const int64_t tile = c.tile;
-        // the segment is the whole tile: it started at stage 0 and ends at the last
-        const bool full = (c.ks + 1 == c.kst) && (c.i >= c.kst - 1);
-        const int r = 32 * warp + lane;
-        const int64_t p = tile * TM + r;
-        const int ep = p < a.P ? __ldg(a.xE + p) : 0;
-        const int slot = (tile == first_tile) ? 0 : 1;
-        double* wp = a.part + (cta * 2 + slot) * (int64_t)(NN * TM) + r;
+    };
+    if (PIPE) {
+      // chunk j + 1's loads are issued right after chunk j's wait
+      load(0, ra);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          if (4 * j >= ncols) continue;
-          const uint32_t c4 = 4u * j;
-          uint32_t g4[4], g5[4], g6[4], lo[4], hi[4];
+      for (int j = 0; j < NJ; ++j) {
+        if (col0 + 4 * j >= ncols) break;
+        tc::tmem_ld_wait();
+        if (j + 1 < NJ && col0 + 4 * (j + 1) < ncols) {
+          if (j & 1)
+            load(j + 1, ra);
+          else
+            load(j + 1, rb);
+        }
+        if (j & 1)
+          work(j, rb);
+        else
+          work(j, ra);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        if (col0 + 4 * j >= ncols) break;
+        load(j, ra);
+        tc::tmem_ld_wait();
+        work(j, ra);
+      }
+    }
+    tc::tmem_st_wait();
+    if (c.seg_last()) {
+      const int64_t tile = c.tile;
+      // the segment is the whole tile: it started at stage 0 and ends at the last
+      const bool full = (c.ks + 1 == c.kst) && (c.i >= c.kst - 1);
+      const int r = 32 * quarter + lane;
+      const int64_t p = tile * TM + r;
+      const int ep = p < a.P ? __ldg(a.xE + p) : 0;
+      const int slot = (tile == first_tile) ? 0 : 1;
+      double* wp = a.part + (cta * 2 + slot) * (int64_t)(NN * TM) + r;
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        if (col0 + 4 * j >= ncols) continue;
+        const uint32_t c4 = 4u * j;
+        uint32_t g4[4] = {0, 0, 0, 0}, g5[4] = {0, 0, 0, 0}, g6[4] = {0, 0, 0, 0}, lo[4], hi[4];
+        if (HIGH) {
           tc::tmem_ld4(tb + 256u + c4, g4);
           tc::tmem_ld4(tb + 320u + c4, g5);
           tc::tmem_ld4(tb + 384u + c4, g6);
-          if (j >= 8) {
-            tc::tmem_ld4(tb + COL_ACC_LO + c4 - 32u, lo);
-            tc::tmem_ld4(tb + COL_ACC_HI + c4 - 32u, hi);
-          }
-          tc::tmem_ld_wait();
+        }
+        if (j >= 8) {
+          tc::tmem_ld4(tb + COL_ACC_LO + c4 - 32u, lo);
+          tc::tmem_ld4(tb + COL_ACC_HI + c4 - 32u, hi);
+        }
+        tc::tmem_ld_wait();
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int col = 4 * j + i;
-            int64_t T;
-            if (j < 8) {
-              T = acc[col];
-              acc[col] = 0;
-            } else {
-              T = (int64_t)(((uint64_t)hi[i] << 32) | lo[i]);
-            }
-            if (p < a.P && col < a.N) {
-              // weights 4..6 in the units of weight 4, in FP32 (their own FP32 sums
-              // carry more rounding than this), then one FP64 multiply-add onto T
-              const float rest = fmaf(__uint_as_float(g6[i]), 0x1p-16f,
-                                      fmaf(__uint_as_float(g5[i]), 0x1p-8f, __uint_as_float(g4[i])));
-              const double sum = fma((double)rest, 0x1p-8, __ll2double_rn(T));  // units of 2^-24
-              const double val = scale2(sum, ep + syE[col] - EXP_OFFSET - 24);
-              if (full) {
-                double* dst = a.C + p * a.csp + (int64_t)col * a.csc;
-                const double av = (a.alpha == 1.0) ? val : (a.alpha == -1.0) ? -val : a.alpha * val;
-                *dst = (a.beta == 0.0) ? av : av + a.beta * (*dst);
-              } else {
-                wp[(int64_t)col * TM] = val;
-              }
-            }
+        for (int i = 0; i < 4; ++i) {
+          const int col = col0 + 4 * j + i;
+          int64_t T;
+          if (j < 8) {
+            T = acc[4 * j + i];
+            acc[4 * j + i] = 0;
+          } else {
+            T = (int64_t)(((uint64_t)hi[i] << 32) | lo[i]);
           }
-          if (j >= 8) {
-            tc::tmem_st4_splat(tb + COL_ACC_LO + c4 - 32u, 0u);
-            tc::tmem_st4_splat(tb + COL_ACC_HI + c4 - 32u, 0u);
+          if (p < a.P && col < a.N) {
+            // weights 4..6 in the units of weight 4, in FP32 (their own FP32 sums
+            // carry more rounding than this), then one FP64 multiply-add onto T
+            const float rest = fmaf(__uint_as_float(g6[i]), 0x1p-16f,
+                                    fmaf(__uint_as_float(g5[i]), 0x1p-8f, __uint_as_float(g4[i])));
+            const double sum = fma((double)rest, 0x1p-8, __ll2double_rn(T));  // units of 2^-24
+            const double val = scale2(sum, ep + syE[col] - EXP_OFFSET - 24);
+            if (full) {
+              double* dst = a.C + p * a.csp + (int64_t)col * a.csc;
+              const double av = (a.alpha == 1.0) ? val : (a.alpha == -1.0) ? -val : a.alpha * val;
+              *dst = (a.beta == 0.0) ? av : av + a.beta * (*dst);
+            } else {
+              wp[(int64_t)col * TM] = val;
+            }
           }
         }
-        tc::tmem_st_wait();
+        if (j >= 8) {
+          tc::tmem_st4_splat(tb + COL_ACC_LO + c4 - 32u, 0u);
+          tc::tmem_st4_splat(tb + COL_ACC_HI + c4 - 32u, 0u);
+        }
       }
-      tc::fence_before_sync();
-      tc::mbar_arrive(&sh.accempty);
+      tc::tmem_st_wait();
     }
+    tc::fence_before_sync();
+    tc::mbar_arrive(&sh.accempty);
+  }
 }
 
 template <bool TRANS>
@@ -680,7 +694,7 @@ __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
   cta_range(a, cta, G, u0, u1);
   if (u0 >= u1) return;
   const Cursor start{u0 / a.kst, (int)(u0 % a.kst), 0, u1 - u0, (int)a.kst};
-  oz_setup(sh, a, NPROD + 1);  // + the arrival that carries the Y bytes
+  oz_setup(sh, a, NPROD + 1, NFLUSH);  // + the arrival that carries the Y bytes
 
   if (warp >= 4 && warp < MMA_WARP) {
     // ---------------------------------------------------------- producers
@@ -740,21 +754,26 @@ __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
       c.next();
     }
   } else if (warp == MMA_WARP) {
-    if (lane == 0) oz_mma_role(sh, start, sm);
+    if (lane == 0) oz_mma_role<true>(sh, start, sm);
     __syncwarp();
   } else if (warp < 4) {
-    oz_flush_role<false>(sh, a, start, cta);
+    oz_flush_role<false, true, 4>(sh, a, start, cta);
   }
   oz_teardown(sh, a);
 }
 
 // The same product with op(X) already cut: img holds, per (tile, stage), the
 // seven digit planes in the stage layout (A_PLANE bytes each, contiguous), so a
-// stage is two bulk copies issued by one thread.  Warps 0..3 flush, warp 4
-// copies, warp 5 issues the MMAs.
-constexpr int NT_IMG = NFLUSH + 64;
+// stage is two bulk copies issued by one thread.  Warps 0..7 flush, warp 8
+// copies, warp 9 issues the MMAs.
+constexpr int NFLUSH_IMG = 256;  // eight flush warps, 32 output columns each
+constexpr int NT_IMG = NFLUSH_IMG + 64;
 
+// LOW: the reduced form -- only digits 0..3 of A and of Y are copied and multiplied
+// (the 10 pairs of weight <= 3, all summed exactly): error ~2^-30 of max|x| max|y|.
+template <bool LOW>
 __global__ void __launch_bounds__(NT_IMG, 1) k_ozgemm_img(OzArgs a, const uint8_t* __restrict__ ximg) {
+  constexpr int SUSE = LOW ? 4 : S;  // digit planes used
   extern __shared__ uint8_t smem_raw[];
   __shared__ OzShared sh;
   const uint32_t raw = tc::smem_addr(smem_raw);
@@ -767,9 +786,9 @@ __global__ void __launch_bounds__(NT_IMG, 1) k_ozgemm_img(OzArgs a, const uint8_
   cta_range(a, cta, G, u0, u1);
   if (u0 >= u1) return;
   const Cursor start{u0 / a.kst, (int)(u0 % a.kst), 0, u1 - u0, (int)a.kst};
-  oz_setup(sh, a, 1);
+  oz_setup(sh, a, 1, NFLUSH_IMG);
 
-  if (warp == 4) {
+  if (warp == 8) {
     if (lane == 0) {
       uint32_t ph_empty[NSTAGE] = {0, 0, 0, 0};
       for (Cursor c = start; c.i < c.n; c.next()) {
@@ -782,18 +801,18 @@ __global__ void __launch_bounds__(NT_IMG, 1) k_ozgemm_img(OzArgs a, const uint8_
           ph_empty[st] ^= 1u;
         }
         uint8_t* sA = sm + st * STAGE;
-        tc::mbar_arrive_expect_tx(&sh.full[st], STAGE);
-        tc::bulk_g2s(sA, ximg + (c.tile * a.kst + c.ks) * (int64_t)(S * A_PLANE), S * A_PLANE,
+        tc::mbar_arrive_expect_tx(&sh.full[st], SUSE * (A_PLANE + Y_PLANE));
+        tc::bulk_g2s(sA, ximg + (c.tile * a.kst + c.ks) * (int64_t)(S * A_PLANE), SUSE * A_PLANE,
                      &sh.full[st]);
-        tc::bulk_g2s(sA + S * A_PLANE, a.img + (int64_t)c.ks * Y_STAGE, Y_STAGE, &sh.full[st]);
+        tc::bulk_g2s(sA + S * A_PLANE, a.img + (int64_t)c.ks * Y_STAGE, SUSE * Y_PLANE, &sh.full[st]);
       }
     }
     __syncwarp();
-  } else if (warp == 5) {
-    if (lane == 0) oz_mma_role(sh, start, sm);
+  } else if (warp == 9) {
+    if (lane == 0) oz_mma_role<!LOW>(sh, start, sm);
     __syncwarp();
   } else {
-    oz_flush_role<true>(sh, a, start, cta);
+    oz_flush_role<true, !LOW, 8>(sh, a, start, cta);
   }
   oz_teardown(sh, a);
 }
@@ -981,10 +1000,11 @@ cudaError_t set_smem_once(F kernel, bool& done) {
 }  // namespace
 
 cudaError_t oz_prepare() {
-  static bool a0 = false, a1 = false, a2 = false;
+  static bool a0 = false, a1 = false, a2 = false, a3 = false;
   cudaError_t e = set_smem_once(k_ozgemm<false>, a0);
   if (e == cudaSuccess) e = set_smem_once(k_ozgemm<true>, a1);
-  if (e == cudaSuccess) e = set_smem_once(k_ozgemm_img, a2);
+  if (e == cudaSuccess) e = set_smem_once(k_ozgemm_img<false>, a2);
+  if (e == cudaSuccess) e = set_smem_once(k_ozgemm_img<true>, a3);
   return e;
 }
 
@@ -1008,7 +1028,7 @@ cudaError_t oz_cut_x(bool trans, int64_t P, int64_t K, const double* X, int64_t 
 
 cudaError_t ozgemm_img(int64_t P, int64_t N, int64_t K, double alpha, const uint8_t* ximg,
                        const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
-                       const OzWorkspace& w, int* flags, cudaStream_t st) {
+                       const OzWorkspace& w, int* flags, cudaStream_t st, bool low) {
   if (P <= 0 || N <= 0) return cudaSuccess;
   if (N > NN || K <= 0 || K > MAX_K) return cudaErrorInvalidValue;
   if (oz_img_bytes(K) > w.img_bytes) return cudaErrorInvalidValue;
@@ -1018,7 +1038,10 @@ cudaError_t ozgemm_img(int64_t P, int64_t N, int64_t K, double alpha, const uint
   if (e != cudaSuccess) return e;
   OzArgs a = make_args(P, N, K, alpha, nullptr, 0, xE, beta, out, w, flags);
   const int G = w.ctas;
-  k_ozgemm_img<<<G, NT_IMG, SMEM_DYN, st>>>(a, ximg);
+  if (low)
+    k_ozgemm_img<true><<<G, NT_IMG, SMEM_DYN, st>>>(a, ximg);
+  else
+    k_ozgemm_img<false><<<G, NT_IMG, SMEM_DYN, st>>>(a, ximg);
   e = launched();
   if (e != cudaSuccess || a.whole_tiles) return e;
   return launch_fixup(a, G, st);

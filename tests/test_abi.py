@@ -60,7 +60,7 @@ BAD = [
     dict(P=-1), dict(P=9), dict(kind=6), dict(eps=0.0), dict(eps=float("nan")), dict(k=101),
     dict(k=91, b=30), dict(kind=lra.SPARSE_SIGN, zeta=0), dict(kind=lra.SPARSE_SIGN, zeta=257),
     dict(kind=lra.SPARSE_SIGN, zeta=101, n=100), dict(p=1.0), dict(p=-0.1), dict(max_blocks=-1),
-    dict(max_blocks=11, b=10), dict(flags=32),
+    dict(max_blocks=11, b=10), dict(flags=64),
 ]
 
 

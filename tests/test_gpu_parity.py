@@ -328,3 +328,39 @@ def test_graphs_change_nothing(kind, p, zeta, P):
     for got in runs:
         assert got[:4] == ref[:4]
         assert np.array_equal(got[4], ref[4]) and np.array_equal(got[5], ref[5])
+
+
+@pytest.mark.parametrize("kind,p,zeta,P,size", [(om.SPARSE_SIGN, 0.0, 8, 1, "small"),
+                                                (om.GAUSSIAN, 0.0, 0, 1, "small"),
+                                                (om.STD_BERNOULLI, 0.5, 0, 2, "small"),
+                                                (om.SPARSE_SIGN, 0.0, 8, 1, "full")],
+                         ids=["ss8_P1", "gauss_P1", "sb_half_P2", "ss8_P1_full"])
+def test_mixed_precision_form(request, kind, p, zeta, P, size):
+    """LRA_FLAG_MIXED: the sketch and power passes from the top 4 of the 7 digits,
+    B_j = Q_j^T A, projections, Gram, Cholesky and indicator FP64-accurate.  Against
+    the FP64 oracle: the same attained rank and status, the final relative error
+    within 1% of the oracle's; and for the basis it found: Q^T Q = I, B = Q^T A and
+    E = ||A - Q B||_F^2 to FP64 accuracy."""
+    if size == "full":
+        A, Ad = request.getfixturevalue("big")
+        b, eps, seed = 50, 1e-2, 1
+    else:
+        A = workload_matrix("dense2000x1000_poly1.5")
+        Ad = dev(A)
+        b, eps, seed = 20, 1e-2, 4
+    m, n = A.shape
+    f = lra.Farpca(m, n, eps=eps, b=b, P=P, kind=kind, zeta=zeta, p=p, seed=seed, mixed=True)
+    f.run(Ad)
+    r = f.result()
+    ref = F.farpca(A, eps, P=P, b=b, kind=kind, seed=seed, zeta=zeta, p=p)
+    assert r["rank"] == ref["rank"] and r["status"] == ref["status"] == 0
+    rel, rel_ref = math.sqrt(max(r["E"], 0.0) / r["normA2"]), math.sqrt(max(ref["E"], 0.0) / ref["normA2"])
+    assert abs(rel - rel_ref) <= 0.01 * rel_ref
+    Q = r["Q"].cpu().numpy()
+    B = r["B"].cpu().numpy()
+    assert float(np.abs(Q.T @ Q - np.eye(Q.shape[1])).max()) <= 1e-12
+    assert maxrel(B, Q.T @ A) <= 1e-10
+    if size == "small":  # E against the residual, computed directly (Sec. 2.1)
+        E_direct = float(np.linalg.norm(A - Q @ B) ** 2)
+        assert abs(r["E"] - E_direct) <= 1e-10 * r["normA2"]
+    f.close()
