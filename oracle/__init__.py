@@ -17,6 +17,8 @@ Modules
                target of the CUDA path.
   farpca_paper the same loop written as Alg. 1 / Alg. 2 print it (Y, W, Z, T,
                eigSVD), used to cross-check ``farpca``.
+  svd          the SVD the method returns (Alg. 1's last steps, QB form) and
+               the post-processing truncation of Sec. 5.3.
 
 Every function is pinned by a ``-m "not gpu"`` test; see the pins listed in
 each module docstring.
