@@ -335,6 +335,7 @@ def main():
 
     if not args.no_extras:
         line["mixed"] = mixed_form(lra, torch, Ad, cfg, m, n, args.steps, res["rel_err"], stream)
+        line["svd"] = svd_extraction(torch, f, args.steps, stream)
         line["sketch_pass"] = sketch_pass(lra, torch, f, Ad, cfg, args.sketch_blocks, peaks, peak_src)
         line["e2e"] = e2e(lra, torch, np, f, A, args.steps)
         if rank == 0 and world == 1:
@@ -397,6 +398,24 @@ def mixed_form(lra, torch, Ad, cfg, m, n, steps, rel_err_fp64, stream):
             "rel_err": r["rel_err"], "rel_err_fp64_form": rel_err_fp64,
             "note": "sketch and power passes from 4 of the 7 digits; B_j, projections, "
                     "Gram, Cholesky and indicator FP64-accurate"}
+
+
+def svd_extraction(torch, f, steps, stream):
+    """lra_svd after the timed runs: the SVD the method returns (Gram B B^T, Jacobi
+    eigendecomposition, U = Q Vt, V = B^T Vt sigma^-1) and the truncated rank."""
+    sv = f.svd()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(steps, 1)
+    e0.record(stream)
+    for _ in range(reps):
+        sv = f.svd()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"ms": ms, "l": sv["l"], "r": sv["r"], "sweeps": sv["sweeps"],
+            "rel_err_r": (max(sv["E_r"], 0.0) / sv["normA2"]) ** 0.5 if sv["normA2"] > 0 else 0.0,
+            "note": "includes two host synchronisations (sweep count, sigma for the truncation)"}
 
 
 def dense_pass(lra, torch, f, Ad, cfg, steps, warmup, peaks, peak_src):

@@ -201,6 +201,42 @@ lra_status lra_farpca_run(lra_ctx* ctx, const lra_matrix* A);
 /* Copy the state of the last run into *out (no device work). */
 lra_status lra_result(const lra_ctx* ctx, lra_result_t* out);
 
+/* The SVD A ~ U diag(sigma) V^T that the method returns (Alg. 1 / Alg. 2, the
+   eigendecompositions after the loop, in the loop's QB form: with B = Q^T A,
+   B B^T = Vt diag(sigma^2) Vt^T, U = Q Vt, V = B^T Vt diag(sigma)^{-1}), and the
+   post-processing truncation of Sec. 5.3.  Device pointers are owned by the
+   context and stay valid until the next lra_svd, lra_farpca_run or
+   lra_destroy. */
+typedef struct {
+  int32_t status;        /* LRA_OK; LRA_NOT_CONVERGED if the eigensolver reached
+                            its sweep cap (results are then its last iterate)  */
+  int32_t sweeps;        /* Jacobi sweeps taken                                 */
+  int64_t l;             /* rank of the run's approximation: columns of U, V    */
+  int64_t r;             /* truncated rank: the smallest r with
+                            ||A||_F^2 - sum_{i<=r} sigma_i^2 < eps^2 ||A||_F^2
+                            (accumulated in this order); l if none; min(k, l)
+                            in fixed-rank mode                                   */
+  double E_r;            /* ||A||_F^2 - sum_{i<=r} sigma_i^2                   */
+  double normA2;         /* ||A||_F^2 of the run                                */
+  const double* U;       /* device, m x l, column-major, ld = ldu               */
+  int64_t ldu;
+  const double* sigma;   /* device, l singular values, descending               */
+  const double* V;       /* device, n x l, column-major, ld = ldv; a column whose
+                            sigma is 0 is 0                                     */
+  int64_t ldv;
+} lra_svd_t;
+
+/* Extract the SVD of the last run's Q B (see lra_svd_t).  The l x l Gram B B^T
+   and the products Q Vt, B^T Vt sigma^{-1} run on the context's GEMM engine;
+   the eigendecomposition is a cyclic Jacobi iteration on the device (one
+   cooperative launch, at most 40 sweeps).  Allocates, on the first call that
+   needs them, about (3 l^2 + 2 (l + 1)^2 + (m + 2n) l) doubles, grown when a
+   later run reaches a larger l.  Synchronises the stream.  l = 0 gives r = 0,
+   E_r = normA2 and NULL pointers.  Errors: LRA_ERR_INVALID_ARG (NULL argument,
+   or the last run failed), LRA_ERR_UNSUPPORTED (l above 12800), LRA_ERR_OOM,
+   LRA_ERR_CUDA, LRA_ERR_TIMEOUT (a bounded device wait gave up). */
+lra_status lra_svd(lra_ctx* ctx, lra_svd_t* out);
+
 /* End-to-end form with host buffers: copy A_host (m x n, ld lda_host) to a
    device buffer owned by the context (allocated on the first call), run
    lra_farpca_run, and copy Q into Q_host (m x rank, ld ldq_host >= m) and B

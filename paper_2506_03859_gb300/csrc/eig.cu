@@ -1,0 +1,358 @@
+// The SVD that farPCA returns (arxiv 2506.03859, Alg. 1 / Alg. 2, the two
+// eigendecompositions after the loop), in the QB form of the loop: with
+// B = Q^T A (l x n), B B^T = Vt diag(lambda) Vt^T, sigma = sqrt(lambda) in
+// descending order, U = Q Vt, V = B^T Vt diag(sigma)^{-1}.  This file holds the
+// l x l symmetric eigendecomposition and the small kernels around it; the Gram
+// B B^T and the lifts by Q and B^T run on the FP64-accurate tensor-core GEMM.
+//
+// Eigensolver: cyclic two-sided Jacobi (Jacobi 1846; the rotation of Golub and
+// Van Loan, "Matrix Computations", Sec. 8.5) with the round-robin ordering, in
+// which one round rotates l/2 disjoint index pairs at once and l - 1 rounds
+// make a sweep that meets every pair once.  One cooperative launch runs all
+// sweeps: a round is one grid-wide pass in which each thread applies the two
+// rotations of one 2 x 2 block of C (C <- J^T C J) or rotates one row of the
+// eigenvector matrix (V <- V J), then a grid barrier.  C is double-buffered, so
+// every CTA computes the round's rotations from the same, unmodified values;
+// each CTA computes all of them into shared memory, which makes the
+// convergence decision (a sweep without a rotation) identical in every CTA.
+// A pair is skipped when |c_pq| <= tol sqrt(|c_pp c_qq|): the relative
+// criterion under which Jacobi keeps the small eigenvalues of a positive
+// definite matrix to high relative accuracy (Demmel and Veselic, SIAM J. Matrix
+// Anal. Appl. 13 (1992)).  The barrier's waits are bounded; a wait that gives
+// up sets FLAG_TIMEOUT and every CTA returns.
+#include <math.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace lra {
+namespace {
+
+constexpr int EIG_NT = 256;
+constexpr long long EIG_SPIN_LIMIT = 1ll << 24;  // ~1-2 s of polling with backoff
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs resident).  bar[0]
+// counts arrivals, bar[1] is the generation.  Returns false once any CTA has
+// given up waiting (FLAG_TIMEOUT in *info).
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* info, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned g = ld_acquire(bar + 1);
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (ld_acquire(bar + 1) == g) {
+        if (++it > EIG_SPIN_LIMIT) {
+          atomicOr(info, FLAG_TIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    *s_ok = (atomicOr(info, 0) & FLAG_TIMEOUT) == 0;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// Pair k (0 <= k < lp/2) of round t (0 <= t < lp - 1) of the circle ordering:
+// index 0 stays, indices 1 .. lp-1 sit on a ring of lp - 1 seats that turns by
+// one seat per round; seat i faces seat lp-1-i, seat 0 faces index 0.
+__device__ __forceinline__ void round_pair(int k, int t, int lp, int& p, int& q) {
+  const int M = lp - 1;
+  auto seat = [&](int i) {
+    int v = i + t;
+    if (v >= M) v -= M;
+    return 1 + v;
+  };
+  int a, b;
+  if (k == 0) {
+    a = 0;
+    b = seat(0);
+  } else {
+    a = seat(k);
+    b = seat(M - k);
+  }
+  p = min(a, b);
+  q = max(a, b);
+}
+
+struct Rot {
+  double c, s, t;  // cos, sin, tan; s == 0 means no rotation
+};
+
+// The rotation J (J_pp = J_qq = c, J_pq = s, J_qp = -s) with (J^T C J)_pq = 0.
+__device__ __forceinline__ Rot jacobi_rot(double app, double aqq, double apq, double tol) {
+  Rot r{1.0, 0.0, 0.0};
+  if (apq == 0.0 || fabs(apq) <= tol * sqrt(fabs(app) * fabs(aqq))) return r;
+  const double theta = (aqq - app) / (2.0 * apq);
+  double t;
+  if (fabs(theta) > 1e150)
+    t = 0.5 / theta;
+  else
+    t = copysign(1.0, theta) / (fabs(theta) + sqrt(fma(theta, theta, 1.0)));
+  const double c = 1.0 / sqrt(fma(t, t, 1.0));
+  r.c = c;
+  r.s = t * c;
+  r.t = t;
+  return r;
+}
+
+struct EigArgs {
+  double* C0;     // lp x lp, ld lp (symmetric): buffer 0
+  double* C1;     // buffer 1
+  double* V;      // lp x lp eigenvectors (columns), starts as I
+  int l, lp, max_sweeps;
+  double tol;
+  unsigned* bar;  // 2 words, zero at launch
+  int* info;      // [0] flags, [1] sweeps, [2] converged, [3] final buffer
+};
+
+__global__ void __launch_bounds__(EIG_NT) k_jacobi(EigArgs a) {
+  extern __shared__ double sm[];
+  const int lp = a.lp, nb2 = lp / 2, M = lp - 1;
+  double* rc = sm;              // cos, per pair of the round
+  double* rs = rc + nb2;        // sin
+  double* rt = rs + nb2;        // tan
+  int2* pq = reinterpret_cast<int2*>(rt + nb2);
+  __shared__ int s_ok;
+  const int64_t TA = (int64_t)nb2 * (nb2 + 1) / 2;  // 2 x 2 blocks (P <= R)
+  const int64_t TB = (int64_t)a.l * nb2;            // (row of V, pair)
+  const int64_t gstride = (int64_t)gridDim.x * EIG_NT;
+  const int64_t gtid = (int64_t)blockIdx.x * EIG_NT + threadIdx.x;
+  int cur = 0, sweep = 0, converged = 0;
+  for (; sweep < a.max_sweeps && !converged; ++sweep) {
+    int any = 0;
+    for (int t = 0; t < M; ++t) {
+      const double* Cc = cur ? a.C1 : a.C0;
+      double* Cn = cur ? a.C0 : a.C1;
+      // the round's rotations, from the unmodified buffer
+      int mine = 0;
+      for (int k = threadIdx.x; k < nb2; k += EIG_NT) {
+        int p, q;
+        round_pair(k, t, lp, p, q);
+        const Rot r = jacobi_rot(__ldcg(Cc + (int64_t)p * lp + p), __ldcg(Cc + (int64_t)q * lp + q),
+                                 __ldcg(Cc + (int64_t)q * lp + p), a.tol);
+        rc[k] = r.c;
+        rs[k] = r.s;
+        rt[k] = r.t;
+        pq[k] = make_int2(p, q);
+        mine |= r.s != 0.0;
+      }
+      any |= __syncthreads_or(mine);
+      for (int64_t w = gtid; w < TA + TB; w += gstride) {
+        if (w < TA) {
+          // (P, R), P <= R, from the triangular index w = R(R+1)/2 + P
+          int R = (int)((sqrtf(8.0f * (float)w + 1.0f) - 1.0f) * 0.5f);
+          while ((int64_t)R * (R + 1) / 2 > w) --R;
+          while ((int64_t)(R + 1) * (R + 2) / 2 <= w) ++R;
+          const int P = (int)(w - (int64_t)R * (R + 1) / 2);
+          const int p = pq[P].x, q = pq[P].y;
+          const double c1 = rc[P], s1 = rs[P];
+          if (P == R) {
+            const double app = __ldcg(Cc + (int64_t)p * lp + p);
+            const double aqq = __ldcg(Cc + (int64_t)q * lp + q);
+            const double apq = __ldcg(Cc + (int64_t)q * lp + p);
+            double npp = app, nqq = aqq, npq = apq;
+            if (s1 != 0.0) {
+              npp = fma(-rt[P], apq, app);
+              nqq = fma(rt[P], apq, aqq);
+              npq = 0.0;
+            }
+            __stcg(Cn + (int64_t)p * lp + p, npp);
+            __stcg(Cn + (int64_t)q * lp + q, nqq);
+            __stcg(Cn + (int64_t)q * lp + p, npq);
+            __stcg(Cn + (int64_t)p * lp + q, npq);
+          } else {
+            const int r = pq[R].x, s = pq[R].y;
+            const double c2 = rc[R], s2 = rs[R];
+            // X = C[{p,q}, {r,s}]; element (i, j) at column j, row i
+            const double x00 = __ldcg(Cc + (int64_t)r * lp + p), x01 = __ldcg(Cc + (int64_t)s * lp + p);
+            const double x10 = __ldcg(Cc + (int64_t)r * lp + q), x11 = __ldcg(Cc + (int64_t)s * lp + q);
+            // Y = J_P^T X
+            const double y00 = c1 * x00 - s1 * x10, y01 = c1 * x01 - s1 * x11;
+            const double y10 = s1 * x00 + c1 * x10, y11 = s1 * x01 + c1 * x11;
+            // X' = Y J_R
+            const double z00 = c2 * y00 - s2 * y01, z01 = s2 * y00 + c2 * y01;
+            const double z10 = c2 * y10 - s2 * y11, z11 = s2 * y10 + c2 * y11;
+            __stcg(Cn + (int64_t)r * lp + p, z00);
+            __stcg(Cn + (int64_t)s * lp + p, z01);
+            __stcg(Cn + (int64_t)r * lp + q, z10);
+            __stcg(Cn + (int64_t)s * lp + q, z11);
+            __stcg(Cn + (int64_t)p * lp + r, z00);
+            __stcg(Cn + (int64_t)p * lp + s, z01);
+            __stcg(Cn + (int64_t)q * lp + r, z10);
+            __stcg(Cn + (int64_t)q * lp + s, z11);
+          }
+        } else {
+          const int64_t u = w - TA;
+          const int P = (int)(u / a.l), i = (int)(u - (int64_t)P * a.l);
+          const double s1 = rs[P];
+          if (s1 != 0.0) {
+            const double c1 = rc[P];
+            double* vp = a.V + (int64_t)pq[P].x * lp + i;
+            double* vq = a.V + (int64_t)pq[P].y * lp + i;
+            const double xp = __ldcg(vp), xq = __ldcg(vq);
+            __stcg(vp, c1 * xp - s1 * xq);
+            __stcg(vq, s1 * xp + c1 * xq);
+          }
+        }
+      }
+      cur ^= 1;
+      if (!grid_barrier(a.bar, gridDim.x, a.info, &s_ok)) return;
+    }
+    converged = !any;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.info[1] = sweep;
+    a.info[2] = converged;
+    a.info[3] = cur;
+  }
+}
+
+// C0[i, j] = G[min(i,j), max(i,j)] for i, j < l (the upper triangle of the
+// Gram, ld ldg), zero in the padding; V = I.
+__global__ void k_eig_init(const double* __restrict__ G, int64_t ldg, int l, int lp,
+                           double* __restrict__ C0, double* __restrict__ V) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)lp * lp) return;
+  const int j = (int)(e / lp), i = (int)(e - (int64_t)j * lp);
+  double c = 0.0;
+  if (i < l && j < l) c = i <= j ? G[i + (int64_t)j * ldg] : G[j + (int64_t)i * ldg];
+  C0[e] = c;
+  V[e] = i == j ? 1.0 : 0.0;
+}
+
+// Descending order of the eigenvalues lambda_i = C[i, i] (ties by index):
+// sigma[rank] = sqrt(max(lambda, 0)), perm[rank] = i, vinv[rank] = 1 / ||V[:, i]||.
+// Every rotation leaves c^2 + s^2 within a rounding error of 1, but for small
+// angles that error leans to one side, and thousands of rotations per column
+// move the column norms by up to ~1e-13; renormalising removes that drift
+// (the pairwise orthogonality error stays a random walk).
+__global__ void k_eig_rank(const double* __restrict__ C, const double* __restrict__ V, int l, int lp,
+                           double* __restrict__ sigma, int* __restrict__ perm,
+                           double* __restrict__ vinv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= l) return;
+  const double li = C[(int64_t)i * lp + i];
+  int rank = 0;
+  for (int j = 0; j < l; ++j) {
+    const double lj = C[(int64_t)j * lp + j];
+    rank += (lj > li) || (lj == li && j < i);
+  }
+  double ss = 0.0;
+  const double* v = V + (int64_t)i * lp;
+  for (int j = 0; j < l; ++j) ss = fma(v[j], v[j], ss);
+  sigma[rank] = sqrt(fmax(li, 0.0));
+  perm[rank] = i;
+  vinv[rank] = 1.0 / sqrt(ss);
+}
+
+// Vs[:, k] = V[0:l, perm[k]] vinv[k] and W[:, k] = Vs[:, k] / sigma[k] (0 if
+// sigma[k] == 0), both l x l, ld l.
+__global__ void k_eig_gather(const double* __restrict__ V, int l, int lp, const int* __restrict__ perm,
+                             const double* __restrict__ vinv, const double* __restrict__ sigma,
+                             double* __restrict__ Vs, double* __restrict__ W) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)l * l) return;
+  const int k = (int)(e / l), i = (int)(e - (int64_t)k * l);
+  const double v = V[(int64_t)perm[k] * lp + i] * vinv[k];
+  const double s = sigma[k];
+  Vs[e] = v;
+  W[e] = s > 0.0 ? v / s : 0.0;
+}
+
+// Bt (n x l, ld ldt) = transpose of B (l x n, ld ldb); 32 x 32 tiles.
+__global__ void k_transpose(const double* __restrict__ B, int64_t ldb, int64_t l, int64_t n,
+                            double* __restrict__ Bt, int64_t ldt) {
+  __shared__ double tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t r = r0 + threadIdx.x, c = c0 + y;
+    if (r < l && c < n) tile[y][threadIdx.x] = B[r + c * ldb];
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t c = c0 + threadIdx.x, r = r0 + y;
+    if (r < l && c < n) Bt[c + r * ldt] = tile[threadIdx.x][y];
+  }
+}
+
+}  // namespace
+
+int64_t eig_padded(int64_t l) { return l + (l & 1); }
+
+int64_t eig_max_l() {
+  // the per-CTA rotation table (32 bytes a pair) must fit in shared memory
+  return 2 * ((200 * 1024) / 32);
+}
+
+cudaError_t eig_sym(const double* G, int64_t ldg, int l, double* C0, double* C1, double* V,
+                    int max_sweeps, double tol, unsigned* bar, int* info, cudaStream_t st) {
+  if (l < 1 || l > eig_max_l()) return cudaErrorInvalidValue;
+  const int lp = (int)eig_padded(l);
+  const int64_t elems = (int64_t)lp * lp;
+  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(info, 0, 4 * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_eig_init<<<(unsigned)((elems + 255) / 256), 256, 0, st>>>(G, ldg, l, lp, C0, V);
+  e = launched();
+  if (e != cudaSuccess) return e;
+  const int nb2 = lp / 2;
+  const size_t smem = (size_t)nb2 * 32;
+  static bool attr = false;
+  if (!attr) {
+    e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int dev = 0, sms = 0, occ = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi, EIG_NT, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  const int64_t tasks = (int64_t)nb2 * (nb2 + 1) / 2 + (int64_t)l * nb2;
+  int64_t grid = (tasks + EIG_NT - 1) / EIG_NT;
+  grid = std::min<int64_t>(grid, (int64_t)occ * sms);
+  grid = std::max<int64_t>(grid, 1);
+  EigArgs a{C0, C1, V, l, lp, max_sweeps, tol, bar, info};
+  void* args[] = {&a};
+  e = cudaLaunchCooperativeKernel((const void*)k_jacobi, dim3((unsigned)grid), dim3(EIG_NT), args,
+                                  smem, st);
+  if (e != cudaSuccess) return e;
+  return launched();
+}
+
+cudaError_t eig_sort(const double* C, int l, double* sigma, int* perm, double* vinv, const double* V,
+                     double* Vs, double* W, cudaStream_t st) {
+  const int lp = (int)eig_padded(l);
+  k_eig_rank<<<(l + 127) / 128, 128, 0, st>>>(C, V, l, lp, sigma, perm, vinv);
+  cudaError_t e = launched();
+  if (e != cudaSuccess) return e;
+  const int64_t elems = (int64_t)l * l;
+  k_eig_gather<<<(unsigned)((elems + 255) / 256), 256, 0, st>>>(V, l, lp, perm, vinv, sigma, Vs, W);
+  return launched();
+}
+
+cudaError_t transpose(const double* B, int64_t ldb, int64_t l, int64_t n, double* Bt, int64_t ldt,
+                      cudaStream_t st) {
+  if (l <= 0 || n <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((n + 31) / 32), (unsigned)((l + 31) / 32));
+  k_transpose<<<grid, dim3(32, 8), 0, st>>>(B, ldb, l, n, Bt, ldt);
+  return launched();
+}
+
+}  // namespace lra

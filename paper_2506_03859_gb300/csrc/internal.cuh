@@ -131,4 +131,23 @@ cudaError_t append_rows(const double* Wt, int64_t ldw, int64_t n, int b, double*
 // X[i, c] = v for all i < rows, c < cols.
 cudaError_t fill(double* X, int64_t ld, int64_t rows, int64_t cols, double v, cudaStream_t st);
 
+// ---------------------------------------------------------------- eig.cu
+// Cyclic Jacobi eigendecomposition of a symmetric l x l matrix given by the upper
+// triangle of G (ld ldg): one cooperative launch.  C0, C1, V: eig_padded(l)^2
+// doubles each; bar: 2 words; info: 4 ints ([0] flags, FLAG_TIMEOUT if a
+// barrier wait gave up; [1] sweeps; [2] converged; [3] 1 if the eigenvalues
+// ended in C1's diagonal, 0 if in C0's).  V's columns are the eigenvectors.
+int64_t eig_padded(int64_t l);
+int64_t eig_max_l();
+cudaError_t eig_sym(const double* G, int64_t ldg, int l, double* C0, double* C1, double* V,
+                    int max_sweeps, double tol, unsigned* bar, int* info, cudaStream_t st);
+// sigma (l, descending) = sqrt of the eigenvalues on C's diagonal; Vs = V's
+// columns in that order, renormalised (l x l, ld l); W = Vs diag(sigma)^{-1}
+// (0 where sigma = 0).  perm, vinv: l entries of scratch.
+cudaError_t eig_sort(const double* C, int l, double* sigma, int* perm, double* vinv, const double* V,
+                     double* Vs, double* W, cudaStream_t st);
+// Bt (n x l, ld ldt) = B^T for B l x n (ld ldb).
+cudaError_t transpose(const double* B, int64_t ldb, int64_t l, int64_t n, double* Bt, int64_t ldt,
+                      cudaStream_t st);
+
 }  // namespace lra

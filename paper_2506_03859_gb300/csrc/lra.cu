@@ -39,6 +39,8 @@ namespace {
 constexpr double PIVOT_TAU = 1e-13;
 constexpr int64_t SPARSE_MAX_NNZ_PER_COL = 256;   // above this expected nnz, Omega is dense
 constexpr int64_t SKETCH_SCRATCH_ENTRIES = 8 << 20;
+constexpr int SVD_MAX_SWEEPS = 40;
+constexpr double SVD_JACOBI_TOL = 1e-15;  // skip a pair when |c_pq| <= tol sqrt(|c_pp c_qq|)
 
 struct Pinned {
   double v[4];
@@ -118,6 +120,17 @@ struct lra_ctx {
   double phase_ms[LRA_NUM_PHASES] = {};
   int64_t phase_calls[LRA_NUM_PHASES] = {};
 
+  // lra_svd: workspace for l <= svd_cap columns (grown on demand)
+  struct SvdWs {
+    int64_t cap = 0;
+    double *Bt = nullptr, *G = nullptr, *C0 = nullptr, *C1 = nullptr, *V = nullptr;
+    double *Vs = nullptr, *W = nullptr, *sigma = nullptr, *U = nullptr, *Vout = nullptr;
+    double* vinv = nullptr;
+    int *perm = nullptr, *info = nullptr, *btrowE = nullptr, *btcolE = nullptr, *qrowE = nullptr;
+    unsigned* bar = nullptr;
+  } svd;
+
+  bool run_ok = false;  // the last lra_farpca_run completed (any non-negative status)
   int32_t status = LRA_OK;
   int64_t rank = 0, blocks = 0;
   double E = 0.0, normA2 = 0.0;
@@ -441,6 +454,7 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
                 ldf = ctx->ldf;
   const int b = ctx->b, P = ctx->P;
   ctx->status = LRA_OK;
+  ctx->run_ok = false;
   ctx->rank = ctx->blocks = 0;
   ctx->E = ctx->normA2 = 0.0;
   CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int), ctx->st));
@@ -459,6 +473,7 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
   ctx->normA2 = ctx->E = normA2;
   if (normA2 == 0.0) {
     ctx->E = 0.0;
+    ctx->run_ok = true;
     return LRA_OK;
   }
   // set-up: exponents of A, its digit images, z = A (p 1) for the shifted sketch
@@ -568,6 +583,7 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
     }
   }
   ctx->status = status;
+  ctx->run_ok = true;
   return (lra_status)status;
 }
 
@@ -589,6 +605,41 @@ lra_status ensure_sketch_scratch(lra_ctx* ctx, int64_t cols, int cap) {
   return LRA_OK;
 }
 
+void svd_free(lra_ctx::SvdWs& w) {
+  void* ptrs[] = {w.Bt, w.G,    w.C0,   w.C1,     w.V,      w.Vs,     w.W,    w.sigma,
+                  w.U,  w.Vout, w.perm, w.info,   w.btrowE, w.btcolE, w.qrowE, w.bar, w.vinv};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  w = lra_ctx::SvdWs{};
+}
+
+// Workspace of lra_svd for l columns (kept, and grown, across calls).
+lra_status svd_alloc(lra_ctx* ctx, int64_t l) {
+  auto& w = ctx->svd;
+  if (w.cap >= l) return LRA_OK;
+  svd_free(w);
+  const int64_t lp = eig_padded(l), m = ctx->m, n = ctx->n;
+  CK(dalloc(&w.Bt, n * l));
+  CK(dalloc(&w.G, l * l));
+  CK(dalloc(&w.C0, lp * lp));
+  CK(dalloc(&w.C1, lp * lp));
+  CK(dalloc(&w.V, lp * lp));
+  CK(dalloc(&w.Vs, l * l));
+  CK(dalloc(&w.W, l * l));
+  CK(dalloc(&w.sigma, l));
+  CK(dalloc(&w.U, m * l));
+  CK(dalloc(&w.Vout, n * l));
+  CK(dalloc(&w.perm, l));
+  CK(dalloc(&w.vinv, l));
+  CK(dalloc(&w.info, 4));
+  CK(dalloc(&w.btrowE, n));
+  CK(dalloc(&w.btcolE, l));
+  CK(dalloc(&w.qrowE, m));
+  CK(dalloc(&w.bar, 2));
+  w.cap = l;
+  return LRA_OK;
+}
+
 void free_all(lra_ctx* c) {
   void* ptrs[] = {c->Q,      c->B,        c->Yk,     c->S0,       c->Yb,        c->T1,
                   c->Tmp,    c->W,        c->G,      c->Wt,       c->F,         c->BOm,
@@ -600,6 +651,7 @@ void free_all(lra_ctx* c) {
                   c->ximg[0], c->ximg[1], c->astat};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  svd_free(c->svd);
   if (c->gpre.exec) cudaGraphExecDestroy(c->gpre.exec);
   for (int i = 0; i < lra_ctx::NCOPY; ++i) {
     if (c->cst[i]) cudaStreamDestroy(c->cst[i]);
@@ -840,6 +892,80 @@ lra_status lra_farpca_run(lra_ctx* ctx, const lra_matrix* A) {
   ctx->err.clear();
   TRY(check_matrix(ctx, A));
   return run(ctx, (const double*)A->data, A->lda);
+}
+
+lra_status lra_svd(lra_ctx* ctx, lra_svd_t* out) {
+  if (!ctx || !out) return LRA_ERR_INVALID_ARG;
+  memset(out, 0, sizeof *out);
+  ctx->err.clear();
+  if (!ctx->run_ok) return fail(ctx, LRA_ERR_INVALID_ARG, "no completed lra_farpca_run");
+  const int64_t l = ctx->rank, m = ctx->m, n = ctx->n;
+  out->l = l;
+  out->normA2 = ctx->normA2;
+  if (l == 0) {
+    out->E_r = ctx->normA2;
+    return LRA_OK;
+  }
+  if (l > eig_max_l()) return fail(ctx, LRA_ERR_UNSUPPORTED, "l = %lld above %lld", (long long)l,
+                                   (long long)eig_max_l());
+  TRY(svd_alloc(ctx, l));
+  auto& w = ctx->svd;
+  cudaStream_t st = ctx->st;
+  const bool tc = ctx->tensor;
+  CK(transpose(ctx->B, ctx->ldb, l, n, w.Bt, n, st));
+  if (tc) {
+    CK(oz_rowcol_exponents(w.Bt, n, n, l, w.btrowE, w.btcolE, st));
+    CK(oz_rowcol_exponents(ctx->Q, ctx->ldq, m, l, w.qrowE, nullptr, st));
+  }
+  // the l x l Gram B B^T = Bt^T Bt, 64 columns per product
+  for (int64_t c0 = 0; c0 < l; c0 += 64) {
+    const int64_t nc = std::min<int64_t>(64, l - c0);
+    TRY(mm(ctx, true, l, nc, n, 1.0, w.Bt, n, tc ? w.btcolE : nullptr, w.Bt + c0 * n, n, 0.0,
+           w.G + c0 * l, 1, l, tc ? w.btcolE + c0 : nullptr));
+  }
+  CK(eig_sym(w.G, l, (int)l, w.C0, w.C1, w.V, SVD_MAX_SWEEPS, SVD_JACOBI_TOL, w.bar, w.info, st));
+  int info[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(info, w.info, sizeof info, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (info[0] & FLAG_TIMEOUT) return fail(ctx, LRA_ERR_TIMEOUT, "eigensolver barrier wait gave up");
+  CK(eig_sort(info[3] ? w.C1 : w.C0, (int)l, w.sigma, w.perm, w.vinv, w.V, w.Vs, w.W, st));
+  // U = Q Vt, V = Bt Vt sigma^{-1}
+  for (int64_t c0 = 0; c0 < l; c0 += 64) {
+    const int64_t nc = std::min<int64_t>(64, l - c0);
+    TRY(mm(ctx, false, m, nc, l, 1.0, ctx->Q, ctx->ldq, tc ? w.qrowE : nullptr, w.Vs + c0 * l, l,
+           0.0, w.U + c0 * m, 1, m));
+    TRY(mm(ctx, false, n, nc, l, 1.0, w.Bt, n, tc ? w.btrowE : nullptr, w.W + c0 * l, l, 0.0,
+           w.Vout + c0 * n, 1, n));
+  }
+  std::vector<double> sig(l);
+  CK(cudaMemcpyAsync(sig.data(), w.sigma, l * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  // post-processing truncation (Sec. 5.3): first r with E_r below the threshold
+  double E = ctx->normA2;
+  int64_t r = l;
+  if (ctx->prm.k > 0) {
+    r = std::min<int64_t>(ctx->prm.k, l);
+    for (int64_t i = 0; i < r; ++i) E -= sig[i] * sig[i];
+  } else {
+    const double thr = ctx->prm.eps * ctx->prm.eps * ctx->normA2;
+    for (int64_t i = 0; i < l; ++i) {
+      E -= sig[i] * sig[i];
+      if (E < thr) {
+        r = i + 1;
+        break;
+      }
+    }
+  }
+  out->status = info[2] ? LRA_OK : LRA_NOT_CONVERGED;
+  out->sweeps = info[1];
+  out->r = r;
+  out->E_r = E;
+  out->U = w.U;
+  out->ldu = m;
+  out->sigma = w.sigma;
+  out->V = w.Vout;
+  out->ldv = n;
+  return LRA_OK;
 }
 
 lra_status lra_phase_times(lra_ctx* ctx, double* ms, int64_t* calls, int32_t nphases,

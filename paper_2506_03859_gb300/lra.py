@@ -29,7 +29,7 @@ MAX_B, MAX_P, MAX_ZETA = 64, 8, 256
 
 EXPORTS = ("lra_create", "lra_destroy", "lra_capacity", "lra_sketch", "lra_farpca_run", "lra_result",
            "lra_farpca_host", "lra_copy_omega", "lra_last_error", "lra_status_string",
-           "lra_kernel_launches", "lra_version", "lra_phase_times", "lra_apply")
+           "lra_kernel_launches", "lra_version", "lra_phase_times", "lra_apply", "lra_svd")
 
 
 class Matrix(Structure):
@@ -47,6 +47,12 @@ class Result(Structure):
     _fields_ = [("status", c_int32), ("reserved", c_int32), ("rank", c_int64), ("blocks", c_int64),
                 ("E", c_double), ("normA2", c_double), ("rel_err", c_double), ("Q", c_void_p),
                 ("ldq", c_int64), ("B", c_void_p), ("ldb", c_int64), ("Y", c_void_p), ("ldy", c_int64)]
+
+
+class SvdResult(Structure):
+    _fields_ = [("status", c_int32), ("sweeps", c_int32), ("l", c_int64), ("r", c_int64),
+                ("E_r", c_double), ("normA2", c_double), ("U", c_void_p), ("ldu", c_int64),
+                ("sigma", c_void_p), ("V", c_void_p), ("ldv", c_int64)]
 
 
 class LraError(RuntimeError):
@@ -96,6 +102,8 @@ def load(path=LIB_PATH):
     lib.lra_phase_times.restype = c_int32
     lib.lra_apply.argtypes = [vp, POINTER(Matrix), c_int32, vp, c_int64, c_int64, vp, c_int64]
     lib.lra_apply.restype = c_int32
+    lib.lra_svd.argtypes = [vp, POINTER(SvdResult)]
+    lib.lra_svd.restype = c_int32
     _lib = lib
     return lib
 
@@ -197,6 +205,22 @@ class Farpca:
             out["B"] = torch.as_tensor(_DeviceView(r.B, (l, self.n), (1, r.ldb), self), device="cuda")
             if r.Y:
                 out["Y"] = torch.as_tensor(_DeviceView(r.Y, (self.m, l), (1, r.ldy), self), device="cuda")
+        return out
+
+    def svd(self):
+        """lra_svd: the SVD of the last run's Q B and its truncation.  A dict with
+        status, sweeps, l, r, E_r, normA2 and zero-copy torch views U (m x l),
+        sigma (l, descending) and V (n x l); views stay valid until the next
+        svd / run on this context."""
+        r = SvdResult()
+        self._check(self._lib.lra_svd(self._ctx, byref(r)))
+        torch = self._torch
+        out = dict(status=r.status, sweeps=r.sweeps, l=r.l, r=r.r, E_r=r.E_r, normA2=r.normA2)
+        l = r.l
+        if l > 0:
+            out["U"] = torch.as_tensor(_DeviceView(r.U, (self.m, l), (1, r.ldu), self), device="cuda")
+            out["sigma"] = torch.as_tensor(_DeviceView(r.sigma, (l,), (1,), self), device="cuda")
+            out["V"] = torch.as_tensor(_DeviceView(r.V, (self.n, l), (1, r.ldv), self), device="cuda")
         return out
 
     def apply(self, A, Y, trans=False, C=None):
