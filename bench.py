@@ -60,7 +60,7 @@ def parse():
                     help="only the timed farPCA steps (for launch-list profiling)")
     ap.add_argument("--engine", choices=("tensor", "fp64_simt"), default="tensor",
                     help="dense passes on the tensor cores (FP64-accurate slicing) or FP64 CUDA cores")
-    ap.add_argument("--only", choices=("sketch", "dense"), default=None,
+    ap.add_argument("--only", choices=("sketch", "dense", "serve"), default=None,
                     help="run only the sketch pass (lra_sketch over --sketch-blocks blocks) or only "
                          "the two dense passes A Y and A^T Y (lra_apply), for profiling")
     return ap.parse_args()
@@ -254,8 +254,10 @@ def main():
     f = lra.Farpca(m, n, eps=cfg["eps"], b=cfg["b"], P=cfg["P"], kind=cfg["kind"], zeta=cfg["zeta"],
                    p=cfg["p"], seed=cfg["seed"] + rank, profile=True, stream=stream,
                    fp64_simt=(args.engine == "fp64_simt"))
-    if args.only in ("sketch", "dense"):
-        if args.only == "sketch":
+    if args.only in ("sketch", "dense", "serve"):
+        if args.only == "serve":
+            out = {"serving": serving(lra, torch, np)}
+        elif args.only == "sketch":
             out = {"sketch_pass": sketch_pass(lra, torch, f, Ad, cfg, args.sketch_blocks, peaks, peak_src)}
         else:
             out = {"dense_pass": dense_pass(lra, torch, f, Ad, cfg, args.steps, args.warmup, peaks, peak_src)}
@@ -336,6 +338,8 @@ def main():
     if not args.no_extras:
         line["mixed"] = mixed_form(lra, torch, Ad, cfg, m, n, args.steps, res["rel_err"], stream)
         line["svd"] = svd_extraction(torch, f, args.steps, stream)
+        line["fp32_input"] = fp32_form(lra, torch, Ad, cfg, m, n, args.steps, stream)
+        line["serving"] = serving(lra, torch, np)
         line["sketch_pass"] = sketch_pass(lra, torch, f, Ad, cfg, args.sketch_blocks, peaks, peak_src)
         line["e2e"] = e2e(lra, torch, np, f, A, args.steps)
         if rank == 0 and world == 1:
@@ -398,6 +402,110 @@ def mixed_form(lra, torch, Ad, cfg, m, n, steps, rel_err_fp64, stream):
             "rel_err": r["rel_err"], "rel_err_fp64_form": rel_err_fp64,
             "note": "sketch and power passes from 4 of the 7 digits; B_j, projections, "
                     "Gram, Cholesky and indicator FP64-accurate"}
+
+
+SERVE_KINDS = ((0, 0.0, 0), (1, 0.5, 0), (2, 0.0, 8), (4, 0.0, 8))   # Gaussian, SB +-1, SS zeta=8, SG 8/n
+
+
+def serve_block(m, n):
+    """Sec. 5.4's block size rule: b = min(max(20, floor(min(m, n) / 100)), 50)."""
+    return min(max(20, min(m, n) // 100), 50)
+
+
+def serving(lra, torch, np, duration_s=3.0, rate=200.0, slots=8, seed=11):
+    """Served solves/s and p50/p99 latency: a Poisson stream (mean `rate` req/s) of
+    FP32 requests, sizes log-uniform 1000x500 .. 40000x20000 (a pool of ten
+    device-resident matrices, exact rank 400, sigma_i = 10^(-i/100)), mixed Omega
+    kinds and eps in {1e-1, 1e-2, 1e-3}, through lra_server; beside it the same
+    trace as plain FP64 one-at-a-time farPCA (one context per request, in arrival
+    order; its queueing follows from the measured service times)."""
+    from lra_inputs import device_low_rank
+    rng = np.random.default_rng(seed)
+    sizes = [int(round(v)) for v in np.exp(np.linspace(np.log(1000), np.log(40000), 10))]
+    pool = [device_low_rank(mm, mm // 2, min(400, mm // 2), 500 + i) for i, mm in enumerate(sizes)]
+    trace, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > duration_s:
+            break
+        k = int(rng.integers(len(sizes)))
+        kind, p, zeta = SERVE_KINDS[int(rng.integers(len(SERVE_KINDS)))]
+        eps = [1e-1, 1e-2, 1e-3][int(rng.integers(3))]
+        mm, nn = pool[k].shape
+        prm = lra.params(eps=eps, b=serve_block(mm, nn), P=1, kind=kind, zeta=zeta, p=p,
+                         seed=int(rng.integers(1 << 62)))
+        trace.append((t, k, prm))
+    torch.cuda.synchronize()
+    srv = lra.Server(slots=slots, flags=lra.FLAG_NO_GRAPHS)
+    t0 = srv.clock()
+    done = []
+    import time
+    for i, (ta, k, prm) in enumerate(trace):
+        while srv.clock() - t0 < ta:
+            done += srv.poll()
+            time.sleep(0.0002)
+        srv.submit(pool[k], prm, i)
+    while len(done) < len(trace):
+        done += srv.poll(wait=True)
+    srv.close()
+    lat = np.array([c["t_done"] - c["t_submit"] for c in done])
+    span = max(c["t_done"] for c in done) - min(c["t_submit"] for c in done)
+    ok = sum(1 for c in done if c["status"] >= 0)
+    # the same trace, FP64, one request at a time
+    pool64 = []
+    for A in pool:
+        B = torch.empty_strided(A.shape, (1, A.shape[0]), dtype=torch.float64, device="cuda")
+        B.copy_(A)
+        pool64.append(B)
+    del pool
+    finish, lat1 = 0.0, []
+    for ta, k, prm in trace:
+        mm, nn = pool64[k].shape
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        f = lra.Farpca(mm, nn, eps=prm.eps, b=prm.b, P=prm.P, kind=prm.kind, zeta=prm.zeta, p=prm.p,
+                       seed=prm.seed)
+        f.run(pool64[k])
+        f.close()
+        torch.cuda.synchronize()
+        service = time.perf_counter() - t1
+        finish = max(finish, ta) + service
+        lat1.append(finish - ta)
+    lat1 = np.array(lat1)
+    span1 = finish - trace[0][0]
+    del pool64
+    return {"requests": len(trace), "completed_ok": ok, "rate_req_s": rate, "slots": slots,
+            "solves_per_s": len(trace) / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "one_at_a_time_fp64": {"solves_per_s": len(trace) / span1,
+                                   "p50_ms": 1e3 * float(np.percentile(lat1, 50)),
+                                   "p99_ms": 1e3 * float(np.percentile(lat1, 99))},
+            "sizes": "log-uniform %dx%d .. %dx%d (10 sizes)" % (sizes[0], sizes[0] // 2, sizes[-1],
+                                                             sizes[-1] // 2)}
+
+
+def fp32_form(lra, torch, Ad, cfg, m, n, steps, stream):
+    """Time-to-eps on the FP32 rounding of the same matrix (FP32 input A: the cut,
+    the statistics pass and the gather read 4-byte entries; every sum is FP64)."""
+    A32 = torch.empty_strided((m, n), (1, m), dtype=torch.float32, device="cuda")
+    A32.copy_(Ad)
+    f = lra.Farpca(m, n, eps=cfg["eps"], b=cfg["b"], P=cfg["P"], kind=cfg["kind"], zeta=cfg["zeta"],
+                   p=cfg["p"], seed=cfg["seed"], stream=stream)
+    for _ in range(2):
+        f.run(A32)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        f.run(A32)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    r = f.result()
+    f.close()
+    del A32
+    return {"value": 1e3 / ms, "unit": "solves/s", "ms_per_step": ms, "rank": r["rank"],
+            "rel_err": r["rel_err"], "bytes_of_A": 4 * m * n}
 
 
 def svd_extraction(torch, f, steps, stream):

@@ -96,6 +96,11 @@ typedef enum { LRA_F64 = 0, LRA_F32 = 1 } lra_dtype;
                                the indicator stay FP64-accurate, so E is exact for
                                the basis found.  Without the images the flag has
                                no effect.                                          */
+#define LRA_FLAG_POOL 64u  /* allocate the context's device memory from the device's
+                              stream-ordered pool on its stream (cudaMallocAsync),
+                              so that creating and destroying contexts next to
+                              running ones synchronises nothing but their own
+                              stream; the serving runtime uses it               */
 
 /* Phases of one block, for lra_phase_times. */
 typedef enum {
@@ -116,7 +121,8 @@ typedef enum {
 typedef struct {
   int64_t m, n;       /* rows, columns (>= 1)                                     */
   int64_t lda;        /* leading dimension in elements, >= m                      */
-  int32_t dtype;      /* lra_dtype; LRA_F64 only (others: LRA_ERR_UNSUPPORTED)     */
+  int32_t dtype;      /* lra_dtype: LRA_F64; LRA_F32 where an entry point says so
+                         (elsewhere LRA_ERR_UNSUPPORTED)                          */
   int32_t reserved;   /* must be 0                                                */
   const void* data;   /* device, column-major; must stay valid while a call runs  */
 } lra_matrix;
@@ -177,7 +183,9 @@ int64_t lra_capacity(const lra_ctx* ctx);
    with the context's kind, seed and b; for the standardized Bernoulli kind each
    block is A B_j - z, z = A (p 1) (Sec. 3.1).  A must be m x n as at create.
    Y: device, m x (nblk * b), column-major, ld = ldy >= m, caller-owned.
-   nblk = 0 is a no-op.  Errors: LRA_ERR_INVALID_ARG, LRA_ERR_CUDA. */
+   nblk = 0 is a no-op.  A may be LRA_F32 for the kinds whose sketch is a pure
+   gather (sparse sign, sparse Gaussian, Bernoulli; entries converted exactly,
+   FP64 sums).  Errors: LRA_ERR_INVALID_ARG, LRA_ERR_UNSUPPORTED, LRA_ERR_CUDA. */
 lra_status lra_sketch(lra_ctx* ctx, const lra_matrix* A, int64_t j0, int64_t nblk,
                       double* Y, int64_t ldy);
 
@@ -195,7 +203,13 @@ lra_status lra_apply(lra_ctx* ctx, const lra_matrix* A, int32_t trans, const dou
    E < eps^2 ||A||_F^2 (LRA_OK), the block cap (LRA_NOT_CONVERGED), a rank-deficient
    block (LRA_BREAKDOWN) or, with k > 0, ceil(k/b) blocks (LRA_OK).
    ||A||_F = 0 gives rank 0 and LRA_OK; a non-finite ||A||_F^2 gives
-   LRA_ERR_INVALID_ARG.  Synchronises the stream once per block for the stop test. */
+   LRA_ERR_INVALID_ARG.  Synchronises the stream once per block for the stop test.
+   A may be LRA_F32 (FP32 data of the 20000 x 10000 kind in Sec. 5's setting):
+   its entries are converted exactly to FP64 where they are read (the pass for
+   ||A||_F^2, the digit cut, the sparse gather), so the run computes the same
+   bits as on the FP64 conversion of A while reading half the bytes; this needs
+   the tensor engine with digit images (LRA_ERR_UNSUPPORTED with
+   LRA_FLAG_FP64_SIMT or LRA_FLAG_NO_A_DIGITS). */
 lra_status lra_farpca_run(lra_ctx* ctx, const lra_matrix* A);
 
 /* Copy the state of the last run into *out (no device work). */
@@ -247,6 +261,12 @@ lra_status lra_farpca_host(lra_ctx* ctx, const double* A_host, int64_t lda_host,
                            double* Q_host, int64_t ldq_host, double* B_host,
                            int64_t ldb_host, lra_result_t* out);
 
+/* lra_farpca_host for FP32 host data (A_host: m x n floats, ld lda_host); the
+   run is lra_farpca_run's LRA_F32 form.  Q_host, B_host as for lra_farpca_host. */
+lra_status lra_farpca_host_f32(lra_ctx* ctx, const float* A_host, int64_t lda_host,
+                               double* Q_host, int64_t ldq_host, double* B_host,
+                               int64_t ldb_host, lra_result_t* out);
+
 /* Omega_j as generated on the device, copied to host buffers (for bit-exact
    comparison).  counts[b]: nonzeros of each column; rows[c * cap + t] and
    vals[c * cap + t], t < counts[c]: row index and value of column c's t-th entry,
@@ -292,6 +312,83 @@ lra_status lra_phase_times(lra_ctx* ctx, double* ms, int64_t* calls, int32_t nph
    LRA_ERR_CUDA. */
 lra_status lra_sketch_noalloc(const lra_matrix* A, const lra_params* params, int64_t j0,
                               int64_t nblk, double* Y, int64_t ldy, void* cuda_stream);
+
+/* Device bytes lra_create would allocate for these arguments (the same sizing,
+   nothing allocated; the lazily grown buffers of lra_sketch, lra_svd and
+   lra_farpca_host are not included), or a negative lra_status for invalid
+   arguments.  The admission test of the serving runtime. */
+int64_t lra_workspace_bytes(int64_t m, int64_t n, const lra_params* params);
+
+/* Device bytes the context has allocated so far; -1 for NULL. */
+int64_t lra_device_bytes(const lra_ctx* ctx);
+
+/* ---- Serving runtime: a stream of independent requests on one GPU --------
+   Each request is a fixed-precision (or fixed-rank) farPCA run on its own
+   matrix.  Requests are admitted in arrival order when a worker slot is free
+   and their workspace (lra_workspace_bytes) fits in the device-memory budget
+   next to the running ones; each runs in its own context on its worker's
+   stream, so the block steps of concurrent requests interleave on the GPU.
+   The per-request state (A, Q, B, E, the block counter, the Philox key) stays
+   on the device; a request's Omega depends only on its own seed, so its result
+   is the same bits alone or in any mix. */
+typedef struct lra_server lra_server;
+
+typedef struct {
+  int64_t hbm_budget;  /* device bytes the admitted requests may hold at once;
+                          0 = 90% of the free device memory at creation       */
+  int32_t slots;       /* requests run at once (worker threads), 1..64        */
+  uint32_t flags;      /* LRA_FLAG_* added to every request's parameters
+                          (LRA_FLAG_POOL is always added)                     */
+} lra_server_params;
+
+typedef struct {
+  uint64_t id;         /* caller's tag, returned in the completion            */
+  lra_matrix A;        /* device (LRA_F64 or LRA_F32), borrowed until the
+                          request completes                                   */
+  lra_params params;
+  int32_t keep;        /* != 0: keep the context for the caller (its results via
+                          lra_result / lra_svd; release with
+                          lra_server_release), else free it on completion     */
+  int32_t reserved;
+} lra_request;
+
+typedef struct {
+  uint64_t id;
+  int32_t status;      /* lra_status of the run, or of a failed create        */
+  int32_t reserved;
+  int64_t rank;
+  double rel_err;
+  double t_submit;     /* seconds on the server's clock (lra_server_clock)    */
+  double t_start;      /* admitted and its context created                    */
+  double t_done;       /* run finished                                        */
+  int64_t bytes;       /* device bytes the request held                       */
+  lra_ctx* ctx;        /* the context when keep != 0 (else NULL)              */
+} lra_completion;
+
+/* Create a server and start its worker threads.  Errors: LRA_ERR_INVALID_ARG,
+   LRA_ERR_CUDA. */
+lra_status lra_server_create(lra_server** out, const lra_server_params* params);
+
+/* Queue a request (returns at once).  LRA_ERR_INVALID_ARG for bad arguments,
+   LRA_ERR_UNSUPPORTED when its workspace alone exceeds the budget. */
+lra_status lra_server_submit(lra_server* srv, const lra_request* req);
+
+/* Move up to max completions, oldest first, into out; returns their number.
+   wait != 0 blocks until at least one is available or nothing is pending. */
+int64_t lra_server_poll(lra_server* srv, lra_completion* out, int64_t max, int32_t wait);
+
+/* Requests submitted and not yet completed. */
+int64_t lra_server_pending(const lra_server* srv);
+
+/* Free a kept request's context and return its bytes to the budget. */
+lra_status lra_server_release(lra_server* srv, lra_ctx* ctx);
+
+/* Seconds since the server was created (steady clock). */
+double lra_server_clock(const lra_server* srv);
+
+/* Wait for every pending request, stop the workers, free what they hold
+   (including kept contexts not released).  NULL is ignored. */
+void lra_server_destroy(lra_server* srv);
 
 /* Message for the last error on ctx ("" if none); never NULL. */
 const char* lra_last_error(const lra_ctx* ctx);

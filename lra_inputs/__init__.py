@@ -87,3 +87,19 @@ def workload_matrix(name, **override):
     cfg.update(override)
     return low_rank_matrix(cfg["m"], cfg["n"], cfg["spectrum"], cfg["seed"], cfg.get("noise", 0.0),
                        cfg.get("rank"))
+
+
+def device_low_rank(m, n, rank, seed, dtype=None, spectrum="exp100", device="cuda"):
+    """A = U diag(sigma) V^T on a CUDA device (torch), column-major, exact rank
+    `rank` (U, V with orthonormal columns from QR of seeded Gaussians), built in
+    float64 and stored as `dtype` (default float32).  For large request pools
+    (the serving workload), where host generation would dominate."""
+    import torch
+    dtype = dtype or torch.float32
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    U = torch.linalg.qr(torch.randn((m, rank), generator=g, dtype=torch.float64, device=device))[0]
+    V = torch.linalg.qr(torch.randn((n, rank), generator=g, dtype=torch.float64, device=device))[0]
+    sig = torch.from_numpy(singular_values(spectrum, rank)).to(device)
+    A = torch.empty_strided((m, n), (1, m), dtype=dtype, device=device)
+    A.copy_((U * sig[None, :]) @ V.T)
+    return A

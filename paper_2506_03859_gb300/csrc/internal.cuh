@@ -59,7 +59,7 @@ cudaError_t omega_dense(const OmegaSpec& s, int64_t j0, int64_t nblk, double* Om
 // Kernel attributes (dynamic shared memory) set once per process, before any
 // stream capture; the prepare functions are idempotent.
 cudaError_t gather_prepare();
-cudaError_t gather_sketch(const double* X, int64_t ldx, int64_t rows_x, const int* counts,
+cudaError_t gather_sketch(const void* X, int dtype, int64_t ldx, int64_t rows_x, const int* counts,
                           const int* rows, const double* vals, int cap, int64_t ncols, double* Y,
                           int64_t ldy, const double* shift, int* flags, cudaStream_t st);
 
@@ -99,8 +99,8 @@ cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, co
 // The digit image of op(X) (P x K): every (128-row tile, 32-deep stage) as seven
 // f16 digit planes, cut once and reused by ozgemm_img.  xE as for ozgemm.
 int64_t oz_ximg_bytes(int64_t P, int64_t K);
-cudaError_t oz_cut_x(bool trans, int64_t P, int64_t K, const double* X, int64_t ldx, const int* xE,
-                     uint8_t* ximg, int ctas, cudaStream_t st);
+cudaError_t oz_cut_x(bool trans, int64_t P, int64_t K, const void* X, int dtype, int64_t ldx,
+                     const int* xE, uint8_t* ximg, int ctas, cudaStream_t st);
 // low: the reduced form (digits 0..3 of both operands; ~2^-30 of max|x| max|y|).
 cudaError_t ozgemm_img(int64_t P, int64_t N, int64_t K, double alpha, const uint8_t* ximg,
                        const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
@@ -118,8 +118,8 @@ cudaError_t col_sums(const double* X, int64_t ld, int64_t rows, int64_t cols, do
 // part, a_stats_part_elems(m, n) doubles), colE / rowE = largest biased exponent
 // of each column / row.  Deterministic.
 int64_t a_stats_part_elems(int64_t m, int64_t n);
-cudaError_t a_stats(const double* A, int64_t lda, int64_t m, int64_t n, double* part, double* colsq,
-                    int* colE, int* rowE, cudaStream_t st);
+cudaError_t a_stats(const void* A, int dtype, int64_t lda, int64_t m, int64_t n, double* part,
+                    double* colsq, int* colE, int* rowE, cudaStream_t st);
 // out[0] = sum of v[0..count) in a fixed order (one CTA).
 cudaError_t total(const double* v, int64_t count, double* out, cudaStream_t st);
 // Cholesky S = R^T R (S: b x b, ld b), R^{-1} into Rinv (b x b, ld b); on a failed

@@ -69,6 +69,7 @@ struct lra_ctx {
     cudaGraphExec_t exec = nullptr;
     const double* A = nullptr;
     int64_t lda = 0;
+    int dtype = LRA_F64;
     int nev0 = 0;            // first profiling event index it records
     int nev = 0;             // profiling events the graph records
     std::vector<int> phase;  // ... and their phases
@@ -130,7 +131,11 @@ struct lra_ctx {
     unsigned* bar = nullptr;
   } svd;
 
+  bool dry = false;     // lra_workspace_bytes: count allocations, make none
+  bool pool = false;    // LRA_FLAG_POOL: stream-ordered allocations
+  int64_t bytes = 0;    // device bytes allocated so far
   bool run_ok = false;  // the last lra_farpca_run completed (any non-negative status)
+  int a_dtype = LRA_F64;  // element type of the A of the current run
   int32_t status = LRA_OK;
   int64_t rank = 0, blocks = 0;
   double E = 0.0, normA2 = 0.0;
@@ -163,11 +168,26 @@ lra_status fail(lra_ctx* c, lra_status s, const char* fmt, ...) {
     if (s_ < 0) return s_;                \
   } while (0)
 
+// Device memory of a context: cudaMalloc, or with LRA_FLAG_POOL the device's
+// stream-ordered pool on the context's stream (freeing it then synchronises
+// nothing but that stream).  A dry context (lra_workspace_bytes) only counts.
 template <class T>
-cudaError_t dalloc(T** p, int64_t count) {
+cudaError_t dalloc(lra_ctx* ctx, T** p, int64_t count) {
   *p = nullptr;
   if (count <= 0) return cudaSuccess;
-  return cudaMalloc((void**)p, (size_t)count * sizeof(T));
+  const size_t bytes = (size_t)count * sizeof(T);
+  ctx->bytes += (int64_t)bytes;
+  if (ctx->dry) return cudaSuccess;
+  if (ctx->pool) return cudaMallocAsync((void**)p, bytes, ctx->st);
+  return cudaMalloc((void**)p, bytes);
+}
+
+void dfree(lra_ctx* ctx, void* p) {
+  if (!p) return;
+  if (ctx->pool)
+    cudaFreeAsync(p, ctx->st);
+  else
+    cudaFree(p);
 }
 
 double default_p(int kind, int64_t n, int zeta) {
@@ -200,19 +220,21 @@ lra_status check_params(lra_ctx* ctx, int64_t m, int64_t n, const lra_params* p)
   if ((int64_t)p->max_blocks * p->b > mn)
     return fail(ctx, LRA_ERR_INVALID_ARG, "max_blocks * b exceeds min(m, n)");
   if (p->flags & ~(LRA_FLAG_KEEP_Y | LRA_FLAG_PROFILE | LRA_FLAG_FP64_SIMT | LRA_FLAG_NO_A_DIGITS |
-                   LRA_FLAG_NO_GRAPHS | LRA_FLAG_MIXED))
+                   LRA_FLAG_NO_GRAPHS | LRA_FLAG_MIXED | LRA_FLAG_POOL))
     return fail(ctx, LRA_ERR_INVALID_ARG, "unknown flags");
   return LRA_OK;
 }
 
-lra_status check_matrix(lra_ctx* ctx, const lra_matrix* A) {
+lra_status check_matrix(lra_ctx* ctx, const lra_matrix* A, bool allow_f32 = false) {
   if (!A || !A->data) return fail(ctx, LRA_ERR_INVALID_ARG, "A is NULL");
   if (A->m != ctx->m || A->n != ctx->n)
     return fail(ctx, LRA_ERR_INVALID_ARG, "A is %lld x %lld, context expects %lld x %lld",
                 (long long)A->m, (long long)A->n, (long long)ctx->m, (long long)ctx->n);
   if (A->lda < A->m) return fail(ctx, LRA_ERR_INVALID_ARG, "lda < m");
-  if (A->dtype != LRA_F64)
-    return fail(ctx, LRA_ERR_UNSUPPORTED, "only LRA_F64 matrices are implemented");
+  if (A->dtype == LRA_F32 && !allow_f32)
+    return fail(ctx, LRA_ERR_UNSUPPORTED, "this entry point takes LRA_F64 matrices only");
+  if (A->dtype != LRA_F64 && A->dtype != LRA_F32)
+    return fail(ctx, LRA_ERR_INVALID_ARG, "unknown dtype %d", (int)A->dtype);
   return LRA_OK;
 }
 
@@ -316,8 +338,8 @@ lra_status make_omega(lra_ctx* ctx, int64_t j) {
 lra_status apply_omega(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows_x, double* out,
                        int64_t ldo, const double* shift, bool x_is_A) {
   if (ctx->sparse) {
-    CK(gather_sketch(X, ldx, rows_x, ctx->om_counts, ctx->om_rows, ctx->om_vals, ctx->cap, ctx->b,
-                     out, ldo, shift, ctx->flags, ctx->st));
+    CK(gather_sketch(X, x_is_A ? ctx->a_dtype : LRA_F64, ldx, rows_x, ctx->om_counts, ctx->om_rows,
+                     ctx->om_vals, ctx->cap, ctx->b, out, ldo, shift, ctx->flags, ctx->st));
     return LRA_OK;
   }
   if (x_is_A)
@@ -396,7 +418,7 @@ lra_status read_record(lra_ctx* ctx) {
 // so the stream stays usable.
 template <typename F>
 lra_status captured(lra_ctx* ctx, lra_ctx::GraphSlot& gs, const double* A, int64_t lda, F&& body) {
-  if (!gs.exec || gs.A != A || gs.lda != lda || gs.nev0 != ctx->nev) {
+  if (!gs.exec || gs.A != A || gs.lda != lda || gs.dtype != ctx->a_dtype || gs.nev0 != ctx->nev) {
     if (gs.exec) {
       cudaGraphExecDestroy(gs.exec);
       gs.exec = nullptr;
@@ -425,6 +447,7 @@ lra_status captured(lra_ctx* ctx, lra_ctx::GraphSlot& gs, const double* A, int64
     }
     gs.A = A;
     gs.lda = lda;
+    gs.dtype = ctx->a_dtype;
     gs.nev0 = nev0;
     gs.nev = nev;
     gs.phase.assign(ctx->ev_phase + nev0, ctx->ev_phase + nev0 + nev);
@@ -444,7 +467,17 @@ lra_status issue(lra_ctx* ctx, lra_ctx::GraphSlot& gs, const double* A, int64_t 
   return body();
 }
 
-lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
+// A: column-major m x n of element type dtype.  FP32 entries are converted
+// exactly to FP64 where they are read (the statistics pass, the digit cut and
+// the sparse gather); nothing else reads A, so a run on FP32 data computes the
+// same bits as a run on its FP64 conversion.
+lra_status run(lra_ctx* ctx, const void* Av, int64_t lda, int dtype) {
+  if (dtype == LRA_F32 && !(ctx->tensor && ctx->ximg[0] && ctx->ximg[1]))
+    return fail(ctx, LRA_ERR_UNSUPPORTED,
+                "LRA_F32 input needs the tensor engine with digit images (no LRA_FLAG_FP64_SIMT, "
+                "no LRA_FLAG_NO_A_DIGITS, and room for the images)");
+  ctx->a_dtype = dtype;
+  const double* A = (const double*)Av;  // dereferenced as double only when dtype is LRA_F64
   // the digit images describe this run's A only: invalid on every way out
   struct ImageScope {
     lra_ctx* c;
@@ -462,7 +495,7 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
   // and columns in the same pass
   PHASE(LRA_PHASE_INDICATOR, {
     if (ctx->tensor)
-      CK(a_stats(A, lda, m, n, ctx->astat, ctx->colsq, ctx->colE, ctx->rowE, ctx->st));
+      CK(a_stats(Av, dtype, lda, m, n, ctx->astat, ctx->colsq, ctx->colE, ctx->rowE, ctx->st));
     else
       CK(col_sums(A, lda, m, n, ctx->colsq, nullptr, ctx->st));
     CK(total(ctx->colsq, n, ctx->scal, ctx->st));
@@ -482,8 +515,8 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
   TRY(issue(ctx, ctx->gpre, A, lda, [&]() -> lra_status {
     if (images) {
       PHASE(LRA_PHASE_CUT, {
-        CK(oz_cut_x(false, m, n, A, lda, ctx->rowE, ctx->ximg[0], ctx->oz.ctas, ctx->st));
-        CK(oz_cut_x(true, n, m, A, lda, ctx->colE, ctx->ximg[1], ctx->oz.ctas, ctx->st));
+        CK(oz_cut_x(false, m, n, Av, dtype, lda, ctx->rowE, ctx->ximg[0], ctx->oz.ctas, ctx->st));
+        CK(oz_cut_x(true, n, m, Av, dtype, lda, ctx->colE, ctx->ximg[1], ctx->oz.ctas, ctx->st));
       });
     }
     if (ctx->tensor) {
@@ -590,26 +623,26 @@ lra_status run(lra_ctx* ctx, const double* A, int64_t lda) {
 lra_status ensure_sketch_scratch(lra_ctx* ctx, int64_t cols, int cap) {
   const int64_t entries = cols * cap;
   if (cols <= ctx->sk_cols && entries <= ctx->sk_entries) return LRA_OK;
-  cudaFree(ctx->sk_counts);
-  cudaFree(ctx->sk_rows);
-  cudaFree(ctx->sk_vals);
+  dfree(ctx, ctx->sk_counts);
+  dfree(ctx, ctx->sk_rows);
+  dfree(ctx, ctx->sk_vals);
   ctx->sk_counts = nullptr;
   ctx->sk_rows = nullptr;
   ctx->sk_vals = nullptr;
   ctx->sk_cols = ctx->sk_entries = 0;
-  CK(dalloc(&ctx->sk_counts, cols));
-  CK(dalloc(&ctx->sk_rows, entries));
-  CK(dalloc(&ctx->sk_vals, entries));
+  CK(dalloc(ctx, &ctx->sk_counts, cols));
+  CK(dalloc(ctx, &ctx->sk_rows, entries));
+  CK(dalloc(ctx, &ctx->sk_vals, entries));
   ctx->sk_cols = cols;
   ctx->sk_entries = entries;
   return LRA_OK;
 }
 
-void svd_free(lra_ctx::SvdWs& w) {
+void svd_free(lra_ctx* ctx) {
+  auto& w = ctx->svd;
   void* ptrs[] = {w.Bt, w.G,    w.C0,   w.C1,     w.V,      w.Vs,     w.W,    w.sigma,
                   w.U,  w.Vout, w.perm, w.info,   w.btrowE, w.btcolE, w.qrowE, w.bar, w.vinv};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  for (void* p : ptrs) dfree(ctx, p);
   w = lra_ctx::SvdWs{};
 }
 
@@ -617,25 +650,25 @@ void svd_free(lra_ctx::SvdWs& w) {
 lra_status svd_alloc(lra_ctx* ctx, int64_t l) {
   auto& w = ctx->svd;
   if (w.cap >= l) return LRA_OK;
-  svd_free(w);
+  svd_free(ctx);
   const int64_t lp = eig_padded(l), m = ctx->m, n = ctx->n;
-  CK(dalloc(&w.Bt, n * l));
-  CK(dalloc(&w.G, l * l));
-  CK(dalloc(&w.C0, lp * lp));
-  CK(dalloc(&w.C1, lp * lp));
-  CK(dalloc(&w.V, lp * lp));
-  CK(dalloc(&w.Vs, l * l));
-  CK(dalloc(&w.W, l * l));
-  CK(dalloc(&w.sigma, l));
-  CK(dalloc(&w.U, m * l));
-  CK(dalloc(&w.Vout, n * l));
-  CK(dalloc(&w.perm, l));
-  CK(dalloc(&w.vinv, l));
-  CK(dalloc(&w.info, 4));
-  CK(dalloc(&w.btrowE, n));
-  CK(dalloc(&w.btcolE, l));
-  CK(dalloc(&w.qrowE, m));
-  CK(dalloc(&w.bar, 2));
+  CK(dalloc(ctx, &w.Bt, n * l));
+  CK(dalloc(ctx, &w.G, l * l));
+  CK(dalloc(ctx, &w.C0, lp * lp));
+  CK(dalloc(ctx, &w.C1, lp * lp));
+  CK(dalloc(ctx, &w.V, lp * lp));
+  CK(dalloc(ctx, &w.Vs, l * l));
+  CK(dalloc(ctx, &w.W, l * l));
+  CK(dalloc(ctx, &w.sigma, l));
+  CK(dalloc(ctx, &w.U, m * l));
+  CK(dalloc(ctx, &w.Vout, n * l));
+  CK(dalloc(ctx, &w.perm, l));
+  CK(dalloc(ctx, &w.vinv, l));
+  CK(dalloc(ctx, &w.info, 4));
+  CK(dalloc(ctx, &w.btrowE, n));
+  CK(dalloc(ctx, &w.btcolE, l));
+  CK(dalloc(ctx, &w.qrowE, m));
+  CK(dalloc(ctx, &w.bar, 2));
   w.cap = l;
   return LRA_OK;
 }
@@ -649,9 +682,8 @@ void free_all(lra_ctx* c) {
                   c->rowE,   c->colE,     c->oz.yE,  c->oz.img,   c->oz.part,
                   c->qrowE,  c->qcolE,    c->browE,  c->bcolE,    c->xrowE,     c->xcolE,
                   c->ximg[0], c->ximg[1], c->astat};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
-  svd_free(c->svd);
+  for (void* p : ptrs) dfree(c, p);
+  svd_free(c);
   if (c->gpre.exec) cudaGraphExecDestroy(c->gpre.exec);
   for (int i = 0; i < lra_ctx::NCOPY; ++i) {
     if (c->cst[i]) cudaStreamDestroy(c->cst[i]);
@@ -697,11 +729,17 @@ const char* lra_last_error(const lra_ctx* ctx) { return ctx ? ctx->err.c_str() :
 
 int64_t lra_capacity(const lra_ctx* ctx) { return ctx ? ctx->lmax : -1; }
 
-lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* params,
-                      void* cuda_stream) {
+namespace {
+
+// lra_create, or with dry = true the same sizing with every allocation only
+// counted (ctx->bytes) and no CUDA object made.
+lra_status create_ctx(lra_ctx** out, int64_t m, int64_t n, const lra_params* params,
+                      void* cuda_stream, bool dry) {
   if (!out || !params) return LRA_ERR_INVALID_ARG;
   *out = nullptr;
   lra_ctx* ctx = new lra_ctx();
+  ctx->dry = dry;
+  ctx->pool = (params->flags & LRA_FLAG_POOL) != 0;
   lra_status s = check_params(ctx, m, n, params);
   if (s != LRA_OK) {
     delete ctx;
@@ -711,7 +749,7 @@ lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
   ctx->n = n;
   ctx->prm = *params;
   ctx->st = (cudaStream_t)cuda_stream;
-  if (!ctx->st) {
+  if (!ctx->st && !dry) {
     // a blocking stream of our own: ordered with the legacy default stream like
     // NULL, but capturable into graphs
     if (cudaStreamCreate(&ctx->st) != cudaSuccess) {
@@ -766,7 +804,7 @@ lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
   const int b = ctx->b;
 #define ALLOC(ptr, count)                                                                  \
   do {                                                                                     \
-    cudaError_t e_ = dalloc(&ctx->ptr, (count));                                           \
+    cudaError_t e_ = dalloc(ctx, &ctx->ptr, (count));                                      \
     if (e_ != cudaSuccess) {                                                               \
       lra_status r_ = fail(ctx, e_ == cudaErrorMemoryAllocation ? LRA_ERR_OOM : LRA_ERR_CUDA, \
                            "allocating %s: %s", #ptr, cudaGetErrorString(e_));             \
@@ -801,7 +839,7 @@ lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
   ctx->tensor = (params->flags & LRA_FLAG_FP64_SIMT) == 0;
   ctx->graphs = (params->flags & LRA_FLAG_NO_GRAPHS) == 0;
   ctx->mixed = (params->flags & LRA_FLAG_MIXED) != 0;
-  {
+  if (!dry) {
     // kernel attributes, before any stream capture
     cudaError_t e = gather_prepare();
     if (e == cudaSuccess && ctx->tensor) e = oz_prepare();
@@ -814,8 +852,11 @@ lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
   }
   if (ctx->tensor) {
     int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 152;  // sizing without a device (dry run): the GB300's SM count
+    }
     ctx->oz.ctas = sms > 0 ? sms : 1;
     ctx->oz.img_bytes = oz_img_bytes(std::max(m, n));
     ALLOC(rowE, m);
@@ -833,11 +874,13 @@ lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
     // A's digit images when the device has room (else every pass cuts A itself)
     if (!(params->flags & LRA_FLAG_NO_A_DIGITS)) {
       const int64_t b0 = oz_ximg_bytes(m, n), b1 = oz_ximg_bytes(n, m);
-      if (cudaMalloc((void**)&ctx->ximg[0], b0) != cudaSuccess ||
-          cudaMalloc((void**)&ctx->ximg[1], b1) != cudaSuccess) {
+      const int64_t before = ctx->bytes;
+      if (dalloc(ctx, &ctx->ximg[0], b0) != cudaSuccess ||
+          dalloc(ctx, &ctx->ximg[1], b1) != cudaSuccess) {
         cudaGetLastError();
-        if (ctx->ximg[0]) cudaFree(ctx->ximg[0]);
+        dfree(ctx, ctx->ximg[0]);
         ctx->ximg[0] = ctx->ximg[1] = nullptr;
+        ctx->bytes = before;
       }
     }
   }
@@ -849,6 +892,10 @@ lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
     ALLOC(om_dense, ctx->ldod * b);
   }
 #undef ALLOC
+  if (dry) {
+    *out = ctx;
+    return LRA_OK;
+  }
   cudaError_t e = cudaMallocHost((void**)&ctx->hp, sizeof(Pinned));
   if (e != cudaSuccess) {
     free_all(ctx);
@@ -879,6 +926,24 @@ lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
   return LRA_OK;
 }
 
+}  // namespace
+
+lra_status lra_create(lra_ctx** out, int64_t m, int64_t n, const lra_params* params,
+                      void* cuda_stream) {
+  return create_ctx(out, m, n, params, cuda_stream, false);
+}
+
+int64_t lra_workspace_bytes(int64_t m, int64_t n, const lra_params* params) {
+  lra_ctx* ctx = nullptr;
+  const lra_status s = create_ctx(&ctx, m, n, params, nullptr, true);
+  if (s != LRA_OK) return s;
+  const int64_t bytes = ctx->bytes + (int64_t)sizeof(Pinned);
+  delete ctx;
+  return bytes;
+}
+
+int64_t lra_device_bytes(const lra_ctx* ctx) { return ctx ? ctx->bytes : -1; }
+
 void lra_destroy(lra_ctx* ctx) {
   if (!ctx) return;
   if (ctx->st) cudaStreamSynchronize(ctx->st);
@@ -890,8 +955,8 @@ void lra_destroy(lra_ctx* ctx) {
 lra_status lra_farpca_run(lra_ctx* ctx, const lra_matrix* A) {
   if (!ctx) return LRA_ERR_INVALID_ARG;
   ctx->err.clear();
-  TRY(check_matrix(ctx, A));
-  return run(ctx, (const double*)A->data, A->lda);
+  TRY(check_matrix(ctx, A, true));
+  return run(ctx, A->data, A->lda, A->dtype);
 }
 
 lra_status lra_svd(lra_ctx* ctx, lra_svd_t* out) {
@@ -1006,7 +1071,10 @@ lra_status lra_sketch(lra_ctx* ctx, const lra_matrix* A, int64_t j0, int64_t nbl
                       int64_t ldy) {
   if (!ctx) return LRA_ERR_INVALID_ARG;
   ctx->err.clear();
-  TRY(check_matrix(ctx, A));
+  TRY(check_matrix(ctx, A, true));
+  if (A->dtype == LRA_F32 && (!ctx->sparse || ctx->sb_sparse))
+    return fail(ctx, LRA_ERR_UNSUPPORTED,
+                "LRA_F32 sketches are implemented for the sparse (pure gather) kinds");
   if (j0 < 0 || nblk < 0 || j0 + nblk > (int64_t)UINT32_MAX)
     return fail(ctx, LRA_ERR_INVALID_ARG, "block range out of [0, 2^32)");
   if (nblk == 0) return LRA_OK;
@@ -1034,7 +1102,8 @@ lra_status lra_sketch(lra_ctx* ctx, const lra_matrix* A, int64_t j0, int64_t nbl
     const int64_t nb = std::min(chunk, j0 + nblk - j);
     CK(omega_sparse(ctx->os, j, nb, ctx->cap, ctx->sk_counts, ctx->sk_rows, ctx->sk_vals,
                     ctx->flags, ctx->st));
-    CK(gather_sketch(Ad, A->lda, ctx->m, ctx->sk_counts, ctx->sk_rows, ctx->sk_vals, ctx->cap,
+    CK(gather_sketch(A->data, A->dtype, A->lda, ctx->m, ctx->sk_counts, ctx->sk_rows, ctx->sk_vals,
+                     ctx->cap,
                      nb * b, Y + (j - j0) * b * ldy, ldy, ctx->sb_sparse ? ctx->z : nullptr,
                      ctx->flags, ctx->st));
   }
@@ -1098,15 +1167,21 @@ lra_status lra_copy_omega(lra_ctx* ctx, int64_t j, int64_t cap, int32_t* counts,
   return LRA_OK;
 }
 
-lra_status lra_farpca_host(lra_ctx* ctx, const double* A_host, int64_t lda_host, double* Q_host,
-                           int64_t ldq_host, double* B_host, int64_t ldb_host, lra_result_t* out) {
+namespace {
+
+// lra_farpca_host for either element type: A_host (m x n, ld lda_host, esize
+// bytes an element) is copied in column chunks into the context's staging
+// buffer (ld = ldq elements of that type) and run there.
+lra_status host_run(lra_ctx* ctx, const void* A_host, int dtype, int64_t lda_host, double* Q_host,
+                    int64_t ldq_host, double* B_host, int64_t ldb_host, lra_result_t* out) {
   if (!ctx || !A_host) return LRA_ERR_INVALID_ARG;
   ctx->err.clear();
   const int64_t m = ctx->m, n = ctx->n;
+  const size_t es = dtype == LRA_F32 ? sizeof(float) : sizeof(double);
   if (lda_host < m) return fail(ctx, LRA_ERR_INVALID_ARG, "lda_host < m");
   if (Q_host && ldq_host < m) return fail(ctx, LRA_ERR_INVALID_ARG, "ldq_host < m");
   if (B_host && ldb_host < ctx->lmax) return fail(ctx, LRA_ERR_INVALID_ARG, "ldb_host < capacity");
-  if (!ctx->A_host_copy) CK(dalloc(&ctx->A_host_copy, ctx->ldq * n));
+  if (!ctx->A_host_copy) CK(dalloc(ctx, &ctx->A_host_copy, ctx->ldq * n));
   if (!ctx->cstart) {
     CK(cudaEventCreateWithFlags(&ctx->cstart, cudaEventDisableTiming));
     for (int i = 0; i < lra_ctx::NCOPY; ++i) {
@@ -1116,18 +1191,19 @@ lra_status lra_farpca_host(lra_ctx* ctx, const double* A_host, int64_t lda_host,
   }
   // A in NCOPY column chunks on as many streams (several copy engines at once), all
   // after the work already on the context's stream and before the run
+  char* dst = reinterpret_cast<char*>(ctx->A_host_copy);
+  const char* src = reinterpret_cast<const char*>(A_host);
   CK(cudaEventRecord(ctx->cstart, ctx->st));
   for (int i = 0; i < lra_ctx::NCOPY; ++i) {
     const int64_t c0 = i * n / lra_ctx::NCOPY, c1 = (i + 1) * n / lra_ctx::NCOPY;
     CK(cudaStreamWaitEvent(ctx->cst[i], ctx->cstart, 0));
     if (c1 > c0)
-      CK(cudaMemcpy2DAsync(ctx->A_host_copy + c0 * ctx->ldq, ctx->ldq * sizeof(double),
-                           A_host + c0 * lda_host, lda_host * sizeof(double), m * sizeof(double),
-                           c1 - c0, cudaMemcpyHostToDevice, ctx->cst[i]));
+      CK(cudaMemcpy2DAsync(dst + c0 * ctx->ldq * es, ctx->ldq * es, src + c0 * lda_host * es,
+                           lda_host * es, m * es, c1 - c0, cudaMemcpyHostToDevice, ctx->cst[i]));
     CK(cudaEventRecord(ctx->cev[i], ctx->cst[i]));
     CK(cudaStreamWaitEvent(ctx->st, ctx->cev[i], 0));
   }
-  lra_status s = run(ctx, ctx->A_host_copy, ctx->ldq);
+  lra_status s = run(ctx, ctx->A_host_copy, ctx->ldq, dtype);
   if (s < 0) return s;
   if (Q_host && ctx->rank > 0)
     CK(cudaMemcpy2DAsync(Q_host, ldq_host * sizeof(double), ctx->Q, ctx->ldq * sizeof(double),
@@ -1138,6 +1214,19 @@ lra_status lra_farpca_host(lra_ctx* ctx, const double* A_host, int64_t lda_host,
   CK(cudaStreamSynchronize(ctx->st));
   if (out) lra_result(ctx, out);
   return s;
+}
+
+}  // namespace
+
+lra_status lra_farpca_host(lra_ctx* ctx, const double* A_host, int64_t lda_host, double* Q_host,
+                           int64_t ldq_host, double* B_host, int64_t ldb_host, lra_result_t* out) {
+  return host_run(ctx, A_host, LRA_F64, lda_host, Q_host, ldq_host, B_host, ldb_host, out);
+}
+
+lra_status lra_farpca_host_f32(lra_ctx* ctx, const float* A_host, int64_t lda_host, double* Q_host,
+                               int64_t ldq_host, double* B_host, int64_t ldb_host,
+                               lra_result_t* out) {
+  return host_run(ctx, A_host, LRA_F32, lda_host, Q_host, ldq_host, B_host, ldb_host, out);
 }
 
 }  // extern "C"

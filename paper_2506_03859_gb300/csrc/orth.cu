@@ -51,7 +51,9 @@ __global__ void __launch_bounds__(256) k_col_sums(const double* __restrict__ X, 
 // rows 512 rb .., columns 32 cb ..; warp w takes 4 of the columns, lane l the
 // rows l, l + 32, ...; per column the warp reduces by shuffles; row maxima meet
 // in shared memory, one atomic per row and CTA.  colE and rowE start at zero.
-__global__ void __launch_bounds__(256) k_a_stats(const double* __restrict__ A, int64_t lda,
+// T: element type of A (float entries are converted exactly to double on load).
+template <typename T>
+__global__ void __launch_bounds__(256) k_a_stats(const T* __restrict__ A, int64_t lda,
                                                  int64_t m, int64_t n, double* __restrict__ part,
                                                  int* __restrict__ colE, int* __restrict__ rowE) {
   __shared__ int srow[8][512];
@@ -64,13 +66,13 @@ __global__ void __launch_bounds__(256) k_a_stats(const double* __restrict__ A, i
   for (int q = 0; q < 4; ++q) {
     const int64_t c = c0 + q;
     if (c >= n) break;  // warp-uniform
-    const double* col = A + c * lda + r0;
+    const T* col = A + c * lda + r0;
     double s0 = 0.0, s1 = 0.0;
     int e = 0;
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       const int64_t r = lane + 32 * k;
-      const double x = (r0 + r < m) ? __ldg(col + r) : 0.0;
+      const double x = (r0 + r < m) ? (double)__ldg(col + r) : 0.0;
       const int ex = (int)((__double_as_longlong(x) >> 52) & 0x7FF);
       e = max(e, ex);
       rmax[k] = max(rmax[k], ex);
@@ -238,14 +240,17 @@ cudaError_t col_sums(const double* X, int64_t ld, int64_t rows, int64_t cols, do
 
 int64_t a_stats_part_elems(int64_t m, int64_t n) { return (m + 511) / 512 * n; }
 
-cudaError_t a_stats(const double* A, int64_t lda, int64_t m, int64_t n, double* part, double* colsq,
-                    int* colE, int* rowE, cudaStream_t st) {
+cudaError_t a_stats(const void* A, int dtype, int64_t lda, int64_t m, int64_t n, double* part,
+                    double* colsq, int* colE, int* rowE, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(colE, 0, n * sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(rowE, 0, m * sizeof(int), st);
   if (e != cudaSuccess) return e;
   const int64_t nrb = (m + 511) / 512;
-  k_a_stats<<<dim3((unsigned)nrb, (unsigned)((n + 31) / 32)), 256, 0, st>>>(A, lda, m, n, part, colE,
-                                                                            rowE);
+  const dim3 grid((unsigned)nrb, (unsigned)((n + 31) / 32));
+  if (dtype == LRA_F32)
+    k_a_stats<float><<<grid, 256, 0, st>>>((const float*)A, lda, m, n, part, colE, rowE);
+  else
+    k_a_stats<double><<<grid, 256, 0, st>>>((const double*)A, lda, m, n, part, colE, rowE);
   e = launched();
   if (e != cudaSuccess) return e;
   k_sum_blocks<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, nrb, n, colsq);

@@ -237,6 +237,7 @@ __global__ void __launch_bounds__(256) k_oz_ycut(const double* __restrict__ Y, i
 struct OzArgs {
   int64_t P, K, N;
   const double* X;
+  const float* X32;    // k_oz_xcut<TRANS, float>: X as float (converted exactly on load)
   int64_t ldx;
   const int* xE;       // biased max exponent of each row of op(X)
   const int* yE;       // biased max exponent of each column of Y
@@ -296,42 +297,57 @@ struct Cursor {
 // 8 (pw / 2 + 4 i) + r8 and k 8 (pw % 2) + 2 (lane / 8) + {0, 1}.
 constexpr int VPT = TM * KS / NPROD;  // values per producer thread per stage
 
-template <bool TRANS>
+template <typename T>
+__device__ __forceinline__ const T* xsrc(const OzArgs& a);
+template <>
+__device__ __forceinline__ const double* xsrc<double>(const OzArgs& a) { return a.X; }
+template <>
+__device__ __forceinline__ const float* xsrc<float>(const OzArgs& a) { return a.X32; }
+
+// T: element type of X in memory (float is converted exactly to double).
+template <bool TRANS, typename T = double>
 __device__ __forceinline__ void fetch(const OzArgs& a, int64_t tile, int ks, int pw, int lane,
                                       double (&v)[VPT]) {
+  const T* X = xsrc<T>(a);
   if (!TRANS) {
     const int64_t p = tile * TM + 32 * (pw & 3) + lane, kb = (int64_t)ks * KS + 8 * (pw >> 2);
-    const double* src = a.X + p + kb * a.ldx;
+    const T* src = X + p + kb * a.ldx;
     if (p < a.P && kb + 8 <= a.K) {
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        v[i] = __ldg(src);
+        v[i] = (double)__ldg(src);
         src += a.ldx;
       }
     } else {
 #pragma unroll
       for (int i = 0; i < 8; ++i)
-        v[i] = (p < a.P && kb + i < a.K) ? __ldg(src + i * a.ldx) : 0.0;
+        v[i] = (p < a.P && kb + i < a.K) ? (double)__ldg(src + i * a.ldx) : 0.0;
     }
   } else {
     const int r8 = lane & 7, q = lane >> 3;
     const int64_t p0 = tile * TM + (pw >> 1) * 8 + r8, k = (int64_t)ks * KS + (pw & 1) * 8 + 2 * q;
-    const double* src = a.X + k + p0 * a.ldx;
+    const T* src = X + k + p0 * a.ldx;
     if (a.vec && tile * TM + TM <= a.P && k + 2 <= a.K) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const double2 t = __ldg(reinterpret_cast<const double2*>(src));
-        v[2 * i] = t.x;
-        v[2 * i + 1] = t.y;
+        if constexpr (sizeof(T) == 8) {
+          const double2 t = __ldg(reinterpret_cast<const double2*>(src));
+          v[2 * i] = t.x;
+          v[2 * i + 1] = t.y;
+        } else {
+          const float2 t = __ldg(reinterpret_cast<const float2*>(src));
+          v[2 * i] = (double)t.x;
+          v[2 * i + 1] = (double)t.y;
+        }
         src += 32 * a.ldx;
       }
     } else {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const bool in = p0 + 32 * i < a.P;
-        const double* s2 = src + 32 * i * a.ldx;
-        v[2 * i] = (in && k < a.K) ? __ldg(s2) : 0.0;
-        v[2 * i + 1] = (in && k + 1 < a.K) ? __ldg(s2 + 1) : 0.0;
+        const T* s2 = src + 32 * i * a.ldx;
+        v[2 * i] = (in && k < a.K) ? (double)__ldg(s2) : 0.0;
+        v[2 * i + 1] = (in && k + 1 < a.K) ? (double)__ldg(s2 + 1) : 0.0;
       }
     }
   }
@@ -819,7 +835,7 @@ __global__ void __launch_bounds__(NT_IMG, 1) k_ozgemm_img(OzArgs a, const uint8_
 
 // Cut op(X) into its digit image (the stage layout of k_ozgemm_img): one CTA of
 // NPROD threads per (tile, stage) unit, grid-stride.
-template <bool TRANS>
+template <bool TRANS, typename E>
 __global__ void __launch_bounds__(NPROD) k_oz_xcut(OzArgs a, uint8_t* __restrict__ ximg) {
   __shared__ int sE[TM];
   const int pw = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -838,7 +854,7 @@ __global__ void __launch_bounds__(NPROD) k_oz_xcut(OzArgs a, uint8_t* __restrict
       prev_tile = tile;
     }
     double v[VPT];
-    fetch<TRANS>(a, tile, ks, pw, lane, v);
+    fetch<TRANS, E>(a, tile, ks, pw, lane, v);
     cut_stage<TRANS>(v, sE, ximg + u * (int64_t)(S * A_PLANE), pw, lane);
   }
 }
@@ -953,6 +969,7 @@ OzArgs make_args(int64_t P, int64_t N, int64_t K, double alpha, const double* X,
   a.K = K;
   a.N = N;
   a.X = X;
+  a.X32 = nullptr;
   a.ldx = ldx;
   a.xE = xE;
   a.yE = w.yE;
@@ -1012,17 +1029,30 @@ int64_t oz_ximg_bytes(int64_t P, int64_t K) {
   return ((P + TM - 1) / TM) * ((K + KS - 1) / KS) * (int64_t)(S * A_PLANE);
 }
 
-cudaError_t oz_cut_x(bool trans, int64_t P, int64_t K, const double* X, int64_t ldx, const int* xE,
-                     uint8_t* ximg, int ctas, cudaStream_t st) {
+cudaError_t oz_cut_x(bool trans, int64_t P, int64_t K, const void* X, int dtype, int64_t ldx,
+                     const int* xE, uint8_t* ximg, int ctas, cudaStream_t st) {
   if (P <= 0 || K <= 0) return cudaSuccess;
   OzWorkspace none{};
-  OzArgs a = make_args(P, 1, K, 1.0, X, ldx, xE, 0.0, GemmOut{nullptr, 0, 0}, none, nullptr);
+  const bool f32 = dtype == LRA_F32;
+  OzArgs a = make_args(P, 1, K, 1.0, f32 ? nullptr : (const double*)X, ldx, xE, 0.0,
+                       GemmOut{nullptr, 0, 0}, none, nullptr);
+  if (f32) {
+    a.X32 = (const float*)X;
+    a.vec = ((reinterpret_cast<uintptr_t>(X) & 7) == 0) && (ldx % 2 == 0);
+  }
   const int64_t units = a.tiles * a.kst;
   const unsigned grid = (unsigned)std::min<int64_t>(units, (int64_t)ctas * 4);
-  if (trans)
-    k_oz_xcut<true><<<grid, NPROD, 0, st>>>(a, ximg);
-  else
-    k_oz_xcut<false><<<grid, NPROD, 0, st>>>(a, ximg);
+  if (f32) {
+    if (trans)
+      k_oz_xcut<true, float><<<grid, NPROD, 0, st>>>(a, ximg);
+    else
+      k_oz_xcut<false, float><<<grid, NPROD, 0, st>>>(a, ximg);
+  } else {
+    if (trans)
+      k_oz_xcut<true, double><<<grid, NPROD, 0, st>>>(a, ximg);
+    else
+      k_oz_xcut<false, double><<<grid, NPROD, 0, st>>>(a, ximg);
+  }
   return launched();
 }
 

@@ -23,12 +23,16 @@ constexpr int GBATCH = 8;    // pieces per batch
 constexpr int GSMEM = GBATCH * GR * 8;  // 32 KB
 constexpr long GWAIT_TRIES = 1L << 22;
 
+// T: element type of X (double, or float converted exactly on load; the sums
+// are FP64 either way).
+template <typename T>
 __global__ void __launch_bounds__(256) k_gather_staged(
-    const double* __restrict__ X, int64_t ldx, int64_t rows_x, const int* __restrict__ counts,
+    const T* __restrict__ X, int64_t ldx, int64_t rows_x, const int* __restrict__ counts,
     const int* __restrict__ rows, const double* __restrict__ vals, int cap, int64_t ncols,
     double* __restrict__ Y, int64_t ldy, const double* __restrict__ shift, bool aligned,
     int* __restrict__ flags) {
-  extern __shared__ __align__(16) double sx[];  // [GBATCH][GR]
+  extern __shared__ __align__(16) unsigned char sx_raw[];
+  T* sx = reinterpret_cast<T*>(sx_raw);  // [GBATCH][GR]
   __shared__ __align__(8) uint64_t bar;
   const int64_t r0 = (int64_t)blockIdx.x * GR;
   const int nr = (int)((rows_x - r0) < GR ? (rows_x - r0) : GR);
@@ -50,10 +54,11 @@ __global__ void __launch_bounds__(256) k_gather_staged(
 #pragma unroll
           for (int q = 0; q < GBATCH; ++q) rr[q] = q < nb ? __ldg(rg + t0 + q) : 0;
           tc::fence_async_smem();  // earlier reads of the buffer before the copies
-          tc::mbar_arrive_expect_tx(&bar, (uint32_t)(nb * GR * 8));
+          tc::mbar_arrive_expect_tx(&bar, (uint32_t)(nb * GR * sizeof(T)));
 #pragma unroll
           for (int q = 0; q < GBATCH; ++q)
-            if (q < nb) tc::bulk_g2s(sx + q * GR, X + (int64_t)rr[q] * ldx + r0, GR * 8, &bar);
+            if (q < nb)
+              tc::bulk_g2s(sx + q * GR, X + (int64_t)rr[q] * ldx + r0, GR * sizeof(T), &bar);
         }
         double v[GBATCH];
 #pragma unroll
@@ -70,19 +75,28 @@ __global__ void __launch_bounds__(256) k_gather_staged(
 #pragma unroll
         for (int q = 0; q < GBATCH; ++q) {
           if (q < nb) {
-            const double2 a = reinterpret_cast<const double2*>(sx + q * GR)[threadIdx.x];
-            acc0 = fma(v[q], a.x, acc0);
-            acc1 = fma(v[q], a.y, acc1);
+            double a0, a1;
+            if constexpr (sizeof(T) == 8) {
+              const double2 a = reinterpret_cast<const double2*>(sx + q * GR)[threadIdx.x];
+              a0 = a.x;
+              a1 = a.y;
+            } else {
+              const float2 a = reinterpret_cast<const float2*>(sx + q * GR)[threadIdx.x];
+              a0 = (double)a.x;
+              a1 = (double)a.y;
+            }
+            acc0 = fma(v[q], a0, acc0);
+            acc1 = fma(v[q], a1, acc1);
           }
         }
         __syncthreads();  // the buffer is refilled by the next batch
       }
     } else {
       for (int t = 0; t < cnt; ++t) {
-        const double* col = X + (int64_t)__ldg(rg + t) * ldx + r0;
+        const T* col = X + (int64_t)__ldg(rg + t) * ldx + r0;
         const double v = __ldg(vg + t);
-        if (i < nr) acc0 = fma(v, __ldg(col + i), acc0);
-        if (i + 1 < nr) acc1 = fma(v, __ldg(col + i + 1), acc1);
+        if (i < nr) acc0 = fma(v, (double)__ldg(col + i), acc0);
+        if (i + 1 < nr) acc1 = fma(v, (double)__ldg(col + i + 1), acc1);
       }
     }
     if (shift) {
@@ -98,13 +112,16 @@ __global__ void __launch_bounds__(256) k_gather_staged(
 cudaError_t gather_prepare() {
   static bool attr = false;
   if (attr) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute((const void*)k_gather_staged,
+  cudaError_t e = cudaFuncSetAttribute((const void*)k_gather_staged<double>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_gather_staged<float>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM);
   if (e == cudaSuccess) attr = true;
   return e;
 }
 
-cudaError_t gather_sketch(const double* X, int64_t ldx, int64_t rows_x, const int* counts,
+cudaError_t gather_sketch(const void* X, int dtype, int64_t ldx, int64_t rows_x, const int* counts,
                           const int* rows, const double* vals, int cap, int64_t ncols, double* Y,
                           int64_t ldy, const double* shift, int* flags, cudaStream_t st) {
   if (ncols <= 0 || rows_x <= 0) return cudaSuccess;
@@ -112,9 +129,17 @@ cudaError_t gather_sketch(const double* X, int64_t ldx, int64_t rows_x, const in
   if (e0 != cudaSuccess) return e0;
   const int64_t chunks = (rows_x + GR - 1) / GR;
   dim3 grid((unsigned)chunks, (unsigned)std::min<int64_t>(ncols, 65535));
-  const bool aligned = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (ldx % 2 == 0);
-  k_gather_staged<<<grid, 256, GSMEM, st>>>(X, ldx, rows_x, counts, rows, vals, cap, ncols, Y, ldy,
-                                            shift, aligned, flags);
+  // bulk copies start on 16-byte boundaries: the base, and every column start
+  const int64_t esize = dtype == LRA_F32 ? 4 : 8;
+  const bool aligned =
+      ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && ((ldx * esize) % 16 == 0);
+  if (dtype == LRA_F32)
+    k_gather_staged<float><<<grid, 256, GSMEM, st>>>((const float*)X, ldx, rows_x, counts, rows,
+                                                     vals, cap, ncols, Y, ldy, shift, aligned, flags);
+  else
+    k_gather_staged<double><<<grid, 256, GSMEM, st>>>((const double*)X, ldx, rows_x, counts, rows,
+                                                      vals, cap, ncols, Y, ldy, shift, aligned,
+                                                      flags);
   return launched();
 }
 

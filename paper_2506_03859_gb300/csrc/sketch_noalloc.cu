@@ -66,7 +66,7 @@ extern "C" lra_status lra_sketch_noalloc(const lra_matrix* A, const lra_params* 
   const int b = params->b;
   if (m < 1 || n < 1 || m > INT32_MAX || n > INT32_MAX || A->lda < m || ldy < m)
     return LRA_ERR_INVALID_ARG;
-  if (A->dtype != LRA_F64) return LRA_ERR_UNSUPPORTED;
+  if (A->dtype != LRA_F64 && A->dtype != LRA_F32) return LRA_ERR_UNSUPPORTED;
   if (b < 1 || b > LRA_MAX_B || b > n) return LRA_ERR_INVALID_ARG;
   if (j0 < 0 || nblk < 0 || j0 + nblk > (int64_t)UINT32_MAX) return LRA_ERR_INVALID_ARG;
   if (!(params->p >= 0.0 && params->p < 1.0)) return LRA_ERR_INVALID_ARG;
@@ -124,12 +124,12 @@ extern "C" lra_status lra_sketch_noalloc(const lra_matrix* A, const lra_params* 
 
   // the flag word must start at zero; the Omega arrays are fully rewritten per chunk
   if (cudaMemsetAsync(flags, 0, sizeof(int), st) != cudaSuccess) return LRA_ERR_CUDA;
-  const double* Ad = (const double*)A->data;
   for (int64_t j = j0; j < j0 + nblk; j += chunk) {
     const int64_t nb = std::min(chunk, j0 + nblk - j);
     if (omega_sparse(os, j, nb, cap, counts, rows, vals, flags, st) != cudaSuccess)
       return LRA_ERR_CUDA;
-    if (gather_sketch(Ad, A->lda, m, counts, rows, vals, cap, nb * b, Y + (j - j0) * b * ldy, ldy,
+    if (gather_sketch(A->data, A->dtype, A->lda, m, counts, rows, vals, cap, nb * b,
+                      Y + (j - j0) * b * ldy, ldy,
                       nullptr, flags, st) != cudaSuccess)
       return LRA_ERR_CUDA;
   }

@@ -24,12 +24,16 @@ FLAG_FP64_SIMT = 4
 FLAG_NO_A_DIGITS = 8
 FLAG_NO_GRAPHS = 16
 FLAG_MIXED = 32
+FLAG_POOL = 64
 PHASES = ("omega", "sketch", "dense", "deflate", "project", "orth", "indicator", "cut")
 MAX_B, MAX_P, MAX_ZETA = 64, 8, 256
 
 EXPORTS = ("lra_create", "lra_destroy", "lra_capacity", "lra_sketch", "lra_farpca_run", "lra_result",
            "lra_farpca_host", "lra_copy_omega", "lra_last_error", "lra_status_string",
-           "lra_kernel_launches", "lra_version", "lra_phase_times", "lra_apply", "lra_svd")
+           "lra_kernel_launches", "lra_version", "lra_phase_times", "lra_apply", "lra_svd", "lra_farpca_host_f32",
+           "lra_workspace_bytes", "lra_device_bytes", "lra_server_create", "lra_server_submit",
+           "lra_server_poll", "lra_server_pending", "lra_server_release", "lra_server_clock",
+           "lra_server_destroy")
 
 
 class Matrix(Structure):
@@ -53,6 +57,21 @@ class SvdResult(Structure):
     _fields_ = [("status", c_int32), ("sweeps", c_int32), ("l", c_int64), ("r", c_int64),
                 ("E_r", c_double), ("normA2", c_double), ("U", c_void_p), ("ldu", c_int64),
                 ("sigma", c_void_p), ("V", c_void_p), ("ldv", c_int64)]
+
+
+class ServerParams(Structure):
+    _fields_ = [("hbm_budget", c_int64), ("slots", c_int32), ("flags", c_uint32)]
+
+
+class Request(Structure):
+    _fields_ = [("id", c_uint64), ("A", Matrix), ("params", Params), ("keep", c_int32),
+                ("reserved", c_int32)]
+
+
+class Completion(Structure):
+    _fields_ = [("id", c_uint64), ("status", c_int32), ("reserved", c_int32), ("rank", c_int64),
+                ("rel_err", c_double), ("t_submit", c_double), ("t_start", c_double),
+                ("t_done", c_double), ("bytes", c_int64), ("ctx", c_void_p)]
 
 
 class LraError(RuntimeError):
@@ -102,6 +121,26 @@ def load(path=LIB_PATH):
     lib.lra_phase_times.restype = c_int32
     lib.lra_apply.argtypes = [vp, POINTER(Matrix), c_int32, vp, c_int64, c_int64, vp, c_int64]
     lib.lra_apply.restype = c_int32
+    lib.lra_farpca_host_f32.argtypes = [vp, vp, c_int64, vp, c_int64, vp, c_int64, POINTER(Result)]
+    lib.lra_farpca_host_f32.restype = c_int32
+    lib.lra_workspace_bytes.argtypes = [c_int64, c_int64, POINTER(Params)]
+    lib.lra_workspace_bytes.restype = c_int64
+    lib.lra_device_bytes.argtypes = [vp]
+    lib.lra_device_bytes.restype = c_int64
+    lib.lra_server_create.argtypes = [POINTER(vp), POINTER(ServerParams)]
+    lib.lra_server_create.restype = c_int32
+    lib.lra_server_submit.argtypes = [vp, POINTER(Request)]
+    lib.lra_server_submit.restype = c_int32
+    lib.lra_server_poll.argtypes = [vp, POINTER(Completion), c_int64, c_int32]
+    lib.lra_server_poll.restype = c_int64
+    lib.lra_server_pending.argtypes = [vp]
+    lib.lra_server_pending.restype = c_int64
+    lib.lra_server_release.argtypes = [vp, vp]
+    lib.lra_server_release.restype = c_int32
+    lib.lra_server_clock.argtypes = [vp]
+    lib.lra_server_clock.restype = c_double
+    lib.lra_server_destroy.argtypes = [vp]
+    lib.lra_server_destroy.restype = None
     lib.lra_svd.argtypes = [vp, POINTER(SvdResult)]
     lib.lra_svd.restype = c_int32
     _lib = lib
@@ -127,12 +166,13 @@ class _DeviceView:
 
 
 def _device_matrix(A, torch):
-    if not (A.is_cuda and A.dtype == torch.float64 and A.dim() == 2):
-        raise TypeError("A must be a 2-D float64 CUDA tensor")
+    if not (A.is_cuda and A.dtype in (torch.float64, torch.float32) and A.dim() == 2):
+        raise TypeError("A must be a 2-D float64 or float32 CUDA tensor")
     m, n = A.shape
     if A.stride(0) != 1 or (n > 1 and A.stride(1) < m):
         raise ValueError("A must be column-major (stride(0) == 1, stride(1) >= m)")
-    return Matrix(m, n, max(A.stride(1), m), F64, 0, A.data_ptr())
+    return Matrix(m, n, max(A.stride(1), m), F64 if A.dtype == torch.float64 else F32, 0,
+                  A.data_ptr())
 
 
 def column_major(t):
@@ -181,6 +221,10 @@ class Farpca:
         if s < 0:
             raise LraError(s, self._lib.lra_last_error(self._ctx).decode())
         return s
+
+    def device_bytes(self):
+        """lra_device_bytes: device memory this context has allocated."""
+        return int(self._lib.lra_device_bytes(self._ctx))
 
     @property
     def capacity(self):
@@ -274,21 +318,115 @@ class Farpca:
         return counts, rows, vals
 
     def run_host(self, A_host, Q_host=None, B_host=None):
-        """lra_farpca_host: A, Q, B in host memory (numpy, column-major; ideally
-        pinned).  Returns the result dict (without device views)."""
+        """lra_farpca_host (float64 A) or lra_farpca_host_f32 (float32 A): A, Q, B in
+        host memory (numpy, column-major; ideally pinned).  Returns the result
+        dict (without device views)."""
         import numpy as np
-        if A_host.dtype != np.float64 or not A_host.flags.f_contiguous:
-            raise ValueError("A_host must be a Fortran-ordered float64 array")
+        if A_host.dtype not in (np.float64, np.float32) or not A_host.flags.f_contiguous:
+            raise ValueError("A_host must be a Fortran-ordered float64 or float32 array")
         r = Result()
         qp = c_void_p(Q_host.ctypes.data) if Q_host is not None else c_void_p(0)
         bp = c_void_p(B_host.ctypes.data) if B_host is not None else c_void_p(0)
         ldq = Q_host.shape[0] if Q_host is not None else 0
         ldb = B_host.shape[0] if B_host is not None else 0
-        s = self._lib.lra_farpca_host(self._ctx, c_void_p(A_host.ctypes.data), A_host.shape[0], qp, ldq,
-                                      bp, ldb, byref(r))
+        fn = self._lib.lra_farpca_host if A_host.dtype == np.float64 else self._lib.lra_farpca_host_f32
+        s = fn(self._ctx, c_void_p(A_host.ctypes.data), A_host.shape[0], qp, ldq, bp, ldb, byref(r))
         self._check(s)
         return dict(status=r.status, rank=r.rank, blocks=r.blocks, E=r.E, normA2=r.normA2,
                     rel_err=r.rel_err)
+
+
+def params(eps=0.0, k=0, b=20, P=1, kind=SPARSE_SIGN, zeta=8, p=0.0, seed=0, max_blocks=0, flags=0):
+    """An lra_params structure (the problem statement's arguments)."""
+    return Params(eps, k, b, P, kind, zeta, p, seed & 0xFFFFFFFFFFFFFFFF, max_blocks, flags)
+
+
+def workspace_bytes(m, n, prm):
+    """lra_workspace_bytes: device bytes a context for these arguments allocates."""
+    v = int(load().lra_workspace_bytes(m, n, byref(prm)))
+    if v < 0:
+        raise LraError(v, "invalid arguments")
+    return v
+
+
+class KeptRun:
+    """A completed request whose context the server kept (lra_request.keep):
+    result() and svd() as for Farpca; release() returns its memory to the server."""
+
+    def __init__(self, server, ctx, m, n):
+        import torch
+        self._server, self._ctx, self.m, self.n = server, c_void_p(ctx), m, n
+        self._lib, self._torch = server._lib, torch
+
+    def _check(self, s):
+        if s < 0:
+            raise LraError(s, self._lib.lra_last_error(self._ctx).decode())
+        return s
+
+    result = lambda self: Farpca.result(self)   # noqa: E731
+    svd = lambda self: Farpca.svd(self)         # noqa: E731
+
+    def release(self):
+        if self._ctx:
+            self._server._check(self._server._lib.lra_server_release(self._server._srv, self._ctx))
+            self._ctx = None
+
+
+class Server:
+    """lra_server: admission by device-memory budget, `slots` requests at once."""
+
+    def __init__(self, hbm_budget=0, slots=8, flags=0):
+        self._lib = load()
+        self._srv = c_void_p()
+        self._check(self._lib.lra_server_create(byref(self._srv), byref(ServerParams(hbm_budget, slots, flags))))
+        self._shapes = {}
+        self._keep = {}
+
+    def _check(self, s):
+        if s < 0:
+            raise LraError(s, "server call failed")
+        return s
+
+    def submit(self, A, prm, rid, keep=False):
+        """Queue a request on a column-major float64/float32 CUDA tensor A (kept
+        alive by the caller until its completion is polled)."""
+        import torch
+        req = Request(rid, _device_matrix(A, torch), prm, 1 if keep else 0, 0)
+        self._check(self._lib.lra_server_submit(self._srv, byref(req)))
+        self._shapes[rid] = tuple(A.shape)
+
+    def poll(self, max_items=256, wait=False):
+        """Completions since the last poll: dicts with id, status, rank, rel_err,
+        t_submit, t_start, t_done, bytes and, for kept requests, `run` (KeptRun)."""
+        buf = (Completion * max_items)()
+        k = int(self._lib.lra_server_poll(self._srv, buf, max_items, 1 if wait else 0))
+        self._check(k)
+        out = []
+        for c in buf[:k]:
+            d = dict(id=c.id, status=c.status, rank=c.rank, rel_err=c.rel_err, t_submit=c.t_submit,
+                     t_start=c.t_start, t_done=c.t_done, bytes=c.bytes)
+            m, n = self._shapes.pop(c.id, (0, 0))
+            if c.ctx:
+                d["run"] = KeptRun(self, c.ctx, m, n)
+            out.append(d)
+        return out
+
+    def pending(self):
+        return int(self._lib.lra_server_pending(self._srv))
+
+    def clock(self):
+        return float(self._lib.lra_server_clock(self._srv))
+
+    def close(self):
+        if self._srv:
+            self._lib.lra_server_destroy(self._srv)
+            self._srv = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sketch_noalloc(A, j0, nblk, b, kind, zeta=8, p=0.0, seed=0, Y=None, stream=None):

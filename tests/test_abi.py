@@ -22,7 +22,7 @@ def lib():
 def declared_functions():
     text = open(os.path.join(ROOT, "include", "lra.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(lra_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(lra_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_declares_the_boundary():
@@ -60,7 +60,7 @@ BAD = [
     dict(P=-1), dict(P=9), dict(kind=6), dict(eps=0.0), dict(eps=float("nan")), dict(k=101),
     dict(k=91, b=30), dict(kind=lra.SPARSE_SIGN, zeta=0), dict(kind=lra.SPARSE_SIGN, zeta=257),
     dict(kind=lra.SPARSE_SIGN, zeta=101, n=100), dict(p=1.0), dict(p=-0.1), dict(max_blocks=-1),
-    dict(max_blocks=11, b=10), dict(flags=64),
+    dict(max_blocks=11, b=10), dict(flags=128),
 ]
 
 

@@ -364,3 +364,97 @@ def test_mixed_precision_form(request, kind, p, zeta, P, size):
         E_direct = float(np.linalg.norm(A - Q @ B) ** 2)
         assert abs(r["E"] - E_direct) <= 1e-10 * r["normA2"]
     f.close()
+
+
+def dev32(A, pad=0):
+    m, n = A.shape
+    buf = torch.empty_strided((m + pad, n), (1, m + pad), dtype=torch.float32, device="cuda")
+    view = buf[:m]
+    view.copy_(torch.from_numpy(np.ascontiguousarray(A.astype(np.float32))))
+    return view
+
+
+def _same_run(f32, f64):
+    """Two contexts' results: identical bits (rank, status, E, Q, B)."""
+    a, b_ = f32.result(), f64.result()
+    assert (a["status"], a["rank"], a["blocks"]) == (b_["status"], b_["rank"], b_["blocks"])
+    assert a["E"] == b_["E"] and a["normA2"] == b_["normA2"]
+    if a["rank"] > 0:
+        assert torch.equal(a["Q"], b_["Q"]) and torch.equal(a["B"], b_["B"])
+    return a
+
+
+# FP32 input: entries are converted exactly where A is read, so the run on FP32
+# data and the run on its FP64 conversion must agree bit for bit (the FP64 run is
+# itself pinned to the oracle above).
+@pytest.mark.parametrize("kind,p,zeta", [KIND_CASES[0], KIND_CASES[1], KIND_CASES[3], KIND_CASES[5]],
+                         ids=["gauss", "sb_half", "ss8", "sg"])
+@pytest.mark.parametrize("P", [0, 1])
+@pytest.mark.parametrize("shape,pad", [((1000, 700), 0), ((1037, 611), 1), ((600, 900), 3)],
+                         ids=["aligned", "ragged", "wide"])
+def test_fp32_input_matches_its_fp64_conversion(kind, p, zeta, P, shape, pad):
+    m, n = shape
+    A = low_rank_matrix(m, n, "poly1.5", 21).astype(np.float32).astype(np.float64)
+    kw = dict(eps=1e-2, b=16, P=P, kind=kind, zeta=zeta, p=p, seed=5)
+    f32, f64 = lra.Farpca(m, n, **kw), lra.Farpca(m, n, **kw)
+    s32, s64 = f32.run(dev32(A, pad)), f64.run(dev(A, pad))
+    assert s32 == s64
+    r = _same_run(f32, f64)
+    assert r["rank"] > 0
+    mixed32, mixed64 = lra.Farpca(m, n, mixed=True, **kw), lra.Farpca(m, n, mixed=True, **kw)
+    mixed32.run(dev32(A, pad))
+    mixed64.run(dev(A, pad))
+    _same_run(mixed32, mixed64)
+    if kind in (lra.SPARSE_SIGN, lra.SPARSE_GAUSSIAN):
+        Y32 = f32.sketch(dev32(A, pad), 0, 3)
+        Y64 = f64.sketch(dev(A, pad), 0, 3)
+        assert torch.equal(Y32, Y64)
+    for f in (f32, f64, mixed32, mixed64):
+        f.close()
+
+
+def test_fp32_host_path_and_unsupported_forms():
+    m, n = 800, 500
+    A = low_rank_matrix(m, n, "poly1.5", 22).astype(np.float32)
+    kw = dict(eps=1e-2, b=10, P=1, kind=lra.SPARSE_SIGN, zeta=8, seed=2)
+    f32, f64 = lra.Farpca(m, n, **kw), lra.Farpca(m, n, **kw)
+    Qh = np.zeros((m, f32.capacity), order="F")
+    r32 = f32.run_host(np.asfortranarray(A), Q_host=Qh)
+    f64.run(dev(A.astype(np.float64)))
+    r64 = f64.result()
+    assert (r32["rank"], r32["E"]) == (r64["rank"], r64["E"])
+    assert np.array_equal(Qh[:, :r32["rank"]], r64["Q"].cpu().numpy())
+    # the allocation-free sketch on FP32 data
+    Y32 = lra.sketch_noalloc(dev32(A.astype(np.float64)), 0, 2, 10, lra.SPARSE_SIGN, zeta=8, seed=2)
+    Y64 = lra.sketch_noalloc(dev(A.astype(np.float64)), 0, 2, 10, lra.SPARSE_SIGN, zeta=8, seed=2)
+    assert torch.equal(Y32, Y64)
+    # forms that read A as FP64 refuse FP32 data
+    simt = lra.Farpca(m, n, fp64_simt=True, **kw)
+    with pytest.raises(lra.LraError) as e:
+        simt.run(dev32(A.astype(np.float64)))
+    assert e.value.status == lra.ERR_UNSUPPORTED
+    with pytest.raises(lra.LraError) as e:
+        f32.apply(dev32(A.astype(np.float64)), torch.zeros((n, 4), dtype=torch.float64, device="cuda").t().contiguous().t())
+    assert e.value.status == lra.ERR_UNSUPPORTED
+    for f in (f32, f64, simt):
+        f.close()
+
+
+def test_fp32_full_size(big):
+    """20000 x 10000 in FP32 (the FP32 form of the same workload): the run on the
+    FP32 data equals the run on its FP64 conversion bit for bit."""
+    A, _ = big
+    A32 = A.astype(np.float32)
+    m, n = A.shape
+    kw = dict(eps=1e-2, b=50, P=1, kind=lra.SPARSE_SIGN, zeta=8, seed=1)
+    f32 = lra.Farpca(m, n, **kw)
+    assert f32.run(dev32(A32.astype(np.float64))) == lra.OK
+    r32 = f32.result()
+    Q32, B32 = r32["Q"].clone(), r32["B"].clone()
+    f32.close()
+    f64 = lra.Farpca(m, n, **kw)
+    assert f64.run(dev(A32.astype(np.float64))) == lra.OK
+    r64 = f64.result()
+    assert (r32["rank"], r32["E"]) == (r64["rank"], r64["E"])
+    assert torch.equal(Q32, r64["Q"]) and torch.equal(B32, r64["B"])
+    f64.close()
