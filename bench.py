@@ -60,7 +60,7 @@ def parse():
                     help="only the timed farPCA steps (for launch-list profiling)")
     ap.add_argument("--engine", choices=("tensor", "fp64_simt"), default="tensor",
                     help="dense passes on the tensor cores (FP64-accurate slicing) or FP64 CUDA cores")
-    ap.add_argument("--only", choices=("sketch", "dense", "serve"), default=None,
+    ap.add_argument("--only", choices=("sketch", "dense", "serve", "batch"), default=None,
                     help="run only the sketch pass (lra_sketch over --sketch-blocks blocks) or only "
                          "the two dense passes A Y and A^T Y (lra_apply), for profiling")
     return ap.parse_args()
@@ -254,9 +254,11 @@ def main():
     f = lra.Farpca(m, n, eps=cfg["eps"], b=cfg["b"], P=cfg["P"], kind=cfg["kind"], zeta=cfg["zeta"],
                    p=cfg["p"], seed=cfg["seed"] + rank, profile=True, stream=stream,
                    fp64_simt=(args.engine == "fp64_simt"))
-    if args.only in ("sketch", "dense", "serve"):
+    if args.only in ("sketch", "dense", "serve", "batch"):
         if args.only == "serve":
             out = {"serving": serving(lra, torch, np)}
+        elif args.only == "batch":
+            out = {"batched": batched(lra, torch, np, peaks, peak_src)}
         elif args.only == "sketch":
             out = {"sketch_pass": sketch_pass(lra, torch, f, Ad, cfg, args.sketch_blocks, peaks, peak_src)}
         else:
@@ -340,6 +342,7 @@ def main():
         line["svd"] = svd_extraction(torch, f, args.steps, stream)
         line["fp32_input"] = fp32_form(lra, torch, Ad, cfg, m, n, args.steps, stream)
         line["serving"] = serving(lra, torch, np)
+        line["batched"] = batched(lra, torch, np, peaks, peak_src)
         line["sketch_pass"] = sketch_pass(lra, torch, f, Ad, cfg, args.sketch_blocks, peaks, peak_src)
         line["e2e"] = e2e(lra, torch, np, f, A, args.steps)
         if rank == 0 and world == 1:
@@ -482,6 +485,43 @@ def serving(lra, torch, np, duration_s=3.0, rate=200.0, slots=8, seed=11):
                                    "p99_ms": 1e3 * float(np.percentile(lat1, 99))},
             "sizes": "log-uniform %dx%d .. %dx%d (10 sizes)" % (sizes[0], sizes[0] // 2, sizes[-1],
                                                              sizes[-1] // 2)}
+
+
+def batched(lra, torch, np, peaks, peak_src, count=4096, reps=3):
+    """The batched form: `count` FP32 problems, rows uniform 64..2048, columns
+    uniform 32..1024 (sigma_i = i^-2, rank <= 64, plus noise 1e-3), eps alternating
+    1e-1 / 1e-2, fixed-zeta sparse sign zeta = 4, b = 16, P = 1, run by one graph
+    launch.  Roofline: the bytes of A each problem's passes must read (one pass for
+    ||A||^2, then per block A^T X, A G, Q_j^T A, and the gathered columns of the
+    sketch), over the batch time, against the HBM copy bandwidth."""
+    from lra_inputs import batch_matrix, batch_shapes
+    shapes = batch_shapes(count, 11)
+    mats = [batch_matrix(m, n, 1000 + k) for k, (m, n) in enumerate(shapes)]
+    eps = [1e-1 if k % 2 else 1e-2 for k in range(count)]
+    seeds = [8000 + k for k in range(count)]
+    bt = lra.Batch(mats, eps, seeds, b=16, P=1, zeta=4)
+    bt.run()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        bt.run()
+        times.append(time.perf_counter() - t0)
+    t = min(times)
+    res = [bt.result(k) for k in range(count)]
+    blocks = [r["rank"] // 16 for r in res]
+    algo = sum(4.0 * m * n * (1 + 3 * nb) + 4.0 * m * 16 * 4 * nb for (m, n), nb in zip(shapes, blocks))
+    gbs = algo / t / 1e9
+    ok = sum(1 for r in res if r["status"] == lra.OK)
+    out = {"problems": count, "ms": 1e3 * t, "problems_per_s": count / t, "steps": bt.steps(),
+           "converged": ok, "mean_rank": float(np.mean([r["rank"] for r in res])),
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": gbs / peaks["hbm_gbs"], "algorithmic_bytes": algo,
+                        "peak_source": peak_src},
+           "device_bytes": bt.device_bytes(), "timing": "wall clock of lra_batch_run (min of %d)" % reps}
+    bt.close()
+    del mats
+    return out
 
 
 def fp32_form(lra, torch, Ad, cfg, m, n, steps, stream):

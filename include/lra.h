@@ -390,6 +390,57 @@ double lra_server_clock(const lra_server* srv);
    (including kept contexts not released).  NULL is ignored. */
 void lra_server_destroy(lra_server* srv);
 
+/* ---- Batched form: many independent problems, one graph launch -----------
+   Fixed-precision farPCA (QB form, fixed-zeta sparse sign Omega) on each of
+   `count` FP32 matrices, advanced together one block per step by a CUDA graph
+   that repeats the block step on the device while a problem is active.  FP32
+   data and passes; Gram sums, Cholesky factors, ||A||_F^2 and the indicator in
+   FP64; the basis by shifted Cholesky QR3.  A problem's Omega_j depends only on
+   its seed, so its result does not depend on the rest of the batch. */
+typedef struct lra_batch lra_batch;
+
+typedef struct {
+  int64_t m, n, lda;   /* FP32 matrix, device, column-major, borrowed while the
+                          batch exists; b <= min(m, n), zeta <= n              */
+  const float* A;
+  double eps;          /* relative tolerance, > 0                             */
+  uint64_t seed;       /* Philox key of its Omega                             */
+} lra_batch_item;
+
+typedef struct {
+  int32_t b;           /* block size: 8, 16 or 32                             */
+  int32_t P;           /* power steps: 0 or 1                                 */
+  int32_t zeta;        /* nonzeros per Omega column, 1..16                    */
+  int32_t max_blocks;  /* per-problem block cap; 0 = ceil(min(m, n) / (2b))   */
+} lra_batch_params;
+
+typedef struct {
+  int32_t status;      /* LRA_OK, LRA_NOT_CONVERGED, LRA_BREAKDOWN, or
+                          LRA_ERR_INVALID_ARG for a non-finite A             */
+  int32_t reserved;
+  int64_t rank;
+  double E, normA2, rel_err;
+  const float* Q;      /* device, m x rank, ld = ldq (owned by the batch)     */
+  int64_t ldq;
+  const float* Bt;     /* device, n x rank = B^T, ld = ldbt                   */
+  int64_t ldbt;
+} lra_batch_result_t;
+
+/* Validate the problems, allocate their workspaces (lra_batch_device_bytes)
+   and build the graph.  Errors: LRA_ERR_INVALID_ARG, LRA_ERR_OOM, LRA_ERR_CUDA. */
+lra_status lra_batch_create(lra_batch** out, const lra_batch_item* items, int64_t count,
+                            const lra_batch_params* params, void* cuda_stream);
+/* Run every problem to its stop test (two set-up kernels and one graph launch);
+   synchronises the stream. */
+lra_status lra_batch_run(lra_batch* batch);
+/* State of problem i (in the order given to lra_batch_create) after the run. */
+lra_status lra_batch_result(const lra_batch* batch, int64_t i, lra_batch_result_t* out);
+/* Block steps the last run took (the largest rank / b); -1 for NULL. */
+int64_t lra_batch_steps(const lra_batch* batch);
+/* Device bytes of the batch's workspaces; -1 for NULL. */
+int64_t lra_batch_device_bytes(const lra_batch* batch);
+void lra_batch_destroy(lra_batch* batch);
+
 /* Message for the last error on ctx ("" if none); never NULL. */
 const char* lra_last_error(const lra_ctx* ctx);
 

@@ -103,3 +103,28 @@ def device_low_rank(m, n, rank, seed, dtype=None, spectrum="exp100", device="cud
     A = torch.empty_strided((m, n), (1, m), dtype=dtype, device=device)
     A.copy_((U * sig[None, :]) @ V.T)
     return A
+
+
+def batch_shapes(count, seed):
+    """Shapes of the batched workload: rows uniform in [64, 2048], columns uniform
+    in [32, 1024] (independently, so m < n occurs)."""
+    rng = np.random.default_rng(seed)
+    return [(int(rng.integers(64, 2049)), int(rng.integers(32, 1025))) for _ in range(count)]
+
+
+def batch_matrix(m, n, seed, rank=64, noise=1e-3, device="cuda"):
+    """One problem of the batched workload on the device, float32, column-major:
+    U diag(sigma) V^T with sigma_i = i^-2 (i <= min(rank, m, n)), plus Gaussian
+    noise of Frobenius norm noise * ||sigma||_2."""
+    import torch
+    r = min(rank, m, n)
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    U = torch.linalg.qr(torch.randn((m, r), generator=g, dtype=torch.float64, device=device))[0]
+    V = torch.linalg.qr(torch.randn((n, r), generator=g, dtype=torch.float64, device=device))[0]
+    sig = torch.from_numpy(singular_values("poly2", r)).to(device)
+    A64 = (U * sig[None, :]) @ V.T
+    A64 += torch.randn((m, n), generator=g, dtype=torch.float64, device=device) * (
+        noise * float(torch.linalg.norm(sig)) / (m * n) ** 0.5)
+    A = torch.empty_strided((m, n), (1, m), dtype=torch.float32, device=device)
+    A.copy_(A64)
+    return A

@@ -33,7 +33,8 @@ EXPORTS = ("lra_create", "lra_destroy", "lra_capacity", "lra_sketch", "lra_farpc
            "lra_kernel_launches", "lra_version", "lra_phase_times", "lra_apply", "lra_svd", "lra_farpca_host_f32",
            "lra_workspace_bytes", "lra_device_bytes", "lra_server_create", "lra_server_submit",
            "lra_server_poll", "lra_server_pending", "lra_server_release", "lra_server_clock",
-           "lra_server_destroy")
+           "lra_server_destroy", "lra_batch_create", "lra_batch_run", "lra_batch_result",
+           "lra_batch_steps", "lra_batch_device_bytes", "lra_batch_destroy")
 
 
 class Matrix(Structure):
@@ -72,6 +73,21 @@ class Completion(Structure):
     _fields_ = [("id", c_uint64), ("status", c_int32), ("reserved", c_int32), ("rank", c_int64),
                 ("rel_err", c_double), ("t_submit", c_double), ("t_start", c_double),
                 ("t_done", c_double), ("bytes", c_int64), ("ctx", c_void_p)]
+
+
+class BatchItem(Structure):
+    _fields_ = [("m", c_int64), ("n", c_int64), ("lda", c_int64), ("A", c_void_p), ("eps", c_double),
+                ("seed", c_uint64)]
+
+
+class BatchParams(Structure):
+    _fields_ = [("b", c_int32), ("P", c_int32), ("zeta", c_int32), ("max_blocks", c_int32)]
+
+
+class BatchResult(Structure):
+    _fields_ = [("status", c_int32), ("reserved", c_int32), ("rank", c_int64), ("E", c_double),
+                ("normA2", c_double), ("rel_err", c_double), ("Q", c_void_p), ("ldq", c_int64),
+                ("Bt", c_void_p), ("ldbt", c_int64)]
 
 
 class LraError(RuntimeError):
@@ -141,6 +157,18 @@ def load(path=LIB_PATH):
     lib.lra_server_clock.restype = c_double
     lib.lra_server_destroy.argtypes = [vp]
     lib.lra_server_destroy.restype = None
+    lib.lra_batch_create.argtypes = [POINTER(vp), POINTER(BatchItem), c_int64, POINTER(BatchParams), vp]
+    lib.lra_batch_create.restype = c_int32
+    lib.lra_batch_run.argtypes = [vp]
+    lib.lra_batch_run.restype = c_int32
+    lib.lra_batch_result.argtypes = [vp, c_int64, POINTER(BatchResult)]
+    lib.lra_batch_result.restype = c_int32
+    lib.lra_batch_steps.argtypes = [vp]
+    lib.lra_batch_steps.restype = c_int64
+    lib.lra_batch_device_bytes.argtypes = [vp]
+    lib.lra_batch_device_bytes.restype = c_int64
+    lib.lra_batch_destroy.argtypes = [vp]
+    lib.lra_batch_destroy.restype = None
     lib.lra_svd.argtypes = [vp, POINTER(SvdResult)]
     lib.lra_svd.restype = c_int32
     _lib = lib
@@ -158,11 +186,11 @@ def kernel_launches():
 class _DeviceView:
     """A __cuda_array_interface__ over library-owned device memory (no copy)."""
 
-    def __init__(self, ptr, shape, strides_elems, owner):
+    def __init__(self, ptr, shape, strides_elems, owner, itemsize=8):
         self._owner = owner
         self.__cuda_array_interface__ = {
-            "shape": tuple(shape), "typestr": "<f8", "data": (int(ptr), False),
-            "strides": tuple(8 * s for s in strides_elems), "version": 3, "stream": None}
+            "shape": tuple(shape), "typestr": "<f%d" % itemsize, "data": (int(ptr), False),
+            "strides": tuple(itemsize * s for s in strides_elems), "version": 3, "stream": None}
 
 
 def _device_matrix(A, torch):
@@ -421,6 +449,68 @@ class Server:
         if self._srv:
             self._lib.lra_server_destroy(self._srv)
             self._srv = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """lra_batch: many independent FP32 problems (fixed-zeta sparse sign Omega),
+    run together by one graph launch.  `mats`: column-major float32 CUDA tensors
+    (kept alive by the caller); `eps`, `seeds`: one per matrix."""
+
+    def __init__(self, mats, eps, seeds, b=16, P=1, zeta=4, max_blocks=0, stream=None):
+        import torch
+        self._lib, self._torch = load(), torch
+        items = (BatchItem * len(mats))()
+        self.shapes = []
+        for k, A in enumerate(mats):
+            if not (A.is_cuda and A.dtype == torch.float32 and A.dim() == 2 and A.stride(0) == 1):
+                raise TypeError("batch matrices must be column-major float32 CUDA tensors")
+            m, n = A.shape
+            items[k] = BatchItem(m, n, max(A.stride(1), m), A.data_ptr(), float(eps[k]),
+                                 int(seeds[k]) & 0xFFFFFFFFFFFFFFFF)
+            self.shapes.append((m, n))
+        self._b = c_void_p()
+        st = c_void_p(stream.cuda_stream) if stream is not None else c_void_p(0)
+        s = self._lib.lra_batch_create(byref(self._b), items, len(mats), byref(BatchParams(b, P, zeta, max_blocks)),
+                                       st)
+        if s < 0:
+            raise LraError(s, "lra_batch_create")
+
+    def run(self):
+        s = self._lib.lra_batch_run(self._b)
+        if s < 0:
+            raise LraError(s, "lra_batch_run")
+
+    def steps(self):
+        return int(self._lib.lra_batch_steps(self._b))
+
+    def device_bytes(self):
+        return int(self._lib.lra_batch_device_bytes(self._b))
+
+    def result(self, i):
+        """Problem i: status, rank, E, normA2, rel_err and float32 views Q (m x rank)
+        and Bt (n x rank, = B^T)."""
+        r = BatchResult()
+        s = self._lib.lra_batch_result(self._b, i, byref(r))
+        if s < 0:
+            raise LraError(s, "lra_batch_result")
+        m, n = self.shapes[i]
+        out = dict(status=r.status, rank=r.rank, E=r.E, normA2=r.normA2, rel_err=r.rel_err)
+        if r.rank > 0:
+            torch = self._torch
+            out["Q"] = torch.as_tensor(_DeviceView(r.Q, (m, r.rank), (1, r.ldq), self, 4), device="cuda")
+            out["Bt"] = torch.as_tensor(_DeviceView(r.Bt, (n, r.rank), (1, r.ldbt), self, 4), device="cuda")
+        return out
+
+    def close(self):
+        if self._b:
+            self._lib.lra_batch_destroy(self._b)
+            self._b = c_void_p()
 
     def __del__(self):
         try:
