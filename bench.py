@@ -60,7 +60,12 @@ def parse():
                     help="only the timed farPCA steps (for launch-list profiling)")
     ap.add_argument("--engine", choices=("tensor", "fp64_simt"), default="tensor",
                     help="dense passes on the tensor cores (FP64-accurate slicing) or FP64 CUDA cores")
-    ap.add_argument("--only", choices=("sketch", "dense", "serve", "batch"), default=None,
+    ap.add_argument("--batch-count", type=int, default=4096,
+                    help="with --only batch: number of problems (4096 is the benchmark batch)")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="with --only batch: launch the batch's steps from the host (for profiling)")
+    ap.add_argument("--only", choices=("sketch", "dense", "serve", "batch", "fixedrank", "stability"),
+                    default=None,
                     help="run only the sketch pass (lra_sketch over --sketch-blocks blocks) or only "
                          "the two dense passes A Y and A^T Y (lra_apply), for profiling")
     return ap.parse_args()
@@ -254,11 +259,16 @@ def main():
     f = lra.Farpca(m, n, eps=cfg["eps"], b=cfg["b"], P=cfg["P"], kind=cfg["kind"], zeta=cfg["zeta"],
                    p=cfg["p"], seed=cfg["seed"] + rank, profile=True, stream=stream,
                    fp64_simt=(args.engine == "fp64_simt"))
-    if args.only in ("sketch", "dense", "serve", "batch"):
-        if args.only == "serve":
+    if args.only in ("sketch", "dense", "serve", "batch", "fixedrank"):
+        if args.only == "stability":
+            out = {"stability": stability(lra, torch)}
+        elif args.only == "fixedrank":
+            out = {"fixed_rank_sweep": fixed_rank_sweep(lra, torch)}
+        elif args.only == "serve":
             out = {"serving": serving(lra, torch, np)}
         elif args.only == "batch":
-            out = {"batched": batched(lra, torch, np, peaks, peak_src)}
+            out = {"batched": batched(lra, torch, np, peaks, peak_src, count=args.batch_count,
+                                      graph=not args.no_graphs)}
         elif args.only == "sketch":
             out = {"sketch_pass": sketch_pass(lra, torch, f, Ad, cfg, args.sketch_blocks, peaks, peak_src)}
         else:
@@ -343,6 +353,7 @@ def main():
         line["fp32_input"] = fp32_form(lra, torch, Ad, cfg, m, n, args.steps, stream)
         line["serving"] = serving(lra, torch, np)
         line["batched"] = batched(lra, torch, np, peaks, peak_src)
+        line["fixed_rank_sweep"] = fixed_rank_sweep(lra, torch)
         line["sketch_pass"] = sketch_pass(lra, torch, f, Ad, cfg, args.sketch_blocks, peaks, peak_src)
         line["e2e"] = e2e(lra, torch, np, f, A, args.steps)
         if rank == 0 and world == 1:
@@ -487,7 +498,7 @@ def serving(lra, torch, np, duration_s=3.0, rate=200.0, slots=8, seed=11):
                                                              sizes[-1] // 2)}
 
 
-def batched(lra, torch, np, peaks, peak_src, count=4096, reps=3):
+def batched(lra, torch, np, peaks, peak_src, count=4096, reps=3, graph=True):
     """The batched form: `count` FP32 problems, rows uniform 64..2048, columns
     uniform 32..1024 (sigma_i = i^-2, rank <= 64, plus noise 1e-3), eps alternating
     1e-1 / 1e-2, fixed-zeta sparse sign zeta = 4, b = 16, P = 1, run by one graph
@@ -499,7 +510,7 @@ def batched(lra, torch, np, peaks, peak_src, count=4096, reps=3):
     mats = [batch_matrix(m, n, 1000 + k) for k, (m, n) in enumerate(shapes)]
     eps = [1e-1 if k % 2 else 1e-2 for k in range(count)]
     seeds = [8000 + k for k in range(count)]
-    bt = lra.Batch(mats, eps, seeds, b=16, P=1, zeta=4)
+    bt = lra.Batch(mats, eps, seeds, b=16, P=1, zeta=4, graph=graph)
     bt.run()
     torch.cuda.synchronize()
     times = []
@@ -522,6 +533,79 @@ def batched(lra, torch, np, peaks, peak_src, count=4096, reps=3):
     bt.close()
     del mats
     return out
+
+
+def fixed_rank_sweep(lra, torch, reps=3):
+    """Sec. 5.1's fixed-rank comparison on the 5000 x 5000 Matrix 1 (sigma_i = i^-2):
+    k = 10 b with b = 20 (ten blocks), P in {0, 1}, every Omega kind with the
+    paper's p (p1 for the standardized Bernoulli kind, p2 for the others; fixed
+    zeta = 8 for the sparse sign kind); ms per solve and the ratio to the Gaussian
+    kind (Remark 3.4 expects (2P + 1) / (2P + 2) passes over A: 0.5 at P = 0, 0.75
+    at P = 1, for the kinds whose sketch is a gather)."""
+    from lra_inputs import workload_matrix
+    A = workload_matrix("matrix1_5000")
+    m, n = A.shape
+    Ad = lra.column_major(torch.from_numpy(A).cuda())
+    kinds = {"gaussian": (lra.GAUSSIAN, 0.0, 0), "std_bernoulli": (lra.STD_BERNOULLI, 0.0, 0),
+             "sparse_sign_zeta8": (lra.SPARSE_SIGN, 0.0, 8), "sparse_gaussian": (lra.SPARSE_GAUSSIAN, 0.0, 0),
+             "bernoulli": (lra.BERNOULLI, 0.0, 0)}
+    out = {}
+    for P in (0, 1):
+        row = {}
+        for name, (kind, p, zeta) in kinds.items():
+            f = lra.Farpca(m, n, k=200, b=20, P=P, kind=kind, zeta=zeta, p=p, seed=3)
+            f.run(Ad)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                f.run(Ad)
+            torch.cuda.synchronize()
+            row[name] = 1e3 * (time.perf_counter() - t0) / reps
+            f.close()
+        g = row["gaussian"]
+        out["P%d" % P] = {k: {"ms": v, "ratio_to_gaussian": v / g} for k, v in row.items()}
+    del Ad
+    return out
+
+
+def table4():
+    """Table 4 (Sec. 5.5) as printed: algorithm -> p -> (d1, d2, d3) success counts."""
+    out = {}
+    with open(os.path.join(ROOT, "tests", "golden", "table4_n5000.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                alg, p, d1, d2, d3 = line.split()
+                out.setdefault(alg, {})[p] = (int(d1), int(d2), int(d3))
+    return out
+
+
+def stability(lra, torch, sims=100, n=5000):
+    """Sec. 5.5: Matrix 1 with a block-diagonal V_A of d in {1, 500, 5000} blocks;
+    the standardized Bernoulli, i.i.d. sparse sign, sparse Gaussian and Bernoulli
+    kinds at p in {ln(n)/n, 2e-3, 1e-2}; eps = 1e-4, b = 50, P = 1, the cap
+    ceil(n / (2b)) blocks; a simulation succeeds when the run ends with LRA_OK.
+    Success rates in `sims` simulations (seeds) beside the paper's Table 4."""
+    import math
+    from lra_inputs import stability_matrix
+    kinds = {"farPCASB": lra.STD_BERNOULLI, "farPCASS": lra.SPARSE_SIGN_IID,
+             "farPCASG": lra.SPARSE_GAUSSIAN, "farPCAB": lra.BERNOULLI}
+    ps = {"ln(n)/n": math.log(n) / n, "2e-3": 2e-3, "1e-2": 1e-2}
+    paper = table4()
+    out = {}
+    t0 = time.perf_counter()
+    for di, d in enumerate((1, 500, 5000)):
+        A = stability_matrix(n, d, 77 + d)
+        for kname, kind in kinds.items():
+            for pname, p in ps.items():
+                ok = 0
+                for s in range(sims):
+                    f = lra.Farpca(n, n, eps=1e-4, b=50, P=1, kind=kind, p=p, seed=10000 + s)
+                    ok += f.run(A) == lra.OK
+                    f.close()
+                out.setdefault(kname, {}).setdefault(pname, {})["d%d" % (di + 1)] = {
+                    "success": ok, "paper": paper[kname][pname][di]}
+        del A
+    return {"simulations": sims, "n": n, "rates": out, "seconds": time.perf_counter() - t0}
 
 
 def fp32_form(lra, torch, Ad, cfg, m, n, steps, stream):

@@ -412,6 +412,9 @@ typedef struct {
   int32_t P;           /* power steps: 0 or 1                                 */
   int32_t zeta;        /* nonzeros per Omega column, 1..16                    */
   int32_t max_blocks;  /* per-problem block cap; 0 = ceil(min(m, n) / (2b))   */
+  uint32_t flags;      /* LRA_FLAG_NO_GRAPHS: launch each step from the host
+                          (reading after each step whether to go on) instead
+                          of the graph; other bits must be 0                  */
 } lra_batch_params;
 
 typedef struct {

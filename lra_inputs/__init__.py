@@ -118,13 +118,44 @@ def batch_matrix(m, n, seed, rank=64, noise=1e-3, device="cuda"):
     noise of Frobenius norm noise * ||sigma||_2."""
     import torch
     r = min(rank, m, n)
+    rng = np.random.default_rng(int(seed))
+    U = torch.from_numpy(haar_columns(m, r, rng)).to(device)
+    V = torch.from_numpy(haar_columns(n, r, rng)).to(device)
+    sig_np = singular_values("poly2", r)
+    sig = torch.from_numpy(sig_np).to(device)
     g = torch.Generator(device=device).manual_seed(int(seed))
-    U = torch.linalg.qr(torch.randn((m, r), generator=g, dtype=torch.float64, device=device))[0]
-    V = torch.linalg.qr(torch.randn((n, r), generator=g, dtype=torch.float64, device=device))[0]
-    sig = torch.from_numpy(singular_values("poly2", r)).to(device)
     A64 = (U * sig[None, :]) @ V.T
     A64 += torch.randn((m, n), generator=g, dtype=torch.float64, device=device) * (
-        noise * float(torch.linalg.norm(sig)) / (m * n) ** 0.5)
+        noise * float(np.linalg.norm(sig_np)) / (m * n) ** 0.5)
     A = torch.empty_strided((m, n), (1, m), dtype=torch.float32, device=device)
     A.copy_(A64)
+    return A
+
+
+def stability_matrix(n, d, seed, device="cuda"):
+    """Sec. 5.5's test matrix on the device (float64, column-major): Matrix 1's
+    form A = U_A diag(1/i^2) V_A^T with U_A Haar (n x n) and V_A block diagonal,
+    d blocks of (n/d) x (n/d), each the orthonormalised factor of a seeded
+    Gaussian block (d = n: V_A diagonal with entries +-1; d = 1: V_A dense)."""
+    import torch
+    assert n % d == 0
+    g = torch.Generator(device=device).manual_seed(int(seed))
+
+    def haar(k):
+        q, r = torch.linalg.qr(torch.randn((k, k), generator=g, dtype=torch.float64, device=device))
+        s = torch.sign(torch.diagonal(r))
+        s[s == 0] = 1.0
+        return q * s[None, :]
+
+    U = haar(n)
+    h = n // d
+    if h == 1:
+        V = torch.diag(torch.sign(torch.randn(n, generator=g, dtype=torch.float64, device=device)))
+    else:
+        V = torch.zeros((n, n), dtype=torch.float64, device=device)
+        for i in range(d):
+            V[i * h:(i + 1) * h, i * h:(i + 1) * h] = haar(h)
+    sig = torch.from_numpy(singular_values("matrix1", n)).to(device)
+    A = torch.empty_strided((n, n), (1, n), dtype=torch.float64, device=device)
+    A.copy_((U * sig[None, :]) @ V.T)
     return A

@@ -50,7 +50,8 @@ struct BProb {
   float *Q, *Bt, *X, *W, *F, *Rinv, *omv;
   int* omr;
   double *rdiag, *cnorm;
-  int c32_first, c32_count;  // this problem's tiles in the column-tile list
+  int c32_first, c32_count;    // this problem's tiles in the 32-column list (||A||^2)
+  int c128_first, c128_count;  // ... in the 128-column list (products X^T Y)
   // state
   double normA2, E;
   int status, rank, active, broke;
@@ -167,17 +168,20 @@ __global__ void __launch_bounds__(128) k_b_sketch(const BProb* __restrict__ pr,
 
 enum TnMode { TN_ATX = 0, TN_QTY = 1, TN_QTA = 2 };
 
-// C = X^T Y over a tile of 32 columns of X (256 threads, warp w: columns
-// 4w..4w+3, lanes over rows):
+// C = X^T Y over a tile of 128 columns of X, 64 threads, each thread two
+// columns (c and c + 64): the thread streams its columns down the rows (16-byte
+// loads where a column is aligned) while the 64-row chunk of Y (b columns) sits
+// in shared memory, read by all threads at the same address, each value used for
+// both columns; each thread keeps its 2 b sums in registers.
 //   TN_ATX: W = A^T X (n x b);  TN_QTY: F = Q^T X (l x b);
 //   TN_QTA: B_j^T = A^T Q_j into Bt's columns l.., and sum of squares -> part.
 template <int B, int MODE>
-__global__ void __launch_bounds__(256) k_b_tn(const BProb* __restrict__ pr,
-                                              const int2* __restrict__ tiles,
-                                              const int* __restrict__ jp,
-                                              double* __restrict__ part) {
-  __shared__ float cs[32][B + 1];
-  __shared__ double red[8];
+__global__ void __launch_bounds__(64) k_b_tn(const BProb* __restrict__ pr,
+                                             const int2* __restrict__ tiles,
+                                             const int* __restrict__ jp,
+                                             double* __restrict__ part) {
+  __shared__ __align__(16) float ys[64][B];
+  __shared__ double red[2];
   const int2 t = tiles[blockIdx.x];
   const BProb& p = pr[t.x];
   const int l = *jp * B;
@@ -190,62 +194,104 @@ __global__ void __launch_bounds__(256) k_b_tn(const BProb* __restrict__ pr,
   const float* X = MODE == TN_QTY ? p.Q : p.A;
   const int64_t ldx = MODE == TN_QTY ? (int64_t)p.m : p.lda;
   const float* Y = MODE == TN_QTA ? p.Q + (int64_t)l * p.m : p.X;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cw = t.y + warp * 4;
-  float acc[4][B];
+  int c[2];
+  bool mine[2];
+  const float* col[2];
+  bool vec = true;
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int k = 0; k < B; ++k) acc[q][k] = 0.f;
-  for (int r = lane; r < p.m; r += 32) {
-    float y[B];
-#pragma unroll
-    for (int k = 0; k < B; ++k) y[k] = Y[r + (int64_t)k * p.m];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float a = (cw + q < cols) ? X[r + (int64_t)(cw + q) * ldx] : 0.f;
-#pragma unroll
-      for (int k = 0; k < B; ++k) acc[q][k] = fmaf(a, y[k], acc[q][k]);
-    }
+  for (int h = 0; h < 2; ++h) {
+    c[h] = t.y + threadIdx.x + 64 * h;
+    mine[h] = c[h] < cols;
+    col[h] = X + (int64_t)(mine[h] ? c[h] : t.y) * ldx;
+    vec = vec && ((reinterpret_cast<uintptr_t>(col[h]) & 15) == 0);
   }
+  float acc[2][B];
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int k = 0; k < B; ++k) acc[h][k] = 0.f;
+  for (int r0 = 0; r0 < p.m; r0 += 64) {
+    const int rn = min(64, p.m - r0);
+    for (int e = threadIdx.x; e < 64 * B; e += 64) {
+      const int rr = e % 64, k = e / 64;
+      ys[rr][k] = rr < rn ? Y[(r0 + rr) + (int64_t)k * p.m] : 0.f;
+    }
+    __syncthreads();
+    if (vec && rn == 64) {
+#pragma unroll
+      for (int q0 = 0; q0 < 16; q0 += 4) {
+        float4 a4[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            a4[h][q] = __ldg(reinterpret_cast<const float4*>(col[h] + r0 + 4 * (q0 + q)));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int rr = 4 * (q0 + q) + e;
+            const float a0 = e == 0 ? a4[0][q].x : e == 1 ? a4[0][q].y : e == 2 ? a4[0][q].z : a4[0][q].w;
+            const float a1 = e == 0 ? a4[1][q].x : e == 1 ? a4[1][q].y : e == 2 ? a4[1][q].z : a4[1][q].w;
+#pragma unroll
+            for (int k = 0; k < B; k += 4) {
+              const float4 y = *reinterpret_cast<const float4*>(&ys[rr][k]);
+              acc[0][k] = fmaf(a0, y.x, acc[0][k]);
+              acc[0][k + 1] = fmaf(a0, y.y, acc[0][k + 1]);
+              acc[0][k + 2] = fmaf(a0, y.z, acc[0][k + 2]);
+              acc[0][k + 3] = fmaf(a0, y.w, acc[0][k + 3]);
+              acc[1][k] = fmaf(a1, y.x, acc[1][k]);
+              acc[1][k + 1] = fmaf(a1, y.y, acc[1][k + 1]);
+              acc[1][k + 2] = fmaf(a1, y.z, acc[1][k + 2]);
+              acc[1][k + 3] = fmaf(a1, y.w, acc[1][k + 3]);
+            }
+          }
+        }
+      }
+    } else {
+      for (int rr = 0; rr < rn; ++rr) {
+        const float a0 = col[0][r0 + rr], a1 = col[1][r0 + rr];
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          acc[0][k] = fmaf(a0, ys[rr][k], acc[0][k]);
+          acc[1][k] = fmaf(a1, ys[rr][k], acc[1][k]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  double sq = 0.0;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (!mine[h]) continue;
 #pragma unroll
     for (int k = 0; k < B; ++k) {
-      float v = acc[q][k];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) cs[warp * 4 + q][k] = v;
-    }
-  __syncthreads();
-  const int cc = threadIdx.x & 31, kk = threadIdx.x >> 5;
-  const int c = t.y + cc;
-  double sq = 0.0;
-  if (c < cols) {
-    for (int k = kk; k < B; k += 8) {
-      const float v = cs[cc][k];
-      if (MODE == TN_ATX) p.W[c + (int64_t)k * p.n] = v;
-      if (MODE == TN_QTY) p.F[c + (int64_t)k * p.lmax] = v;
+      const float v = acc[h][k];
+      if (MODE == TN_ATX) p.W[c[h] + (int64_t)k * p.n] = v;
+      if (MODE == TN_QTY) p.F[c[h] + (int64_t)k * p.lmax] = v;
       if (MODE == TN_QTA) {
-        p.Bt[c + (int64_t)(l + k) * p.n] = v;
+        p.Bt[c[h] + (int64_t)(l + k) * p.n] = v;
         sq += (double)v * (double)v;
       }
     }
   }
   if (MODE == TN_QTA) {
-    const double s = block_sum(sq, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    const double s2 = block_sum(sq, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s2;
   }
 }
 
 enum NnMode { NN_AX = 0, NN_YQF = 1 };
 
-// Row tile (problem, 128 rows), a thread per row:
+// Row tile (problem, 128 rows), 64 threads, each thread rows i and i + 64:
 //   NN_AX: X = A W (m x b, W = G after orthonormalisation);  NN_YQF: X -= Q F.
+// The 64-column chunk of the right operand sits in shared memory, each value
+// used for both rows.
 template <int B, int MODE>
-__global__ void __launch_bounds__(128) k_b_nn(const BProb* __restrict__ pr,
-                                              const int2* __restrict__ tiles,
-                                              const int* __restrict__ jp) {
-  __shared__ float ys[64][B];
+__global__ void __launch_bounds__(64) k_b_nn(const BProb* __restrict__ pr,
+                                             const int2* __restrict__ tiles,
+                                             const int* __restrict__ jp) {
+  __shared__ __align__(16) float ys[64][B];
   const int2 t = tiles[blockIdx.x];
   const BProb& p = pr[t.x];
   if (!p.active || p.broke) return;
@@ -256,34 +302,68 @@ __global__ void __launch_bounds__(128) k_b_nn(const BProb* __restrict__ pr,
   const int64_t ldx = MODE == NN_AX ? p.lda : (int64_t)p.m;
   const float* Y = MODE == NN_AX ? p.W : p.F;
   const int64_t ldy = MODE == NN_AX ? (int64_t)p.n : (int64_t)p.lmax;
-  const int i = t.y + threadIdx.x;
-  float acc[B];
+  const int i0 = t.y + threadIdx.x, i1 = i0 + 64;
+  const bool in0 = i0 < p.m, in1 = i1 < p.m;
+  const float* x0 = X + (in0 ? i0 : 0);
+  const float* x1 = X + (in1 ? i1 : 0);
+  float acc[2][B];
 #pragma unroll
-  for (int k = 0; k < B; ++k) acc[k] = 0.f;
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int k = 0; k < B; ++k) acc[h][k] = 0.f;
   for (int k0 = 0; k0 < K; k0 += 64) {
     const int kn = min(64, K - k0);
-    for (int e = threadIdx.x; e < 64 * B; e += 128) {
+    for (int e = threadIdx.x; e < 64 * B; e += 64) {
       const int kk = e % 64, k = e / 64;
       ys[kk][k] = kk < kn ? Y[(k0 + kk) + (int64_t)k * ldy] : 0.f;
     }
     __syncthreads();
-    if (i < p.m) {
-      for (int kk = 0; kk < kn; ++kk) {
-        const float a = X[i + (int64_t)(k0 + kk) * ldx];
+    int kk = 0;
+    // eight columns' loads for both rows in flight, then their FMAs
+    for (; kk + 8 <= kn; kk += 8) {
+      float a[2][8];
 #pragma unroll
-        for (int k = 0; k < B; ++k) acc[k] = fmaf(a, ys[kk][k], acc[k]);
+      for (int u = 0; u < 8; ++u) {
+        a[0][u] = __ldg(x0 + (int64_t)(k0 + kk + u) * ldx);
+        a[1][u] = __ldg(x1 + (int64_t)(k0 + kk + u) * ldx);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int k = 0; k < B; k += 4) {
+          const float4 y = *reinterpret_cast<const float4*>(&ys[kk + u][k]);
+          acc[0][k] = fmaf(a[0][u], y.x, acc[0][k]);
+          acc[0][k + 1] = fmaf(a[0][u], y.y, acc[0][k + 1]);
+          acc[0][k + 2] = fmaf(a[0][u], y.z, acc[0][k + 2]);
+          acc[0][k + 3] = fmaf(a[0][u], y.w, acc[0][k + 3]);
+          acc[1][k] = fmaf(a[1][u], y.x, acc[1][k]);
+          acc[1][k + 1] = fmaf(a[1][u], y.y, acc[1][k + 1]);
+          acc[1][k + 2] = fmaf(a[1][u], y.z, acc[1][k + 2]);
+          acc[1][k + 3] = fmaf(a[1][u], y.w, acc[1][k + 3]);
+        }
+    }
+    for (; kk < kn; ++kk) {
+      const float a0 = x0[(int64_t)(k0 + kk) * ldx], a1 = x1[(int64_t)(k0 + kk) * ldx];
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        acc[0][k] = fmaf(a0, ys[kk][k], acc[0][k]);
+        acc[1][k] = fmaf(a1, ys[kk][k], acc[1][k]);
       }
     }
     __syncthreads();
   }
-  if (i >= p.m) return;
 #pragma unroll
-  for (int k = 0; k < B; ++k) {
-    float* o = p.X + i + (int64_t)k * p.m;
-    if (MODE == NN_AX)
-      *o = acc[k];
-    else
-      *o -= acc[k];
+  for (int h = 0; h < 2; ++h) {
+    const int i = h ? i1 : i0;
+    if (!(h ? in1 : in0)) continue;
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      float* o = p.X + i + (int64_t)k * p.m;
+      if (MODE == NN_AX)
+        *o = acc[h][k];
+      else
+        *o -= acc[h][k];
+    }
   }
 }
 
@@ -432,7 +512,7 @@ __global__ void k_b_indicator(BProb* __restrict__ pr, int np, const int* __restr
     return;
   }
   double s = 0.0;
-  for (int q = 0; q < p.c32_count; ++q) s += part[p.c32_first + q];
+  for (int q = 0; q < p.c128_count; ++q) s += part[p.c128_first + q];
   p.E -= s;
   p.rank = (j + 1) * B;
   if (p.E < p.eps2 * p.normA2) {
@@ -446,14 +526,19 @@ __global__ void k_b_indicator(BProb* __restrict__ pr, int np, const int* __restr
   }
 }
 
-// End of a step: j += 1, and the while node repeats while a problem is active.
+// End of a step: j += 1, and the while node repeats while a problem is active
+// (graph mode); without the graph, *more tells the host.
+template <bool GRAPH>
 __global__ void k_b_next(int* __restrict__ jp, int* __restrict__ count, int max_steps,
-                         cudaGraphConditionalHandle h) {
+                         cudaGraphConditionalHandle h, int* __restrict__ more_out) {
   const int j = *jp + 1;
   *jp = j;
   const int more = (*count > 0) && (j < max_steps);
   *count = 0;
-  cudaGraphSetConditional(h, more ? 1u : 0u);
+  if (GRAPH)
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+  else
+    *more_out = more;
 }
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -468,10 +553,11 @@ struct lra_batch {
   lra::BProb* d_pr = nullptr;
   std::vector<lra::BProb> h_pr;  // after lra_batch_run: the final state
   std::vector<int> order;        // caller index -> internal index
-  int2 *d_c32 = nullptr, *d_rm = nullptr, *d_rn = nullptr, *d_q32 = nullptr;
-  int n_c32 = 0, n_rm = 0, n_rn = 0, n_q32 = 0;
+  int2 *d_c32 = nullptr, *d_c128 = nullptr, *d_rm = nullptr, *d_rn = nullptr, *d_q128 = nullptr;
+  int n_c32 = 0, n_c128 = 0, n_rm = 0, n_rn = 0, n_q128 = 0;
   double* d_part = nullptr;
-  int *d_j = nullptr, *d_count = nullptr;
+  int *d_j = nullptr, *d_count = nullptr, *d_more = nullptr;
+  bool graph_mode = true;
   char* d_pool = nullptr;
   int64_t pool_bytes = 0;
   cudaGraph_t graph = nullptr;
@@ -483,12 +569,11 @@ struct lra_batch {
 namespace lra {
 namespace {
 
+// The kernels of one block step, on bt->st (captured into the graph's body, or
+// launched directly when the batch runs without the graph).
 template <int B>
-cudaError_t capture_step(lra_batch* bt, cudaGraph_t body, cudaGraphConditionalHandle h) {
+cudaError_t issue_step(lra_batch* bt, bool graph, cudaGraphConditionalHandle h) {
   cudaStream_t st = bt->st;
-  cudaError_t e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0,
-                                                cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return e;
   const int np = bt->np;
   uint64_t n = 0;
   cudaError_t first = cudaSuccess;
@@ -505,9 +590,9 @@ cudaError_t capture_step(lra_batch* bt, cudaGraph_t body, cudaGraphConditionalHa
   // X <- (I - Q Q^T) X, twice; then X <- orth(X) (into Q's columns l.. when to_q)
   auto project = [&]() {
     for (int pass = 0; pass < 2; ++pass) {
-      k_b_tn<B, TN_QTY><<<bt->n_q32, 256, 0, st>>>(pr, bt->d_q32, jp, bt->d_part);
+      k_b_tn<B, TN_QTY><<<bt->n_q128, 64, 0, st>>>(pr, bt->d_q128, jp, bt->d_part);
       L(cudaGetLastError());
-      k_b_nn<B, NN_YQF><<<bt->n_rm, 128, 0, st>>>(pr, bt->d_rm, jp);
+      k_b_nn<B, NN_YQF><<<bt->n_rm, 64, 0, st>>>(pr, bt->d_rm, jp);
       L(cudaGetLastError());
     }
   };
@@ -526,7 +611,7 @@ cudaError_t capture_step(lra_batch* bt, cudaGraph_t body, cudaGraphConditionalHa
     // W' = A^T orth((I - Q Q^T) A Omega_j); G = orth(W'); Y_j = A G
     project();
     orth_x(false);
-    k_b_tn<B, TN_ATX><<<bt->n_c32, 256, 0, st>>>(pr, bt->d_c32, jp, bt->d_part);
+    k_b_tn<B, TN_ATX><<<bt->n_c128, 64, 0, st>>>(pr, bt->d_c128, jp, bt->d_part);
     L(cudaGetLastError());
     for (int ps = 0; ps < 3; ++ps) {
       k_b_gram_chol<B, true><<<np, 256, 0, st>>>(pr, ps);
@@ -534,21 +619,40 @@ cudaError_t capture_step(lra_batch* bt, cudaGraph_t body, cudaGraphConditionalHa
       k_b_rinv<B, true, false><<<bt->n_rn, 128, 0, st>>>(pr, bt->d_rn, jp);
       L(cudaGetLastError());
     }
-    k_b_nn<B, NN_AX><<<bt->n_rm, 128, 0, st>>>(pr, bt->d_rm, jp);
+    k_b_nn<B, NN_AX><<<bt->n_rm, 64, 0, st>>>(pr, bt->d_rm, jp);
     L(cudaGetLastError());
   }
   project();  // Y' = (I - Q Q^T) Y_j, twice
   orth_x(true);
-  k_b_tn<B, TN_QTA><<<bt->n_c32, 256, 0, st>>>(pr, bt->d_c32, jp, bt->d_part);
+  k_b_tn<B, TN_QTA><<<bt->n_c128, 64, 0, st>>>(pr, bt->d_c128, jp, bt->d_part);
   L(cudaGetLastError());
   k_b_indicator<B><<<(np + 127) / 128, 128, 0, st>>>(pr, np, jp, bt->d_part, bt->d_count);
   L(cudaGetLastError());
-  k_b_next<<<1, 1, 0, st>>>(bt->d_j, bt->d_count, bt->max_steps, h);
+  if (graph)
+    k_b_next<true><<<1, 1, 0, st>>>(bt->d_j, bt->d_count, bt->max_steps, h, nullptr);
+  else
+    k_b_next<false><<<1, 1, 0, st>>>(bt->d_j, bt->d_count, bt->max_steps, h, bt->d_more);
   L(cudaGetLastError());
-  cudaGraph_t g = nullptr;
-  const cudaError_t ec = cudaStreamEndCapture(st, &g);
   bt->launches_per_step = n;
-  return first != cudaSuccess ? first : ec;
+  return first;
+}
+
+template <int B>
+cudaError_t capture_step(lra_batch* bt, cudaGraph_t body, cudaGraphConditionalHandle h) {
+  cudaError_t e = cudaStreamBeginCaptureToGraph(bt->st, body, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  const cudaError_t ei = issue_step<B>(bt, true, h);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(bt->st, &g);
+  return ei != cudaSuccess ? ei : ec;
+}
+
+cudaError_t issue_step_any(lra_batch* bt) {
+  cudaGraphConditionalHandle h{};
+  if (bt->b == 8) return issue_step<8>(bt, false, h);
+  if (bt->b == 16) return issue_step<16>(bt, false, h);
+  return issue_step<32>(bt, false, h);
 }
 
 cudaError_t build_graph(lra_batch* bt) {
@@ -579,8 +683,8 @@ cudaError_t build_graph(lra_batch* bt) {
 void batch_free(lra_batch* bt) {
   if (bt->exec) cudaGraphExecDestroy(bt->exec);
   if (bt->graph) cudaGraphDestroy(bt->graph);
-  void* ptrs[] = {bt->d_pr, bt->d_c32, bt->d_rm, bt->d_rn, bt->d_q32, bt->d_part,
-                  bt->d_j,  bt->d_count, bt->d_pool};
+  void* ptrs[] = {bt->d_pr, bt->d_c32, bt->d_c128, bt->d_rm, bt->d_rn, bt->d_q128, bt->d_part,
+                  bt->d_j,  bt->d_count, bt->d_more, bt->d_pool};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (bt->own_stream && bt->st) cudaStreamDestroy(bt->st);
@@ -599,7 +703,7 @@ lra_status lra_batch_create(lra_batch** out, const lra_batch_item* items, int64_
   *out = nullptr;
   const int B = prm->b;
   if ((B != 8 && B != 16 && B != 32) || prm->P < 0 || prm->P > 1 || prm->zeta < 1 ||
-      prm->zeta > ZMAX || prm->max_blocks < 0)
+      prm->zeta > ZMAX || prm->max_blocks < 0 || (prm->flags & ~LRA_FLAG_NO_GRAPHS))
     return LRA_ERR_INVALID_ARG;
   for (int64_t i = 0; i < count; ++i) {
     const lra_batch_item& it = items[i];
@@ -628,7 +732,7 @@ lra_status lra_batch_create(lra_batch** out, const lra_batch_item* items, int64_
   bt->order.assign(count, 0);
   for (int k = 0; k < (int)count; ++k) bt->order[ord[k]] = k;
   std::vector<BProb> h(count);
-  std::vector<int2> c32, rm, rn, q32;
+  std::vector<int2> c32, c128, rm, rn, q128;
   int64_t off = 0;
   std::vector<int64_t> offs(count * 12);
   for (int k = 0; k < (int)count; ++k) {
@@ -661,25 +765,31 @@ lra_status lra_batch_create(lra_batch** out, const lra_batch_item* items, int64_
     p.c32_first = (int)c32.size();
     for (int c0 = 0; c0 < p.n; c0 += 32) c32.push_back(make_int2(k, c0));
     p.c32_count = (int)c32.size() - p.c32_first;
+    p.c128_first = (int)c128.size();
+    for (int c0 = 0; c0 < p.n; c0 += 128) c128.push_back(make_int2(k, c0));
+    p.c128_count = (int)c128.size() - p.c128_first;
     for (int r0 = 0; r0 < p.m; r0 += 128) rm.push_back(make_int2(k, r0));
     for (int r0 = 0; r0 < p.n; r0 += 128) rn.push_back(make_int2(k, r0));
-    for (int c0 = 0; c0 < p.lmax; c0 += 32) q32.push_back(make_int2(k, c0));
+    for (int c0 = 0; c0 < p.lmax; c0 += 128) q128.push_back(make_int2(k, c0));
     bt->max_steps = std::max(bt->max_steps, p.cap);
   }
   bt->pool_bytes = off;
   bt->n_c32 = (int)c32.size();
   bt->n_rm = (int)rm.size();
   bt->n_rn = (int)rn.size();
-  bt->n_q32 = (int)q32.size();
+  bt->n_q128 = (int)q128.size();
+  bt->n_c128 = (int)c128.size();
   cudaError_t e = cudaMalloc((void**)&bt->d_pool, (size_t)std::max<int64_t>(off, 256));
   if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_pr, sizeof(BProb) * count);
   if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_c32, sizeof(int2) * c32.size());
   if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_rm, sizeof(int2) * rm.size());
   if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_rn, sizeof(int2) * rn.size());
-  if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_q32, sizeof(int2) * q32.size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_q128, sizeof(int2) * q128.size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_c128, sizeof(int2) * c128.size());
   if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_part, sizeof(double) * c32.size());
   if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_j, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_count, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_more, sizeof(int));
   if (e != cudaSuccess) {
     cudaGetLastError();
     batch_free(bt);
@@ -708,10 +818,13 @@ lra_status lra_batch_create(lra_batch** out, const lra_batch_item* items, int64_
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(bt->d_rn, rn.data(), sizeof(int2) * rn.size(), cudaMemcpyHostToDevice, bt->st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(bt->d_q32, q32.data(), sizeof(int2) * q32.size(), cudaMemcpyHostToDevice, bt->st);
+    e = cudaMemcpyAsync(bt->d_q128, q128.data(), sizeof(int2) * q128.size(), cudaMemcpyHostToDevice, bt->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(bt->d_c128, c128.data(), sizeof(int2) * c128.size(), cudaMemcpyHostToDevice, bt->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(bt->d_pool, 0, (size_t)off, bt->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(bt->st);
-  if (e == cudaSuccess) e = build_graph(bt);
+  bt->graph_mode = (prm->flags & LRA_FLAG_NO_GRAPHS) == 0;
+  if (e == cudaSuccess && bt->graph_mode) e = build_graph(bt);
   if (e != cudaSuccess) {
     cudaGetLastError();
     batch_free(bt);
@@ -732,7 +845,16 @@ lra_status lra_batch_run(lra_batch* bt) {
     k_b_start<<<(bt->np + 127) / 128, 128, 0, bt->st>>>(bt->d_pr, bt->np, bt->d_part, bt->d_j);
     e = launched();
   }
-  if (e == cudaSuccess) e = cudaGraphLaunch(bt->exec, bt->st);
+  if (e == cudaSuccess && bt->graph_mode) e = cudaGraphLaunch(bt->exec, bt->st);
+  // without the graph: one step at a time, the host reads whether to go on
+  for (int j = 0; e == cudaSuccess && !bt->graph_mode && j < bt->max_steps; ++j) {
+    e = issue_step_any(bt);
+    int more = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&more, bt->d_more, sizeof(int), cudaMemcpyDeviceToHost, bt->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(bt->st);
+    if (e == cudaSuccess) g_launches.fetch_add(bt->launches_per_step);
+    if (!more) break;
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(bt->h_pr.data(), bt->d_pr, sizeof(BProb) * bt->np, cudaMemcpyDeviceToHost,
                         bt->st);
@@ -744,7 +866,7 @@ lra_status lra_batch_run(lra_batch* bt) {
     return LRA_ERR_CUDA;
   }
   bt->steps_last = steps;
-  g_launches.fetch_add((uint64_t)steps * bt->launches_per_step);
+  if (bt->graph_mode) g_launches.fetch_add((uint64_t)steps * bt->launches_per_step);
   return LRA_OK;
 }
 

@@ -81,7 +81,8 @@ class BatchItem(Structure):
 
 
 class BatchParams(Structure):
-    _fields_ = [("b", c_int32), ("P", c_int32), ("zeta", c_int32), ("max_blocks", c_int32)]
+    _fields_ = [("b", c_int32), ("P", c_int32), ("zeta", c_int32), ("max_blocks", c_int32),
+                ("flags", c_uint32)]
 
 
 class BatchResult(Structure):
@@ -462,7 +463,7 @@ class Batch:
     run together by one graph launch.  `mats`: column-major float32 CUDA tensors
     (kept alive by the caller); `eps`, `seeds`: one per matrix."""
 
-    def __init__(self, mats, eps, seeds, b=16, P=1, zeta=4, max_blocks=0, stream=None):
+    def __init__(self, mats, eps, seeds, b=16, P=1, zeta=4, max_blocks=0, stream=None, graph=True):
         import torch
         self._lib, self._torch = load(), torch
         items = (BatchItem * len(mats))()
@@ -476,7 +477,7 @@ class Batch:
             self.shapes.append((m, n))
         self._b = c_void_p()
         st = c_void_p(stream.cuda_stream) if stream is not None else c_void_p(0)
-        s = self._lib.lra_batch_create(byref(self._b), items, len(mats), byref(BatchParams(b, P, zeta, max_blocks)),
+        s = self._lib.lra_batch_create(byref(self._b), items, len(mats), byref(BatchParams(b, P, zeta, max_blocks, 0 if graph else FLAG_NO_GRAPHS)),
                                        st)
         if s < 0:
             raise LraError(s, "lra_batch_create")

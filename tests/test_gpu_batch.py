@@ -102,10 +102,19 @@ def test_batch_independence_and_edge_states():
     assert torch.equal(a["Q"], m["Q"]) and torch.equal(a["Bt"], m["Bt"])
     z = mixed.result(4)
     assert (z["status"], z["rank"], z["E"], z["normA2"]) == (lra.OK, 0, 0.0, 0.0)
-    # a second run of the same batch gives the same bits
+    # a second run of the same batch gives the same bits, and so does the
+    # host-driven form (each step launched from the host instead of the graph)
     q0 = m["Q"].clone()
     mixed.run()
     assert torch.equal(mixed.result(1)["Q"], q0)
+    host = lra.Batch(mats + [zero], eps + [1e-2], seeds + [1], b=16, P=1, zeta=4, graph=False)
+    host.run()
+    for k in range(5):
+        a, h = mixed.result(k), host.result(k)
+        assert (a["status"], a["rank"], a["E"]) == (h["status"], h["rank"], h["E"])
+        if a["rank"]:
+            assert torch.equal(a["Q"], h["Q"]) and torch.equal(a["Bt"], h["Bt"])
+    host.close()
     alone.close()
     mixed.close()
 
