@@ -359,7 +359,8 @@ typedef struct {
   int64_t rank;
   double rel_err;
   double t_submit;     /* seconds on the server's clock (lra_server_clock)    */
-  double t_start;      /* admitted and its context created                    */
+  double t_admit;      /* admitted (first come, first served)                 */
+  double t_start;      /* its context created                                 */
   double t_done;       /* run finished                                        */
   int64_t bytes;       /* device bytes the request held                       */
   lra_ctx* ctx;        /* the context when keep != 0 (else NULL)              */

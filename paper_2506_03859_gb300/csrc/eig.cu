@@ -10,11 +10,15 @@
 // which one round rotates l/2 disjoint index pairs at once and l - 1 rounds
 // make a sweep that meets every pair once.  One cooperative launch runs all
 // sweeps: a round is one grid-wide pass in which each thread applies the two
-// rotations of one 2 x 2 block of C (C <- J^T C J) or rotates one row of the
-// eigenvector matrix (V <- V J), then a grid barrier.  C is double-buffered, so
-// every CTA computes the round's rotations from the same, unmodified values;
-// each CTA computes all of them into shared memory, which makes the
-// convergence decision (a sweep without a rotation) identical in every CTA.
+// rotations of one 2 x 2 block of C (C <- J^T C J, in place: every element
+// belongs to exactly one block of the round) or rotates one row of the
+// eigenvector matrix (V <- V J), then a grid barrier.  The three entries each
+// pair of the next round needs (c_pp, c_qq, c_pq) are written, by the threads
+// that produce them, into a small double-buffered snapshot, so every CTA computes
+// the round's rotations from the same values without re-reading C; each CTA
+// computes all of them into shared memory, which makes the convergence decision
+// (a sweep without a rotation) identical in every CTA.  A block whose two
+// rotations are both the identity is left as it is.
 // A pair is skipped when |c_pq| <= tol sqrt(|c_pp c_qq|): the relative
 // criterion under which Jacobi keeps the small eigenvalues of a positive
 // definite matrix to high relative accuracy (Demmel and Veselic, SIAM J. Matrix
@@ -39,13 +43,15 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 }
 
 // Grid-wide barrier for a cooperative launch (all CTAs resident).  bar[0]
-// counts arrivals, bar[1] is the generation.  Returns false once any CTA has
-// given up waiting (FLAG_TIMEOUT in *info).
+// counts arrivals, bar[1] is the generation.  Returns false when this CTA gave
+// up waiting (and set FLAG_TIMEOUT in *info); the other CTAs then give up at
+// their next wait, each after the same bounded spin.
 __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* info, int* s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned g = ld_acquire(bar + 1);
+    int ok = 1;
     if (atomicAdd(bar, 1u) == nblocks - 1) {
       atomicExch(bar, 0u);
       __threadfence();
@@ -55,16 +61,27 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* info, int* s_
       while (ld_acquire(bar + 1) == g) {
         if (++it > EIG_SPIN_LIMIT) {
           atomicOr(info, FLAG_TIMEOUT);
+          ok = 0;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
     __threadfence();
-    *s_ok = (atomicOr(info, 0) & FLAG_TIMEOUT) == 0;
+    *s_ok = ok;
   }
   __syncthreads();
   return *s_ok != 0;
+}
+
+// Pair index of index x in round t (the inverse of round_pair).
+__device__ __forceinline__ int pair_of(int x, int t, int lp) {
+  if (x == 0) return 0;
+  const int M = lp - 1;
+  int i = (x - 1 - t) % M;
+  if (i < 0) i += M;
+  if (i == 0) return 0;
+  return i < lp / 2 ? i : M - i;
 }
 
 // Pair k (0 <= k < lp/2) of round t (0 <= t < lp - 1) of the circle ordering:
@@ -111,14 +128,26 @@ __device__ __forceinline__ Rot jacobi_rot(double app, double aqq, double apq, do
 }
 
 struct EigArgs {
-  double* C0;     // lp x lp, ld lp (symmetric): buffer 0
-  double* C1;     // buffer 1
+  double* C;      // lp x lp, ld lp (symmetric), updated in place
+  double* snap;   // 2 x (lp/2) x 3: c_pp, c_qq, c_pq of each pair of a round
   double* V;      // lp x lp eigenvectors (columns), starts as I
   int l, lp, max_sweeps;
   double tol;
   unsigned* bar;  // 2 words, zero at launch
-  int* info;      // [0] flags, [1] sweeps, [2] converged, [3] final buffer
+  int* info;      // [0] flags, [1] sweeps, [2] converged, [3] 0
 };
+
+// An element (x, y) of C holding value v after round t: if x and y form a pair
+// of the next round (or x == y belongs to one), record v in that pair's
+// snapshot entry.
+__device__ __forceinline__ void snap_put(double* nsnap, int x, int y, double v, int tn, int lp) {
+  const int kx = pair_of(x, tn, lp);
+  if (kx != pair_of(y, tn, lp)) return;
+  int p, q;
+  round_pair(kx, tn, lp, p, q);
+  const int slot = x != y ? 2 : (x == p ? 0 : 1);
+  nsnap[3 * kx + slot] = v;
+}
 
 __global__ void __launch_bounds__(EIG_NT) k_jacobi(EigArgs a) {
   extern __shared__ double sm[];
@@ -132,19 +161,32 @@ __global__ void __launch_bounds__(EIG_NT) k_jacobi(EigArgs a) {
   const int64_t TB = (int64_t)a.l * nb2;            // (row of V, pair)
   const int64_t gstride = (int64_t)gridDim.x * EIG_NT;
   const int64_t gtid = (int64_t)blockIdx.x * EIG_NT + threadIdx.x;
-  int cur = 0, sweep = 0, converged = 0;
+  double* C = a.C;
+  int sweep = 0, converged = 0;
+  int64_t g = 0;  // rounds done
   for (; sweep < a.max_sweeps && !converged; ++sweep) {
     int any = 0;
-    for (int t = 0; t < M; ++t) {
-      const double* Cc = cur ? a.C1 : a.C0;
-      double* Cn = cur ? a.C0 : a.C1;
-      // the round's rotations, from the unmodified buffer
+    for (int t = 0; t < M; ++t, ++g) {
+      const double* csnap = a.snap + (g & 1) * 3 * nb2;
+      double* nsnap = a.snap + ((g + 1) & 1) * 3 * nb2;
+      const int tn = t + 1 == M ? 0 : t + 1;
+      // the round's rotations: from C itself before the first round, else from
+      // the snapshot the previous round wrote
       int mine = 0;
       for (int k = threadIdx.x; k < nb2; k += EIG_NT) {
         int p, q;
         round_pair(k, t, lp, p, q);
-        const Rot r = jacobi_rot(__ldcg(Cc + (int64_t)p * lp + p), __ldcg(Cc + (int64_t)q * lp + q),
-                                 __ldcg(Cc + (int64_t)q * lp + p), a.tol);
+        double app, aqq, apq;
+        if (g == 0) {
+          app = __ldcg(C + (int64_t)p * lp + p);
+          aqq = __ldcg(C + (int64_t)q * lp + q);
+          apq = __ldcg(C + (int64_t)q * lp + p);
+        } else {
+          app = __ldcg(csnap + 3 * k);
+          aqq = __ldcg(csnap + 3 * k + 1);
+          apq = __ldcg(csnap + 3 * k + 2);
+        }
+        const Rot r = jacobi_rot(app, aqq, apq, a.tol);
         rc[k] = r.c;
         rs[k] = r.s;
         rt[k] = r.t;
@@ -162,39 +204,49 @@ __global__ void __launch_bounds__(EIG_NT) k_jacobi(EigArgs a) {
           const int p = pq[P].x, q = pq[P].y;
           const double c1 = rc[P], s1 = rs[P];
           if (P == R) {
-            const double app = __ldcg(Cc + (int64_t)p * lp + p);
-            const double aqq = __ldcg(Cc + (int64_t)q * lp + q);
-            const double apq = __ldcg(Cc + (int64_t)q * lp + p);
-            double npp = app, nqq = aqq, npq = apq;
+            double npp = __ldcg(C + (int64_t)p * lp + p);
+            double nqq = __ldcg(C + (int64_t)q * lp + q);
+            double npq = __ldcg(C + (int64_t)q * lp + p);
             if (s1 != 0.0) {
-              npp = fma(-rt[P], apq, app);
-              nqq = fma(rt[P], apq, aqq);
+              const double apq = npq;
+              npp = fma(-rt[P], apq, npp);
+              nqq = fma(rt[P], apq, nqq);
               npq = 0.0;
+              __stcg(C + (int64_t)p * lp + p, npp);
+              __stcg(C + (int64_t)q * lp + q, nqq);
+              __stcg(C + (int64_t)q * lp + p, npq);
+              __stcg(C + (int64_t)p * lp + q, npq);
             }
-            __stcg(Cn + (int64_t)p * lp + p, npp);
-            __stcg(Cn + (int64_t)q * lp + q, nqq);
-            __stcg(Cn + (int64_t)q * lp + p, npq);
-            __stcg(Cn + (int64_t)p * lp + q, npq);
+            snap_put(nsnap, p, p, npp, tn, lp);
+            snap_put(nsnap, q, q, nqq, tn, lp);
+            snap_put(nsnap, p, q, npq, tn, lp);
           } else {
             const int r = pq[R].x, s = pq[R].y;
             const double c2 = rc[R], s2 = rs[R];
             // X = C[{p,q}, {r,s}]; element (i, j) at column j, row i
-            const double x00 = __ldcg(Cc + (int64_t)r * lp + p), x01 = __ldcg(Cc + (int64_t)s * lp + p);
-            const double x10 = __ldcg(Cc + (int64_t)r * lp + q), x11 = __ldcg(Cc + (int64_t)s * lp + q);
-            // Y = J_P^T X
-            const double y00 = c1 * x00 - s1 * x10, y01 = c1 * x01 - s1 * x11;
-            const double y10 = s1 * x00 + c1 * x10, y11 = s1 * x01 + c1 * x11;
-            // X' = Y J_R
-            const double z00 = c2 * y00 - s2 * y01, z01 = s2 * y00 + c2 * y01;
-            const double z10 = c2 * y10 - s2 * y11, z11 = s2 * y10 + c2 * y11;
-            __stcg(Cn + (int64_t)r * lp + p, z00);
-            __stcg(Cn + (int64_t)s * lp + p, z01);
-            __stcg(Cn + (int64_t)r * lp + q, z10);
-            __stcg(Cn + (int64_t)s * lp + q, z11);
-            __stcg(Cn + (int64_t)p * lp + r, z00);
-            __stcg(Cn + (int64_t)p * lp + s, z01);
-            __stcg(Cn + (int64_t)q * lp + r, z10);
-            __stcg(Cn + (int64_t)q * lp + s, z11);
+            double z00 = __ldcg(C + (int64_t)r * lp + p), z01 = __ldcg(C + (int64_t)s * lp + p);
+            double z10 = __ldcg(C + (int64_t)r * lp + q), z11 = __ldcg(C + (int64_t)s * lp + q);
+            if (s1 != 0.0 || s2 != 0.0) {
+              // Y = J_P^T X, then X' = Y J_R
+              const double y00 = c1 * z00 - s1 * z10, y01 = c1 * z01 - s1 * z11;
+              const double y10 = s1 * z00 + c1 * z10, y11 = s1 * z01 + c1 * z11;
+              z00 = c2 * y00 - s2 * y01;
+              z01 = s2 * y00 + c2 * y01;
+              z10 = c2 * y10 - s2 * y11;
+              z11 = s2 * y10 + c2 * y11;
+              __stcg(C + (int64_t)r * lp + p, z00);
+              __stcg(C + (int64_t)s * lp + p, z01);
+              __stcg(C + (int64_t)r * lp + q, z10);
+              __stcg(C + (int64_t)s * lp + q, z11);
+              __stcg(C + (int64_t)p * lp + r, z00);
+              __stcg(C + (int64_t)p * lp + s, z01);
+              __stcg(C + (int64_t)q * lp + r, z10);
+              __stcg(C + (int64_t)q * lp + s, z11);
+            }
+            snap_put(nsnap, p, r, z00, tn, lp);
+            snap_put(nsnap, p, s, z01, tn, lp);
+            snap_put(nsnap, q, r, z10, tn, lp);
+            snap_put(nsnap, q, s, z11, tn, lp);
           }
         } else {
           const int64_t u = w - TA;
@@ -210,7 +262,6 @@ __global__ void __launch_bounds__(EIG_NT) k_jacobi(EigArgs a) {
           }
         }
       }
-      cur ^= 1;
       if (!grid_barrier(a.bar, gridDim.x, a.info, &s_ok)) return;
     }
     converged = !any;
@@ -218,7 +269,7 @@ __global__ void __launch_bounds__(EIG_NT) k_jacobi(EigArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.info[1] = sweep;
     a.info[2] = converged;
-    a.info[3] = cur;
+    a.info[3] = 0;
   }
 }
 
@@ -299,7 +350,7 @@ int64_t eig_max_l() {
   return 2 * ((200 * 1024) / 32);
 }
 
-cudaError_t eig_sym(const double* G, int64_t ldg, int l, double* C0, double* C1, double* V,
+cudaError_t eig_sym(const double* G, int64_t ldg, int l, double* C0, double* snap, double* V,
                     int max_sweeps, double tol, unsigned* bar, int* info, cudaStream_t st) {
   if (l < 1 || l > eig_max_l()) return cudaErrorInvalidValue;
   const int lp = (int)eig_padded(l);
@@ -328,7 +379,7 @@ cudaError_t eig_sym(const double* G, int64_t ldg, int l, double* C0, double* C1,
   int64_t grid = (tasks + EIG_NT - 1) / EIG_NT;
   grid = std::min<int64_t>(grid, (int64_t)occ * sms);
   grid = std::max<int64_t>(grid, 1);
-  EigArgs a{C0, C1, V, l, lp, max_sweeps, tol, bar, info};
+  EigArgs a{C0, snap, V, l, lp, max_sweeps, tol, bar, info};
   void* args[] = {&a};
   e = cudaLaunchCooperativeKernel((const void*)k_jacobi, dim3((unsigned)grid), dim3(EIG_NT), args,
                                   smem, st);

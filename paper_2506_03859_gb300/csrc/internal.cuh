@@ -133,13 +133,13 @@ cudaError_t fill(double* X, int64_t ld, int64_t rows, int64_t cols, double v, cu
 
 // ---------------------------------------------------------------- eig.cu
 // Cyclic Jacobi eigendecomposition of a symmetric l x l matrix given by the upper
-// triangle of G (ld ldg): one cooperative launch.  C0, C1, V: eig_padded(l)^2
-// doubles each; bar: 2 words; info: 4 ints ([0] flags, FLAG_TIMEOUT if a
-// barrier wait gave up; [1] sweeps; [2] converged; [3] 1 if the eigenvalues
-// ended in C1's diagonal, 0 if in C0's).  V's columns are the eigenvectors.
+// triangle of G (ld ldg): one cooperative launch.  C, V: eig_padded(l)^2 doubles
+// each (the eigenvalues end on C's diagonal, the eigenvectors in V's columns);
+// snap: 3 eig_padded(l) doubles; bar: 2 words; info: 4 ints ([0] flags,
+// FLAG_TIMEOUT if a barrier wait gave up; [1] sweeps; [2] converged; [3] 0).
 int64_t eig_padded(int64_t l);
 int64_t eig_max_l();
-cudaError_t eig_sym(const double* G, int64_t ldg, int l, double* C0, double* C1, double* V,
+cudaError_t eig_sym(const double* G, int64_t ldg, int l, double* C, double* snap, double* V,
                     int max_sweeps, double tol, unsigned* bar, int* info, cudaStream_t st);
 // sigma (l, descending) = sqrt of the eigenvalues on C's diagonal; Vs = V's
 // columns in that order, renormalised (l x l, ld l); W = Vs diag(sigma)^{-1}

@@ -655,7 +655,7 @@ lra_status svd_alloc(lra_ctx* ctx, int64_t l) {
   CK(dalloc(ctx, &w.Bt, n * l));
   CK(dalloc(ctx, &w.G, l * l));
   CK(dalloc(ctx, &w.C0, lp * lp));
-  CK(dalloc(ctx, &w.C1, lp * lp));
+  CK(dalloc(ctx, &w.C1, std::max<int64_t>(lp * lp, 3 * lp)));  // the Jacobi snapshot
   CK(dalloc(ctx, &w.V, lp * lp));
   CK(dalloc(ctx, &w.Vs, l * l));
   CK(dalloc(ctx, &w.W, l * l));
@@ -988,12 +988,12 @@ lra_status lra_svd(lra_ctx* ctx, lra_svd_t* out) {
     TRY(mm(ctx, true, l, nc, n, 1.0, w.Bt, n, tc ? w.btcolE : nullptr, w.Bt + c0 * n, n, 0.0,
            w.G + c0 * l, 1, l, tc ? w.btcolE + c0 : nullptr));
   }
-  CK(eig_sym(w.G, l, (int)l, w.C0, w.C1, w.V, SVD_MAX_SWEEPS, SVD_JACOBI_TOL, w.bar, w.info, st));
+  CK(eig_sym(w.G, l, (int)l, w.C0, w.C1, w.V, SVD_MAX_SWEEPS, SVD_JACOBI_TOL, w.bar, w.info, st));  // C1: snapshot
   int info[4] = {0, 0, 0, 0};
   CK(cudaMemcpyAsync(info, w.info, sizeof info, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (info[0] & FLAG_TIMEOUT) return fail(ctx, LRA_ERR_TIMEOUT, "eigensolver barrier wait gave up");
-  CK(eig_sort(info[3] ? w.C1 : w.C0, (int)l, w.sigma, w.perm, w.vinv, w.V, w.Vs, w.W, st));
+  CK(eig_sort(w.C0, (int)l, w.sigma, w.perm, w.vinv, w.V, w.Vs, w.W, st));
   // U = Q Vt, V = Bt Vt sigma^{-1}
   for (int64_t c0 = 0; c0 < l; c0 += 64) {
     const int64_t nc = std::min<int64_t>(64, l - c0);

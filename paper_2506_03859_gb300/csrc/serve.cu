@@ -56,11 +56,12 @@ double clock_of(const lra_server* s) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
 }
 
-lra_completion run_one(lra_server* s, const Item& it, cudaStream_t st) {
+lra_completion run_one(lra_server* s, const Item& it, double t_admit, cudaStream_t st) {
   lra_completion c;
   memset(&c, 0, sizeof c);
   c.id = it.req.id;
   c.t_submit = it.t_submit;
+  c.t_admit = t_admit;
   lra_params p = it.req.params;
   p.flags |= s->prm.flags | LRA_FLAG_POOL;
   lra_ctx* ctx = nullptr;
@@ -94,8 +95,9 @@ void worker(lra_server* s, int slot) {
       if (s->stop && s->adm->waiting() == 0) return;
       s->cv_work.wait(lk);
     }
+    const double t_admit = clock_of(s);
     lk.unlock();
-    lra_completion c = run_one(s, it, s->streams[slot]);
+    lra_completion c = run_one(s, it, t_admit, s->streams[slot]);
     lk.lock();
     if (c.ctx) {
       s->kept[c.ctx] = bytes;

@@ -71,7 +71,7 @@ class Request(Structure):
 
 class Completion(Structure):
     _fields_ = [("id", c_uint64), ("status", c_int32), ("reserved", c_int32), ("rank", c_int64),
-                ("rel_err", c_double), ("t_submit", c_double), ("t_start", c_double),
+                ("rel_err", c_double), ("t_submit", c_double), ("t_admit", c_double), ("t_start", c_double),
                 ("t_done", c_double), ("bytes", c_int64), ("ctx", c_void_p)]
 
 
@@ -433,7 +433,7 @@ class Server:
         out = []
         for c in buf[:k]:
             d = dict(id=c.id, status=c.status, rank=c.rank, rel_err=c.rel_err, t_submit=c.t_submit,
-                     t_start=c.t_start, t_done=c.t_done, bytes=c.bytes)
+                     t_admit=c.t_admit, t_start=c.t_start, t_done=c.t_done, bytes=c.bytes)
             m, n = self._shapes.pop(c.id, (0, 0))
             if c.ctx:
                 d["run"] = KeptRun(self, c.ctx, m, n)

@@ -62,7 +62,7 @@ def test_results_equal_alone_and_in_the_mix():
             got[c["id"]] = c
     for r in reqs:
         c = got[r["id"]]
-        assert c["status"] >= 0 and c["t_submit"] <= c["t_start"] <= c["t_done"]
+        assert c["status"] >= 0 and c["t_submit"] <= c["t_admit"] <= c["t_start"] <= c["t_done"]
         mix = c["run"].result()
         m, n = r["A"].shape
         pr = r["prm"]
@@ -92,13 +92,15 @@ def test_admission_limits_and_order():
     srv.close()
     by_id = {c["id"]: c for c in done}
     assert all(c["status"] >= 0 for c in done)
-    # arrival order: a request never starts before an earlier one
-    starts = [by_id[i]["t_start"] for i in range(len(reqs))]
-    assert all(a <= b for a, b in zip(starts, starts[1:]))
-    # at every start, the requests then running fit the budget and the slots
+    # arrival order: a request is never admitted before an earlier one
+    admits = [by_id[i]["t_admit"] for i in range(len(reqs))]
+    assert all(a <= b for a, b in zip(admits, admits[1:]))
+    assert all(by_id[i]["t_submit"] <= by_id[i]["t_admit"] <= by_id[i]["t_start"] <= by_id[i]["t_done"]
+               for i in range(len(reqs)))
+    # at every admission, the requests then running fit the budget and the slots
     for i in range(len(reqs)):
-        t = by_id[i]["t_start"]
-        live = [j for j in range(len(reqs)) if by_id[j]["t_start"] <= t < by_id[j]["t_done"]]
+        t = by_id[i]["t_admit"]
+        live = [j for j in range(len(reqs)) if by_id[j]["t_admit"] <= t < by_id[j]["t_done"]]
         assert len(live) <= 3
         assert sum(need[j] for j in live) <= budget
 
