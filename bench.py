@@ -64,7 +64,7 @@ def parse():
                     help="with --only batch: number of problems (4096 is the benchmark batch)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="with --only batch: launch the batch's steps from the host (for profiling)")
-    ap.add_argument("--only", choices=("sketch", "dense", "serve", "batch", "fixedrank", "stability"),
+    ap.add_argument("--only", choices=("sketch", "dense", "serve", "batch", "fixedrank", "stability", "svd"),
                     default=None,
                     help="run only the sketch pass (lra_sketch over --sketch-blocks blocks) or only "
                          "the two dense passes A Y and A^T Y (lra_apply), for profiling")
@@ -259,8 +259,11 @@ def main():
     f = lra.Farpca(m, n, eps=cfg["eps"], b=cfg["b"], P=cfg["P"], kind=cfg["kind"], zeta=cfg["zeta"],
                    p=cfg["p"], seed=cfg["seed"] + rank, profile=True, stream=stream,
                    fp64_simt=(args.engine == "fp64_simt"))
-    if args.only in ("sketch", "dense", "serve", "batch", "fixedrank", "stability"):
-        if args.only == "stability":
+    if args.only in ("sketch", "dense", "serve", "batch", "fixedrank", "stability", "svd"):
+        if args.only == "svd":
+            f.run(Ad)
+            out = {"svd": svd_extraction(torch, f, args.steps, stream)}
+        elif args.only == "stability":
             out = {"stability": stability(lra, torch)}
         elif args.only == "fixedrank":
             out = {"fixed_rank_sweep": fixed_rank_sweep(lra, torch)}
