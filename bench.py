@@ -60,6 +60,8 @@ def parse():
                     help="only the timed farPCA steps (for launch-list profiling)")
     ap.add_argument("--engine", choices=("tensor", "fp64_simt"), default="tensor",
                     help="dense passes on the tensor cores (FP64-accurate slicing) or FP64 CUDA cores")
+    ap.add_argument("--serve-slots", type=int, default=8,
+                    help="with --only serve: requests run at once")
     ap.add_argument("--batch-count", type=int, default=4096,
                     help="with --only batch: number of problems (4096 is the benchmark batch)")
     ap.add_argument("--no-graphs", action="store_true",
@@ -260,15 +262,16 @@ def main():
                    p=cfg["p"], seed=cfg["seed"] + rank, profile=True, stream=stream,
                    fp64_simt=(args.engine == "fp64_simt"))
     if args.only in ("sketch", "dense", "serve", "batch", "fixedrank", "stability", "svd"):
-        if args.only == "svd":
+        if args.only == "serve":
+            out = {"serving": serving(lra, torch, np, slots=args.serve_slots)}
+        elif args.only == "svd":
             f.run(Ad)
             out = {"svd": svd_extraction(torch, f, args.steps, stream)}
         elif args.only == "stability":
             out = {"stability": stability(lra, torch)}
         elif args.only == "fixedrank":
             out = {"fixed_rank_sweep": fixed_rank_sweep(lra, torch)}
-        elif args.only == "serve":
-            out = {"serving": serving(lra, torch, np)}
+
         elif args.only == "batch":
             out = {"batched": batched(lra, torch, np, peaks, peak_src, count=args.batch_count,
                                       graph=not args.no_graphs)}

@@ -23,6 +23,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -46,6 +47,43 @@ struct Pinned {
   double v[4];
   int flags;
 };
+
+// The small pinned blocks through which every context reads its scalars back
+// (one per context).  They come from page-locked chunks allocated once and
+// kept for the process: releasing page-locked memory can synchronise the
+// device, which would stall every other context at each destroy (the serving
+// runtime creates and destroys contexts next to running ones).
+class PinnedArena {
+ public:
+  Pinned* get() {
+    std::lock_guard<std::mutex> lk(mu_);
+    if (free_.empty()) {
+      Pinned* chunk = nullptr;
+      if (cudaMallocHost((void**)&chunk, sizeof(Pinned) * kChunk) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+      for (int i = kChunk - 1; i >= 0; --i) free_.push_back(chunk + i);
+    }
+    Pinned* p = free_.back();
+    free_.pop_back();
+    return p;
+  }
+  void put(Pinned* p) {
+    std::lock_guard<std::mutex> lk(mu_);
+    free_.push_back(p);
+  }
+
+ private:
+  static constexpr int kChunk = 256;
+  std::mutex mu_;
+  std::vector<Pinned*> free_;
+};
+
+PinnedArena& pinned_arena() {
+  static PinnedArena* a = new PinnedArena();  // never destroyed: outlives every context
+  return *a;
+}
 
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
@@ -684,6 +722,11 @@ void free_all(lra_ctx* c) {
                   c->ximg[0], c->ximg[1], c->astat};
   for (void* p : ptrs) dfree(c, p);
   svd_free(c);
+  if (c->hp) {
+    if (c->st) cudaStreamSynchronize(c->st);  // no copy into the slot may be pending
+    pinned_arena().put(c->hp);
+    c->hp = nullptr;
+  }
   if (c->gpre.exec) cudaGraphExecDestroy(c->gpre.exec);
   for (int i = 0; i < lra_ctx::NCOPY; ++i) {
     if (c->cst[i]) cudaStreamDestroy(c->cst[i]);
@@ -696,7 +739,6 @@ void free_all(lra_ctx* c) {
   }
   for (auto& g : c->gblock)
     if (g.exec) cudaGraphExecDestroy(g.exec);
-  if (c->hp) cudaFreeHost(c->hp);
   for (int i = 0; i < lra_ctx::NEV; ++i) {
     if (c->ev0[i]) cudaEventDestroy(c->ev0[i]);
     if (c->ev1[i]) cudaEventDestroy(c->ev1[i]);
@@ -896,7 +938,8 @@ lra_status create_ctx(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
     *out = ctx;
     return LRA_OK;
   }
-  cudaError_t e = cudaMallocHost((void**)&ctx->hp, sizeof(Pinned));
+  ctx->hp = pinned_arena().get();
+  cudaError_t e = ctx->hp ? cudaSuccess : cudaErrorMemoryAllocation;
   if (e != cudaSuccess) {
     free_all(ctx);
     delete ctx;
