@@ -10,7 +10,8 @@
  * eps^2 ||A||_F^2 (the relative test of Sec. 5.2), or a fixed rank is reached.
  *
  * Conventions for every entry point:
- *  - Matrices are column-major (element (i, j) at ptr[i + j * ld]), FP64.
+ *  - Matrices are column-major (element (i, j) at ptr[i + j * ld]), FP64
+ *    unless an entry point states that it takes FP32 (LRA_F32) data.
  *  - "device" pointers are CUDA device memory of the current device; "host"
  *    pointers are ordinary (ideally pinned) host memory.  The library never
  *    frees memory it did not allocate.
@@ -21,6 +22,14 @@
  *    are undefined.  A NULL ctx or NULL required pointer gives
  *    LRA_ERR_INVALID_ARG.
  *  - A context is not thread-safe: one host thread at a time per context.
+ *    Different contexts may be created and used from different threads at once
+ *    (the serving runtime does so); a server and a batch handle their own
+ *    locking as stated at their entry points.
+ *
+ * Beyond the loop itself: the SVD the method returns and its truncation
+ * (lra_svd), FP32 input (lra_farpca_run, lra_farpca_host_f32), a serving
+ * runtime for streams of requests (lra_server_*) and a batched form for many
+ * small problems in one graph launch (lra_batch_*).
  */
 #ifndef LRA_H
 #define LRA_H

@@ -363,11 +363,11 @@ cudaError_t eig_sym(const double* G, int64_t ldg, int l, double* C0, double* sna
   if (e != cudaSuccess) return e;
   const int nb2 = lp / 2;
   const size_t smem = (size_t)nb2 * 32;
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<bool> attr{false};  // concurrent first calls set it twice, harmlessly
+  if (!attr.load(std::memory_order_acquire)) {
     e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr.store(true, std::memory_order_release);
   }
   int dev = 0, sms = 0, occ = 0;
   e = cudaGetDevice(&dev);

@@ -1007,17 +1007,18 @@ cudaError_t prepare_y(const double* Y, int64_t ldy, int64_t K, int64_t N, const 
 }
 
 template <typename F>
-cudaError_t set_smem_once(F kernel, bool& done) {
-  if (done) return cudaSuccess;
+cudaError_t set_smem_once(F kernel, std::atomic<bool>& done) {
+  if (done.load(std::memory_order_acquire)) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        SMEM_DYN);
-  if (e == cudaSuccess) done = true;
+  if (e == cudaSuccess) done.store(true, std::memory_order_release);
   return e;
 }
 }  // namespace
 
 cudaError_t oz_prepare() {
-  static bool a0 = false, a1 = false, a2 = false, a3 = false;
+  // set once per process; concurrent first calls set the same attribute twice
+  static std::atomic<bool> a0{false}, a1{false}, a2{false}, a3{false};
   cudaError_t e = set_smem_once(k_ozgemm<false>, a0);
   if (e == cudaSuccess) e = set_smem_once(k_ozgemm<true>, a1);
   if (e == cudaSuccess) e = set_smem_once(k_ozgemm_img<false>, a2);

@@ -110,14 +110,14 @@ __global__ void __launch_bounds__(256) k_gather_staged(
 }
 
 cudaError_t gather_prepare() {
-  static bool attr = false;
-  if (attr) return cudaSuccess;
+  static std::atomic<bool> attr{false};  // concurrent first calls set it twice, harmlessly
+  if (attr.load(std::memory_order_acquire)) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute((const void*)k_gather_staged<double>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void*)k_gather_staged<float>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM);
-  if (e == cudaSuccess) attr = true;
+  if (e == cudaSuccess) attr.store(true, std::memory_order_release);
   return e;
 }
 
