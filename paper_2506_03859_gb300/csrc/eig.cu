@@ -9,16 +9,21 @@
 // Van Loan, "Matrix Computations", Sec. 8.5) with the round-robin ordering, in
 // which one round rotates l/2 disjoint index pairs at once and l - 1 rounds
 // make a sweep that meets every pair once.  One cooperative launch runs all
-// sweeps: a round is one grid-wide pass in which each thread applies the two
-// rotations of one 2 x 2 block of C (C <- J^T C J, in place: every element
-// belongs to exactly one block of the round) or rotates one row of the
-// eigenvector matrix (V <- V J), then a grid barrier.  The three entries each
-// pair of the next round needs (c_pp, c_qq, c_pq) are written, by the threads
-// that produce them, into a small double-buffered snapshot, so every CTA computes
-// the round's rotations from the same values without re-reading C; each CTA
-// computes all of them into shared memory, which makes the convergence decision
-// (a sweep without a rotation) identical in every CTA.  A block whose two
-// rotations are both the identity is left as it is.
+// sweeps: a round is one grid-wide pass that applies the round's rotations to
+// the 2 x 2 blocks of C (C <- J^T C J, in place: every element belongs to
+// exactly one block of the round) and to the rows of the eigenvector matrix
+// (V <- V J), then a grid barrier.  The round's pairs are cut into S slices and
+// the work into S (S + 1) / 2 CTAs, one per pair of slices (ka <= kb), so that a
+// CTA computes only the rotations of its two slices (FP64 square roots and
+// divisions are the long part of a round on this GPU's narrow FP64 pipe).  The
+// three entries each pair of the next round needs (c_pp, c_qq, c_pq) are
+// written, by the threads that produce them, into a small double-buffered
+// snapshot, so the rotations come from the same values in every CTA without
+// re-reading C.  Each slice's rotations are counted once per sweep in a global
+// counter (three slots in turn, so that one is read, one filled and one cleared
+// in any sweep); a sweep whose count is zero ends the iteration, a decision
+// every CTA reads after the same barrier.  A block whose two rotations are
+// both the identity is left as it is.
 // A pair is skipped when |c_pq| <= tol sqrt(|c_pp c_qq|): the relative
 // criterion under which Jacobi keeps the small eigenvalues of a positive
 // definite matrix to high relative accuracy (Demmel and Veselic, SIAM J. Matrix
@@ -132,8 +137,10 @@ struct EigArgs {
   double* snap;   // 2 x (lp/2) x 3: c_pp, c_qq, c_pq of each pair of a round
   double* V;      // lp x lp eigenvectors (columns), starts as I
   int l, lp, max_sweeps;
+  int S, sz;      // pair slices of a round (S (S + 1) / 2 CTAs), pairs per slice
   double tol;
   unsigned* bar;  // 2 words, zero at launch
+  int* rotcnt;    // 3 per-sweep rotation counters, zero at launch
   int* info;      // [0] flags, [1] sweeps, [2] converged, [3] 0
 };
 
@@ -149,113 +156,137 @@ __device__ __forceinline__ void snap_put(double* nsnap, int x, int y, double v, 
   nsnap[3 * kx + slot] = v;
 }
 
+// The pairs of a round are cut into S slices of sz consecutive pair indices; CTA
+// (ka, kb), ka <= kb, applies the 2 x 2 blocks (P, R) with P in slice ka and R
+// in slice kb (P <= R), and rotates the eigenvector rows of slice ka in row
+// chunk kb and of slice kb in row chunk ka (the rows split in S chunks).  It
+// needs the rotations of its two slices only.  Every block and every (row,
+// pair) belongs to exactly one CTA.
 __global__ void __launch_bounds__(EIG_NT) k_jacobi(EigArgs a) {
   extern __shared__ double sm[];
-  const int lp = a.lp, nb2 = lp / 2, M = lp - 1;
-  double* rc = sm;              // cos, per pair of the round
-  double* rs = rc + nb2;        // sin
-  double* rt = rs + nb2;        // tan
-  int2* pq = reinterpret_cast<int2*>(rt + nb2);
+  const int lp = a.lp, nb2 = lp / 2, M = lp - 1, sz = a.sz;
+  double* rc = sm;              // cos of the CTA's 2 sz pairs (slice ka, then slice kb)
+  double* rs = rc + 2 * sz;     // sin
+  double* rt = rs + 2 * sz;     // tan
+  int2* pq = reinterpret_cast<int2*>(rt + 2 * sz);
   __shared__ int s_ok;
-  const int64_t TA = (int64_t)nb2 * (nb2 + 1) / 2;  // 2 x 2 blocks (P <= R)
-  const int64_t TB = (int64_t)a.l * nb2;            // (row of V, pair)
-  const int64_t gstride = (int64_t)gridDim.x * EIG_NT;
-  const int64_t gtid = (int64_t)blockIdx.x * EIG_NT + threadIdx.x;
+  int kb = 0;
+  while ((kb + 1) * (kb + 2) / 2 <= (int)blockIdx.x) ++kb;
+  const int ka = (int)blockIdx.x - kb * (kb + 1) / 2;
+  const int a0 = ka * sz, na = max(0, min(sz, nb2 - a0));
+  const int b0 = kb * sz, nbk = max(0, min(sz, nb2 - b0));
+  const int rch = (a.l + a.S - 1) / a.S;
   double* C = a.C;
   int sweep = 0, converged = 0;
   int64_t g = 0;  // rounds done
   for (; sweep < a.max_sweeps && !converged; ++sweep) {
-    int any = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(a.rotcnt + (sweep + 1) % 3, 0);
     for (int t = 0; t < M; ++t, ++g) {
       const double* csnap = a.snap + (g & 1) * 3 * nb2;
       double* nsnap = a.snap + ((g + 1) & 1) * 3 * nb2;
       const int tn = t + 1 == M ? 0 : t + 1;
-      // the round's rotations: from C itself before the first round, else from
-      // the snapshot the previous round wrote
-      int mine = 0;
-      for (int k = threadIdx.x; k < nb2; k += EIG_NT) {
-        int p, q;
-        round_pair(k, t, lp, p, q);
-        double app, aqq, apq;
-        if (g == 0) {
-          app = __ldcg(C + (int64_t)p * lp + p);
-          aqq = __ldcg(C + (int64_t)q * lp + q);
-          apq = __ldcg(C + (int64_t)q * lp + p);
-        } else {
-          app = __ldcg(csnap + 3 * k);
-          aqq = __ldcg(csnap + 3 * k + 1);
-          apq = __ldcg(csnap + 3 * k + 2);
-        }
-        const Rot r = jacobi_rot(app, aqq, apq, a.tol);
-        rc[k] = r.c;
-        rs[k] = r.s;
-        rt[k] = r.t;
-        pq[k] = make_int2(p, q);
-        mine |= r.s != 0.0;
-      }
-      any |= __syncthreads_or(mine);
-      for (int64_t w = gtid; w < TA + TB; w += gstride) {
-        if (w < TA) {
-          // (P, R), P <= R, from the triangular index w = R(R+1)/2 + P
-          int R = (int)((sqrtf(8.0f * (float)w + 1.0f) - 1.0f) * 0.5f);
-          while ((int64_t)R * (R + 1) / 2 > w) --R;
-          while ((int64_t)(R + 1) * (R + 2) / 2 <= w) ++R;
-          const int P = (int)(w - (int64_t)R * (R + 1) / 2);
-          const int p = pq[P].x, q = pq[P].y;
-          const double c1 = rc[P], s1 = rs[P];
-          if (P == R) {
-            double npp = __ldcg(C + (int64_t)p * lp + p);
-            double nqq = __ldcg(C + (int64_t)q * lp + q);
-            double npq = __ldcg(C + (int64_t)q * lp + p);
-            if (s1 != 0.0) {
-              const double apq = npq;
-              npp = fma(-rt[P], apq, npp);
-              nqq = fma(rt[P], apq, nqq);
-              npq = 0.0;
-              __stcg(C + (int64_t)p * lp + p, npp);
-              __stcg(C + (int64_t)q * lp + q, nqq);
-              __stcg(C + (int64_t)q * lp + p, npq);
-              __stcg(C + (int64_t)p * lp + q, npq);
-            }
-            snap_put(nsnap, p, p, npp, tn, lp);
-            snap_put(nsnap, q, q, nqq, tn, lp);
-            snap_put(nsnap, p, q, npq, tn, lp);
+      // the rotations of the CTA's two slices: from C itself before the first
+      // round, else from the snapshot the previous round wrote
+      int rotated = 0;
+      for (int slot = threadIdx.x; slot < 2 * sz; slot += EIG_NT) {
+        const int h = slot / sz, u = slot % sz;
+        const int k = (h ? b0 : a0) + u;
+        if (u < (h ? nbk : na)) {
+          int p, q;
+          round_pair(k, t, lp, p, q);
+          double app, aqq, apq;
+          if (g == 0) {
+            app = __ldcg(C + (int64_t)p * lp + p);
+            aqq = __ldcg(C + (int64_t)q * lp + q);
+            apq = __ldcg(C + (int64_t)q * lp + p);
           } else {
-            const int r = pq[R].x, s = pq[R].y;
-            const double c2 = rc[R], s2 = rs[R];
-            // X = C[{p,q}, {r,s}]; element (i, j) at column j, row i
-            double z00 = __ldcg(C + (int64_t)r * lp + p), z01 = __ldcg(C + (int64_t)s * lp + p);
-            double z10 = __ldcg(C + (int64_t)r * lp + q), z11 = __ldcg(C + (int64_t)s * lp + q);
-            if (s1 != 0.0 || s2 != 0.0) {
-              // Y = J_P^T X, then X' = Y J_R
-              const double y00 = c1 * z00 - s1 * z10, y01 = c1 * z01 - s1 * z11;
-              const double y10 = s1 * z00 + c1 * z10, y11 = s1 * z01 + c1 * z11;
-              z00 = c2 * y00 - s2 * y01;
-              z01 = s2 * y00 + c2 * y01;
-              z10 = c2 * y10 - s2 * y11;
-              z11 = s2 * y10 + c2 * y11;
-              __stcg(C + (int64_t)r * lp + p, z00);
-              __stcg(C + (int64_t)s * lp + p, z01);
-              __stcg(C + (int64_t)r * lp + q, z10);
-              __stcg(C + (int64_t)s * lp + q, z11);
-              __stcg(C + (int64_t)p * lp + r, z00);
-              __stcg(C + (int64_t)p * lp + s, z01);
-              __stcg(C + (int64_t)q * lp + r, z10);
-              __stcg(C + (int64_t)q * lp + s, z11);
-            }
-            snap_put(nsnap, p, r, z00, tn, lp);
-            snap_put(nsnap, p, s, z01, tn, lp);
-            snap_put(nsnap, q, r, z10, tn, lp);
-            snap_put(nsnap, q, s, z11, tn, lp);
+            app = __ldcg(csnap + 3 * k);
+            aqq = __ldcg(csnap + 3 * k + 1);
+            apq = __ldcg(csnap + 3 * k + 2);
           }
-        } else {
-          const int64_t u = w - TA;
-          const int P = (int)(u / a.l), i = (int)(u - (int64_t)P * a.l);
-          const double s1 = rs[P];
+          const Rot r = jacobi_rot(app, aqq, apq, a.tol);
+          rc[slot] = r.c;
+          rs[slot] = r.s;
+          rt[slot] = r.t;
+          pq[slot] = make_int2(p, q);
+          // each slice's rotations are counted once, by its diagonal CTA
+          rotated += (h == 0 && ka == kb && r.s != 0.0) ? 1 : 0;
+        }
+      }
+      const int cnt = __syncthreads_count(rotated);
+      if (cnt && threadIdx.x == 0) atomicAdd(a.rotcnt + sweep % 3, cnt);
+      // 2 x 2 blocks (P, R): P in slice ka (slot i), R in slice kb (slot sz + j)
+      const int nblk = ka < kb ? na * nbk : na * (na + 1) / 2;
+      for (int w = threadIdx.x; w < nblk; w += EIG_NT) {
+        int i, j;
+        if (ka < kb) {
+          i = w / nbk;
+          j = w - i * nbk;
+        } else {  // i <= j within the slice: w = j (j + 1) / 2 + i
+          j = 0;
+          while ((j + 1) * (j + 2) / 2 <= w) ++j;
+          i = w - j * (j + 1) / 2;
+        }
+        const int sP = i, sR = ka < kb ? sz + j : j;
+        const int p = pq[sP].x, q = pq[sP].y;
+        const double c1 = rc[sP], s1 = rs[sP];
+        if (ka == kb && i == j) {
+          double npp = __ldcg(C + (int64_t)p * lp + p);
+          double nqq = __ldcg(C + (int64_t)q * lp + q);
+          double npq = __ldcg(C + (int64_t)q * lp + p);
           if (s1 != 0.0) {
-            const double c1 = rc[P];
-            double* vp = a.V + (int64_t)pq[P].x * lp + i;
-            double* vq = a.V + (int64_t)pq[P].y * lp + i;
+            const double apq = npq;
+            npp = fma(-rt[sP], apq, npp);
+            nqq = fma(rt[sP], apq, nqq);
+            npq = 0.0;
+            __stcg(C + (int64_t)p * lp + p, npp);
+            __stcg(C + (int64_t)q * lp + q, nqq);
+            __stcg(C + (int64_t)q * lp + p, npq);
+            __stcg(C + (int64_t)p * lp + q, npq);
+          }
+          snap_put(nsnap, p, p, npp, tn, lp);
+          snap_put(nsnap, q, q, nqq, tn, lp);
+          snap_put(nsnap, p, q, npq, tn, lp);
+        } else {
+          const int r = pq[sR].x, s2i = pq[sR].y;
+          const double c2 = rc[sR], s2 = rs[sR];
+          double z00 = __ldcg(C + (int64_t)r * lp + p), z01 = __ldcg(C + (int64_t)s2i * lp + p);
+          double z10 = __ldcg(C + (int64_t)r * lp + q), z11 = __ldcg(C + (int64_t)s2i * lp + q);
+          if (s1 != 0.0 || s2 != 0.0) {
+            // Y = J_P^T X, then X' = Y J_R
+            const double y00 = c1 * z00 - s1 * z10, y01 = c1 * z01 - s1 * z11;
+            const double y10 = s1 * z00 + c1 * z10, y11 = s1 * z01 + c1 * z11;
+            z00 = c2 * y00 - s2 * y01;
+            z01 = s2 * y00 + c2 * y01;
+            z10 = c2 * y10 - s2 * y11;
+            z11 = s2 * y10 + c2 * y11;
+            __stcg(C + (int64_t)r * lp + p, z00);
+            __stcg(C + (int64_t)s2i * lp + p, z01);
+            __stcg(C + (int64_t)r * lp + q, z10);
+            __stcg(C + (int64_t)s2i * lp + q, z11);
+            __stcg(C + (int64_t)p * lp + r, z00);
+            __stcg(C + (int64_t)p * lp + s2i, z01);
+            __stcg(C + (int64_t)q * lp + r, z10);
+            __stcg(C + (int64_t)q * lp + s2i, z11);
+          }
+          snap_put(nsnap, p, r, z00, tn, lp);
+          snap_put(nsnap, p, s2i, z01, tn, lp);
+          snap_put(nsnap, q, r, z10, tn, lp);
+          snap_put(nsnap, q, s2i, z11, tn, lp);
+        }
+      }
+      // eigenvector rows: (slice ka, row chunk kb) and, off the diagonal, (slice kb, chunk ka)
+      for (int part = 0; part < (ka < kb ? 2 : 1); ++part) {
+        const int np = part ? nbk : na, base = part ? sz : 0;
+        const int c0 = (part ? ka : kb) * rch, c1r = min(a.l, c0 + rch);
+        const int rows = max(0, c1r - c0);
+        for (int w = threadIdx.x; w < np * rows; w += EIG_NT) {
+          const int u = w / rows, i = c0 + (w - u * rows);
+          const double s1 = rs[base + u];
+          if (s1 != 0.0) {
+            const double c1 = rc[base + u];
+            double* vp = a.V + (int64_t)pq[base + u].x * lp + i;
+            double* vq = a.V + (int64_t)pq[base + u].y * lp + i;
             const double xp = __ldcg(vp), xq = __ldcg(vq);
             __stcg(vp, c1 * xp - s1 * xq);
             __stcg(vq, s1 * xp + c1 * xq);
@@ -264,7 +295,7 @@ __global__ void __launch_bounds__(EIG_NT) k_jacobi(EigArgs a) {
       }
       if (!grid_barrier(a.bar, gridDim.x, a.info, &s_ok)) return;
     }
-    converged = !any;
+    converged = atomicAdd(a.rotcnt + sweep % 3, 0) == 0;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.info[1] = sweep;
@@ -362,7 +393,6 @@ cudaError_t eig_sym(const double* G, int64_t ldg, int l, double* C0, double* sna
   e = launched();
   if (e != cudaSuccess) return e;
   const int nb2 = lp / 2;
-  const size_t smem = (size_t)nb2 * 32;
   static std::atomic<bool> attr{false};  // concurrent first calls set it twice, harmlessly
   if (!attr.load(std::memory_order_acquire)) {
     e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -372,14 +402,18 @@ cudaError_t eig_sym(const double* G, int64_t ldg, int l, double* C0, double* sna
   int dev = 0, sms = 0, occ = 0;
   e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // S pair slices -> S (S + 1) / 2 CTAs, about one per SM (and co-resident)
+  int S = 1;
+  while (S < nb2 && (S + 1) * (S + 2) / 2 <= sms) ++S;
+  const int sz = (nb2 + S - 1) / S;
+  const size_t smem = (size_t)2 * sz * 32;
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi, EIG_NT, smem);
   if (e != cudaSuccess) return e;
-  if (occ < 1) return cudaErrorInvalidConfiguration;
-  const int64_t tasks = (int64_t)nb2 * (nb2 + 1) / 2 + (int64_t)l * nb2;
-  int64_t grid = (tasks + EIG_NT - 1) / EIG_NT;
-  grid = std::min<int64_t>(grid, (int64_t)occ * sms);
-  grid = std::max<int64_t>(grid, 1);
-  EigArgs a{C0, snap, V, l, lp, max_sweeps, tol, bar, info};
+  if (occ < 1 || S * (S + 1) / 2 > occ * sms) return cudaErrorInvalidConfiguration;
+  const int64_t grid = (int64_t)S * (S + 1) / 2;
+  e = cudaMemsetAsync(bar + 2, 0, 3 * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  EigArgs a{C0, snap, V, l, lp, max_sweeps, S, sz, tol, bar, reinterpret_cast<int*>(bar + 2), info};
   void* args[] = {&a};
   e = cudaLaunchCooperativeKernel((const void*)k_jacobi, dim3((unsigned)grid), dim3(EIG_NT), args,
                                   smem, st);

@@ -706,7 +706,7 @@ lra_status svd_alloc(lra_ctx* ctx, int64_t l) {
   CK(dalloc(ctx, &w.btrowE, n));
   CK(dalloc(ctx, &w.btcolE, l));
   CK(dalloc(ctx, &w.qrowE, m));
-  CK(dalloc(ctx, &w.bar, 2));
+  CK(dalloc(ctx, &w.bar, 5));
   w.cap = l;
   return LRA_OK;
 }
