@@ -127,32 +127,41 @@ __global__ void __launch_bounds__(1024) k_total(const double* __restrict__ v, in
   }
 }
 
-// Upper Cholesky R of S (b <= 64) and R^{-1}, right-looking so that every step is
-// one parallel update over the CTA: at column c the pivot d = S_cc - sum_{k<c} R_kc^2
-// (the trailing block already holds the subtracted sum) must pass d > tau * S_cc
-// (original diagonal) and be finite; with r = 1/sqrt(d), R_cc = d r and row c of R
-// is the pivot row times r; the trailing block loses the outer product of that
-// row.  R^{-1} by back substitution over rows, bottom up: row k of X is final once
-// scaled by r_k = 1/R_kk, then it is subtracted, times R_ik, from every row i < k.
+// Upper Cholesky R of S (b <= 64) and R^{-1}, right-looking: at column c the
+// pivot d = S_cc - sum_{k<c} R_kc^2 (the trailing block already holds the
+// subtracted sum) must pass d > tau * S_cc (original diagonal) and be finite;
+// with r = 1/sqrt(d), R_cc = d r and row c of R is the pivot row times r; the
+// trailing block loses the outer product of that row.  R^{-1} comes out of the
+// same sweep as Z^T, Z = L^{-1} for L = R^T by forward substitution: once row c
+// of R (column c of L) and r are known, row c of Z is row c of the reduced
+// right-hand side (the identity at the start) times r, and every row i > c of
+// the right-hand side loses R_ci times it.  Both updates are one FMA per
+// element; Z is lower triangular, so only columns <= c change.
 //
-// The FP64 pipe is narrow (a warp instruction occupies it for many cycles), so no
-// lane may idle: the trailing-update pairs (i, j), c < i <= j, are read from a
-// table of all pairs i <= j sorted by i descending -- those of step c are its
-// first (b - c)(b - c + 1) / 2 entries -- and the back-substitution pairs
-// (i < k <= j) are numbered densely, i = e mod k, j = k + e div k.
+// GB300's FP64 pipe retires about one warp instruction per 64 cycles per
+// scheduler, and one dependent FP64 operation takes as long, so the sweep is
+// laid out around the chain of pivots: while six worker warps apply column c's
+// updates, thread 0 already finishes pivot c + 1 (its last update, the test and
+// the reciprocal square root); warp 4, which shares thread 0's scheduler, keeps
+// off the FP64 pipe meanwhile.  Two barriers per column.  The trailing pairs
+// (i, j), c < i <= j, come from a table of all pairs i <= j sorted by i
+// descending (those of column c are its first (b-1-c)(b-c)/2 entries); the Z
+// updates (i > c, j <= c) are numbered densely, i = c + 1 + f div (c + 1).
 __global__ void __launch_bounds__(256) k_chol_inv(const double* __restrict__ S, int b, double tau,
                                                   double* __restrict__ Rinv, int* __restrict__ flags) {
-  __shared__ double M[64][65];
-  __shared__ double X[64][65];
-  __shared__ double Sd[64];
-  __shared__ double dinv[64];
+  constexpr int NWORK = 192;
+  __shared__ double M[64][65];  // trailing block (upper triangle); row c becomes row c of R
+  __shared__ double Z[64][65];  // right-hand side, rows of Z once final (lower triangle)
+  __shared__ double Sd[64], dpiv[64], rpiv[64];
   __shared__ uint16_t pairs[64 * 65 / 2];  // (i << 8) | j, i <= j, i descending
   __shared__ int bad;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, warp = t >> 5;
+  // workers: warps 1, 2, 3, 5, 6, 7 (index 0 .. 191); thread 0 takes the pivots
+  const int wk = (warp == 0 || warp == 4) ? -1 : (warp < 4 ? warp - 1 : warp - 2) * 32 + (t & 31);
   for (int e = t; e < b * b; e += 256) {
     const int i = e % b, j = e / b;
     M[i][j] = S[i + j * b];
-    X[i][j] = (i == j) ? 1.0 : 0.0;
+    Z[i][j] = (i == j) ? 1.0 : 0.0;
   }
   // entry e of the pair table: rows b-1, b-2, ... in turn, row i holding j = i..b-1;
   // the rows above i (i' > i) take sum_{i' > i} (b - i') = (b-1-i)(b-i)/2 entries
@@ -161,29 +170,46 @@ __global__ void __launch_bounds__(256) k_chol_inv(const double* __restrict__ S, 
     for (int j = i; j < b; ++j) pairs[base + (j - i)] = (uint16_t)((i << 8) | j);
   }
   if (t < b) Sd[t] = S[t + t * b];
-  if (t == 0) bad = 0;
+  if (t == 0) {
+    const double d = S[0];
+    bad = !(isfinite(d) && d > tau * d);
+    dpiv[0] = d;
+    rpiv[0] = bad ? 0.0 : rsqrt(d);
+  }
   __syncthreads();
   for (int c = 0; c < b; ++c) {
-    if (t == 0) {
-      const double d = M[c][c];
-      if (!(isfinite(d) && d > tau * Sd[c])) {
-        bad = 1;
-      } else {
-        const double r = rsqrt(d);
-        M[c][c] = d * r;
-        dinv[c] = r;
-      }
-    }
-    __syncthreads();
-    if (bad) break;
-    const double r = dinv[c];
-    for (int j = c + 1 + t; j < b; j += 256) M[c][j] *= r;
+    if (bad) break;  // set before the last barrier: the same decision in every thread
+    const double r = rpiv[c];
+    // row c of R (R_cc = d r) and row c of Z
+    for (int j = c + t; j < b; j += 256) M[c][j] = (j == c) ? dpiv[c] * r : M[c][j] * r;
+    for (int j = t; j <= c; j += 256) Z[c][j] *= r;
     __syncthreads();
     const int nt = b - c - 1;
-    const int count = nt * (nt + 1) / 2;
-    for (int e = t; e < count; e += 256) {
-      const int ij = pairs[e], i = ij >> 8, j = ij & 255;
-      M[i][j] -= M[c][i] * M[c][j];
+    if (t == 0) {
+      if (nt > 0) {
+        const double rc1 = M[c][c + 1];
+        const double d = fma(-rc1, rc1, M[c + 1][c + 1]);
+        if (!(isfinite(d) && d > tau * Sd[c + 1])) {
+          bad = 1;
+        } else {
+          dpiv[c + 1] = d;
+          rpiv[c + 1] = rsqrt(d);
+        }
+      }
+    } else if (wk >= 0) {
+      const int ntrail = nt * (nt + 1) / 2, ntot = ntrail + nt * (c + 1);
+      const float kinv = 1.0f / (float)(c + 1);
+      for (int e = wk; e < ntot; e += NWORK) {
+        if (e < ntrail) {
+          const int ij = pairs[e], i = ij >> 8, j = ij & 255;
+          if (i != c + 1 || j != c + 1) M[i][j] = fma(-M[c][i], M[c][j], M[i][j]);  // pivot: thread 0
+        } else {
+          const int f = e - ntrail;
+          const int q = (int)(((float)f + 0.5f) * kinv);  // f div (c + 1); f < 4096, exact enough
+          const int j = f - q * (c + 1), i = c + 1 + q;
+          Z[i][j] = fma(-M[c][i], Z[c][j], Z[i][j]);
+        }
+      }
     }
     __syncthreads();
   }
@@ -192,25 +218,10 @@ __global__ void __launch_bounds__(256) k_chol_inv(const double* __restrict__ S, 
     for (int e = t; e < b * b; e += 256) Rinv[e] = 0.0;
     return;
   }
-  for (int k = b - 1; k >= 0; --k) {
-    const double r = dinv[k];
-    for (int j = k + t; j < b; j += 256) X[k][j] *= r;
-    __syncthreads();
-    const int count = k * (b - k);
-    if (count > 0) {
-      const float kinv = 1.0f / (float)k;
-      for (int e = t; e < count; e += 256) {
-        int q = (int)(((float)e + 0.5f) * kinv);  // e div k (e < 4096: the float is exact enough)
-        const int i = e - q * k;
-        const int j = k + q;
-        X[i][j] -= M[i][k] * X[k][j];
-      }
-    }
-    __syncthreads();
-  }
+  // R^{-1} = Z^T
   for (int e = t; e < b * b; e += 256) {
     const int i = e % b, j = e / b;
-    Rinv[i + j * b] = X[i][j];
+    Rinv[i + j * b] = i <= j ? Z[j][i] : 0.0;
   }
 }
 

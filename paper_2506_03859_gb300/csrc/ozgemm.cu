@@ -860,30 +860,43 @@ __global__ void __launch_bounds__(NPROD) k_oz_xcut(OzArgs a, uint8_t* __restrict
 }
 
 // Combine the partial tiles of tiles split across CTAs, in a fixed order.  Grid:
-// (tiles, TM * NN * LANES / 256); each CTA handles 256 / LANES elements of its tile
+// (tiles, ceil(TM N LANES / 256)); the elements of tile t (rows_t x N of them,
+// row index fastest) are numbered densely and each CTA takes 256 / LANES of them
 // with LANES threads per element: thread l sums the partials of the contributing
-// CTAs cf + l, cf + l + LANES, ... in CTA order, and the LANES sums are added in
-// lane order.  Tile t is covered by CTAs cf..cl; every one of them but cf starts
-// its range inside t, so t is its first tile (slot 0); cf holds t in slot 1
-// unless its range also starts inside t.  CTAs with an empty range (more CTAs
+// CTAs cf + l, cf + l + LANES, ... in CTA order (four running sums, so that four
+// loads are in flight, combined in a fixed order), and the LANES sums are added
+// in lane order.  Tile t is covered by CTAs cf..cl; every one of them but cf
+// starts its range inside t, so t is its first tile (slot 0); cf holds t in slot
+// 1 unless its range also starts inside t.  CTAs with an empty range (more CTAs
 // than units) wrote nothing and are skipped.
+//
+// CTA c's range starts at floor(c T / G), so the owner of unit u (the last CTA
+// whose range starts at or before u) is floor(((u + 1) G - 1) / T), and cf's
+// range starts inside t exactly when cf T >= t kst G.  The owner is estimated in
+// FP32 and corrected with exact integer products (no 64-bit division).
+__device__ __forceinline__ int64_t oz_owner(int64_t u, int64_t T, int64_t G) {
+  const int64_t x = (u + 1) * G - 1;
+  int64_t c = (int64_t)((float)x / (float)T);
+  while (c > 0 && c * T > x) --c;
+  while ((c + 1) * T <= x) ++c;
+  return c;
+}
+
 template <int LANES>
-__global__ void __launch_bounds__(256) k_oz_fixup(OzArgs a, int G) {
+__global__ void __launch_bounds__(256, 6) k_oz_fixup(OzArgs a, int G) {
   constexpr int ELEMS = 256 / LANES;
   __shared__ int64_t s_cf, s_cl;
   __shared__ int s_slot_f;
   const int64_t t = blockIdx.x;
   const int64_t T = a.tiles * a.kst;
+  const int rows_t = (int)min((int64_t)TM, a.P - t * TM);
+  const int nel = rows_t * (int)min(a.N, (int64_t)NN);
+  if ((int)blockIdx.y * ELEMS >= nel) return;  // the whole CTA
   if (threadIdx.x == 0) {
-    auto owner = [&](int64_t u) {
-      int64_t c = u * G / T;
-      while (c + 1 < G && (c + 1) * T / G <= u) ++c;
-      while (c > 0 && c * T / G > u) --c;
-      return c;
-    };
-    s_cf = owner(t * a.kst);
-    s_cl = owner((t + 1) * a.kst - 1);
-    s_slot_f = ((s_cf * T / G) / a.kst == t) ? 0 : 1;
+    const int64_t cf = oz_owner(t * a.kst, T, G);
+    s_cf = cf;
+    s_cl = oz_owner((t + 1) * a.kst - 1, T, G);
+    s_slot_f = (cf * T >= t * a.kst * G) ? 0 : 1;
   }
   __syncthreads();
   const int64_t cf = s_cf, cl = s_cl;
@@ -891,13 +904,11 @@ __global__ void __launch_bounds__(256) k_oz_fixup(OzArgs a, int G) {
   const int slot_f = s_slot_f;
   const int lane = threadIdx.x % LANES;
   const int e = blockIdx.y * ELEMS + threadIdx.x / LANES;
-  const int r = e % TM, c = e / TM;
+  const bool valid = e < nel;  // the same in the LANES threads of an element
+  const int c = valid ? e / rows_t : 0, r = valid ? e - c * rows_t : 0;
   const int64_t p = t * TM + r;
-  const bool valid = p < a.P && c < a.N;
   const double* src = a.part + (int64_t)c * TM + r;
   const bool all_nonempty = T >= G;  // then every CTA's range holds a unit
-  // four independent running sums over the lane's partials (the k-th takes every
-  // fourth), so that four loads are in flight; combined in a fixed order
   auto part = [&](int64_t q) -> double {
     const int slot = (q == cf) ? slot_f : 0;
     return (all_nonempty || q * T / G < (q + 1) * T / G) ? src[(q * 2 + slot) * (int64_t)(NN * TM)]
@@ -913,7 +924,9 @@ __global__ void __launch_bounds__(256) k_oz_fixup(OzArgs a, int G) {
       s2 += v2;
       s3 += v3;
     }
-    for (; q <= cl; q += LANES) s0 += part(q);
+    if (q <= cl) s0 += part(q);  // fewer than four left
+    if (q + LANES <= cl) s1 += part(q + LANES);
+    if (q + 2 * LANES <= cl) s2 += part(q + 2 * LANES);
   }
   double s = (s0 + s1) + (s2 + s3);
   // lanes of one element are adjacent threads of one warp
@@ -928,14 +941,18 @@ __global__ void __launch_bounds__(256) k_oz_fixup(OzArgs a, int G) {
   }
 }
 
-// The fixup launch: one lane per element when a CTA's range spans a tile or more
-// (a tile then has two or three parts), four when tiles span many CTAs.
+// The fixup launch: lanes per element by the number of CTAs that share a tile
+// (about G kst / T + 1): one up to eight sharers, four up to 64, sixteen beyond.
 cudaError_t launch_fixup(const OzArgs& a, int G, cudaStream_t st) {
   const int64_t T = a.tiles * a.kst;
-  if (T >= (int64_t)G * a.kst) {
-    k_oz_fixup<1><<<dim3((unsigned)a.tiles, TM * NN / 256), 256, 0, st>>>(a, G);
+  const int64_t elems = (int64_t)TM * std::min<int64_t>(a.N, NN);
+  const int64_t sharers = (int64_t)G * a.kst / std::max<int64_t>(T, 1) + 1;
+  if (sharers <= 8) {
+    k_oz_fixup<1><<<dim3((unsigned)a.tiles, (unsigned)((elems + 255) / 256)), 256, 0, st>>>(a, G);
+  } else if (sharers <= 64) {
+    k_oz_fixup<4><<<dim3((unsigned)a.tiles, (unsigned)((elems * 4 + 255) / 256)), 256, 0, st>>>(a, G);
   } else {
-    k_oz_fixup<4><<<dim3((unsigned)a.tiles, TM * NN * 4 / 256), 256, 0, st>>>(a, G);
+    k_oz_fixup<16><<<dim3((unsigned)a.tiles, (unsigned)((elems * 16 + 255) / 256)), 256, 0, st>>>(a, G);
   }
   return launched();
 }
