@@ -138,34 +138,37 @@ __global__ void __launch_bounds__(1024) k_total(const double* __restrict__ v, in
 // the right-hand side loses R_ci times it.  Both updates are one FMA per
 // element; Z is lower triangular, so only columns <= c change.
 //
-// GB300's FP64 pipe retires about one warp instruction per 64 cycles per
-// scheduler, and one dependent FP64 operation takes as long, so the sweep is
-// laid out around the chain of pivots: while six worker warps apply column c's
-// updates, thread 0 already finishes pivot c + 1 (its last update, the test and
-// the reciprocal square root); warp 4, which shares thread 0's scheduler, keeps
-// off the FP64 pipe meanwhile.  Two barriers per column.  The trailing pairs
+// On GB300 one dependent FP64 operation takes ~64 cycles and the SM's FP64 pipe
+// retires about one warp instruction per ~19 cycles, so the sweep is laid out
+// around the chain of pivots: while the other 31 warps apply column c's updates
+// (about one element each, so that the index arithmetic and shared-memory
+// latencies of an update overlap across warps instead of queueing in a few),
+// thread 0 already finishes pivot c + 1 (its last update, the test and the
+// reciprocal square root).  Two barriers per column.  The trailing pairs
 // (i, j), c < i <= j, come from a table of all pairs i <= j sorted by i
 // descending (those of column c are its first (b-1-c)(b-c)/2 entries); the Z
 // updates (i > c, j <= c) are numbered densely, i = c + 1 + f div (c + 1).
-__global__ void __launch_bounds__(256) k_chol_inv(const double* __restrict__ S, int b, double tau,
-                                                  double* __restrict__ Rinv, int* __restrict__ flags) {
-  constexpr int NWORK = 192;
+constexpr int CHOL_NT = 1024;
+
+__global__ void __launch_bounds__(CHOL_NT) k_chol_inv(const double* __restrict__ S, int b, double tau,
+                                                      double* __restrict__ Rinv, int* __restrict__ flags) {
+  constexpr int NWORK = CHOL_NT - 32;
   __shared__ double M[64][65];  // trailing block (upper triangle); row c becomes row c of R
   __shared__ double Z[64][65];  // right-hand side, rows of Z once final (lower triangle)
   __shared__ double Sd[64], dpiv[64], rpiv[64];
   __shared__ uint16_t pairs[64 * 65 / 2];  // (i << 8) | j, i <= j, i descending
   __shared__ int bad;
-  const int t = threadIdx.x, warp = t >> 5;
-  // workers: warps 1, 2, 3, 5, 6, 7 (index 0 .. 191); thread 0 takes the pivots
-  const int wk = (warp == 0 || warp == 4) ? -1 : (warp < 4 ? warp - 1 : warp - 2) * 32 + (t & 31);
-  for (int e = t; e < b * b; e += 256) {
+  const int t = threadIdx.x;
+  // workers: warps 1 .. 31; thread 0 takes the pivots
+  const int wk = t - 32;
+  for (int e = t; e < b * b; e += CHOL_NT) {
     const int i = e % b, j = e / b;
     M[i][j] = S[i + j * b];
     Z[i][j] = (i == j) ? 1.0 : 0.0;
   }
   // entry e of the pair table: rows b-1, b-2, ... in turn, row i holding j = i..b-1;
   // the rows above i (i' > i) take sum_{i' > i} (b - i') = (b-1-i)(b-i)/2 entries
-  for (int i = t; i < b; i += 256) {
+  for (int i = t; i < b; i += CHOL_NT) {
     const int base = (b - 1 - i) * (b - i) / 2;
     for (int j = i; j < b; ++j) pairs[base + (j - i)] = (uint16_t)((i << 8) | j);
   }
@@ -181,8 +184,8 @@ __global__ void __launch_bounds__(256) k_chol_inv(const double* __restrict__ S, 
     if (bad) break;  // set before the last barrier: the same decision in every thread
     const double r = rpiv[c];
     // row c of R (R_cc = d r) and row c of Z
-    for (int j = c + t; j < b; j += 256) M[c][j] = (j == c) ? dpiv[c] * r : M[c][j] * r;
-    for (int j = t; j <= c; j += 256) Z[c][j] *= r;
+    if (t >= c && t < b) M[c][t] = (t == c) ? dpiv[c] * r : M[c][t] * r;
+    else if (t >= 64 && t - 64 <= c) Z[c][t - 64] *= r;
     __syncthreads();
     const int nt = b - c - 1;
     if (t == 0) {
@@ -215,11 +218,11 @@ __global__ void __launch_bounds__(256) k_chol_inv(const double* __restrict__ S, 
   }
   if (bad) {
     if (t == 0) atomicOr(flags, FLAG_BREAKDOWN);
-    for (int e = t; e < b * b; e += 256) Rinv[e] = 0.0;
+    for (int e = t; e < b * b; e += CHOL_NT) Rinv[e] = 0.0;
     return;
   }
   // R^{-1} = Z^T
-  for (int e = t; e < b * b; e += 256) {
+  for (int e = t; e < b * b; e += CHOL_NT) {
     const int i = e % b, j = e / b;
     Rinv[i + j * b] = i <= j ? Z[j][i] : 0.0;
   }
@@ -274,7 +277,7 @@ cudaError_t total(const double* v, int64_t count, double* out, cudaStream_t st) 
 }
 
 cudaError_t chol_inv(const double* S, int b, double tau, double* Rinv, int* flags, cudaStream_t st) {
-  k_chol_inv<<<1, 256, 0, st>>>(S, b, tau, Rinv, flags);
+  k_chol_inv<<<1, CHOL_NT, 0, st>>>(S, b, tau, Rinv, flags);
   return launched();
 }
 

@@ -864,8 +864,8 @@ __global__ void __launch_bounds__(NPROD) k_oz_xcut(OzArgs a, uint8_t* __restrict
 // row index fastest) are numbered densely and each CTA takes 256 / LANES of them
 // with LANES threads per element: thread l sums the partials of the contributing
 // CTAs cf + l, cf + l + LANES, ... in CTA order (four running sums, so that four
-// loads are in flight, combined in a fixed order), and the LANES sums are added
-// in lane order.  Tile t is covered by CTAs cf..cl; every one of them but cf
+// loads are in flight, combined in a fixed order; one sum when LANES = 1), and
+// the LANES sums are added in lane order.  Tile t is covered by CTAs cf..cl; every one of them but cf
 // starts its range inside t, so t is its first tile (slot 0); cf holds t in slot
 // 1 unless its range also starts inside t.  CTAs with an empty range (more CTAs
 // than units) wrote nothing and are skipped.
@@ -914,8 +914,13 @@ __global__ void __launch_bounds__(256, 6) k_oz_fixup(OzArgs a, int G) {
     return (all_nonempty || q * T / G < (q + 1) * T / G) ? src[(q * 2 + slot) * (int64_t)(NN * TM)]
                                                           : 0.0;
   };
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  if (valid) {
+  double s = 0.0;
+  if (valid && LANES == 1) {
+    // a few partials: one running sum (the FP64 pipe, not memory, limits this case)
+    s = part(cf);
+    for (int64_t q = cf + 1; q <= cl; ++q) s += part(q);
+  } else if (valid) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int64_t q = cf + lane;
     for (; q + 3 * LANES <= cl; q += 4 * LANES) {
       const double v0 = part(q), v1 = part(q + LANES), v2 = part(q + 2 * LANES), v3 = part(q + 3 * LANES);
@@ -927,8 +932,8 @@ __global__ void __launch_bounds__(256, 6) k_oz_fixup(OzArgs a, int G) {
     if (q <= cl) s0 += part(q);  // fewer than four left
     if (q + LANES <= cl) s1 += part(q + LANES);
     if (q + 2 * LANES <= cl) s2 += part(q + 2 * LANES);
+    s = (s0 + s1) + (s2 + s3);
   }
-  double s = (s0 + s1) + (s2 + s3);
   // lanes of one element are adjacent threads of one warp
 #pragma unroll
   for (int o = 1; o < LANES; o <<= 1) {
@@ -937,7 +942,8 @@ __global__ void __launch_bounds__(256, 6) k_oz_fixup(OzArgs a, int G) {
   }
   if (lane == 0 && valid) {
     double* dst = a.C + p * a.csp + (int64_t)c * a.csc;
-    *dst = (a.beta == 0.0) ? a.alpha * s : a.alpha * s + a.beta * (*dst);
+    const double as = (a.alpha == 1.0) ? s : a.alpha * s;
+    *dst = (a.beta == 0.0) ? as : as + a.beta * (*dst);
   }
 }
 
