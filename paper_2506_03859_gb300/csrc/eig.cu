@@ -48,29 +48,27 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 }
 
 // Grid-wide barrier for a cooperative launch (all CTAs resident).  bar[0]
-// counts arrivals, bar[1] is the generation.  Returns false when this CTA gave
-// up waiting (and set FLAG_TIMEOUT in *info); the other CTAs then give up at
-// their next wait, each after the same bounded spin.
-__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* info, int* s_ok) {
+// counts arrivals over the whole launch and is never reset: the k-th barrier
+// (k = 0, 1, ...) is passed once it reaches nblocks (k + 1), so an arrival is
+// one fire-and-forget reduction and the release needs no extra step by the last
+// CTA (the count stays below 2^32 for any launch: nblocks * rounds).  Returns
+// false when this CTA gave up waiting (and set FLAG_TIMEOUT in *info); the
+// other CTAs then give up at their next wait, each after the same bounded spin.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned passed, int* info, int* s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
+    const unsigned target = nblocks * (passed + 1u);
     __threadfence();
-    const unsigned g = ld_acquire(bar + 1);
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar), "r"(1u) : "memory");
     int ok = 1;
-    if (atomicAdd(bar, 1u) == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long it = 0;
-      while (ld_acquire(bar + 1) == g) {
-        if (++it > EIG_SPIN_LIMIT) {
-          atomicOr(info, FLAG_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
+    long long it = 0;
+    while ((int)(ld_acquire(bar) - target) < 0) {
+      if (++it > EIG_SPIN_LIMIT) {
+        atomicOr(info, FLAG_TIMEOUT);
+        ok = 0;
+        break;
       }
+      __nanosleep(32);
     }
     __threadfence();
     *s_ok = ok;
@@ -139,7 +137,7 @@ struct EigArgs {
   int l, lp, max_sweeps;
   int S, sz;      // pair slices of a round (S (S + 1) / 2 CTAs), pairs per slice
   double tol;
-  unsigned* bar;  // 2 words, zero at launch
+  unsigned* bar;  // arrival count, zero at launch
   int* rotcnt;    // 3 per-sweep rotation counters, zero at launch
   int* info;      // [0] flags, [1] sweeps, [2] converged, [3] 0
 };
@@ -293,7 +291,7 @@ __global__ void __launch_bounds__(EIG_NT) k_jacobi(EigArgs a) {
           }
         }
       }
-      if (!grid_barrier(a.bar, gridDim.x, a.info, &s_ok)) return;
+      if (!grid_barrier(a.bar, gridDim.x, (unsigned)g, a.info, &s_ok)) return;
     }
     converged = atomicAdd(a.rotcnt + sweep % 3, 0) == 0;
   }
