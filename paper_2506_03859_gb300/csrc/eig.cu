@@ -23,7 +23,9 @@
 // counter (three slots in turn, so that one is read, one filled and one cleared
 // in any sweep); a sweep whose count is zero ends the iteration, a decision
 // every CTA reads after the same barrier.  A block whose two rotations are
-// both the identity is left as it is.
+// both the identity is left as it is.  A thread's first block and first
+// eigenvector rows are loaded before the round's rotations are computed (their
+// indices depend on the round alone), so those loads overlap the rotations.
 // A pair is skipped when |c_pq| <= tol sqrt(|c_pp c_qq|): the relative
 // criterion under which Jacobi keeps the small eigenvalues of a positive
 // definite matrix to high relative accuracy (Demmel and Veselic, SIAM J. Matrix
@@ -154,6 +156,19 @@ __device__ __forceinline__ void snap_put(double* nsnap, int x, int y, double v, 
   nsnap[3 * kx + slot] = v;
 }
 
+// Block w of a CTA's 2 x 2 blocks: (i, j) = (w div nbk, w mod nbk) for two
+// different slices, else i <= j within the slice with w = j (j + 1) / 2 + i.
+__device__ __forceinline__ void block_of(int w, bool two, int nbk, int& i, int& j) {
+  if (two) {
+    i = w / nbk;
+    j = w - i * nbk;
+  } else {
+    j = 0;
+    while ((j + 1) * (j + 2) / 2 <= w) ++j;
+    i = w - j * (j + 1) / 2;
+  }
+}
+
 // The pairs of a round are cut into S slices of sz consecutive pair indices; CTA
 // (ka, kb), ka <= kb, applies the 2 x 2 blocks (P, R) with P in slice ka and R
 // in slice kb (P <= R), and rotates the eigenvector rows of slice ka in row
@@ -183,6 +198,39 @@ __global__ void __launch_bounds__(EIG_NT) k_jacobi(EigArgs a) {
       const double* csnap = a.snap + (g & 1) * 3 * nb2;
       double* nsnap = a.snap + ((g + 1) & 1) * 3 * nb2;
       const int tn = t + 1 == M ? 0 : t + 1;
+      // The thread's first 2 x 2 block and first eigenvector rows are loaded
+      // before the rotations are known: their indices depend on the round alone,
+      // so the loads overlap the rotation arithmetic.
+      const int nblk = ka < kb ? na * nbk : na * (na + 1) / 2;
+      double pz[4] = {0.0, 0.0, 0.0, 0.0}, pv[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+      if ((int)threadIdx.x < nblk) {
+        int i, j, p, q;
+        block_of((int)threadIdx.x, ka < kb, nbk, i, j);
+        round_pair(a0 + i, t, lp, p, q);
+        if (ka == kb && i == j) {
+          pz[0] = __ldcg(C + (int64_t)p * lp + p);
+          pz[1] = __ldcg(C + (int64_t)q * lp + q);
+          pz[2] = __ldcg(C + (int64_t)q * lp + p);
+        } else {
+          int r, s2i;
+          round_pair((ka < kb ? b0 : a0) + j, t, lp, r, s2i);
+          pz[0] = __ldcg(C + (int64_t)r * lp + p);
+          pz[1] = __ldcg(C + (int64_t)s2i * lp + p);
+          pz[2] = __ldcg(C + (int64_t)r * lp + q);
+          pz[3] = __ldcg(C + (int64_t)s2i * lp + q);
+        }
+      }
+      for (int part = 0; part < (ka < kb ? 2 : 1); ++part) {
+        const int np = part ? nbk : na, c0 = (part ? ka : kb) * rch;
+        const int rows = max(0, min(a.l, c0 + rch) - c0);
+        if ((int)threadIdx.x < np * rows) {
+          const int u = (int)threadIdx.x / rows, i = c0 + ((int)threadIdx.x - u * rows);
+          int p, q;
+          round_pair((part ? b0 : a0) + u, t, lp, p, q);
+          pv[part][0] = __ldcg(a.V + (int64_t)p * lp + i);
+          pv[part][1] = __ldcg(a.V + (int64_t)q * lp + i);
+        }
+      }
       // the rotations of the CTA's two slices: from C itself before the first
       // round, else from the snapshot the previous round wrote
       int rotated = 0;
@@ -214,24 +262,17 @@ __global__ void __launch_bounds__(EIG_NT) k_jacobi(EigArgs a) {
       const int cnt = __syncthreads_count(rotated);
       if (cnt && threadIdx.x == 0) atomicAdd(a.rotcnt + sweep % 3, cnt);
       // 2 x 2 blocks (P, R): P in slice ka (slot i), R in slice kb (slot sz + j)
-      const int nblk = ka < kb ? na * nbk : na * (na + 1) / 2;
       for (int w = threadIdx.x; w < nblk; w += EIG_NT) {
+        const bool first = w == (int)threadIdx.x;
         int i, j;
-        if (ka < kb) {
-          i = w / nbk;
-          j = w - i * nbk;
-        } else {  // i <= j within the slice: w = j (j + 1) / 2 + i
-          j = 0;
-          while ((j + 1) * (j + 2) / 2 <= w) ++j;
-          i = w - j * (j + 1) / 2;
-        }
+        block_of(w, ka < kb, nbk, i, j);
         const int sP = i, sR = ka < kb ? sz + j : j;
         const int p = pq[sP].x, q = pq[sP].y;
         const double c1 = rc[sP], s1 = rs[sP];
         if (ka == kb && i == j) {
-          double npp = __ldcg(C + (int64_t)p * lp + p);
-          double nqq = __ldcg(C + (int64_t)q * lp + q);
-          double npq = __ldcg(C + (int64_t)q * lp + p);
+          double npp = first ? pz[0] : __ldcg(C + (int64_t)p * lp + p);
+          double nqq = first ? pz[1] : __ldcg(C + (int64_t)q * lp + q);
+          double npq = first ? pz[2] : __ldcg(C + (int64_t)q * lp + p);
           if (s1 != 0.0) {
             const double apq = npq;
             npp = fma(-rt[sP], apq, npp);
@@ -248,8 +289,18 @@ __global__ void __launch_bounds__(EIG_NT) k_jacobi(EigArgs a) {
         } else {
           const int r = pq[sR].x, s2i = pq[sR].y;
           const double c2 = rc[sR], s2 = rs[sR];
-          double z00 = __ldcg(C + (int64_t)r * lp + p), z01 = __ldcg(C + (int64_t)s2i * lp + p);
-          double z10 = __ldcg(C + (int64_t)r * lp + q), z11 = __ldcg(C + (int64_t)s2i * lp + q);
+          double z00, z01, z10, z11;
+          if (first) {
+            z00 = pz[0];
+            z01 = pz[1];
+            z10 = pz[2];
+            z11 = pz[3];
+          } else {
+            z00 = __ldcg(C + (int64_t)r * lp + p);
+            z01 = __ldcg(C + (int64_t)s2i * lp + p);
+            z10 = __ldcg(C + (int64_t)r * lp + q);
+            z11 = __ldcg(C + (int64_t)s2i * lp + q);
+          }
           if (s1 != 0.0 || s2 != 0.0) {
             // Y = J_P^T X, then X' = Y J_R
             const double y00 = c1 * z00 - s1 * z10, y01 = c1 * z01 - s1 * z11;
@@ -285,7 +336,8 @@ __global__ void __launch_bounds__(EIG_NT) k_jacobi(EigArgs a) {
             const double c1 = rc[base + u];
             double* vp = a.V + (int64_t)pq[base + u].x * lp + i;
             double* vq = a.V + (int64_t)pq[base + u].y * lp + i;
-            const double xp = __ldcg(vp), xq = __ldcg(vq);
+            const bool first = w == (int)threadIdx.x;
+            const double xp = first ? pv[part][0] : __ldcg(vp), xq = first ? pv[part][1] : __ldcg(vq);
             __stcg(vp, c1 * xp - s1 * xq);
             __stcg(vq, s1 * xp + c1 * xq);
           }
