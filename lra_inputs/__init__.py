@@ -68,7 +68,7 @@ def exact_rank_matrix(m, n, r, seed, spectrum="poly1"):
     return low_rank_matrix(m, n, spectrum, seed, rank=r)
 
 
-# Named workloads: BASELINE-style configurations and the paper's Table 1 inputs.
+# Named workloads: the benchmark and parity-test matrices and the paper's Table 1 inputs.
 WORKLOADS = {
     # 2000 x 1000, sigma_i = i^-1.5, b = 20, P = 1, eps = 1e-2, zeta = 8
     "dense2000x1000_poly1.5": dict(m=2000, n=1000, spectrum="poly1.5", noise=0.0, seed=1001),
