@@ -331,6 +331,18 @@ int64_t lra_workspace_bytes(int64_t m, int64_t n, const lra_params* params);
 /* Device bytes the context has allocated so far; -1 for NULL. */
 int64_t lra_device_bytes(const lra_ctx* ctx);
 
+/* Diagnostic: runs the library's two kinds of bounded device wait (an
+   mbarrier wait as in the tensor-core GEMM, the grid barrier of the
+   eigensolver) against conditions that never come true, each with a short
+   limit (milliseconds).  Every wait of the library ends this way when its
+   limit runs out: the kernel records FLAG_TIMEOUT and returns, the call
+   reports LRA_ERR_TIMEOUT, and the device stays usable.  Returns
+   LRA_ERR_TIMEOUT when a wait gave up (the expected outcome: both), LRA_OK if
+   none did, LRA_ERR_CUDA on a launch or copy error; *which (may be NULL) gets
+   bit 0 for the mbarrier wait and bit 1 for the grid barrier.  Runs on its
+   own stream and synchronises it. */
+lra_status lra_selftest_waits(int* which);
+
 /* ---- Serving runtime: a stream of independent requests on one GPU --------
    Each request is a fixed-precision (or fixed-rank) farPCA run on its own
    matrix.  Requests are admitted in arrival order when a worker slot is free

@@ -36,6 +36,7 @@
 #include <algorithm>
 
 #include "internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace lra {
 namespace {
@@ -56,7 +57,8 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 // CTA (the count stays below 2^32 for any launch: nblocks * rounds).  Returns
 // false when this CTA gave up waiting (and set FLAG_TIMEOUT in *info); the
 // other CTAs then give up at their next wait, each after the same bounded spin.
-__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned passed, int* info, int* s_ok) {
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned passed, int* info, int* s_ok,
+                             long long limit = EIG_SPIN_LIMIT) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned target = nblocks * (passed + 1u);
@@ -65,7 +67,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned passed, i
     int ok = 1;
     long long it = 0;
     while ((int)(ld_acquire(bar) - target) < 0) {
-      if (++it > EIG_SPIN_LIMIT) {
+      if (++it > limit) {
         atomicOr(info, FLAG_TIMEOUT);
         ok = 0;
         break;
@@ -422,6 +424,20 @@ __global__ void k_transpose(const double* __restrict__ B, int64_t ldb, int64_t l
   }
 }
 
+// The two kinds of bounded device wait, each against a condition that never
+// comes true: an mbarrier that expects one arrival nobody makes, and the grid
+// barrier of a two-CTA group launched with one CTA.  Both must give up after
+// their limit and report FLAG_TIMEOUT (info[0] bit 0: the mbarrier wait, bit 1:
+// the grid barrier), leaving the context usable.  One CTA of 32 threads.
+__global__ void k_wait_selftest(unsigned* bar, int* info) {
+  __shared__ uint64_t mb;
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) tc::mbar_init(&mb, 1);
+  __syncthreads();
+  if (threadIdx.x == 0 && !tc::mbar_wait(&mb, 0u, 1L << 14)) atomicOr(info, 1);
+  if (!grid_barrier(bar, 2u, 0u, info + 1, &s_ok, 1ll << 14) && threadIdx.x == 0) atomicOr(info, 2);
+}
+
 }  // namespace
 
 int64_t eig_padded(int64_t l) { return l + (l & 1); }
@@ -488,6 +504,30 @@ cudaError_t transpose(const double* B, int64_t ldb, int64_t l, int64_t n, double
   dim3 grid((unsigned)((n + 31) / 32), (unsigned)((l + 31) / 32));
   k_transpose<<<grid, dim3(32, 8), 0, st>>>(B, ldb, l, n, Bt, ldt);
   return launched();
+}
+
+// Runs k_wait_selftest on its own buffers; *which = the waits that gave up
+// (bit 0: mbarrier, bit 1: grid barrier).
+cudaError_t wait_selftest(int* which, cudaStream_t st) {
+  *which = 0;
+  int* buf = nullptr;  // [0] bar, [1] bits, [2] the grid barrier's flags
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), 4 * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(buf, 0, 4 * sizeof(int), st);
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, 32, 0, st>>>(reinterpret_cast<unsigned*>(buf), buf + 1);
+    e = cudaGetLastError();
+  }
+  int host[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, buf, sizeof(host), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(buf, st);
+  if (e == cudaSuccess) {
+    e = cudaStreamSynchronize(st);
+    *which = host[1] & 3;
+    if (!(host[2] & FLAG_TIMEOUT)) *which &= ~2;
+  }
+  return e;
 }
 
 }  // namespace lra

@@ -135,10 +135,12 @@ cudaError_t fill(double* X, int64_t ld, int64_t rows, int64_t cols, double v, cu
 // Cyclic Jacobi eigendecomposition of a symmetric l x l matrix given by the upper
 // triangle of G (ld ldg): one cooperative launch.  C, V: eig_padded(l)^2 doubles
 // each (the eigenvalues end on C's diagonal, the eigenvectors in V's columns);
-// snap: 3 eig_padded(l) doubles; bar: 5 words; info: 4 ints ([0] flags,
+// snap: 3 eig_padded(l) doubles; bar: 5 words (zeroed here); info: 4 ints ([0] flags,
 // FLAG_TIMEOUT if a barrier wait gave up; [1] sweeps; [2] converged; [3] 0).
 int64_t eig_padded(int64_t l);
 int64_t eig_max_l();
+// Bounded-wait self-test (k_wait_selftest): *which = the waits that gave up.
+cudaError_t wait_selftest(int* which, cudaStream_t st);
 cudaError_t eig_sym(const double* G, int64_t ldg, int l, double* C, double* snap, double* V,
                     int max_sweeps, double tol, unsigned* bar, int* info, cudaStream_t st);
 // sigma (l, descending) = sqrt of the eigenvalues on C's diagonal; Vs = V's

@@ -987,6 +987,18 @@ int64_t lra_workspace_bytes(int64_t m, int64_t n, const lra_params* params) {
 
 int64_t lra_device_bytes(const lra_ctx* ctx) { return ctx ? ctx->bytes : -1; }
 
+lra_status lra_selftest_waits(int* which) {
+  if (which) *which = 0;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return LRA_ERR_CUDA;
+  int w = 0;
+  const cudaError_t e = wait_selftest(&w, st);
+  cudaStreamDestroy(st);
+  if (e != cudaSuccess) return LRA_ERR_CUDA;
+  if (which) *which = w;
+  return w ? LRA_ERR_TIMEOUT : LRA_OK;
+}
+
 void lra_destroy(lra_ctx* ctx) {
   if (!ctx) return;
   if (ctx->st) cudaStreamSynchronize(ctx->st);

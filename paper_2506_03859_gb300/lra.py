@@ -34,7 +34,7 @@ EXPORTS = ("lra_create", "lra_destroy", "lra_capacity", "lra_sketch", "lra_farpc
            "lra_workspace_bytes", "lra_device_bytes", "lra_server_create", "lra_server_submit",
            "lra_server_poll", "lra_server_pending", "lra_server_release", "lra_server_clock",
            "lra_server_destroy", "lra_batch_create", "lra_batch_run", "lra_batch_result",
-           "lra_batch_steps", "lra_batch_device_bytes", "lra_batch_destroy")
+           "lra_batch_steps", "lra_batch_device_bytes", "lra_batch_destroy", "lra_selftest_waits")
 
 
 class Matrix(Structure):
@@ -144,6 +144,8 @@ def load(path=LIB_PATH):
     lib.lra_workspace_bytes.restype = c_int64
     lib.lra_device_bytes.argtypes = [vp]
     lib.lra_device_bytes.restype = c_int64
+    lib.lra_selftest_waits.argtypes = [POINTER(c_int32)]
+    lib.lra_selftest_waits.restype = c_int32
     lib.lra_server_create.argtypes = [POINTER(vp), POINTER(ServerParams)]
     lib.lra_server_create.restype = c_int32
     lib.lra_server_submit.argtypes = [vp, POINTER(Request)]
@@ -376,6 +378,15 @@ def workspace_bytes(m, n, prm):
     if v < 0:
         raise LraError(v, "invalid arguments")
     return v
+
+
+def selftest_waits():
+    """lra_selftest_waits: (status, which) after running both kinds of bounded
+    device wait against conditions that never come true (expected:
+    ERR_TIMEOUT and which == 3)."""
+    which = c_int32(0)
+    st = int(load().lra_selftest_waits(byref(which)))
+    return st, int(which.value)
 
 
 class KeptRun:
