@@ -117,17 +117,28 @@ struct Rot {
   double c, s, t;  // cos, sin, tan; s == 0 means no rotation
 };
 
-// The rotation J (J_pp = J_qq = c, J_pq = s, J_qp = -s) with (J^T C J)_pq = 0.
+// The rotation J (J_pp = J_qq = c, J_pq = s, J_qp = -s) with (J^T C J)_pq = 0:
+// t = tan = sgn(theta) / (|theta| + sqrt(theta^2 + 1)), theta = x / y with
+// x = c_qq - c_pp, y = 2 c_pq, c = 1 / sqrt(1 + t^2), s = t c.  Multiplying by |y|
+// gives t = sgn(x) y / (|x| + sqrt(x^2 + y^2)), one FP64 division fewer on the
+// round's critical path (FP64 division and square root are long sequences on
+// this GPU); the theta form is kept where x^2 + y^2 could overflow or
+// underflow.  The skip test is evaluated beside the rotation, not before it.
 __device__ __forceinline__ Rot jacobi_rot(double app, double aqq, double apq, double tol) {
-  Rot r{1.0, 0.0, 0.0};
-  if (apq == 0.0 || fabs(apq) <= tol * sqrt(fabs(app) * fabs(aqq))) return r;
-  const double theta = (aqq - app) / (2.0 * apq);
+  const bool skip = apq == 0.0 || fabs(apq) <= tol * sqrt(fabs(app) * fabs(aqq));
+  const double x = aqq - app, y = 2.0 * apq;
+  const double mx = fmax(fabs(x), fabs(y));
   double t;
-  if (fabs(theta) > 1e150)
-    t = 0.5 / theta;
-  else
-    t = copysign(1.0, theta) / (fabs(theta) + sqrt(fma(theta, theta, 1.0)));
-  const double c = 1.0 / sqrt(fma(t, t, 1.0));
+  if (mx < 1e150 && mx > 1e-150) {
+    t = copysign(1.0, x) * y / (fabs(x) + sqrt(fma(x, x, y * y)));
+  } else {
+    const double theta = x / y;
+    t = fabs(theta) > 1e150 ? 0.5 / theta
+                            : copysign(1.0, theta) / (fabs(theta) + sqrt(fma(theta, theta, 1.0)));
+  }
+  Rot r{1.0, 0.0, 0.0};
+  if (skip) return r;
+  const double c = rsqrt(fma(t, t, 1.0));
   r.c = c;
   r.s = t * c;
   r.t = t;
