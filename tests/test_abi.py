@@ -76,3 +76,53 @@ def test_create_rejects_bad_arguments(lib, bad):
     assert s == lra.ERR_INVALID_ARG
     assert not ctx.value
     assert lib.lra_create(None, 10, 10, ctypes.byref(prm), None) == lra.ERR_INVALID_ARG
+
+
+def test_other_entry_points_reject_null_and_bad_arguments(lib):
+    """Host-side validation of the SVD, serving, batched and sizing entry points
+    (each returns before any device call)."""
+    r = lra.SvdResult()
+    assert lib.lra_svd(None, ctypes.byref(r)) == lra.ERR_INVALID_ARG
+    assert lib.lra_workspace_bytes(2000, 1000, None) == lra.ERR_INVALID_ARG
+    bad = lra.params(eps=0.0, b=16)  # eps = 0 without a fixed rank
+    assert lib.lra_workspace_bytes(2000, 1000, ctypes.byref(bad)) == lra.ERR_INVALID_ARG
+    srv = ctypes.c_void_p()
+    for slots, budget in ((0, 0), (65, 0), (4, -1)):
+        sp = lra.ServerParams(budget, slots, 0)
+        assert lib.lra_server_create(ctypes.byref(srv), ctypes.byref(sp)) == lra.ERR_INVALID_ARG
+        assert not srv.value
+    assert lib.lra_server_submit(None, None) == lra.ERR_INVALID_ARG
+    assert lib.lra_server_pending(None) < 0
+    lib.lra_server_destroy(None)
+    assert lib.lra_batch_create(None, None, 0, None, None) == lra.ERR_INVALID_ARG
+    assert lib.lra_batch_steps(None) < 0 and lib.lra_batch_device_bytes(None) < 0
+    lib.lra_batch_destroy(None)
+    assert lib.lra_device_bytes(None) == -1
+
+
+def _ws(lib, m, n, **kw):
+    prm = lra.params(**kw)
+    return int(lib.lra_workspace_bytes(m, n, ctypes.byref(prm)))
+
+
+@pytest.mark.parametrize("m,n", [(2000, 1000), (20001, 10003), (129, 17), (300, 5000)])
+def test_workspace_holds_the_two_digit_images(lib, m, n):
+    """The device workspace of the tensor-core engine holds A's two digit images
+    (7 f16 digits, 14 bytes per element): the row-scaled one in 128-row tiles of
+    16-deep stages over m x n, the column-scaled one likewise over n x m.
+    Without them (LRA_FLAG_NO_A_DIGITS or the FP64 SIMT engine) exactly those
+    bytes are gone."""
+    base = dict(eps=1e-2, b=16, P=1, kind=lra.SPARSE_SIGN, zeta=8, seed=1)
+    up = lambda x, t: -(-x // t) * t  # noqa: E731
+    images = 14 * (up(m, 128) * up(n, 16) + up(n, 128) * up(m, 16))
+    with_images = _ws(lib, m, n, **base)
+    assert with_images - _ws(lib, m, n, flags=lra.FLAG_NO_A_DIGITS, **base) == images
+    assert _ws(lib, m, n, flags=lra.FLAG_FP64_SIMT, **base) < with_images - images + 1
+
+
+def test_workspace_grows_with_the_problem(lib):
+    base = dict(eps=1e-2, b=16, P=1, kind=lra.SPARSE_SIGN, zeta=8, seed=1)
+    w = _ws(lib, 2000, 1000, **base)
+    assert 0 < w < _ws(lib, 4000, 1000, **base)
+    assert w < _ws(lib, 2000, 2000, **base)
+    assert w <= _ws(lib, 2000, 1000, **dict(base, b=32))
