@@ -96,7 +96,7 @@ int64_t oz_max_k();
 cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, const double* X,
                    int64_t ldx, const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
                    const OzWorkspace& w, int* flags, cudaStream_t st, const int* yE_known = nullptr);
-// The digit image of op(X) (P x K): every (128-row tile, 32-deep stage) as seven
+// The digit image of op(X) (P x K): every (128-row tile, 16-deep stage) as seven
 // f16 digit planes, cut once and reused by ozgemm_img.  xE as for ozgemm.
 int64_t oz_ximg_bytes(int64_t P, int64_t K);
 cudaError_t oz_cut_x(bool trans, int64_t P, int64_t K, const void* X, int dtype, int64_t ldx,

@@ -246,7 +246,7 @@ struct OzArgs {
   double* C;
   int64_t csp, csc;
   double* part;        // [cta][2][NN][TM] partial tiles
-  int64_t tiles, kst;  // row tiles; 32-deep stages per tile
+  int64_t tiles, kst;  // row tiles; 16-deep stages per tile
   int* flags;
   bool vec;            // 16-byte loads allowed (trans layout)
   bool whole_tiles;    // ranges hold whole tiles: no tile is split, no fixup
