@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "batch_plan.h"
 #include "philox.cuh"
 
 namespace lra {
@@ -541,8 +542,6 @@ __global__ void k_b_next(int* __restrict__ jp, int* __restrict__ count, int max_
     *more_out = more;
 }
 
-int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
-
 }  // namespace
 }  // namespace lra
 
@@ -723,20 +722,24 @@ lra_status lra_batch_create(lra_batch** out, const lra_batch_item* items, int64_
     }
     bt->own_stream = true;
   }
-  // internal order: largest problems first (their tiles start first)
-  std::vector<int> ord(count);
-  std::iota(ord.begin(), ord.end(), 0);
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b2) {
-    return items[a].m * items[a].n > items[b2].m * items[b2].n;
-  });
-  bt->order.assign(count, 0);
-  for (int k = 0; k < (int)count; ++k) bt->order[ord[k]] = k;
+  // order, caps, pool offsets and tile lists (batch_plan.h)
+  std::vector<int64_t> ms(count), ns(count);
+  for (int64_t i = 0; i < count; ++i) {
+    ms[i] = items[i].m;
+    ns[i] = items[i].n;
+  }
+  const BatchPlan plan = make_batch_plan(ms, ns, B, prm->max_blocks, ZMAX);
+  static_assert(sizeof(BatchTile) == sizeof(int2), "tile lists are read as int2 on the device");
+  const std::vector<BatchTile>& c32 = plan.c32;
+  const std::vector<BatchTile>& c128 = plan.c128;
+  const std::vector<BatchTile>& rm = plan.rm;
+  const std::vector<BatchTile>& rn = plan.rn;
+  const std::vector<BatchTile>& q128 = plan.q128;
+  bt->order = plan.order;
   std::vector<BProb> h(count);
-  std::vector<int2> c32, c128, rm, rn, q128;
-  int64_t off = 0;
-  std::vector<int64_t> offs(count * 12);
   for (int k = 0; k < (int)count; ++k) {
-    const lra_batch_item& it = items[ord[k]];
+    const lra_batch_item& it = items[plan.ord[k]];
+    const BatchProblemPlan& pp = plan.prob[k];
     BProb& p = h[k];
     memset(&p, 0, sizeof p);
     p.A = it.A;
@@ -744,35 +747,18 @@ lra_status lra_batch_create(lra_batch** out, const lra_batch_item* items, int64_
     p.m = (int)it.m;
     p.n = (int)it.n;
     p.zeta = prm->zeta;
-    const int mn = std::min(p.m, p.n);
-    int cap = (mn + 2 * B - 1) / (2 * B);
-    if (prm->max_blocks > 0) cap = std::min(cap, prm->max_blocks);
-    p.cap = std::max(cap, 1);
-    p.lmax = p.cap * B;
+    p.cap = pp.cap;
+    p.lmax = pp.lmax;
     p.eps2 = it.eps * it.eps;
     p.k0 = (uint32_t)(it.seed & 0xFFFFFFFFull);
     p.k1 = (uint32_t)(it.seed >> 32);
-    const int64_t sz[12] = {(int64_t)p.m * p.lmax * 4, (int64_t)p.n * p.lmax * 4,
-                            (int64_t)p.m * B * 4,      (int64_t)p.n * B * 4,
-                            0,                         (int64_t)p.lmax * B * 4,
-                            (int64_t)B * B * 4,        (int64_t)B * ZMAX * 4,
-                            (int64_t)B * ZMAX * 4,     (int64_t)B * 8,
-                            (int64_t)B * 8,            0};
-    for (int q = 0; q < 12; ++q) {
-      offs[k * 12 + q] = off;
-      off += align_up(sz[q], 256);
-    }
-    p.c32_first = (int)c32.size();
-    for (int c0 = 0; c0 < p.n; c0 += 32) c32.push_back(make_int2(k, c0));
-    p.c32_count = (int)c32.size() - p.c32_first;
-    p.c128_first = (int)c128.size();
-    for (int c0 = 0; c0 < p.n; c0 += 128) c128.push_back(make_int2(k, c0));
-    p.c128_count = (int)c128.size() - p.c128_first;
-    for (int r0 = 0; r0 < p.m; r0 += 128) rm.push_back(make_int2(k, r0));
-    for (int r0 = 0; r0 < p.n; r0 += 128) rn.push_back(make_int2(k, r0));
-    for (int c0 = 0; c0 < p.lmax; c0 += 128) q128.push_back(make_int2(k, c0));
-    bt->max_steps = std::max(bt->max_steps, p.cap);
+    p.c32_first = pp.c32_first;
+    p.c32_count = pp.c32_count;
+    p.c128_first = pp.c128_first;
+    p.c128_count = pp.c128_count;
   }
+  bt->max_steps = plan.max_steps;
+  const int64_t off = plan.pool_bytes;
   bt->pool_bytes = off;
   bt->n_c32 = (int)c32.size();
   bt->n_rm = (int)rm.size();
@@ -798,7 +784,7 @@ lra_status lra_batch_create(lra_batch** out, const lra_batch_item* items, int64_
   for (int k = 0; k < (int)count; ++k) {
     BProb& p = h[k];
     char* base = bt->d_pool;
-    const int64_t* o = &offs[k * 12];
+    const int64_t* o = plan.prob[k].offs;
     p.Q = (float*)(base + o[0]);
     p.Bt = (float*)(base + o[1]);
     p.X = (float*)(base + o[2]);

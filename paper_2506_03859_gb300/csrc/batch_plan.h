@@ -1,0 +1,102 @@
+// Host-side plan of a batch of the batched form (batch.cu): the internal order
+// of the problems, each problem's block cap and workspace offsets in the
+// device pool, and the static (problem, first row or column) tile lists that
+// the step kernels walk.  Plain C++, no CUDA, so that its rules can be checked
+// on a host without a GPU.
+//
+// Rules: problems are taken largest first (m n descending, ties in the caller's
+// order), so their tiles are issued first and the hardware scheduler balances
+// the tail; a problem stops after cap = ceil(min(m, n) / 2b) blocks (or
+// max_blocks, if smaller; at least one), so its basis holds lmax = cap b
+// columns; its buffers are laid out one after another, each starting on a
+// 256-byte boundary; tiles cover its columns in 32s (norm partials) and 128s
+// (products X^T Y), its rows in 128s, the rows of A^T in 128s and its basis
+// columns in 128s, each list in internal order.
+#pragma once
+
+#include <stdint.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+namespace lra {
+
+struct BatchTile {
+  int prob;   // internal index of the problem
+  int start;  // first row or column of the tile
+};
+
+// Buffers of one problem in the pool, in this order (bytes, before alignment):
+// Q m lmax 4, B^T n lmax 4, X m b 4, W n b 4, (none), F lmax b 4, R^{-1} b b 4,
+// Omega values b zmax 4, Omega rows b zmax 4, R diagonal b 8, column norms b 8, (none).
+constexpr int BATCH_BUFFERS = 12;
+
+struct BatchProblemPlan {
+  int cap, lmax;
+  int64_t offs[BATCH_BUFFERS];
+  int c32_first, c32_count;
+  int c128_first, c128_count;
+};
+
+struct BatchPlan {
+  std::vector<int> ord;    // internal index -> caller's index
+  std::vector<int> order;  // caller's index -> internal index
+  std::vector<BatchProblemPlan> prob;  // by internal index
+  std::vector<BatchTile> c32, c128, rm, rn, q128;
+  int64_t pool_bytes = 0;
+  int max_steps = 0;
+};
+
+inline int64_t batch_align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// ms[i], ns[i]: the shape of problem i in the caller's order (validated by the
+// caller: 1 <= b <= min(m, n)); b: block size; max_blocks: 0 or a cap on the
+// blocks; zmax: the largest zeta the Omega buffers hold.
+inline BatchPlan make_batch_plan(const std::vector<int64_t>& ms, const std::vector<int64_t>& ns,
+                                 int b, int max_blocks, int zmax) {
+  BatchPlan plan;
+  const int count = (int)ms.size();
+  plan.ord.resize(count);
+  std::iota(plan.ord.begin(), plan.ord.end(), 0);
+  std::stable_sort(plan.ord.begin(), plan.ord.end(),
+                   [&](int x, int y) { return ms[x] * ns[x] > ms[y] * ns[y]; });
+  plan.order.assign(count, 0);
+  for (int k = 0; k < count; ++k) plan.order[plan.ord[k]] = k;
+  plan.prob.resize(count);
+  int64_t off = 0;
+  for (int k = 0; k < count; ++k) {
+    const int i = plan.ord[k];
+    const int m = (int)ms[i], n = (int)ns[i];
+    BatchProblemPlan& p = plan.prob[k];
+    const int mn = std::min(m, n);
+    int cap = (mn + 2 * b - 1) / (2 * b);
+    if (max_blocks > 0) cap = std::min(cap, max_blocks);
+    p.cap = std::max(cap, 1);
+    p.lmax = p.cap * b;
+    const int64_t sz[BATCH_BUFFERS] = {(int64_t)m * p.lmax * 4, (int64_t)n * p.lmax * 4,
+                                       (int64_t)m * b * 4,      (int64_t)n * b * 4,
+                                       0,                       (int64_t)p.lmax * b * 4,
+                                       (int64_t)b * b * 4,      (int64_t)b * zmax * 4,
+                                       (int64_t)b * zmax * 4,   (int64_t)b * 8,
+                                       (int64_t)b * 8,          0};
+    for (int q = 0; q < BATCH_BUFFERS; ++q) {
+      p.offs[q] = off;
+      off += batch_align_up(sz[q], 256);
+    }
+    p.c32_first = (int)plan.c32.size();
+    for (int c0 = 0; c0 < n; c0 += 32) plan.c32.push_back(BatchTile{k, c0});
+    p.c32_count = (int)plan.c32.size() - p.c32_first;
+    p.c128_first = (int)plan.c128.size();
+    for (int c0 = 0; c0 < n; c0 += 128) plan.c128.push_back(BatchTile{k, c0});
+    p.c128_count = (int)plan.c128.size() - p.c128_first;
+    for (int r0 = 0; r0 < m; r0 += 128) plan.rm.push_back(BatchTile{k, r0});
+    for (int r0 = 0; r0 < n; r0 += 128) plan.rn.push_back(BatchTile{k, r0});
+    for (int c0 = 0; c0 < p.lmax; c0 += 128) plan.q128.push_back(BatchTile{k, c0});
+    plan.max_steps = std::max(plan.max_steps, p.cap);
+  }
+  plan.pool_bytes = off;
+  return plan;
+}
+
+}  // namespace lra
