@@ -334,7 +334,7 @@ int64_t lra_device_bytes(const lra_ctx* ctx);
 /* Diagnostic: runs the library's two kinds of bounded device wait (an
    mbarrier wait as in the tensor-core GEMM, the grid barrier of the
    eigensolver) against conditions that never come true, each with a short
-   limit (milliseconds).  Every wait of the library ends this way when its
+   limit (2^14 polls).  Every wait of the library ends this way when its
    limit runs out: the kernel records FLAG_TIMEOUT and returns, the call
    reports LRA_ERR_TIMEOUT, and the device stays usable.  Returns
    LRA_ERR_TIMEOUT when a wait gave up (the expected outcome: both), LRA_OK if

@@ -2,7 +2,7 @@
 
 lra_selftest_waits runs an mbarrier wait (the form the tensor-core GEMM's roles
 use) and the eigensolver's grid barrier against conditions that never come
-true, each with a limit of milliseconds.  Both must give up, report the timeout,
+true, each with a limit of 2^14 polls.  Both must give up, report the timeout,
 and leave the device usable: a farPCA run and its SVD (which uses the same grid
 barrier) afterwards end normally.  Nothing faults or hangs: every wait is a
 bounded loop.
