@@ -59,3 +59,21 @@ def test_device_low_rank():
     s = np.linalg.svd(A, compute_uv=False)
     assert np.allclose(s[:30], 10.0 ** (-np.arange(1, 31) / 100.0), rtol=1e-10)
     assert s[30] < 1e-12
+
+
+@pytest.mark.parametrize("spectrum", ["exp100", "matrix1", "matrix2", "poly1.5"])
+def test_low_rank_matrix_spectrum(spectrum):
+    """The Sec. 5 recipe: A = U diag(sigma) V^T with orthonormal U, V, so its
+    singular values are the named spectrum's first `rank` values, the rest zero;
+    column-major; the same seed gives the same matrix; noise adds N(0, noise^2)."""
+    from lra_inputs import low_rank_matrix, singular_values
+    m, n, r = 300, 200, 120
+    A = low_rank_matrix(m, n, spectrum, 4, rank=r)
+    assert A.flags["F_CONTIGUOUS"] and A.dtype == np.float64
+    s = np.linalg.svd(A, compute_uv=False)
+    sig = singular_values(spectrum, r)
+    assert np.allclose(s[:r], sig, rtol=1e-10, atol=1e-14 * sig[0])
+    assert s[r] <= 1e-13 * sig[0]
+    assert np.array_equal(A, low_rank_matrix(m, n, spectrum, 4, rank=r))
+    N = low_rank_matrix(m, n, spectrum, 4, rank=r, noise=1e-3) - A
+    assert abs(np.linalg.norm(N) / np.sqrt(m * n) - 1e-3) < 1e-4
