@@ -312,13 +312,16 @@ lra_status lra_phase_times(lra_ctx* ctx, double* ms, int64_t* calls, int32_t nph
    b * (4 + 12 cap) bytes with cap = zeta (fixed-zeta kind) or n (the i.i.d.
    kinds), must fit in the array minus 768 bytes, else LRA_ERR_INVALID_ARG;
    longer block ranges are processed in chunks.
-   The first call on each device looks up the array's device address
-   (cudaGetSymbolAddress); make that first call before any stream capture
-   starts.  All calls share the array and leave the last call's contents in it:
-   calls that can overlap on the GPU (other streams, other host threads) race
-   on it, so issue them in order on one stream.  The call synchronises its
-   stream before returning.  Errors: LRA_ERR_INVALID_ARG, LRA_ERR_UNSUPPORTED,
-   LRA_ERR_CUDA. */
+   Every call looks up the array's device address in the current device's
+   context (cudaGetSymbolAddress); the first call on a device also loads the
+   library's device code there, so make that first call before any stream
+   capture starts.  All calls share the array and leave the last call's
+   contents in it: calls that can overlap on the GPU (other streams, other host
+   threads) race on it, so issue them in order on one stream.  The call copies
+   its error word to the host and synchronises its stream before returning.
+   Errors: LRA_ERR_INVALID_ARG, LRA_ERR_UNSUPPORTED, LRA_ERR_CUDA, and
+   LRA_ERR_TIMEOUT when a bounded device wait of the gather gave up (Y is then
+   incomplete; the device stays usable). */
 lra_status lra_sketch_noalloc(const lra_matrix* A, const lra_params* params, int64_t j0,
                               int64_t nblk, double* Y, int64_t ldy, void* cuda_stream);
 

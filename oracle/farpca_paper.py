@@ -4,9 +4,11 @@ Keeps the paper's cumulative Y, W (sketches and their A^T images), Z = Y^T Y,
 T = W^T W, and the deflation W (Z^{-1} (W^T G_j)) literally; the basis of each
 power step comes from eigSVD (the economic SVD through the eigendecomposition
 of the Gram matrix, the routine Alg. 1 cites).  Readings:
-  * the indicator line "E = E - tr(T Z^{-1})" with cumulative T and Z is read as
-    E_j = ||A||_F^2 - tr(T_j Z_j^{-1}) (subtracting the running total each block
-    would count earlier blocks again);
+  * Alg. 1 / 2 update the indicator by subtracting tr(T Z^{-1}) of the
+    cumulative T and Z; here the indicator after block j is
+    E_j = ||A||_F^2 - tr(T_j Z_j^{-1}) (tr(T_j Z_j^{-1}) already holds every block
+    so far, so subtracting it from the previous E would count earlier blocks
+    again);
   * the stop test is relative, E < eps^2 ||A||_F^2 (Sec. 5.2);
   * the shift alpha only acts from the third power step on (Alg. 1 updates it
     after step k > 1 and uses it at step k + 1), so it is omitted for P <= 2.

@@ -16,7 +16,6 @@
 #include <math.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "internal.cuh"
 
@@ -25,26 +24,18 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[LRA_NOALLOC_SCRATCH_BYTES];
 
-constexpr int MAX_DEVICES = 64;
-std::mutex g_setup_mu;
-void* g_scratch_ptr[MAX_DEVICES] = {};
-
-// Device address of the scratch array on the current device, looked up once
-// per device.  In host code the array's name is only a host-side stand-in: the
-// device address must come from cudaGetSymbolAddress.
+// Device address of the scratch array in the current device's context.  In host
+// code the array's name is only a host-side stand-in: the device address must
+// come from cudaGetSymbolAddress.  It is looked up on every call (a cheap table
+// lookup once the module is loaded), so an address is never reused across
+// contexts: after cudaDeviceReset, or under another driver context on the same
+// device, the module and its array may live elsewhere.  The first lookup in a
+// context loads the library's device code there.
 cudaError_t scratch_on_current_device(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
+  *out = p;
   return cudaSuccess;
 }
 

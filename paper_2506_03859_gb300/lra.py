@@ -544,6 +544,14 @@ def sketch_noalloc(A, j0, nblk, b, kind, zeta=8, p=0.0, seed=0, Y=None, stream=N
     m = A.shape[0]
     if Y is None:
         Y = torch.empty_strided((m, nblk * b), (1, m), dtype=torch.float64, device=A.device)
+    else:
+        # the library writes m x nblk*b doubles, column-major with ld = Y.stride(1)
+        if Y.dtype != torch.float64 or Y.device != A.device or Y.dim() != 2:
+            raise ValueError("Y must be a 2-D float64 tensor on A's device")
+        if tuple(Y.shape) != (m, nblk * b):
+            raise ValueError("Y must be m x nblk*b = %d x %d" % (m, nblk * b))
+        if Y.stride(0) != 1 or (nblk * b > 1 and Y.stride(1) < m):
+            raise ValueError("Y must be column-major (stride(0) == 1, stride(1) >= m)")
     prm = Params(0.0, 0, b, 0, kind, zeta, p, seed & 0xFFFFFFFFFFFFFFFF, 0, 0)
     if stream is None:
         stream = torch.cuda.current_stream()

@@ -59,3 +59,27 @@ def test_noalloc_rejects_what_does_not_fit():
     with pytest.raises(lra.LraError) as e:
         lra.sketch_noalloc(A, 0, 1, 2, lra.GAUSSIAN)
     assert e.value.status == lra.ERR_UNSUPPORTED
+
+
+def test_noalloc_allocates_nothing():
+    """The defining property: once the library's device code is loaded (first
+    call), further calls of other shapes and chunk counts leave the device's free
+    memory unchanged when the caller supplies Y."""
+    m, n, b = 2500, 1800, 16
+    A = column_major_random(m, n, 9)
+    Ys = [torch.empty_strided((m, nblk * b), (1, m), dtype=torch.float64, device="cuda")
+          for nblk in (1, 4, 40)]
+    lra.sketch_noalloc(A, 0, 1, b, lra.SPARSE_SIGN, zeta=8, seed=3, Y=Ys[0])  # warm-up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for Y, (kind, zeta) in zip(Ys, [(lra.SPARSE_SIGN, 4), (lra.SPARSE_GAUSSIAN, 8),
+                                    (lra.SPARSE_SIGN_IID, 0)]):
+        nblk = Y.shape[1] // b
+        lra.sketch_noalloc(A, 2, nblk, b, kind, zeta=zeta, seed=11, Y=Y)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    # a Y of the wrong layout is refused by the binding before the library writes it
+    with pytest.raises(ValueError):
+        lra.sketch_noalloc(A, 0, 1, b, lra.SPARSE_SIGN, zeta=8, Y=torch.empty((m, b), dtype=torch.float64,
+                                                                               device="cuda"))
