@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--sketch-blocks", type=int, default=64)
+    ap.add_argument("--sketch-blocks", type=int, default=100,
+                    help="blocks of the sketch-only pass (one launch over all of them)")
     ap.add_argument("--no-extras", action="store_true",
                     help="only the timed farPCA steps (for launch-list profiling)")
     ap.add_argument("--engine", choices=("tensor", "fp64_simt"), default="tensor",
@@ -66,7 +67,8 @@ def parse():
                     help="with --only batch: number of problems (4096 is the benchmark batch)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="with --only batch: launch the batch's steps from the host (for profiling)")
-    ap.add_argument("--only", choices=("sketch", "dense", "serve", "batch", "fixedrank", "stability", "svd"),
+    ap.add_argument("--only", choices=("sketch", "dense", "serve", "batch", "fixedrank", "stability", "svd",
+                                       "runlist"),
                     default=None,
                     help="run only the sketch pass (lra_sketch over --sketch-blocks blocks) or only "
                          "the two dense passes A Y and A^T Y (lra_apply), for profiling")
@@ -220,8 +222,9 @@ def run_reference(args, cfg):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": dict(workload_config(args, cfg, A.shape[0], A.shape[1], 1), rank=r["rank"],
-                       blocks=r["blocks"], rel_err=(max(r["E"], 0) / r["normA2"]) ** 0.5),
+        "config": workload_config(args, cfg, A.shape[0], A.shape[1], 1),
+        "result": {"rank": r["rank"], "blocks": r["blocks"], "rel_err": (max(r["E"], 0) / r["normA2"]) ** 0.5,
+                   "status": ["LRA_OK", "LRA_NOT_CONVERGED", "LRA_BREAKDOWN"][r["status"]]},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
                          "sample": "one full fixed-precision solve of the workload per step "
                                    "(numpy/OpenBLAS FP64, QB form)"},
@@ -261,8 +264,10 @@ def main():
     f = lra.Farpca(m, n, eps=cfg["eps"], b=cfg["b"], P=cfg["P"], kind=cfg["kind"], zeta=cfg["zeta"],
                    p=cfg["p"], seed=cfg["seed"] + rank, profile=True, stream=stream,
                    fp64_simt=(args.engine == "fp64_simt"))
-    if args.only in ("sketch", "dense", "serve", "batch", "fixedrank", "stability", "svd"):
-        if args.only == "serve":
+    if args.only in ("sketch", "dense", "serve", "batch", "fixedrank", "stability", "svd", "runlist"):
+        if args.only == "runlist":
+            out = {"run_list": run_list(lra, torch, np, Ad, peaks, peak_src, stream)}
+        elif args.only == "serve":
             out = {"serving": serving(lra, torch, np, slots=args.serve_slots)}
         elif args.only == "svd":
             f.run(Ad)
@@ -337,15 +342,18 @@ def main():
                                     "frac": tflops / peaks["bf16_tflops"],
                                     "note": "28 f16 digit-pair products per FP64 product, N padded to 64"}}
     roofline.update({"algorithmic_per_launch": {"bytes": algo_bytes, "flops_fp64": algo_flops},
-                     "avg_launch_ms": dense_avg_ms, "launches": dense_calls})
+                     "avg_launch_ms": dense_avg_ms, "launches": dense_calls,
+                     "time_to_eps": solve_roofline(m, n, cfg["b"], cfg["P"], res["blocks"], cfg["kind"],
+                                                   cfg["zeta"], ms / args.steps, peaks, peak_src)})
     total_phase = sum(v[0] for v in phases.values()) or 1.0
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(workload_config(args, cfg, m, n, world), rank=res["rank"], blocks=res["blocks"],
-                       rel_err=res["rel_err"], status=lra.status_string(res["status"])),
+        "config": workload_config(args, cfg, m, n, world),
+        "result": {"rank": res["rank"], "blocks": res["blocks"], "rel_err": res["rel_err"],
+                   "status": lra.status_string(res["status"])},
         "roofline": roofline,
         "phase_share": {k: round(v[0] / total_phase, 4) for k, v in phases.items()},
         "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
@@ -358,6 +366,7 @@ def main():
         # host and device memory
         line["e2e"] = e2e(lra, torch, np, f, A, args.steps)
         line["sketch_pass"] = sketch_pass(lra, torch, f, Ad, cfg, args.sketch_blocks, peaks, peak_src)
+        line["run_list"] = run_list(lra, torch, np, Ad, peaks, peak_src, stream)
         line["mixed"] = mixed_form(lra, torch, Ad, cfg, m, n, args.steps, res["rel_err"], stream)
         line["svd"] = svd_extraction(torch, f, args.steps, stream)
         line["fp32_input"] = fp32_form(lra, torch, Ad, cfg, m, n, args.steps, stream)
@@ -373,6 +382,113 @@ def main():
     f.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def solve_bytes(m, n, b, P, blocks, kind, zeta):
+    """Algorithmic bytes of one fixed-precision solve (what an FP64 implementation of
+    the steps must move through HBM), and the number of full passes over A.
+
+    ||A||_F^2: one pass (8 m n).  Per block j (l = j b columns of Q and rows of B so far):
+    the sketch (a gather of the distinct columns of A for the sparse kinds, a full pass
+    for the dense ones); with P >= 1 the power step A^T S0 and P - 1 more pairs A G /
+    A^T T, each deflated with B (B Omega_j or B G, then B^T F: B read twice) and
+    orthonormalised (CholQR2 of an n x b panel: two Grams and two X R^-1); Y_j = A G;
+    two projections against Q (Q^T Y and Y - Q F); CholQR2 of the m x b block;
+    B_j = Q_j^T A (a full pass); ||B_j||_F^2 and the append of B_j."""
+    e = 8.0
+    dense_kind = kind in (0, 1)  # Gaussian and standardized Bernoulli: a dense sketch pass
+    pass_bytes = e * (m * n + (m + n) * b)
+    total, passes = e * m * n, 1
+    for j in range(blocks):
+        l = j * b
+        if dense_kind:
+            total += pass_bytes
+            passes += 1
+        else:
+            total += e * m * (min(zeta * b if zeta > 0 else n, n) + b)
+        if P >= 1:
+            for _ in range(P):
+                total += 2 * pass_bytes if _ > 0 else pass_bytes
+                passes += 2 if _ > 0 else 1
+                if l > 0:
+                    total += e * 2 * (l * n + l * b + n * b)
+                total += e * 6 * n * b
+            total += pass_bytes  # Y_j = A G
+            passes += 1
+        if l > 0:
+            total += 2 * e * ((m * l + m * b + l * b) + (m * l + l * b + 2 * m * b))
+        total += e * 6 * m * b
+        total += pass_bytes  # B_j = Q_j^T A
+        passes += 1
+        total += e * 2 * n * b
+    return total, passes
+
+
+def solve_roofline(m, n, b, P, blocks, kind, zeta, ms, peaks, peak_src):
+    """Time-to-eps roofline of one solve: its algorithmic bytes (solve_bytes) over the HBM
+    copy bandwidth, against the measured time per solve.  The FP64 flops are not a bound
+    here: the dense passes run FP64-accurate on the tensor cores (28 bf16 digit-pair
+    products per FP64 product, N padded to 64), whose own floor is given beside it."""
+    total, passes = solve_bytes(m, n, b, P, blocks, kind, zeta)
+    hbm_ms = total / (peaks["hbm_gbs"] * 1e9) * 1e3
+    # the full passes of this design: max(image-free HBM time, 28-pair tensor time) each
+    pass_hbm = 8.0 * (m * n + (m + n) * b) / (peaks["hbm_gbs"] * 1e9) * 1e3
+    pass_tc = 28 * 2.0 * m * n * 64 / (peaks["bf16_tflops"] * 1e12) * 1e3
+    design_ms = hbm_ms + (passes - 1) * max(0.0, pass_tc - pass_hbm)
+    return {"bound": "hbm", "algorithmic_bytes": total, "full_passes": passes,
+            "roofline_ms": hbm_ms, "measured_ms": ms, "frac": hbm_ms / ms,
+            "design_floor_ms": design_ms, "frac_of_design_floor": design_ms / ms,
+            "peak": peaks["hbm_gbs"], "peak_source": peak_src + " HBM copy bandwidth",
+            "note": "design floor: each full pass over A at max(its HBM time, the tensor time of "
+                    "its 28 digit-pair products at the bf16 peak)"}
+
+
+def run_list(lra, torch, np, Ad, peaks, peak_src, stream, reps=3):
+    """The measurement runs beside the headline: the 2000 x 1000 workload (sigma_i =
+    i^-1.5, b = 20, P = 1, eps = 1e-2) with the four hot-path kinds, and the variants of
+    the 20000 x 10000 workload (P in {0, 2}, zeta in {4, 16}, eps in {1e-1, 1e-3} -- the
+    latter ends NOT_CONVERGED at the block cap, the noise floor being ~3e-3 -- and the
+    Gaussian, standardized Bernoulli +-1 and sparse Gaussian kinds).  Per run: rank,
+    blocks, status, final relative error, ms per solve and the time-to-eps roofline."""
+    from lra_inputs import workload_matrix
+    kinds = {"ss8": (lra.SPARSE_SIGN, 0.0, 8), "gauss": (lra.GAUSSIAN, 0.0, 0),
+             "sb_pm1": (lra.STD_BERNOULLI, 0.5, 0), "sg8": (lra.SPARSE_GAUSSIAN, 0.0, 8)}
+
+    def timed(A, m, n, b, P, eps, kind, p, zeta, k_reps):
+        f = lra.Farpca(m, n, eps=eps, b=b, P=P, kind=kind, zeta=zeta, p=p, seed=1, stream=stream)
+        f.run(A)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k_reps):
+            f.run(A)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k_reps
+        r = f.result()
+        f.close()
+        rl = solve_roofline(m, n, b, P, r["blocks"], kind, zeta, ms, peaks, peak_src)
+        return {"rank": r["rank"], "blocks": r["blocks"], "status": lra.status_string(r["status"]),
+                "rel_err": r["rel_err"], "ms": ms, "solves_per_s": 1e3 / ms,
+                "time_to_eps_frac": rl["frac"], "frac_of_design_floor": rl["frac_of_design_floor"]}
+
+    out = {}
+    A1 = lra.column_major(torch.from_numpy(workload_matrix("dense2000x1000_poly1.5")).cuda())
+    for name, (kind, p, zeta) in kinds.items():
+        out["C1_2000x1000_%s_P1_eps1e-2" % name] = timed(A1, 2000, 1000, 20, 1, 1e-2, kind, p, zeta, 10)
+    del A1
+    m, n = Ad.shape
+    c2 = [("ss8_P0_eps1e-2", "ss8", 0, 1e-2), ("ss8_P2_eps1e-2", "ss8", 2, 1e-2),
+          ("ss4_P1_eps1e-2", (lra.SPARSE_SIGN, 0.0, 4), 1, 1e-2),
+          ("ss16_P1_eps1e-2", (lra.SPARSE_SIGN, 0.0, 16), 1, 1e-2),
+          ("ss8_P1_eps1e-1", "ss8", 1, 1e-1), ("gauss_P1_eps1e-2", "gauss", 1, 1e-2),
+          ("sb_pm1_P1_eps1e-2", "sb_pm1", 1, 1e-2), ("sg8_P1_eps1e-2", "sg8", 1, 1e-2),
+          ("ss8_P1_eps1e-3_capped", "ss8", 1, 1e-3)]
+    for name, kd, P, eps in c2:
+        kind, p, zeta = kinds[kd] if isinstance(kd, str) else kd
+        out["C2_20000x10000_%s" % name] = timed(Ad, m, n, 50, P, eps, kind, p, zeta,
+                                               1 if eps < 1e-2 else reps)
+    return out
 
 
 def sketch_pass(lra, torch, f, Ad, cfg, nblk, peaks, peak_src):

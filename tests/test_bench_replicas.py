@@ -79,7 +79,8 @@ def test_single_rank_needs_no_process_group():
 
 
 def test_reference_line_carries_the_same_config_keys(monkeypatch):
-    """The reference arm's JSON line: same metric, unit, direction and config keys as ours."""
+    """The reference arm's JSON line: same metric, unit, direction and config as ours (run
+    results such as the attained rank sit under "result", outside the config)."""
     import bench
     import numpy as np
     monkeypatch.setenv("RANK", "0")
@@ -97,6 +98,29 @@ def test_reference_line_carries_the_same_config_keys(monkeypatch):
     assert line["impl"] == "reference"
     assert line["metric"] == bench.METRIC and line["unit"] == "solves/s" and line["higher_is_better"]
     ours = bench.workload_config(args, cfg, 120, 80, 1)
-    assert set(ours) <= set(line["config"])
+    assert line["config"] == ours  # the same workload description in both arms
+    assert set(line["result"]) == {"rank", "blocks", "rel_err", "status"}
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_solve_bytes_pass_count():
+    """The time-to-eps roofline counts the full passes over A of Sec. 3's cost model
+    (Remark 3.4): one for ||A||_F^2, then 2P + 1 per block for a gathered sketch and
+    2P + 2 for a dense one; each full pass moves A once plus its skinny operands."""
+    import bench
+    m, n, b = 2000, 1000, 20
+    for P in (0, 1, 2):
+        for blocks in (1, 5):
+            _, sparse = bench.solve_bytes(m, n, b, P, blocks, 2, 8)
+            _, dense = bench.solve_bytes(m, n, b, P, blocks, 0, 0)
+            assert sparse == 1 + blocks * (2 * P + 1)
+            assert dense == 1 + blocks * (2 * P + 2)
+    total, passes = bench.solve_bytes(20000, 10000, 50, 1, 5, 2, 8)
+    assert passes == 16
+    # the full passes dominate: 16 x 8 m n bytes of A, plus everything else
+    assert 16 * 8.0 * 20000 * 10000 < total < 1.2 * 16 * 8.0 * 20000 * 10000
+    rl = bench.solve_roofline(20000, 10000, 50, 1, 5, 2, 8, 15.6, {"hbm_gbs": 6700.0, "bf16_tflops": 1900.0},
+                              "test")
+    assert rl["roofline_ms"] == pytest.approx(total / 6.7e12 * 1e3)
+    assert rl["roofline_ms"] < rl["design_floor_ms"] < 15.6
