@@ -148,7 +148,18 @@ __global__ void __launch_bounds__(1024) k_total(const double* __restrict__ v, in
 // (i, j), c < i <= j, come from a table of all pairs i <= j sorted by i
 // descending (those of column c are its first (b-1-c)(b-c)/2 entries); the Z
 // updates (i > c, j <= c) are numbered densely, i = c + 1 + f div (c + 1).
+//
+// Near the identity the sweep is not needed.  The second Gram of CholQR2 is
+// S = I + E with E of the order of the first pass's loss of orthogonality.
+// With R = I + U (U upper), R^T R = I + E gives U = Phi(E) - Phi(U^T U), where
+// Phi keeps the strict upper triangle and halves the diagonal, and
+// R^{-1} = I - U + U^2 - ...; so R^{-1} = I - Phi(E) up to terms bounded by
+// 2 b max|E|^2 per entry.  When max|E| <= 2^-34 that is at most 2^-61 for
+// b <= 64, below the rounding of the entries near 1 and far below what
+// X R^{-1} can resolve, and R^{-1} is written directly (every pivot is then
+// ~1 and passes the breakdown test).
 constexpr int CHOL_NT = 1024;
+constexpr double CHOL_NEAR_I = 0x1p-34;
 
 __global__ void __launch_bounds__(CHOL_NT) k_chol_inv(const double* __restrict__ S, int b, double tau,
                                                       double* __restrict__ Rinv, int* __restrict__ flags) {
@@ -161,10 +172,22 @@ __global__ void __launch_bounds__(CHOL_NT) k_chol_inv(const double* __restrict__
   const int t = threadIdx.x;
   // workers: warps 1 .. 31; thread 0 takes the pivots
   const int wk = t - 32;
+  int far = 0;  // an entry of S - I above 2^-34, or not finite
   for (int e = t; e < b * b; e += CHOL_NT) {
     const int i = e % b, j = e / b;
-    M[i][j] = S[i + j * b];
+    const double v = S[i + j * b];
+    M[i][j] = v;
     Z[i][j] = (i == j) ? 1.0 : 0.0;
+    far |= !(fabs(i == j ? v - 1.0 : v) <= CHOL_NEAR_I);
+  }
+  if (!__syncthreads_or(far)) {
+    // R^{-1} = I - Phi(S - I): -S_ij above the diagonal, 1 - (S_ii - 1)/2 on it
+    for (int e = t; e < b * b; e += CHOL_NT) {
+      const int i = e % b, j = e / b;
+      const double v = M[i][j];
+      Rinv[i + j * b] = i < j ? -v : (i == j ? fma(-0.5, v - 1.0, 1.0) : 0.0);
+    }
+    return;
   }
   // entry e of the pair table: rows b-1, b-2, ... in turn, row i holding j = i..b-1;
   // the rows above i (i' > i) take sum_{i' > i} (b - i') = (b-1-i)(b-i)/2 entries

@@ -287,3 +287,19 @@ def test_y_sensitivity_to_summation_order():
     s1 = F.farpca(A, 1e-2, P=0, b=20, kind=om.SPARSE_SIGN, seed=2024, zeta=8, keep_y=True)
     s2 = F.farpca(A[perm], 1e-2, P=0, b=20, kind=om.SPARSE_SIGN, seed=2024, zeta=8, keep_y=True)
     assert np.linalg.norm(s1["Y"] - s2["Y"][inv]) <= 1e-14 * np.linalg.norm(s1["Y"])
+
+
+def test_cholesky_inverse_near_identity():
+    """CholQR2's second Gram is S = I + E with tiny E.  With R = I + U the upper
+    Cholesky factor, R^-1 = I - Phi(E) up to 2 b max|E|^2 per entry (Phi: strict
+    upper triangle of E plus half its diagonal), the closed form the device uses
+    when max|E| <= 2^-34.  Checked against the inverse of LAPACK's Cholesky factor
+    (whose own rounding adds a few units of 2^-53)."""
+    rng = np.random.default_rng(5)
+    for b in (1, 7, 50, 64):
+        E = rng.uniform(-1, 1, (b, b))
+        E = (E + E.T) * 2.0 ** -35
+        S = np.eye(b) + E
+        Rinv = np.linalg.inv(np.linalg.cholesky(S).T)
+        closed = np.eye(b) - (np.triu(E, 1) + np.diag(np.diag(E)) / 2)
+        assert np.abs(closed - Rinv).max() <= 2 * b * np.abs(E).max() ** 2 + 4 * np.finfo(float).eps
