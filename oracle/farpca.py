@@ -23,9 +23,13 @@ by a direct SVD.  This module writes that QB form out, block by block:
 orth(X) is the Q factor of the QR factorisation of X with positive diagonal R
 (unique for full-rank X), computed as X R^{-1} with R = chol(X^T X), twice
 (CholQR2).  The paper's eigSVD gives another basis of the same span; for
-P <= 2 the attained rank and E are the same.  Breakdown rule: a Cholesky pivot
-d_c (the diagonal before the square root) that is not > 1e-13 * S_cc, or not
-finite, ends the run with status BREAKDOWN; results stay those of block j-1.
+P <= 2 the attained rank and E are the same.  A Cholesky pivot d_c (the
+diagonal before the square root) that is not > 1e-13 * S_cc, or not finite,
+marks column c numerically dependent.  In a power-step panel W the run goes on:
+orth_panel replaces the dependent columns by fixed random directions, as the
+near-null columns of the paper's eigSVD are noise directions.  In the block
+Y' that is appended to Q it ends the run with status BREAKDOWN; results stay
+those of block j-1.
 
 Pins (tests/test_oracle_farpca.py): Q^T Q = I; E = ||A - QB||_F^2 computed
 directly; the Eckart-Young lower bound and the bound of eq. (4.9) against a
@@ -66,6 +70,47 @@ def cholesky_upper(S, tau=PIVOT_TAU):
         R[c, c] = math.sqrt(d)
         R[c, c + 1:] = (S[c, c + 1:] - R[:c, c] @ R[:c, c + 1:]) / R[c, c]
     return R
+
+
+def cholesky_upper_skip(S, tau=PIVOT_TAU):
+    """cholesky_upper that passes over a failed pivot instead of stopping: column c
+    is then marked dependent, its row of R is e_c (it takes no part in the later
+    columns' updates), and the factor of the remaining columns is that of S with
+    the dependent rows and columns left out.  Returns (R, dead)."""
+    b = S.shape[0]
+    R = np.zeros_like(S)
+    dead = np.zeros(b, dtype=bool)
+    for c in range(b):
+        d = S[c, c] - R[:c, c] @ R[:c, c]
+        if not (np.isfinite(d) and d > tau * S[c, c]):
+            dead[c] = True
+            R[c, c] = 1.0
+            continue
+        R[c, c] = math.sqrt(d)
+        R[c, c + 1:] = (S[c, c + 1:] - R[:c, c] @ R[:c, c + 1:]) / R[c, c]
+    return R, dead
+
+
+def orth_panel(X, j, step, seed, tau=PIVOT_TAU):
+    """Orthonormal basis G of a power-step panel (Alg. 1's eigSVD step) that keeps
+    going when the panel is numerically rank deficient.
+
+    The paper's eigSVD returns, for the near-null directions of X^T X, columns made
+    of rounding noise; this reading replaces them by fixed random directions: the
+    first CholQR pass skips the failed pivots (cholesky_upper_skip), the columns it
+    marks dependent are replaced by +-1/sqrt(n) columns of the TAG_FILL stream
+    (column counter c + 64 step), and a second, plain CholQR pass orthonormalises the
+    completed panel.  With no failed pivot this is orth(X) exactly.  Returns None
+    only if the second pass fails."""
+    R1, dead = cholesky_upper_skip(X.T @ X, tau)
+    X1 = solve_triangular(R1, X.T, trans='T', lower=False).T
+    if dead.any():
+        for c in np.nonzero(dead)[0]:
+            X1[:, c] = om.fill_column(X.shape[0], j, int(c) + 64 * step, seed)
+    R2 = cholesky_upper(X1.T @ X1, tau)
+    if R2 is None:
+        return None
+    return solve_triangular(R2, X1.T, trans='T', lower=False).T
 
 
 def orth(X, tau=PIVOT_TAU):
@@ -149,12 +194,12 @@ def farpca(A, eps=0.0, P=1, b=20, kind=om.SPARSE_SIGN, seed=0, zeta=8, p=0.0,
         # a3 + a4: deflated power steps
         if P >= 1:
             W = A.T @ S0 - B.T @ BOm
-            G = orth(W)
-            for _ in range(1, P):
+            G = orth_panel(W, j, 0, seed)
+            for s in range(1, P):
                 if G is None:
                     break
                 W = A.T @ (A @ G) - B.T @ (B @ G)
-                G = orth(W)
+                G = orth_panel(W, j, s, seed)
             if G is None:
                 status = BREAKDOWN
                 break

@@ -32,6 +32,10 @@ zeta) or the row r (i.i.d. kinds), and tag names the stream:
   TAG_GAUSS        Box-Muller from two 53-bit uniforms: a = (k(u0,u1) + 1) 2^-53
                    in (0, 1], c = k(u2,u3) 2^-53 in [0, 1), with
                    k(x, y) = (x >> 5) 2^26 + (y >> 6); value sqrt(-2 ln a) cos(2 pi c).
+  TAG_FILL         the direction that replaces a dependent column of a power-step
+                   panel (oracle.farpca.orth_panel): entry r of column c is
+                   +-1/sqrt(n), + if bit 0 of u0 is 0, with counter (r, j, c', TAG_FILL),
+                   c' = c + 64 s for power step s.
 
 Pins (tests/test_oracle_omega.py): exactly zeta distinct rows per column;
 entry mean 0 / variance 1 after standardisation; Hoeffding's nnz bound
@@ -59,6 +63,7 @@ KIND_NAMES = {GAUSSIAN: "farPCA", STD_BERNOULLI: "farPCASB", SPARSE_SIGN: "farPC
 TAG_SPARSE_SIGN = 1
 TAG_MASK = 2
 TAG_GAUSS = 3
+TAG_FILL = 4
 
 TWO32 = 4294967296.0
 TWO_M53 = 2.0 ** -53
@@ -124,6 +129,15 @@ def mask_and_u1(j, n, b, p, seed):
     c = np.arange(b, dtype=np.uint64)[None, :]
     u0, u1, _, _ = _draw(r, j, c, TAG_MASK, seed)
     return u0 < np.uint64(mask_threshold(p)), u1
+
+
+def fill_column(n, j, c, seed):
+    """A +-1/sqrt(n) column from the TAG_FILL stream: the direction that replaces a
+    numerically dependent column of a power-step panel."""
+    r = np.arange(n, dtype=np.uint64)
+    u0, _, _, _ = _draw(r, j, c, TAG_FILL, seed)
+    v = 1.0 / math.sqrt(n)
+    return np.where((u0 & np.uint64(1)) == 0, v, -v)
 
 
 def gaussian(j, n, b, seed):

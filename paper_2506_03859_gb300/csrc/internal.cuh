@@ -27,7 +27,7 @@ enum : int {
 };
 
 // Philox stream tags (counter word 3); see philox.cuh.
-enum : uint32_t { TAG_SPARSE_SIGN = 1, TAG_MASK = 2, TAG_GAUSS = 3 };
+enum : uint32_t { TAG_SPARSE_SIGN = 1, TAG_MASK = 2, TAG_GAUSS = 3, TAG_FILL = 4 };
 
 // ---------------------------------------------------------------- omega.cu
 struct OmegaSpec {
@@ -51,6 +51,11 @@ cudaError_t omega_sparse(const OmegaSpec& s, int64_t j0, int64_t nblk, int cap, 
 // as their definition.
 cudaError_t omega_dense(const OmegaSpec& s, int64_t j0, int64_t nblk, double* Om, int64_t ldo,
                         cudaStream_t st);
+// Columns c < b of X (rows x b, ld ldx) with dead[c] != 0 become +-1/sqrt(rows)
+// from the TAG_FILL stream, counter (r, j, c + 64 step): the directions that
+// replace the dependent columns of a power-step panel.
+cudaError_t fill_dead(double* X, int64_t ldx, int64_t rows, int b, const int* dead, uint32_t k0,
+                      uint32_t k1, int64_t j, int step, cudaStream_t st);
 
 // ---------------------------------------------------------------- sketch.cu
 // Y[i, g] = sum_t vals[g*cap+t] * X[i, rows[g*cap+t]] - (shift ? shift[i] : 0)
@@ -102,9 +107,14 @@ int64_t oz_ximg_bytes(int64_t P, int64_t K);
 cudaError_t oz_cut_x(bool trans, int64_t P, int64_t K, const void* X, int dtype, int64_t ldx,
                      const int* xE, uint8_t* ximg, int ctas, cudaStream_t st);
 // low: the reduced form (digits 0..3 of both operands; ~2^-30 of max|x| max|y|).
+// ydig1: every column of Y is a multiple of a single power of two (its entries
+// 0 and +-2^k, e.g. a +-1/2 test matrix), so Y's digits beyond the first are zero
+// and only the pairs (s, 0) are multiplied: the same result, exactly, from a
+// quarter of the tensor work and one Y digit plane per stage.
 cudaError_t ozgemm_img(int64_t P, int64_t N, int64_t K, double alpha, const uint8_t* ximg,
                        const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
-                       const OzWorkspace& w, int* flags, cudaStream_t st, bool low = false);
+                       const OzWorkspace& w, int* flags, cudaStream_t st, bool low = false,
+                       bool ydig1 = false);
 // rowE[r] / colE[c] = largest biased exponent in row r / column c of X (either may
 // be NULL).  accumulate_rows: rowE[r] = max(rowE[r], ...) instead of overwriting.
 cudaError_t oz_rowcol_exponents(const double* X, int64_t ld, int64_t rows, int64_t cols,
@@ -124,7 +134,11 @@ cudaError_t a_stats(const void* A, int dtype, int64_t lda, int64_t m, int64_t n,
 cudaError_t total(const double* v, int64_t count, double* out, cudaStream_t st);
 // Cholesky S = R^T R (S: b x b, ld b), R^{-1} into Rinv (b x b, ld b); on a failed
 // pivot (d_c not > tau * S_cc or not finite) sets FLAG_BREAKDOWN in *flags.
-cudaError_t chol_inv(const double* S, int b, double tau, double* Rinv, int* flags, cudaStream_t st);
+// With dead != NULL a failed pivot instead marks its column dependent (dead[c] = 1,
+// every entry of dead[0..b) written): the column takes no part in the other
+// columns' factor, and row and column c of Rinv are zero.
+cudaError_t chol_inv(const double* S, int b, double tau, double* Rinv, int* flags, cudaStream_t st,
+                     int* dead = nullptr);
 // B[row0 + c, r] = Wt[r, c] (Wt: n x b, ld ldw); zB[row0 + c] = p * colsum[c] if zB.
 cudaError_t append_rows(const double* Wt, int64_t ldw, int64_t n, int b, double* B, int64_t ldb,
                         int64_t row0, const double* colsum, double p, double* zB, cudaStream_t st);

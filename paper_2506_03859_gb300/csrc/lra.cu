@@ -134,6 +134,7 @@ struct lra_ctx {
   int64_t ws_elems = 0;
   double* astat = nullptr;  // per-(512-row block, column) sums of squares of A
   double *gram = nullptr, *Rinv = nullptr;
+  int* dead = nullptr;  // dependent columns of a power-step panel (LRA_MAX_B ints)
   double *colsq = nullptr, *colsum = nullptr, *scal = nullptr;
   int* flags = nullptr;
   int *om_counts = nullptr, *om_rows = nullptr;
@@ -289,15 +290,18 @@ lra_status gemm(lra_ctx* ctx, bool trans, int64_t P, int64_t N, int64_t K, doubl
 // A full pass over A: C = alpha op(A) Y + beta C (op(A) = A^T when trans).  Inside
 // lra_farpca_run the digit images of A, once cut, replace A itself.
 // power: a sketch or power-step pass, which the mixed precision form runs reduced.
+// ydig1: Y holds 0 and +-2^k per column only (the +-1/2 and 0/1 test matrices), so
+// the image-fed pass multiplies its first digit plane alone (the same result).
 lra_status dense(lra_ctx* ctx, bool trans, int64_t N, double alpha, const double* A, int64_t lda,
                  const double* Y, int64_t ldy, double beta, double* C, int64_t csp, int64_t csc,
-                 bool power = false) {
+                 bool power = false, bool ydig1 = false) {
   const int64_t P = trans ? ctx->n : ctx->m, K = trans ? ctx->m : ctx->n;
   if (!ctx->tensor || K > oz_max_k())
     return gemm(ctx, trans, P, N, K, alpha, A, lda, Y, ldy, beta, C, csp, csc);
   if (ctx->ximg_ready) {
     CK(ozgemm_img(P, N, K, alpha, ctx->ximg[trans ? 1 : 0], trans ? ctx->colE : ctx->rowE, Y, ldy,
-                  beta, GemmOut{C, csp, csc}, ctx->oz, ctx->flags, ctx->st, power && ctx->mixed));
+                  beta, GemmOut{C, csp, csc}, ctx->oz, ctx->flags, ctx->st, power && ctx->mixed,
+                  ydig1));
     return LRA_OK;
   }
   CK(ozgemm(trans, P, N, K, alpha, A, lda, trans ? ctx->colE : ctx->rowE, Y, ldy, beta,
@@ -362,6 +366,24 @@ lra_status orth(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows, double
   return LRA_OK;
 }
 
+// The basis G of the power-step panel W of block j, power step s (the eigSVD step
+// of Alg. 1).  A numerically dependent column of W does not end the run: the first
+// CholQR pass skips its pivot, the column of W R^{-1} is replaced by a fixed
+// random direction (+-1/sqrt(rows), TAG_FILL stream), and the second pass
+// orthonormalises the completed panel.  Without a dependent column this is orth().
+lra_status orth_panel(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows, double* out,
+                      int64_t ldo, int64_t j, int s) {
+  const int b = ctx->b;
+  TRY(gram(ctx, X, ldx, rows));
+  CK(chol_inv(ctx->gram, b, PIVOT_TAU, ctx->Rinv, ctx->flags, ctx->st, ctx->dead));
+  TRY(right_apply_rinv(ctx, X, ldx, rows, ctx->Tmp, ctx->lds));
+  CK(fill_dead(ctx->Tmp, ctx->lds, rows, b, ctx->dead, ctx->os.k0, ctx->os.k1, j, s, ctx->st));
+  TRY(gram(ctx, ctx->Tmp, ctx->lds, rows));
+  CK(chol_inv(ctx->gram, b, PIVOT_TAU, ctx->Rinv, ctx->flags, ctx->st));
+  TRY(right_apply_rinv(ctx, ctx->Tmp, ctx->lds, rows, out, ldo));
+  return LRA_OK;
+}
+
 lra_status make_omega(lra_ctx* ctx, int64_t j) {
   if (ctx->sparse)
     CK(omega_sparse(ctx->os, j, 1, ctx->cap, ctx->om_counts, ctx->om_rows, ctx->om_vals, ctx->flags,
@@ -380,8 +402,14 @@ lra_status apply_omega(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows_
                      ctx->om_vals, ctx->cap, ctx->b, out, ldo, shift, ctx->flags, ctx->st));
     return LRA_OK;
   }
-  if (x_is_A)
-    return dense(ctx, false, ctx->b, 1.0, X, ldx, ctx->om_dense, ctx->ldod, 0.0, out, 1, ldo, true);
+  if (x_is_A) {
+    // the standardized Bernoulli matrix at p = 1/2 (entries B - p = +-1/2) and the
+    // Bernoulli matrix (0 / 1) are one digit each
+    const bool one_digit = (ctx->kind == LRA_OMEGA_STD_BERNOULLI && ctx->os.p == 0.5) ||
+                           ctx->kind == LRA_OMEGA_BERNOULLI;
+    return dense(ctx, false, ctx->b, 1.0, X, ldx, ctx->om_dense, ctx->ldod, 0.0, out, 1, ldo, true,
+                 one_digit);
+  }
   return mm(ctx, false, rows_x, ctx->b, ctx->n, 1.0, X, ldx, ctx->browE, ctx->om_dense, ctx->ldod, 0.0,
             out, 1, ldo);
 }
@@ -587,7 +615,7 @@ lra_status run(lra_ctx* ctx, const void* Av, int64_t lda, int dtype) {
                    lds));
           });
         }
-        PHASE(LRA_PHASE_ORTH, TRY(orth(ctx, ctx->W, lds, n, ctx->G, lds)));
+        PHASE(LRA_PHASE_ORTH, TRY(orth_panel(ctx, ctx->W, lds, n, ctx->G, lds, j, 0)));
         for (int s = 1; s < P; ++s) {
           PHASE(LRA_PHASE_DENSE,
                 TRY(dense(ctx, false, b, 1.0, A, lda, ctx->G, lds, 0.0, ctx->T1, 1, lds, true)));
@@ -601,7 +629,7 @@ lra_status run(lra_ctx* ctx, const void* Av, int64_t lda, int dtype) {
                      lds));
             });
           }
-          PHASE(LRA_PHASE_ORTH, TRY(orth(ctx, ctx->W, lds, n, ctx->G, lds)));
+          PHASE(LRA_PHASE_ORTH, TRY(orth_panel(ctx, ctx->W, lds, n, ctx->G, lds, j, s)));
         }
         PHASE(LRA_PHASE_DENSE,
               TRY(dense(ctx, false, b, 1.0, A, lda, ctx->G, lds, 0.0, ctx->Yb, 1, lds, true)));
@@ -714,7 +742,7 @@ lra_status svd_alloc(lra_ctx* ctx, int64_t l) {
 void free_all(lra_ctx* c) {
   void* ptrs[] = {c->Q,      c->B,        c->Yk,     c->S0,       c->Yb,        c->T1,
                   c->Tmp,    c->W,        c->G,      c->Wt,       c->F,         c->BOm,
-                  c->z,      c->zB,       c->wvec,   c->ws,       c->gram,      c->Rinv,
+                  c->z,      c->zB,       c->wvec,   c->ws,       c->gram,      c->Rinv,   c->dead,
                   c->colsq,  c->colsum,   c->scal,   c->flags,    c->om_counts, c->om_rows,
                   c->om_vals, c->om_dense, c->sk_counts, c->sk_rows, c->sk_vals, c->A_host_copy,
                   c->rowE,   c->colE,     c->oz.yE,  c->oz.img,   c->oz.part,
@@ -874,6 +902,7 @@ lra_status create_ctx(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
   ALLOC(ws, ctx->ws_elems);
   ALLOC(gram, LRA_MAX_B * LRA_MAX_B);
   ALLOC(Rinv, LRA_MAX_B * LRA_MAX_B);
+  ALLOC(dead, LRA_MAX_B);
   ALLOC(colsq, std::max<int64_t>(n, LRA_MAX_B));
   ALLOC(colsum, std::max<int64_t>(n, LRA_MAX_B));
   ALLOC(scal, 8);

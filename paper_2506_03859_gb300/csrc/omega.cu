@@ -132,6 +132,26 @@ cudaError_t omega_sparse(const OmegaSpec& s, int64_t j0, int64_t nblk, int cap, 
   return launched();
 }
 
+__global__ void __launch_bounds__(256) k_fill_dead(double* __restrict__ X, int64_t ldx, int64_t rows,
+                                                   const int* __restrict__ dead, uint32_t k0,
+                                                   uint32_t k1, uint32_t j, uint32_t c0) {
+  const int c = blockIdx.y;
+  if (!dead[c]) return;
+  const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (r >= rows) return;
+  const U32x4 u = philox4x32_10((uint32_t)r, j, c0 + (uint32_t)c, TAG_FILL, k0, k1);
+  const double v = 1.0 / sqrt((double)rows);  // IEEE square root and division
+  X[r + (int64_t)c * ldx] = (u.x & 1u) ? -v : v;
+}
+
+cudaError_t fill_dead(double* X, int64_t ldx, int64_t rows, int b, const int* dead, uint32_t k0,
+                      uint32_t k1, int64_t j, int step, cudaStream_t st) {
+  if (rows <= 0 || b <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((rows + 255) / 256), (unsigned)b);
+  k_fill_dead<<<grid, 256, 0, st>>>(X, ldx, rows, dead, k0, k1, (uint32_t)j, (uint32_t)(64 * step));
+  return launched();
+}
+
 cudaError_t omega_dense(const OmegaSpec& s, int64_t j0, int64_t nblk, double* Om, int64_t ldo,
                         cudaStream_t st) {
   const int64_t ncols = nblk * s.b;

@@ -161,15 +161,25 @@ __global__ void __launch_bounds__(1024) k_total(const double* __restrict__ v, in
 constexpr int CHOL_NT = 1024;
 constexpr double CHOL_NEAR_I = 0x1p-34;
 
+//
+// Skip mode (dead != NULL, the first pass over a power-step panel): a failed
+// pivot marks column c dependent instead of ending the factorisation.  Its
+// reciprocal pivot is taken as 0, so row c of R beyond the diagonal and row c of
+// Z are zero: the column updates nothing after it, no other column of R^{-1}
+// refers to it, and column c of R^{-1} is zero (the caller replaces that column
+// of X R^{-1}).
 __global__ void __launch_bounds__(CHOL_NT) k_chol_inv(const double* __restrict__ S, int b, double tau,
-                                                      double* __restrict__ Rinv, int* __restrict__ flags) {
+                                                      double* __restrict__ Rinv, int* __restrict__ flags,
+                                                      int* __restrict__ dead) {
   constexpr int NWORK = CHOL_NT - 32;
   __shared__ double M[64][65];  // trailing block (upper triangle); row c becomes row c of R
   __shared__ double Z[64][65];  // right-hand side, rows of Z once final (lower triangle)
   __shared__ double Sd[64], dpiv[64], rpiv[64];
   __shared__ uint16_t pairs[64 * 65 / 2];  // (i << 8) | j, i <= j, i descending
   __shared__ int bad;
+  __shared__ int sdead[64];
   const int t = threadIdx.x;
+  const bool skip = dead != nullptr;
   // workers: warps 1 .. 31; thread 0 takes the pivots
   const int wk = t - 32;
   int far = 0;  // an entry of S - I above 2^-34, or not finite
@@ -187,8 +197,10 @@ __global__ void __launch_bounds__(CHOL_NT) k_chol_inv(const double* __restrict__
       const double v = M[i][j];
       Rinv[i + j * b] = i < j ? -v : (i == j ? fma(-0.5, v - 1.0, 1.0) : 0.0);
     }
+    if (skip && t < b) dead[t] = 0;
     return;
   }
+  if (t < 64) sdead[t] = 0;
   // entry e of the pair table: rows b-1, b-2, ... in turn, row i holding j = i..b-1;
   // the rows above i (i' > i) take sum_{i' > i} (b - i') = (b-1-i)(b-i)/2 entries
   for (int i = t; i < b; i += CHOL_NT) {
@@ -198,17 +210,19 @@ __global__ void __launch_bounds__(CHOL_NT) k_chol_inv(const double* __restrict__
   if (t < b) Sd[t] = S[t + t * b];
   if (t == 0) {
     const double d = S[0];
-    bad = !(isfinite(d) && d > tau * d);
+    const int fail = !(isfinite(d) && d > tau * d);
+    bad = fail && !skip;
+    if (fail && skip) sdead[0] = 1;
     dpiv[0] = d;
-    rpiv[0] = bad ? 0.0 : rsqrt(d);
+    rpiv[0] = fail ? 0.0 : rsqrt(d);
   }
   __syncthreads();
   for (int c = 0; c < b; ++c) {
     if (bad) break;  // set before the last barrier: the same decision in every thread
     const double r = rpiv[c];
-    // row c of R (R_cc = d r) and row c of Z
-    if (t >= c && t < b) M[c][t] = (t == c) ? dpiv[c] * r : M[c][t] * r;
-    else if (t >= 64 && t - 64 <= c) Z[c][t - 64] *= r;
+    // row c of R (R_cc = d r) and row c of Z (both zero for a dependent column)
+    if (t >= c && t < b) M[c][t] = (r == 0.0) ? 0.0 : (t == c) ? dpiv[c] * r : M[c][t] * r;
+    else if (t >= 64 && t - 64 <= c) Z[c][t - 64] = (r == 0.0) ? 0.0 : Z[c][t - 64] * r;
     __syncthreads();
     const int nt = b - c - 1;
     if (t == 0) {
@@ -216,7 +230,13 @@ __global__ void __launch_bounds__(CHOL_NT) k_chol_inv(const double* __restrict__
         const double rc1 = M[c][c + 1];
         const double d = fma(-rc1, rc1, M[c + 1][c + 1]);
         if (!(isfinite(d) && d > tau * Sd[c + 1])) {
-          bad = 1;
+          if (skip) {
+            sdead[c + 1] = 1;
+            dpiv[c + 1] = 0.0;
+            rpiv[c + 1] = 0.0;
+          } else {
+            bad = 1;
+          }
         } else {
           dpiv[c + 1] = d;
           rpiv[c + 1] = rsqrt(d);
@@ -249,6 +269,7 @@ __global__ void __launch_bounds__(CHOL_NT) k_chol_inv(const double* __restrict__
     const int i = e % b, j = e / b;
     Rinv[i + j * b] = i <= j ? Z[j][i] : 0.0;
   }
+  if (skip && t < b) dead[t] = sdead[t];
 }
 
 __global__ void k_append_rows(const double* __restrict__ Wt, int64_t ldw, int64_t n, int b,
@@ -299,8 +320,9 @@ cudaError_t total(const double* v, int64_t count, double* out, cudaStream_t st) 
   return launched();
 }
 
-cudaError_t chol_inv(const double* S, int b, double tau, double* Rinv, int* flags, cudaStream_t st) {
-  k_chol_inv<<<1, CHOL_NT, 0, st>>>(S, b, tau, Rinv, flags);
+cudaError_t chol_inv(const double* S, int b, double tau, double* Rinv, int* flags, cudaStream_t st,
+                     int* dead) {
+  k_chol_inv<<<1, CHOL_NT, 0, st>>>(S, b, tau, Rinv, flags, dead);
   return launched();
 }
 

@@ -430,7 +430,9 @@ __device__ __forceinline__ void oz_teardown(OzShared& sh, const OzArgs& a) {
 // stages' weight >= 4 MMAs, the wait, then both stages' exact MMAs.  A new
 // segment first waits for the flush to finish the previous one (its FP32 sums).
 // HIGH = false: the reduced form (digits 0..3 of both operands only), exact MMAs alone.
-template <bool HIGH>
+// YD1: Y has a single nonzero digit plane (plane 0, e.g. a +-1/2 test matrix), so the
+// only nonzero pairs are (s, 0): one MMA of N = 64 per X plane, weight s.
+template <bool HIGH, bool YD1 = false>
 __device__ __forceinline__ void oz_mma_role(OzShared& sh, const Cursor& start, uint8_t* sm) {
   volatile int& s_abort = sh.abort;
   const uint32_t tmem = sh.tmem;
@@ -450,6 +452,12 @@ __device__ __forceinline__ void oz_mma_role(OzShared& sh, const Cursor& start, u
   auto high = [&](int st, bool fresh) {
     if (!HIGH) return;
     const uint32_t a0 = tc::smem_addr(sm + st * STAGE), y0 = a0 + S * A_PLANE;
+    if (YD1) {
+      mma_group(tmem, a0, y0, 4, 0, 1, fresh ? 0u : 1u);
+      mma_group(tmem, a0, y0, 5, 0, 1, fresh ? 0u : 1u);
+      mma_group(tmem, a0, y0, 6, 0, 1, fresh ? 0u : 1u);
+      return;
+    }
     mma_group(tmem, a0, y0, 0, 4, 3, fresh ? 0u : 1u);
     mma_group(tmem, a0, y0, 1, 3, 3, 1u);
     mma_group(tmem, a0, y0, 2, 2, 3, 1u);
@@ -460,6 +468,14 @@ __device__ __forceinline__ void oz_mma_role(OzShared& sh, const Cursor& start, u
   };
   auto exact = [&](int st) {
     const uint32_t a0 = tc::smem_addr(sm + st * STAGE), y0 = a0 + S * A_PLANE;
+    if (YD1) {
+      mma_group(tmem, a0, y0, 0, 0, 1, 1u);
+      mma_group(tmem, a0, y0, 1, 0, 1, 1u);
+      mma_group(tmem, a0, y0, 2, 0, 1, 1u);
+      mma_group(tmem, a0, y0, 3, 0, 1, 1u);
+      tc::mma_commit(&sh.empty[st]);
+      return;
+    }
     mma_group(tmem, a0, y0, 0, 0, 4, 1u);
     mma_group(tmem, a0, y0, 1, 0, 3, 1u);
     mma_group(tmem, a0, y0, 2, 0, 2, 1u);
@@ -787,9 +803,10 @@ constexpr int NT_IMG = NFLUSH_IMG + 64;
 
 // LOW: the reduced form -- only digits 0..3 of A and of Y are copied and multiplied
 // (the 10 pairs of weight <= 3, all summed exactly): error ~2^-30 of max|x| max|y|.
-template <bool LOW>
+template <bool LOW, bool YD1>
 __global__ void __launch_bounds__(NT_IMG, 1) k_ozgemm_img(OzArgs a, const uint8_t* __restrict__ ximg) {
-  constexpr int SUSE = LOW ? 4 : S;  // digit planes used
+  constexpr int SUSE = LOW ? 4 : S;   // digit planes of X used
+  constexpr int YUSE = YD1 ? 1 : SUSE;  // digit planes of Y copied
   extern __shared__ uint8_t smem_raw[];
   __shared__ OzShared sh;
   const uint32_t raw = tc::smem_addr(smem_raw);
@@ -817,15 +834,15 @@ __global__ void __launch_bounds__(NT_IMG, 1) k_ozgemm_img(OzArgs a, const uint8_
           ph_empty[st] ^= 1u;
         }
         uint8_t* sA = sm + st * STAGE;
-        tc::mbar_arrive_expect_tx(&sh.full[st], SUSE * (A_PLANE + Y_PLANE));
+        tc::mbar_arrive_expect_tx(&sh.full[st], SUSE * A_PLANE + YUSE * Y_PLANE);
         tc::bulk_g2s(sA, ximg + (c.tile * a.kst + c.ks) * (int64_t)(S * A_PLANE), SUSE * A_PLANE,
                      &sh.full[st]);
-        tc::bulk_g2s(sA + S * A_PLANE, a.img + (int64_t)c.ks * Y_STAGE, SUSE * Y_PLANE, &sh.full[st]);
+        tc::bulk_g2s(sA + S * A_PLANE, a.img + (int64_t)c.ks * Y_STAGE, YUSE * Y_PLANE, &sh.full[st]);
       }
     }
     __syncwarp();
   } else if (warp == 9) {
-    if (lane == 0) oz_mma_role<!LOW>(sh, start, sm);
+    if (lane == 0) oz_mma_role<!LOW, YD1>(sh, start, sm);
     __syncwarp();
   } else {
     oz_flush_role<true, !LOW, 8>(sh, a, start, cta);
@@ -1041,11 +1058,13 @@ cudaError_t set_smem_once(F kernel, std::atomic<bool>& done) {
 
 cudaError_t oz_prepare() {
   // set once per process; concurrent first calls set the same attribute twice
-  static std::atomic<bool> a0{false}, a1{false}, a2{false}, a3{false};
+  static std::atomic<bool> a0{false}, a1{false}, a2{false}, a3{false}, a4{false}, a5{false};
   cudaError_t e = set_smem_once(k_ozgemm<false>, a0);
   if (e == cudaSuccess) e = set_smem_once(k_ozgemm<true>, a1);
-  if (e == cudaSuccess) e = set_smem_once(k_ozgemm_img<false>, a2);
-  if (e == cudaSuccess) e = set_smem_once(k_ozgemm_img<true>, a3);
+  if (e == cudaSuccess) e = set_smem_once(k_ozgemm_img<false, false>, a2);
+  if (e == cudaSuccess) e = set_smem_once(k_ozgemm_img<true, false>, a3);
+  if (e == cudaSuccess) e = set_smem_once(k_ozgemm_img<false, true>, a4);
+  if (e == cudaSuccess) e = set_smem_once(k_ozgemm_img<true, true>, a5);
   return e;
 }
 
@@ -1082,7 +1101,7 @@ cudaError_t oz_cut_x(bool trans, int64_t P, int64_t K, const void* X, int dtype,
 
 cudaError_t ozgemm_img(int64_t P, int64_t N, int64_t K, double alpha, const uint8_t* ximg,
                        const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
-                       const OzWorkspace& w, int* flags, cudaStream_t st, bool low) {
+                       const OzWorkspace& w, int* flags, cudaStream_t st, bool low, bool ydig1) {
   if (P <= 0 || N <= 0) return cudaSuccess;
   if (N > NN || K <= 0 || K > MAX_K) return cudaErrorInvalidValue;
   if (oz_img_bytes(K) > w.img_bytes) return cudaErrorInvalidValue;
@@ -1092,10 +1111,14 @@ cudaError_t ozgemm_img(int64_t P, int64_t N, int64_t K, double alpha, const uint
   if (e != cudaSuccess) return e;
   OzArgs a = make_args(P, N, K, alpha, nullptr, 0, xE, beta, out, w, flags);
   const int G = w.ctas;
-  if (low)
-    k_ozgemm_img<true><<<G, NT_IMG, SMEM_DYN, st>>>(a, ximg);
+  if (low && ydig1)
+    k_ozgemm_img<true, true><<<G, NT_IMG, SMEM_DYN, st>>>(a, ximg);
+  else if (low)
+    k_ozgemm_img<true, false><<<G, NT_IMG, SMEM_DYN, st>>>(a, ximg);
+  else if (ydig1)
+    k_ozgemm_img<false, true><<<G, NT_IMG, SMEM_DYN, st>>>(a, ximg);
   else
-    k_ozgemm_img<false><<<G, NT_IMG, SMEM_DYN, st>>>(a, ximg);
+    k_ozgemm_img<false, false><<<G, NT_IMG, SMEM_DYN, st>>>(a, ximg);
   e = launched();
   if (e != cudaSuccess || a.whole_tiles) return e;
   return launch_fixup(a, G, st);

@@ -303,3 +303,51 @@ def test_cholesky_inverse_near_identity():
         Rinv = np.linalg.inv(np.linalg.cholesky(S).T)
         closed = np.eye(b) - (np.triu(E, 1) + np.diag(np.diag(E)) / 2)
         assert np.abs(closed - Rinv).max() <= 2 * b * np.abs(E).max() ** 2 + 4 * np.finfo(float).eps
+
+
+def _diag_v_matrix(n, seed):
+    """Sec. 5.5's hard case: Matrix 1's spectrum with V_A = diag(+-1) (d = n)."""
+    rng = np.random.default_rng(seed)
+    U, R = np.linalg.qr(rng.standard_normal((n, n)))
+    U *= np.sign(np.diag(R))[None, :]
+    return np.asfortranarray((U * (1.0 / np.arange(1, n + 1) ** 2)[None, :]) * rng.choice([-1.0, 1.0], n)[None, :])
+
+
+def test_orth_panel_completes_a_dependent_panel():
+    """orth_panel: without a dependent column it is orth() exactly; with one, the
+    dependent column is marked (its pivot fails), the result is orthonormal, spans
+    the other columns, and its new direction is the TAG_FILL column made
+    orthogonal to them (Gram-Schmidt of a fixed +-1/sqrt(n) vector)."""
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((300, 6))
+    assert np.array_equal(F.orth_panel(X, 0, 0, 1), F.orth(X))
+    Xd = X.copy()
+    Xd[:, 2] = X[:, 0] - 2.0 * X[:, 1]          # column 2 depends on columns 0 and 1
+    _, dead = F.cholesky_upper_skip(Xd.T @ Xd)
+    assert dead.tolist() == [False, False, True, False, False, False]
+    G = F.orth_panel(Xd, 5, 1, 9)
+    assert np.abs(G.T @ G - np.eye(6)).max() < 1e-13
+    live = Xd[:, [0, 1, 3, 4, 5]]
+    assert np.linalg.norm(live - G @ (G.T @ live)) < 1e-12 * np.linalg.norm(live)
+    f = om.fill_column(300, 5, 2 + 64, 9)
+    assert np.all(np.abs(np.abs(f) - 1 / np.sqrt(300)) == 0)
+    # G's column 2: f with its components along columns 0 and 1 of G removed, normalised
+    # (the completed panel's column order: 0, 1, then the fill, then 3, 4, 5)
+    g2 = f - G[:, :2] @ (G[:, :2].T @ f)
+    g2 /= np.linalg.norm(g2)
+    assert np.abs(G[:, 2] - g2).max() < 1e-12
+
+
+@pytest.mark.parametrize("kind,p", [(om.STD_BERNOULLI, 0.0), (om.SPARSE_SIGN_IID, 2e-3)])
+def test_dependent_power_panels_do_not_end_the_run(kind, p):
+    """Sec. 5.5, V_A with d = n blocks (A^T A diagonal): the power-step panel is
+    numerically rank deficient, which the paper's eigSVD passes over.  The run goes
+    on (no breakdown), and what it returns is still a valid QB: Q^T Q = I,
+    B = Q^T A, E = ||A - QB||_F^2."""
+    A = _diag_v_matrix(400, 12)
+    r = F.farpca(A, 1e-4, P=1, b=20, kind=kind, seed=4, p=p)
+    assert r["status"] != F.BREAKDOWN and r["rank"] > 0
+    Q, B = r["Q"], r["B"]
+    assert np.abs(Q.T @ Q - np.eye(Q.shape[1])).max() < 1e-12
+    assert np.abs(B - Q.T @ A).max() < 1e-12 * np.abs(B).max()
+    assert abs(r["E"] - np.linalg.norm(A - Q @ B) ** 2) < 1e-12 * r["normA2"]
