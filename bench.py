@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--no-graphs", action="store_true",
                     help="with --only batch: launch the batch's steps from the host (for profiling)")
     ap.add_argument("--only", choices=("sketch", "dense", "serve", "batch", "fixedrank", "stability", "svd",
-                                       "runlist"),
+                                       "runlist", "precision"),
                     default=None,
                     help="run only the sketch pass (lra_sketch over --sketch-blocks blocks) or only "
                          "the two dense passes A Y and A^T Y (lra_apply), for profiling")
@@ -264,8 +264,11 @@ def main():
     f = lra.Farpca(m, n, eps=cfg["eps"], b=cfg["b"], P=cfg["P"], kind=cfg["kind"], zeta=cfg["zeta"],
                    p=cfg["p"], seed=cfg["seed"] + rank, profile=True, stream=stream,
                    fp64_simt=(args.engine == "fp64_simt"))
-    if args.only in ("sketch", "dense", "serve", "batch", "fixedrank", "stability", "svd", "runlist"):
-        if args.only == "runlist":
+    if args.only in ("sketch", "dense", "serve", "batch", "fixedrank", "stability", "svd", "runlist",
+                     "precision"):
+        if args.only == "precision":
+            out = {"precision_cfg3": precision_workload(lra, torch, np, stream)}
+        elif args.only == "runlist":
             out = {"run_list": run_list(lra, torch, np, Ad, peaks, peak_src, stream)}
         elif args.only == "serve":
             out = {"serving": serving(lra, torch, np, slots=args.serve_slots)}
@@ -368,6 +371,7 @@ def main():
         line["sketch_pass"] = sketch_pass(lra, torch, f, Ad, cfg, args.sketch_blocks, peaks, peak_src)
         line["run_list"] = run_list(lra, torch, np, Ad, peaks, peak_src, stream)
         line["mixed"] = mixed_form(lra, torch, Ad, cfg, m, n, args.steps, res["rel_err"], stream)
+        line["precision_cfg3"] = precision_workload(lra, torch, np, stream)
         line["svd"] = svd_extraction(torch, f, args.steps, stream)
         line["fp32_input"] = fp32_form(lra, torch, Ad, cfg, m, n, args.steps, stream)
         if rank == 0 and world == 1:
@@ -491,6 +495,59 @@ def run_list(lra, torch, np, Ad, peaks, peak_src, stream, reps=3):
     return out
 
 
+def precision_workload(lra, torch, np, stream, m=60000, n=20000, rank=11000, oracle_blocks=2):
+    """The precision workload: 60000 x 20000 FP64, sigma_i = i^-1 on rank 11000 (built in
+    FP32 on the device), b = 64, P = 1, eps = 1e-3, the standardized Bernoulli +-1 sketch
+    (and the sparse sign sketch, zeta = 8, beside it).  eps is out of reach within the cap
+    ceil(n / 2b) = 157 blocks (rank 10048), so every run ends NOT_CONVERGED at the cap:
+    reported are the time to the cap and the final error of the FP64-accurate form and of
+    the mixed precision form (LRA_FLAG_MIXED), and, against the FP64 CPU oracle at an equal
+    block count (`oracle_blocks` blocks, the oracle's cost bound), the indicator and final
+    error of both forms."""
+    import math
+    from lra_inputs import device_low_rank
+    from oracle import farpca as F
+    A = device_low_rank(m, n, rank, 4242, dtype=torch.float64, spectrum="poly1", build_dtype=torch.float32)
+    torch.cuda.synchronize()
+    out = {"workload": "precision_%dx%d_poly1_rank%d_b64_P1_eps1e-3" % (m, n, rank)}
+    kinds = {"sb_pm1": (lra.STD_BERNOULLI, 0.5, 0), "ss8": (lra.SPARSE_SIGN, 0.0, 8)}
+    for kname, (kind, p, zeta) in kinds.items():
+        for mixed in (False, True):
+            f = lra.Farpca(m, n, eps=1e-3, b=64, P=1, kind=kind, zeta=zeta, p=p, seed=5, mixed=mixed,
+                           stream=stream)
+            f.run(A)   # warm-up (captures the block graphs)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = f.run(A)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            r = f.result()
+            out["%s_%s" % (kname, "mixed" if mixed else "fp64")] = {
+                "ms_to_cap": e0.elapsed_time(e1), "status": lra.status_string(st), "rank": r["rank"],
+                "blocks": r["blocks"], "rel_err": r["rel_err"]}
+            f.close()
+    # against the oracle at an equal block count (standardized Bernoulli +-1)
+    Ah = A.cpu().numpy()
+    t0 = time.perf_counter()
+    ref = F.farpca(Ah, 1e-3, P=1, b=64, kind=lra.STD_BERNOULLI, seed=5, p=0.5, max_blocks=oracle_blocks)
+    t_oracle = time.perf_counter() - t0
+    cmp = {}
+    for mixed in (False, True):
+        f = lra.Farpca(m, n, eps=1e-3, b=64, P=1, kind=lra.STD_BERNOULLI, p=0.5, seed=5, mixed=mixed,
+                       max_blocks=oracle_blocks, stream=stream)
+        f.run(A)
+        r = f.result()
+        rel, rel_ref = (math.sqrt(max(x, 0.0) / ref["normA2"]) for x in (r["E"], ref["E"]))
+        cmp["mixed" if mixed else "fp64"] = {
+            "rank": r["rank"], "rank_oracle": ref["rank"], "dE_over_normA2": abs(r["E"] - ref["E"]) / ref["normA2"],
+            "rel_err": rel, "rel_err_oracle": rel_ref, "rel_err_dev": abs(rel - rel_ref) / rel_ref}
+        f.close()
+    out["vs_oracle"] = dict(cmp, blocks=oracle_blocks, oracle_seconds=t_oracle, cores=oracle_threads())
+    del A, Ah
+    return out
+
+
 def sketch_pass(lra, torch, f, Ad, cfg, nblk, peaks, peak_src):
     """lra_sketch over nblk consecutive blocks (one launch of the gather kernel)."""
     m, n, b = f.m, f.n, f.b
@@ -550,16 +607,23 @@ def serve_block(m, n):
     return min(max(20, min(m, n) // 100), 50)
 
 
-def serving(lra, torch, np, duration_s=3.0, rate=200.0, slots=8, seed=11):
+def serving(lra, torch, np, duration_s=3.0, rate=200.0, slots=8, seed=11, pool_size=24):
     """Served solves/s and p50/p99 latency: a Poisson stream (mean `rate` req/s) of
-    FP32 requests, sizes log-uniform 1000x500 .. 40000x20000 (a pool of ten
-    device-resident matrices, exact rank 400, sigma_i = 10^(-i/100)), mixed Omega
-    kinds and eps in {1e-1, 1e-2, 1e-3}, through lra_server; beside it the same
-    trace as plain FP64 one-at-a-time farPCA (one context per request, in arrival
-    order; its queueing follows from the measured service times)."""
+    FP32 requests, sizes log-uniform 1000x500 .. 40000x20000 (a pool of `pool_size`
+    device-resident matrices of seeded log-uniform sizes, n = m/2, exact rank 400,
+    sigma_i = 10^(-i/100)), mixed Omega kinds and eps in {1e-1, 1e-2, 1e-3}.
+
+    Three arms on the same trace, every latency measured (completion time minus
+    arrival time on the host clock):
+      * served, mixed precision form (LRA_FLAG_MIXED): lra_server, `slots` at once;
+      * served, FP64-accurate form: the same server without the flag;
+      * plain FP64 one at a time: the trace replayed in real time by one host loop
+        that waits for each arrival, then runs the request alone (a context from the
+        same stream-ordered pool as the server's, LRA_FLAG_POOL) and waits for it."""
     from lra_inputs import device_low_rank
     rng = np.random.default_rng(seed)
-    sizes = [int(round(v)) for v in np.exp(np.linspace(np.log(1000), np.log(40000), 10))]
+    sizes = sorted(int(round(v)) for v in np.exp(rng.uniform(np.log(1000), np.log(40000), pool_size)))
+    sizes[0], sizes[-1] = 1000, 40000   # both ends of the range are in the pool
     pool = [device_low_rank(mm, mm // 2, min(400, mm // 2), 500 + i) for i, mm in enumerate(sizes)]
     trace, t = [], 0.0
     while True:
@@ -573,53 +637,63 @@ def serving(lra, torch, np, duration_s=3.0, rate=200.0, slots=8, seed=11):
         prm = lra.params(eps=eps, b=serve_block(mm, nn), P=1, kind=kind, zeta=zeta, p=p,
                          seed=int(rng.integers(1 << 62)))
         trace.append((t, k, prm))
-    torch.cuda.synchronize()
-    srv = lra.Server(slots=slots, flags=lra.FLAG_NO_GRAPHS)
-    t0 = srv.clock()
-    done = []
-    import time
-    for i, (ta, k, prm) in enumerate(trace):
-        while srv.clock() - t0 < ta:
-            done += srv.poll()
-            time.sleep(0.0002)
-        srv.submit(pool[k], prm, i)
-    while len(done) < len(trace):
-        done += srv.poll(wait=True)
-    srv.close()
-    lat = np.array([c["t_done"] - c["t_submit"] for c in done])
-    span = max(c["t_done"] for c in done) - min(c["t_submit"] for c in done)
-    ok = sum(1 for c in done if c["status"] >= 0)
-    # the same trace, FP64, one request at a time
+
+    def served(flags):
+        torch.cuda.synchronize()
+        srv = lra.Server(slots=slots, flags=flags)
+        t0 = srv.clock()
+        done = []
+        for i, (ta, k, prm) in enumerate(trace):
+            while srv.clock() - t0 < ta:
+                done += srv.poll()
+                time.sleep(0.0002)
+            srv.submit(pool[k], prm, i)
+        while len(done) < len(trace):
+            done += srv.poll(wait=True)
+        srv.close()
+        lat = np.array([c["t_done"] - c["t_submit"] for c in done])
+        span = max(c["t_done"] for c in done) - min(c["t_submit"] for c in done)
+        ok = sum(1 for c in done if c["status"] >= 0)
+        return {"solves_per_s": len(trace) / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)), "completed_ok": ok,
+                "mean_rel_err": float(np.mean([c["rel_err"] for c in done]))}
+
+    mixed = served(lra.FLAG_NO_GRAPHS | lra.FLAG_MIXED)
+    fp64_served = served(lra.FLAG_NO_GRAPHS)
+    # the same trace, plain FP64, one request at a time, replayed in real time
     pool64 = []
     for A in pool:
         B = torch.empty_strided(A.shape, (1, A.shape[0]), dtype=torch.float64, device="cuda")
         B.copy_(A)
         pool64.append(B)
-    del pool
-    finish, lat1 = 0.0, []
+    torch.cuda.synchronize()
+    lat1 = []
+    t0 = time.perf_counter()
     for ta, k, prm in trace:
+        now = time.perf_counter() - t0
+        if now < ta:
+            time.sleep(ta - now)
         mm, nn = pool64[k].shape
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
         f = lra.Farpca(mm, nn, eps=prm.eps, b=prm.b, P=prm.P, kind=prm.kind, zeta=prm.zeta, p=prm.p,
-                       seed=prm.seed)
+                       seed=prm.seed, pool=True, graphs=False)
         f.run(pool64[k])
         f.close()
         torch.cuda.synchronize()
-        service = time.perf_counter() - t1
-        finish = max(finish, ta) + service
-        lat1.append(finish - ta)
+        lat1.append(time.perf_counter() - t0 - ta)
+    span1 = time.perf_counter() - t0 - trace[0][0]
     lat1 = np.array(lat1)
-    span1 = finish - trace[0][0]
-    del pool64
-    return {"requests": len(trace), "completed_ok": ok, "rate_req_s": rate, "slots": slots,
-            "solves_per_s": len(trace) / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-            "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+    del pool64, pool
+    return {"requests": len(trace), "rate_req_s": rate, "slots": slots,
+            "solves_per_s": mixed["solves_per_s"], "p50_ms": mixed["p50_ms"], "p99_ms": mixed["p99_ms"],
+            "form": "mixed precision (LRA_FLAG_MIXED)", "completed_ok": mixed["completed_ok"],
+            "served_mixed": mixed, "served_fp64": fp64_served,
             "one_at_a_time_fp64": {"solves_per_s": len(trace) / span1,
                                    "p50_ms": 1e3 * float(np.percentile(lat1, 50)),
-                                   "p99_ms": 1e3 * float(np.percentile(lat1, 99))},
-            "sizes": "log-uniform %dx%d .. %dx%d (10 sizes)" % (sizes[0], sizes[0] // 2, sizes[-1],
-                                                             sizes[-1] // 2)}
+                                   "p99_ms": 1e3 * float(np.percentile(lat1, 99)),
+                                   "allocation": "stream-ordered pool (LRA_FLAG_POOL)",
+                                   "latency": "measured (real-time replay of the trace)"},
+            "sizes": "log-uniform %dx%d .. %dx%d (%d matrices)" % (sizes[0], sizes[0] // 2, sizes[-1],
+                                                                 sizes[-1] // 2, len(sizes))}
 
 
 def batched(lra, torch, np, peaks, peak_src, count=4096, reps=3, graph=True):

@@ -89,17 +89,20 @@ def workload_matrix(name, **override):
                        cfg.get("rank"))
 
 
-def device_low_rank(m, n, rank, seed, dtype=None, spectrum="exp100", device="cuda"):
+def device_low_rank(m, n, rank, seed, dtype=None, spectrum="exp100", device="cuda", build_dtype=None):
     """A = U diag(sigma) V^T on a CUDA device (torch), column-major, exact rank
     `rank` (U, V with orthonormal columns from QR of seeded Gaussians), built in
-    float64 and stored as `dtype` (default float32).  For large request pools
-    (the serving workload), where host generation would dominate."""
+    `build_dtype` (default float64) and stored as `dtype` (default float32).  For
+    large request pools (the serving workload) and the 60000 x 20000 precision
+    workload, where host generation would dominate; building in float32 keeps
+    the singular values to ~1e-6 relative, which is all these workloads need."""
     import torch
     dtype = dtype or torch.float32
+    build_dtype = build_dtype or torch.float64
     g = torch.Generator(device=device).manual_seed(int(seed))
-    U = torch.linalg.qr(torch.randn((m, rank), generator=g, dtype=torch.float64, device=device))[0]
-    V = torch.linalg.qr(torch.randn((n, rank), generator=g, dtype=torch.float64, device=device))[0]
-    sig = torch.from_numpy(singular_values(spectrum, rank)).to(device)
+    U = torch.linalg.qr(torch.randn((m, rank), generator=g, dtype=build_dtype, device=device))[0]
+    V = torch.linalg.qr(torch.randn((n, rank), generator=g, dtype=build_dtype, device=device))[0]
+    sig = torch.from_numpy(singular_values(spectrum, rank)).to(device=device, dtype=build_dtype)
     A = torch.empty_strided((m, n), (1, m), dtype=dtype, device=device)
     A.copy_((U * sig[None, :]) @ V.T)
     return A

@@ -219,14 +219,15 @@ class Farpca:
 
     def __init__(self, m, n, eps=0.0, k=0, b=20, P=1, kind=SPARSE_SIGN, zeta=8, p=0.0, seed=0,
                  max_blocks=0, keep_y=False, profile=False, fp64_simt=False, a_digits=True,
-                 graphs=True, mixed=False, stream=None):
+                 graphs=True, mixed=False, pool=False, stream=None):
         import torch
         self._torch = torch
         self._lib = load()
         self.m, self.n, self.b = m, n, b
         flags = ((FLAG_KEEP_Y if keep_y else 0) | (FLAG_PROFILE if profile else 0)
                  | (FLAG_FP64_SIMT if fp64_simt else 0) | (0 if a_digits else FLAG_NO_A_DIGITS)
-                 | (0 if graphs else FLAG_NO_GRAPHS) | (FLAG_MIXED if mixed else 0))
+                 | (0 if graphs else FLAG_NO_GRAPHS) | (FLAG_MIXED if mixed else 0)
+                 | (FLAG_POOL if pool else 0))
         self.params = Params(eps, k, b, P, kind, zeta, p, seed & 0xFFFFFFFFFFFFFFFF, max_blocks, flags)
         self._ctx = c_void_p()
         if stream is None and torch.cuda.is_available():

@@ -2,15 +2,21 @@
 
 Each request's Omega comes from its own Philox key and every kernel of the path
 is deterministic, so a request's result must be the same bits whether it runs
-alone or beside others; the admission rules (budget, slots, arrival order) are
-checked against the completions' own start and finish times.
+alone or beside others; served results also match the FP64 CPU oracle at the
+parity bars of tests/test_gpu_parity.py (the mixed precision served form at its
+own bar: the same rank and status, the final error within 1%); the admission
+rules (budget, slots, arrival order) are checked against the completions' own
+start and finish times.
 """
+import math
+
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
 from lra_inputs import low_rank_matrix  # noqa: E402
+from oracle import farpca as F  # noqa: E402
 from paper_2506_03859_gb300 import lra  # noqa: E402
 from paper_2506_03859_gb300.build import build  # noqa: E402
 
@@ -121,3 +127,81 @@ def test_refusals():
     f = lra.Farpca(600, 400, eps=1e-2, b=16, P=1, kind=lra.SPARSE_SIGN, zeta=8, seed=1)
     assert f.device_bytes() + 64 >= lra.workspace_bytes(600, 400, prm) >= f.device_bytes()
     f.close()
+
+
+def _served(reqs, flags):
+    """Serve every request (kept), return {id: completion with its result}."""
+    srv = lra.Server(slots=4, flags=flags)
+    for r in reqs:
+        srv.submit(r["A"], r["prm"], r["id"], keep=True)
+    got = {}
+    while len(got) < len(reqs):
+        for c in srv.poll(wait=True):
+            got[c["id"]] = c
+    for c in got.values():
+        c["result"] = c["run"].result()
+    return srv, got
+
+
+def _oracle_requests():
+    """One small request per hot-path kind (FP64 and FP32 data, eps 1e-2 and 1e-3).
+    The rank (500) exceeds what eps = 1e-3 needs (~300 singular values of
+    10^(-i/100)) and the block cap (ceil(n / 32) blocks of 16) leaves room for it, so
+    no run ends at the edge of the exact rank, where a breakdown would hinge on
+    rounding noise that the mixed form does not share."""
+    out = []
+    for i, (kind, p, zeta) in enumerate(KINDS):
+        m, n = 1400 + 37 * i, 900 - 41 * i
+        A = low_rank_matrix(m, n, "exp100", 300 + i, rank=500)
+        dtype = torch.float32 if i % 2 else torch.float64
+        if dtype == torch.float32:
+            A = A.astype(np.float32).astype(np.float64)
+        eps = 1e-2 if i < 2 else 1e-3
+        out.append(dict(id=i, host=A, A=dev(A, dtype), kind=kind, p=p, zeta=zeta, eps=eps,
+                        prm=lra.params(eps=eps, b=16, P=1, kind=kind, zeta=zeta, p=p, seed=700 + i)))
+    return out
+
+
+def test_served_results_match_the_oracle():
+    """FP64 served form: rank and status equal; E within 5e-14 ||A||_F^2, the final
+    relative error within 1e-10 (or the FP64 indicator's resolution at eps = 1e-3),
+    Q within 1e-10, B within 1e-10 of max |B|."""
+    reqs = _oracle_requests()
+    srv, got = _served(reqs, lra.FLAG_NO_GRAPHS)
+    for r in reqs:
+        res = got[r["id"]]["result"]
+        ref = F.farpca(r["host"], r["eps"], P=1, b=16, kind=r["kind"], seed=700 + r["id"], zeta=r["zeta"],
+                       p=r["p"])
+        assert (res["status"], res["rank"]) == (ref["status"], ref["rank"]) and ref["rank"] > 0
+        nA = ref["normA2"]
+        dE = abs(res["E"] - ref["E"]) / nA
+        rel, rel_ref = (math.sqrt(max(x, 0.0) / nA) for x in (res["E"], ref["E"]))
+        dQ = float(np.abs(res["Q"].cpu().numpy() - ref["Q"]).max())
+        dB = float(np.abs(res["B"].cpu().numpy() - ref["B"]).max() / np.abs(ref["B"]).max())
+        # final error: 1e-10 relative, or the FP64 indicator's resolution 8 * 2^-53 / rel^2
+        rel_bar = max(1e-10, 8 * 2.0 ** -53 / rel_ref ** 2)
+        print("PARITY served_%d E=%.3e rel_err=%.3e (bar %.1e) Q=%.3e B=%.3e"
+              % (r["id"], dE, abs(rel - rel_ref) / rel_ref, rel_bar, dQ, dB))
+        assert dE <= 5e-14 and abs(rel - rel_ref) <= rel_bar * rel_ref and dQ <= 1e-10 and dB <= 1e-10
+        got[r["id"]]["run"].release()
+    srv.close()
+
+
+def test_mixed_served_form_against_the_oracle():
+    """The mixed precision served form (LRA_FLAG_MIXED for every request): against
+    the FP64 oracle the same rank and status and the final relative error within 1%;
+    for the basis it found, Q^T Q = I and B = Q^T A to FP64 accuracy."""
+    reqs = _oracle_requests()
+    srv, got = _served(reqs, lra.FLAG_NO_GRAPHS | lra.FLAG_MIXED)
+    for r in reqs:
+        res = got[r["id"]]["result"]
+        ref = F.farpca(r["host"], r["eps"], P=1, b=16, kind=r["kind"], seed=700 + r["id"], zeta=r["zeta"],
+                       p=r["p"])
+        assert (res["status"], res["rank"]) == (ref["status"], ref["rank"])
+        rel, rel_ref = (math.sqrt(max(x, 0.0) / ref["normA2"]) for x in (res["E"], ref["E"]))
+        assert abs(rel - rel_ref) <= 0.01 * rel_ref
+        Q, B = res["Q"].cpu().numpy(), res["B"].cpu().numpy()
+        assert np.abs(Q.T @ Q - np.eye(Q.shape[1])).max() <= 1e-12
+        assert np.abs(B - Q.T @ r["host"]).max() <= 1e-10 * np.abs(B).max()
+        got[r["id"]]["run"].release()
+    srv.close()
