@@ -565,6 +565,8 @@ __device__ __forceinline__ void oz_flush_role(OzShared& sh, const OzArgs& a, con
   for (int i = 0; i < 32; ++i) acc[i] = 0;
   uint32_t ph_af = 0;
   const int ncols = min((int)a.N, NN);  // output columns actually read
+  const int amode = a.alpha == 1.0 ? 0 : a.alpha == -1.0 ? 1 : 2;  // decided once, not per output
+  const bool beta0 = a.beta == 0.0;
   for (Cursor c = start; c.i < c.n; c.next()) {
     if (!c.win_last()) continue;
     // lane 0 waits; the warp follows its decision (tcgen05.ld is warp-collective)
@@ -691,8 +693,8 @@ __device__ __forceinline__ void oz_flush_role(OzShared& sh, const OzArgs& a, con
             const double val = scale2(sum, ep + syE[col] - EXP_OFFSET - 24);
             if (full) {
               double* dst = a.C + p * a.csp + (int64_t)col * a.csc;
-              const double av = (a.alpha == 1.0) ? val : (a.alpha == -1.0) ? -val : a.alpha * val;
-              *dst = (a.beta == 0.0) ? av : av + a.beta * (*dst);
+              const double av = amode == 0 ? val : amode == 1 ? -val : a.alpha * val;
+              *dst = beta0 ? av : av + a.beta * (*dst);
             } else {
               wp[(int64_t)col * TM] = val;
             }
