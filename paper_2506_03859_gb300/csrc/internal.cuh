@@ -86,6 +86,7 @@ int64_t dgemm_ws_elems();
 // FP64-accurate C = alpha op(X) Y + beta C on the tcgen05 tensor cores (error-free
 // bf16 slicing).  xE: biased max exponent of each row of op(X) (P entries).
 struct OzWorkspace {
+  int* count;        // arrival counter of the fused Gram + Cholesky (zero between launches)
   int* yE;           // 64 ints
   uint8_t* img;      // pre-sliced Y, img_bytes
   int64_t img_bytes;
@@ -98,9 +99,18 @@ int64_t oz_part_elems(int ctas);
 // Largest K the tensor engine accepts (its exact int64 sums stay in range).
 int64_t oz_max_k();
 // yE_known: biased max exponents of Y's columns when the caller has them.
+// chol: the product is a b x b Gram (C column-major with ld b); factor it in the
+// same launch as the Gram's fixup (k_oz_fixup_chol), as chol_inv would.
+struct CholJob {
+  double* Rinv;
+  int* dead;   // NULL: breakdown ends the factorisation; else skip mode (chol_inv)
+  int* count;  // the workspace's arrival counter
+  double tau;
+};
 cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, const double* X,
                    int64_t ldx, const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
-                   const OzWorkspace& w, int* flags, cudaStream_t st, const int* yE_known = nullptr);
+                   const OzWorkspace& w, int* flags, cudaStream_t st, const int* yE_known = nullptr,
+                   const CholJob* chol = nullptr);
 // The digit image of op(X) (P x K): every (128-row tile, 16-deep stage) as seven
 // f16 digit planes, cut once and reused by ozgemm_img.  xE as for ozgemm.
 int64_t oz_ximg_bytes(int64_t P, int64_t K);

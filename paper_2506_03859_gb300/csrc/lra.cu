@@ -342,6 +342,24 @@ lra_status gram(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows) {
   return mm(ctx, true, b, b, rows, 1.0, X, ldx, xE, X, ldx, 0.0, ctx->gram, 1, b, xE);
 }
 
+// The Gram S = X^T X and its Cholesky factor R^{-1} (into ctx->Rinv): on the tensor
+// engine in one launch after the product (the fused fixup + Cholesky); dead as
+// for chol_inv.
+lra_status gram_chol(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows, int* dead) {
+  const int b = ctx->b;
+  if (!ctx->tensor || rows > oz_max_k()) {
+    TRY(gram(ctx, X, ldx, rows));
+    CK(chol_inv(ctx->gram, b, PIVOT_TAU, ctx->Rinv, ctx->flags, ctx->st, dead));
+    return LRA_OK;
+  }
+  CK(oz_rowcol_exponents(X, ldx, rows, b, nullptr, ctx->xcolE, ctx->st));
+  const CholJob job{ctx->Rinv, dead, ctx->oz.count, PIVOT_TAU};
+  // X^T X: the right operand's column exponents are the left operand's row exponents
+  CK(ozgemm(true, b, b, rows, 1.0, X, ldx, ctx->xcolE, X, ldx, 0.0, GemmOut{ctx->gram, 1, b}, ctx->oz,
+            ctx->flags, ctx->st, ctx->xcolE, &job));
+  return LRA_OK;
+}
+
 lra_status right_apply_rinv(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows, double* out,
                             int64_t ldo) {
   const int b = ctx->b;
@@ -356,12 +374,9 @@ lra_status right_apply_rinv(lra_ctx* ctx, const double* X, int64_t ldx, int64_t 
 // out (rows x b, ld ldo) = Q factor of X (rows x b, ld ldx), CholQR2.
 lra_status orth(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows, double* out,
                 int64_t ldo) {
-  const int b = ctx->b;
-  TRY(gram(ctx, X, ldx, rows));
-  CK(chol_inv(ctx->gram, b, PIVOT_TAU, ctx->Rinv, ctx->flags, ctx->st));
+  TRY(gram_chol(ctx, X, ldx, rows, nullptr));
   TRY(right_apply_rinv(ctx, X, ldx, rows, ctx->Tmp, ctx->lds));
-  TRY(gram(ctx, ctx->Tmp, ctx->lds, rows));
-  CK(chol_inv(ctx->gram, b, PIVOT_TAU, ctx->Rinv, ctx->flags, ctx->st));
+  TRY(gram_chol(ctx, ctx->Tmp, ctx->lds, rows, nullptr));
   TRY(right_apply_rinv(ctx, ctx->Tmp, ctx->lds, rows, out, ldo));
   return LRA_OK;
 }
@@ -374,12 +389,10 @@ lra_status orth(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows, double
 lra_status orth_panel(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows, double* out,
                       int64_t ldo, int64_t j, int s) {
   const int b = ctx->b;
-  TRY(gram(ctx, X, ldx, rows));
-  CK(chol_inv(ctx->gram, b, PIVOT_TAU, ctx->Rinv, ctx->flags, ctx->st, ctx->dead));
+  TRY(gram_chol(ctx, X, ldx, rows, ctx->dead));
   TRY(right_apply_rinv(ctx, X, ldx, rows, ctx->Tmp, ctx->lds));
   CK(fill_dead(ctx->Tmp, ctx->lds, rows, b, ctx->dead, ctx->os.k0, ctx->os.k1, j, s, ctx->st));
-  TRY(gram(ctx, ctx->Tmp, ctx->lds, rows));
-  CK(chol_inv(ctx->gram, b, PIVOT_TAU, ctx->Rinv, ctx->flags, ctx->st));
+  TRY(gram_chol(ctx, ctx->Tmp, ctx->lds, rows, nullptr));
   TRY(right_apply_rinv(ctx, ctx->Tmp, ctx->lds, rows, out, ldo));
   return LRA_OK;
 }
@@ -745,7 +758,7 @@ void free_all(lra_ctx* c) {
                   c->z,      c->zB,       c->wvec,   c->ws,       c->gram,      c->Rinv,   c->dead,
                   c->colsq,  c->colsum,   c->scal,   c->flags,    c->om_counts, c->om_rows,
                   c->om_vals, c->om_dense, c->sk_counts, c->sk_rows, c->sk_vals, c->A_host_copy,
-                  c->rowE,   c->colE,     c->oz.yE,  c->oz.img,   c->oz.part,
+                  c->rowE,   c->colE,     c->oz.yE,  c->oz.img,   c->oz.part,  c->oz.count,
                   c->qrowE,  c->qcolE,    c->browE,  c->bcolE,    c->xrowE,     c->xcolE,
                   c->ximg[0], c->ximg[1], c->astat};
   for (void* p : ptrs) dfree(c, p);
@@ -941,6 +954,14 @@ lra_status create_ctx(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
     ALLOC(oz.yE, LRA_MAX_B);
     ALLOC(oz.img, ctx->oz.img_bytes);
     ALLOC(oz.part, oz_part_elems(ctx->oz.ctas));
+    ALLOC(oz.count, 1);
+    if (!ctx->dry && cudaMemsetAsync(ctx->oz.count, 0, sizeof(int), ctx->st) != cudaSuccess) {
+      const lra_status r_ = fail(ctx, LRA_ERR_CUDA, "cudaMemsetAsync of the arrival counter failed");
+      cudaGetLastError();
+      free_all(ctx);
+      delete ctx;
+      return r_;
+    }
     ALLOC(astat, a_stats_part_elems(m, n));
     // A's digit images when the device has room (else every pass cuts A itself)
     if (!(params->flags & LRA_FLAG_NO_A_DIGITS)) {

@@ -54,6 +54,7 @@
 
 #include <algorithm>
 
+#include "chol.cuh"
 #include "internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -901,9 +902,11 @@ __device__ __forceinline__ int64_t oz_owner(int64_t u, int64_t T, int64_t G) {
   return c;
 }
 
-template <int LANES>
-__global__ void __launch_bounds__(256, 6) k_oz_fixup(OzArgs a, int G) {
-  constexpr int ELEMS = 256 / LANES;
+// One CTA's share of the fixup: NTHR threads, LANES per element.  Returns early
+// (the whole CTA alike) when it has nothing to sum.
+template <int LANES, int NTHR>
+__device__ __forceinline__ void oz_fixup_cta(const OzArgs& a, int G) {
+  constexpr int ELEMS = NTHR / LANES;
   __shared__ int64_t s_cf, s_cl;
   __shared__ int s_slot_f;
   const int64_t t = blockIdx.x;
@@ -964,6 +967,28 @@ __global__ void __launch_bounds__(256, 6) k_oz_fixup(OzArgs a, int G) {
     const double as = (a.alpha == 1.0) ? s : a.alpha * s;
     *dst = (a.beta == 0.0) ? as : as + a.beta * (*dst);
   }
+}
+
+template <int LANES>
+__global__ void __launch_bounds__(256, 6) k_oz_fixup(OzArgs a, int G) { oz_fixup_cta<LANES, 256>(a, G); }
+
+// The fused Gram + Cholesky (the b x b Gram S = X^T X of CholQR, Alg. 1's Z = Y^T Y
+// in QB form): the fixup of the split Gram, then the CTA that finishes last -- the
+// one whose increment of the launch's arrival counter completes it -- factors S
+// (chol.cuh) and resets the counter for the next launch.  Writers publish S with
+// a fence before their arrival; the last CTA reads it after its own fence, with
+// loads that bypass L1.  Nothing waits on another CTA.
+__global__ void __launch_bounds__(CHOL_NT) k_oz_fixup_chol(OzArgs a, int G, CholJob job) {
+  __shared__ int s_last;
+  oz_fixup_cta<16, CHOL_NT>(a, G);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(job.count, 1) == (int)(gridDim.x * gridDim.y) - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  chol_inv_cta(a.C, (int)a.N, job.tau, job.Rinv, a.flags, job.dead);
+  if (threadIdx.x == 0) *job.count = 0;
 }
 
 // The fixup launch: lanes per element by the number of CTAs that share a tile
@@ -1128,7 +1153,8 @@ cudaError_t ozgemm_img(int64_t P, int64_t N, int64_t K, double alpha, const uint
 
 cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, const double* X,
                    int64_t ldx, const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
-                   const OzWorkspace& w, int* flags, cudaStream_t st, const int* yE_known) {
+                   const OzWorkspace& w, int* flags, cudaStream_t st, const int* yE_known,
+                   const CholJob* chol) {
   if (P <= 0 || N <= 0) return cudaSuccess;
   if (N > NN || K <= 0 || K > MAX_K) return cudaErrorInvalidValue;
   if (oz_img_bytes(K) > w.img_bytes) return cudaErrorInvalidValue;
@@ -1144,7 +1170,15 @@ cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, co
   else
     k_ozgemm<false><<<G, NT, SMEM_DYN, st>>>(a);
   e = launched();
-  if (e != cudaSuccess || a.whole_tiles) return e;
+  if (e != cudaSuccess) return e;
+  if (chol) {
+    // the product is the b x b Gram (P = N = b <= 64, C with ld b): factor it
+    if (a.whole_tiles) return chol_inv(out.C, (int)N, chol->tau, chol->Rinv, flags, st, chol->dead);
+    const int64_t elems = (int64_t)P * N;
+    k_oz_fixup_chol<<<dim3(1, (unsigned)((elems * 16 + CHOL_NT - 1) / CHOL_NT)), CHOL_NT, 0, st>>>(a, G, *chol);
+    return launched();
+  }
+  if (a.whole_tiles) return e;
   return launch_fixup(a, G, st);
 }
 
