@@ -711,6 +711,8 @@ def batched(lra, torch, np, peaks, peak_src, count=4096, reps=3, graph=True):
     bt = lra.Batch(mats, eps, seeds, b=16, P=1, zeta=4, graph=graph)
     bt.run()
     torch.cuda.synchronize()
+    # the autotuner picks the tile shape of each shape class on this batch
+    tuned = bt.tune(reps=2) if graph else None
     times = []
     for _ in range(reps):
         t0 = time.perf_counter()
@@ -727,7 +729,11 @@ def batched(lra, torch, np, peaks, peak_src, count=4096, reps=3, graph=True):
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": gbs / peaks["hbm_gbs"], "algorithmic_bytes": algo,
                         "peak_source": peak_src},
-           "device_bytes": bt.device_bytes(), "timing": "wall clock of lra_batch_run (min of %d)" % reps}
+           "device_bytes": bt.device_bytes(), "timing": "wall clock of lra_batch_run (min of %d)" % reps,
+           "tiling": {"chosen": tuned and {"tn": tuned["tn"], "nn": tuned["nn"]},
+                      "tuned_ms": tuned and tuned["ms"], "default_ms": tuned and tuned["base_ms"],
+                      "classes": "tn by n: <256, <640, rest; nn by m: <384, <1200, rest (columns / rows "
+                                 "per thread, 64 threads per tile)"}}
     bt.close()
     del mats
     return out

@@ -469,6 +469,35 @@ int64_t lra_batch_steps(const lra_batch* batch);
 int64_t lra_batch_device_bytes(const lra_batch* batch);
 void lra_batch_destroy(lra_batch* batch);
 
+/* Tile shapes of the batched products, per shape class: tn[c] columns per thread
+   of the X^T Y products (A^T X, Q^T X, Q_j^T A; 64 threads, tiles of 64 tn[c]
+   columns) for problems with n < 256 (c = 0), < 640 (1), the rest (2); nn[c] rows
+   per thread of the row products (A G, X - Q F; tiles of 64 nn[c] rows) for
+   m < 384, < 1200, the rest.  Each 1, 2 or 4; the default is 2 everywhere.  The
+   tiling changes how the work is cut, not what any thread sums nor the order of
+   its sums: results are the same bits under every tiling.  Not in the paper (its
+   MATLAB code runs one matrix at a time). */
+typedef struct {
+  int32_t tn[3];
+  int32_t nn[3];
+} lra_batch_tiling;
+
+/* Use tiling t from the next lra_batch_run on (rebuilds the tile lists and the
+   graph; results of earlier runs are no longer readable).  Errors:
+   LRA_ERR_INVALID_ARG (NULL, or an entry not 1, 2 or 4), LRA_ERR_CUDA. */
+lra_status lra_batch_set_tiling(lra_batch* batch, const lra_batch_tiling* t);
+lra_status lra_batch_get_tiling(const lra_batch* batch, lra_batch_tiling* t);
+/* The autotuner: coordinate descent over the knobs of the shape classes the
+   batch holds (each tried at 1, 2 and 4 with the others fixed, in the order
+   tn[0..2], nn[0..2]), every candidate timed by `reps` (>= 1) runs of the whole
+   batch on its stream (CUDA events; the minimum counts).  Leaves the fastest
+   tiling in place and returns it in *best and its time (ms per run) in *best_ms;
+   *base_ms gets the time of the tiling in place at the call (either pointer may
+   be NULL).  Synchronises the stream; results of earlier runs are no longer
+   readable.  Errors: LRA_ERR_INVALID_ARG, LRA_ERR_CUDA. */
+lra_status lra_batch_tune(lra_batch* batch, int32_t reps, lra_batch_tiling* best, double* best_ms,
+                          double* base_ms);
+
 /* Message for the last error on ctx ("" if none); never NULL. */
 const char* lra_last_error(const lra_ctx* ctx);
 

@@ -52,7 +52,7 @@ struct BProb {
   int* omr;
   double *rdiag, *cnorm;
   int c32_first, c32_count;    // this problem's tiles in the 32-column list (||A||^2)
-  int c128_first, c128_count;  // ... in the 128-column list (products X^T Y)
+  int g64_first, g64_count;    // its 64-column groups (partial sums of ||B_j||_F^2)
   // state
   double normA2, E;
   int status, rank, active, broke;
@@ -169,46 +169,35 @@ __global__ void __launch_bounds__(128) k_b_sketch(const BProb* __restrict__ pr,
 
 enum TnMode { TN_ATX = 0, TN_QTY = 1, TN_QTA = 2 };
 
-// C = X^T Y over a tile of 128 columns of X, 64 threads, each thread two
-// columns (c and c + 64): the thread streams its columns down the rows (16-byte
-// loads where a column is aligned) while the 64-row chunk of Y (b columns) sits
-// in shared memory, read by all threads at the same address, each value used for
-// both columns; each thread keeps its 2 b sums in registers.
+// C = X^T Y over a tile of 64 CPT columns of X, 64 threads, each thread CPT
+// columns (c, c + 64, ...; CPT = the problem's tn, its class's tile shape): the
+// thread streams its columns down the rows (16-byte loads where a column is
+// aligned) while the 64-row chunk of Y (b columns) sits in shared memory, read by
+// all threads at the same address, each value used for all CPT columns; each
+// thread keeps its CPT b sums in registers.  A column's sum runs over the rows in
+// the same order whatever CPT is.
 //   TN_ATX: W = A^T X (n x b);  TN_QTY: F = Q^T X (l x b);
 //   TN_QTA: B_j^T = A^T Q_j into Bt's columns l.., and sum of squares -> part.
-template <int B, int MODE>
-__global__ void __launch_bounds__(64) k_b_tn(const BProb* __restrict__ pr,
-                                             const int2* __restrict__ tiles,
-                                             const int* __restrict__ jp,
-                                             double* __restrict__ part) {
-  __shared__ __align__(16) float ys[64][B];
-  __shared__ double red[2];
-  const int2 t = tiles[blockIdx.x];
-  const BProb& p = pr[t.x];
-  const int l = *jp * B;
-  const bool live = p.active && !p.broke;
-  const int cols = MODE == TN_QTY ? l : p.n;
-  if (!live || t.y >= cols) {
-    if (MODE == TN_QTA && threadIdx.x == 0) part[blockIdx.x] = 0.0;
-    return;
-  }
+template <int B, int MODE, int CPT>
+__device__ __forceinline__ void tn_tile(const BProb& p, int2 t, int l, int cols, double* __restrict__ part,
+                                        float (*ys)[B], double* red) {
   const float* X = MODE == TN_QTY ? p.Q : p.A;
   const int64_t ldx = MODE == TN_QTY ? (int64_t)p.m : p.lda;
   const float* Y = MODE == TN_QTA ? p.Q + (int64_t)l * p.m : p.X;
-  int c[2];
-  bool mine[2];
-  const float* col[2];
+  int c[CPT];
+  bool mine[CPT];
+  const float* col[CPT];
   bool vec = true;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
+  for (int h = 0; h < CPT; ++h) {
     c[h] = t.y + threadIdx.x + 64 * h;
     mine[h] = c[h] < cols;
     col[h] = X + (int64_t)(mine[h] ? c[h] : t.y) * ldx;
     vec = vec && ((reinterpret_cast<uintptr_t>(col[h]) & 15) == 0);
   }
-  float acc[2][B];
+  float acc[CPT][B];
 #pragma unroll
-  for (int h = 0; h < 2; ++h)
+  for (int h = 0; h < CPT; ++h)
 #pragma unroll
     for (int k = 0; k < B; ++k) acc[h][k] = 0.f;
   for (int r0 = 0; r0 < p.m; r0 += 64) {
@@ -221,9 +210,9 @@ __global__ void __launch_bounds__(64) k_b_tn(const BProb* __restrict__ pr,
     if (vec && rn == 64) {
 #pragma unroll
       for (int q0 = 0; q0 < 16; q0 += 4) {
-        float4 a4[2][4];
+        float4 a4[CPT][4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+        for (int h = 0; h < CPT; ++h)
 #pragma unroll
           for (int q = 0; q < 4; ++q)
             a4[h][q] = __ldg(reinterpret_cast<const float4*>(col[h] + r0 + 4 * (q0 + q)));
@@ -232,84 +221,106 @@ __global__ void __launch_bounds__(64) k_b_tn(const BProb* __restrict__ pr,
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int rr = 4 * (q0 + q) + e;
-            const float a0 = e == 0 ? a4[0][q].x : e == 1 ? a4[0][q].y : e == 2 ? a4[0][q].z : a4[0][q].w;
-            const float a1 = e == 0 ? a4[1][q].x : e == 1 ? a4[1][q].y : e == 2 ? a4[1][q].z : a4[1][q].w;
 #pragma unroll
             for (int k = 0; k < B; k += 4) {
               const float4 y = *reinterpret_cast<const float4*>(&ys[rr][k]);
-              acc[0][k] = fmaf(a0, y.x, acc[0][k]);
-              acc[0][k + 1] = fmaf(a0, y.y, acc[0][k + 1]);
-              acc[0][k + 2] = fmaf(a0, y.z, acc[0][k + 2]);
-              acc[0][k + 3] = fmaf(a0, y.w, acc[0][k + 3]);
-              acc[1][k] = fmaf(a1, y.x, acc[1][k]);
-              acc[1][k + 1] = fmaf(a1, y.y, acc[1][k + 1]);
-              acc[1][k + 2] = fmaf(a1, y.z, acc[1][k + 2]);
-              acc[1][k + 3] = fmaf(a1, y.w, acc[1][k + 3]);
+#pragma unroll
+              for (int h = 0; h < CPT; ++h) {
+                const float ah = e == 0 ? a4[h][q].x : e == 1 ? a4[h][q].y : e == 2 ? a4[h][q].z : a4[h][q].w;
+                acc[h][k] = fmaf(ah, y.x, acc[h][k]);
+                acc[h][k + 1] = fmaf(ah, y.y, acc[h][k + 1]);
+                acc[h][k + 2] = fmaf(ah, y.z, acc[h][k + 2]);
+                acc[h][k + 3] = fmaf(ah, y.w, acc[h][k + 3]);
+              }
             }
           }
         }
       }
     } else {
       for (int rr = 0; rr < rn; ++rr) {
-        const float a0 = col[0][r0 + rr], a1 = col[1][r0 + rr];
 #pragma unroll
-        for (int k = 0; k < B; ++k) {
-          acc[0][k] = fmaf(a0, ys[rr][k], acc[0][k]);
-          acc[1][k] = fmaf(a1, ys[rr][k], acc[1][k]);
+        for (int h = 0; h < CPT; ++h) {
+          const float ah = col[h][r0 + rr];
+#pragma unroll
+          for (int k = 0; k < B; ++k) acc[h][k] = fmaf(ah, ys[rr][k], acc[h][k]);
         }
       }
     }
     __syncthreads();
   }
-  double sq = 0.0;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    if (!mine[h]) continue;
+  for (int h = 0; h < CPT; ++h) {
+    double sq = 0.0;  // this thread's column of the 64-column group t.y / 64 + h
+    if (mine[h]) {
 #pragma unroll
-    for (int k = 0; k < B; ++k) {
-      const float v = acc[h][k];
-      if (MODE == TN_ATX) p.W[c[h] + (int64_t)k * p.n] = v;
-      if (MODE == TN_QTY) p.F[c[h] + (int64_t)k * p.lmax] = v;
-      if (MODE == TN_QTA) {
-        p.Bt[c[h] + (int64_t)(l + k) * p.n] = v;
-        sq += (double)v * (double)v;
+      for (int k = 0; k < B; ++k) {
+        const float v = acc[h][k];
+        if (MODE == TN_ATX) p.W[c[h] + (int64_t)k * p.n] = v;
+        if (MODE == TN_QTY) p.F[c[h] + (int64_t)k * p.lmax] = v;
+        if (MODE == TN_QTA) {
+          p.Bt[c[h] + (int64_t)(l + k) * p.n] = v;
+          sq += (double)v * (double)v;
+        }
       }
     }
+    if (MODE == TN_QTA) {
+      // one partial per 64-column group, summed in the same order whatever the tile
+      const double s2 = block_sum(sq, red);
+      const int g = t.y / 64 + h;
+      if (threadIdx.x == 0 && g < p.g64_count) part[p.g64_first + g] = s2;
+    }
   }
-  if (MODE == TN_QTA) {
-    const double s2 = block_sum(sq, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = s2;
+}
+
+// One shape class's tiles: tiles[off ..] (TN_QTA: the partial sums of the tile's
+// 64-column groups in part[g64_first + group]).
+template <int B, int MODE, int CPT>
+__global__ void __launch_bounds__(64) k_b_tn(const BProb* __restrict__ pr,
+                                             const int2* __restrict__ tiles, int off,
+                                             const int* __restrict__ jp,
+                                             double* __restrict__ part) {
+  __shared__ __align__(16) float ys[64][B];
+  __shared__ double red[2];
+  const int2 t = tiles[off + (int)blockIdx.x];
+  const BProb& p = pr[t.x];
+  const int l = *jp * B;
+  const bool live = p.active && !p.broke;
+  const int cols = MODE == TN_QTY ? l : p.n;
+  if (!live || t.y >= cols) {
+    if (MODE == TN_QTA && threadIdx.x == 0)
+      for (int h = 0; h < CPT; ++h)
+        if (t.y / 64 + h < p.g64_count) part[p.g64_first + t.y / 64 + h] = 0.0;
+    return;
   }
+  tn_tile<B, MODE, CPT>(p, t, l, cols, part, ys, red);
 }
 
 enum NnMode { NN_AX = 0, NN_YQF = 1 };
 
-// Row tile (problem, 128 rows), 64 threads, each thread rows i and i + 64:
+// Row tile (problem, 64 RPT rows), 64 threads, each thread RPT rows i, i + 64, ...
+// (RPT = the problem's nn, its class's tile shape):
 //   NN_AX: X = A W (m x b, W = G after orthonormalisation);  NN_YQF: X -= Q F.
-// The 64-column chunk of the right operand sits in shared memory, each value
-// used for both rows.
-template <int B, int MODE>
-__global__ void __launch_bounds__(64) k_b_nn(const BProb* __restrict__ pr,
-                                             const int2* __restrict__ tiles,
-                                             const int* __restrict__ jp) {
-  __shared__ __align__(16) float ys[64][B];
-  const int2 t = tiles[blockIdx.x];
-  const BProb& p = pr[t.x];
-  if (!p.active || p.broke) return;
-  const int l = *jp * B;
-  const int K = MODE == NN_AX ? p.n : l;
-  if (K == 0) return;
+// The 64-column chunk of the right operand sits in shared memory, each value used
+// for all RPT rows.  A row's sum runs over the columns in the same order whatever
+// RPT is.
+template <int B, int MODE, int RPT>
+__device__ __forceinline__ void nn_tile(const BProb& p, int2 t, int K, float (*ys)[B]) {
   const float* X = MODE == NN_AX ? p.A : p.Q;
   const int64_t ldx = MODE == NN_AX ? p.lda : (int64_t)p.m;
   const float* Y = MODE == NN_AX ? p.W : p.F;
   const int64_t ldy = MODE == NN_AX ? (int64_t)p.n : (int64_t)p.lmax;
-  const int i0 = t.y + threadIdx.x, i1 = i0 + 64;
-  const bool in0 = i0 < p.m, in1 = i1 < p.m;
-  const float* x0 = X + (in0 ? i0 : 0);
-  const float* x1 = X + (in1 ? i1 : 0);
-  float acc[2][B];
+  int i[RPT];
+  bool in[RPT];
+  const float* x[RPT];
 #pragma unroll
-  for (int h = 0; h < 2; ++h)
+  for (int h = 0; h < RPT; ++h) {
+    i[h] = t.y + threadIdx.x + 64 * h;
+    in[h] = i[h] < p.m;
+    x[h] = X + (in[h] ? i[h] : 0);
+  }
+  float acc[RPT][B];
+#pragma unroll
+  for (int h = 0; h < RPT; ++h)
 #pragma unroll
     for (int k = 0; k < B; ++k) acc[h][k] = 0.f;
   for (int k0 = 0; k0 < K; k0 += 64) {
@@ -320,52 +331,64 @@ __global__ void __launch_bounds__(64) k_b_nn(const BProb* __restrict__ pr,
     }
     __syncthreads();
     int kk = 0;
-    // eight columns' loads for both rows in flight, then their FMAs
+    // eight columns' loads for every row in flight, then their FMAs
     for (; kk + 8 <= kn; kk += 8) {
-      float a[2][8];
+      float a[RPT][8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        a[0][u] = __ldg(x0 + (int64_t)(k0 + kk + u) * ldx);
-        a[1][u] = __ldg(x1 + (int64_t)(k0 + kk + u) * ldx);
-      }
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int h = 0; h < RPT; ++h) a[h][u] = __ldg(x[h] + (int64_t)(k0 + kk + u) * ldx);
 #pragma unroll
       for (int u = 0; u < 8; ++u)
 #pragma unroll
         for (int k = 0; k < B; k += 4) {
           const float4 y = *reinterpret_cast<const float4*>(&ys[kk + u][k]);
-          acc[0][k] = fmaf(a[0][u], y.x, acc[0][k]);
-          acc[0][k + 1] = fmaf(a[0][u], y.y, acc[0][k + 1]);
-          acc[0][k + 2] = fmaf(a[0][u], y.z, acc[0][k + 2]);
-          acc[0][k + 3] = fmaf(a[0][u], y.w, acc[0][k + 3]);
-          acc[1][k] = fmaf(a[1][u], y.x, acc[1][k]);
-          acc[1][k + 1] = fmaf(a[1][u], y.y, acc[1][k + 1]);
-          acc[1][k + 2] = fmaf(a[1][u], y.z, acc[1][k + 2]);
-          acc[1][k + 3] = fmaf(a[1][u], y.w, acc[1][k + 3]);
+#pragma unroll
+          for (int h = 0; h < RPT; ++h) {
+            acc[h][k] = fmaf(a[h][u], y.x, acc[h][k]);
+            acc[h][k + 1] = fmaf(a[h][u], y.y, acc[h][k + 1]);
+            acc[h][k + 2] = fmaf(a[h][u], y.z, acc[h][k + 2]);
+            acc[h][k + 3] = fmaf(a[h][u], y.w, acc[h][k + 3]);
+          }
         }
     }
     for (; kk < kn; ++kk) {
-      const float a0 = x0[(int64_t)(k0 + kk) * ldx], a1 = x1[(int64_t)(k0 + kk) * ldx];
 #pragma unroll
-      for (int k = 0; k < B; ++k) {
-        acc[0][k] = fmaf(a0, ys[kk][k], acc[0][k]);
-        acc[1][k] = fmaf(a1, ys[kk][k], acc[1][k]);
+      for (int h = 0; h < RPT; ++h) {
+        const float ah = x[h][(int64_t)(k0 + kk) * ldx];
+#pragma unroll
+        for (int k = 0; k < B; ++k) acc[h][k] = fmaf(ah, ys[kk][k], acc[h][k]);
       }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int i = h ? i1 : i0;
-    if (!(h ? in1 : in0)) continue;
+  for (int h = 0; h < RPT; ++h) {
+    if (!in[h]) continue;
 #pragma unroll
     for (int k = 0; k < B; ++k) {
-      float* o = p.X + i + (int64_t)k * p.m;
+      float* o = p.X + i[h] + (int64_t)k * p.m;
       if (MODE == NN_AX)
         *o = acc[h][k];
       else
         *o -= acc[h][k];
     }
   }
+}
+
+// One shape class's tiles: tiles[off ..].
+template <int B, int MODE, int RPT>
+__global__ void __launch_bounds__(64) k_b_nn(const BProb* __restrict__ pr,
+                                             const int2* __restrict__ tiles, int off,
+                                             const int* __restrict__ jp) {
+  __shared__ __align__(16) float ys[64][B];
+  const int2 t = tiles[off + (int)blockIdx.x];
+  const BProb& p = pr[t.x];
+  if (!p.active || p.broke) return;
+  const int l = *jp * B;
+  const int K = MODE == NN_AX ? p.n : l;
+  if (K == 0) return;
+  nn_tile<B, MODE, RPT>(p, t, K, ys);
 }
 
 // One pass of shifted Cholesky QR3 on the rows x b panel (W: rows n, else X:
@@ -513,7 +536,7 @@ __global__ void k_b_indicator(BProb* __restrict__ pr, int np, const int* __restr
     return;
   }
   double s = 0.0;
-  for (int q = 0; q < p.c128_count; ++q) s += part[p.c128_first + q];
+  for (int q = 0; q < p.g64_count; ++q) s += part[p.g64_first + q];
   p.E -= s;
   p.rank = (j + 1) * B;
   if (p.E < p.eps2 * p.normA2) {
@@ -552,8 +575,15 @@ struct lra_batch {
   lra::BProb* d_pr = nullptr;
   std::vector<lra::BProb> h_pr;  // after lra_batch_run: the final state
   std::vector<int> order;        // caller index -> internal index
-  int2 *d_c32 = nullptr, *d_c128 = nullptr, *d_rm = nullptr, *d_rn = nullptr, *d_q128 = nullptr;
-  int n_c32 = 0, n_c128 = 0, n_rm = 0, n_rn = 0, n_q128 = 0;
+  int2 *d_c32 = nullptr, *d_ctn = nullptr, *d_rm = nullptr, *d_rn = nullptr, *d_qtn = nullptr,
+       *d_rnn = nullptr;
+  int n_c32 = 0, n_rm = 0, n_rn = 0;
+  int ctn_off[4] = {}, qtn_off[4] = {}, rnn_off[4] = {};  // the tunable lists' class sections
+  // the tile shape in use, and what re-planning for another one needs
+  lra::BatchTiling tiling = lra::batch_default_tiling();
+  std::vector<int64_t> ms, ns;
+  int max_blocks = 0;
+  std::vector<lra::BProb> h_init;  // the problems as created (pointers, parameters, shapes)
   double* d_part = nullptr;
   int *d_j = nullptr, *d_count = nullptr, *d_more = nullptr;
   bool graph_mode = true;
@@ -567,6 +597,40 @@ struct lra_batch {
 
 namespace lra {
 namespace {
+
+// The X^T Y and row products: one launch per shape class present, each with the
+// kernel of its class's tile shape.
+template <int B, int MODE, typename F>
+void tn_launch(lra_batch* bt, const int2* tiles, const int* off, F&& L) {
+  for (int c = 0; c < BATCH_CLASSES; ++c) {
+    const int cnt = off[c + 1] - off[c];
+    if (cnt <= 0) continue;
+    const int v = bt->tiling.tn[c];
+    if (v == 1)
+      k_b_tn<B, MODE, 1><<<cnt, 64, 0, bt->st>>>(bt->d_pr, tiles, off[c], bt->d_j, bt->d_part);
+    else if (v == 4)
+      k_b_tn<B, MODE, 4><<<cnt, 64, 0, bt->st>>>(bt->d_pr, tiles, off[c], bt->d_j, bt->d_part);
+    else
+      k_b_tn<B, MODE, 2><<<cnt, 64, 0, bt->st>>>(bt->d_pr, tiles, off[c], bt->d_j, bt->d_part);
+    L(cudaGetLastError());
+  }
+}
+
+template <int B, int MODE, typename F>
+void nn_launch(lra_batch* bt, F&& L) {
+  for (int c = 0; c < BATCH_CLASSES; ++c) {
+    const int cnt = bt->rnn_off[c + 1] - bt->rnn_off[c];
+    if (cnt <= 0) continue;
+    const int v = bt->tiling.nn[c];
+    if (v == 1)
+      k_b_nn<B, MODE, 1><<<cnt, 64, 0, bt->st>>>(bt->d_pr, bt->d_rnn, bt->rnn_off[c], bt->d_j);
+    else if (v == 4)
+      k_b_nn<B, MODE, 4><<<cnt, 64, 0, bt->st>>>(bt->d_pr, bt->d_rnn, bt->rnn_off[c], bt->d_j);
+    else
+      k_b_nn<B, MODE, 2><<<cnt, 64, 0, bt->st>>>(bt->d_pr, bt->d_rnn, bt->rnn_off[c], bt->d_j);
+    L(cudaGetLastError());
+  }
+}
 
 // The kernels of one block step, on bt->st (captured into the graph's body, or
 // launched directly when the batch runs without the graph).
@@ -589,10 +653,8 @@ cudaError_t issue_step(lra_batch* bt, bool graph, cudaGraphConditionalHandle h) 
   // X <- (I - Q Q^T) X, twice; then X <- orth(X) (into Q's columns l.. when to_q)
   auto project = [&]() {
     for (int pass = 0; pass < 2; ++pass) {
-      k_b_tn<B, TN_QTY><<<bt->n_q128, 64, 0, st>>>(pr, bt->d_q128, jp, bt->d_part);
-      L(cudaGetLastError());
-      k_b_nn<B, NN_YQF><<<bt->n_rm, 64, 0, st>>>(pr, bt->d_rm, jp);
-      L(cudaGetLastError());
+      tn_launch<B, TN_QTY>(bt, bt->d_qtn, bt->qtn_off, L);
+      nn_launch<B, NN_YQF>(bt, L);
     }
   };
   auto orth_x = [&](bool to_q) {
@@ -610,21 +672,18 @@ cudaError_t issue_step(lra_batch* bt, bool graph, cudaGraphConditionalHandle h) 
     // W' = A^T orth((I - Q Q^T) A Omega_j); G = orth(W'); Y_j = A G
     project();
     orth_x(false);
-    k_b_tn<B, TN_ATX><<<bt->n_c128, 64, 0, st>>>(pr, bt->d_c128, jp, bt->d_part);
-    L(cudaGetLastError());
+    tn_launch<B, TN_ATX>(bt, bt->d_ctn, bt->ctn_off, L);
     for (int ps = 0; ps < 3; ++ps) {
       k_b_gram_chol<B, true><<<np, 256, 0, st>>>(pr, ps);
       L(cudaGetLastError());
       k_b_rinv<B, true, false><<<bt->n_rn, 128, 0, st>>>(pr, bt->d_rn, jp);
       L(cudaGetLastError());
     }
-    k_b_nn<B, NN_AX><<<bt->n_rm, 64, 0, st>>>(pr, bt->d_rm, jp);
-    L(cudaGetLastError());
+    nn_launch<B, NN_AX>(bt, L);
   }
   project();  // Y' = (I - Q Q^T) Y_j, twice
   orth_x(true);
-  k_b_tn<B, TN_QTA><<<bt->n_c128, 64, 0, st>>>(pr, bt->d_c128, jp, bt->d_part);
-  L(cudaGetLastError());
+  tn_launch<B, TN_QTA>(bt, bt->d_ctn, bt->ctn_off, L);
   k_b_indicator<B><<<(np + 127) / 128, 128, 0, st>>>(pr, np, jp, bt->d_part, bt->d_count);
   L(cudaGetLastError());
   if (graph)
@@ -679,10 +738,50 @@ cudaError_t build_graph(lra_batch* bt) {
   return cudaGraphInstantiate(&bt->exec, bt->graph, 0);
 }
 
+// Re-plans the tunable tile lists for tiling tl (the order and the pool stay),
+// uploads them with the problems' records (which also resets the problems' state:
+// lra_batch_run re-initialises it anyway) and rebuilds the step graph.
+cudaError_t apply_tiling(lra_batch* bt, const BatchTiling& tl) {
+  const BatchPlan plan = make_batch_plan(bt->ms, bt->ns, bt->b, bt->max_blocks, ZMAX, tl);
+  std::vector<BProb> h = bt->h_init;
+  for (int k = 0; k < bt->np; ++k) {
+    const BatchProblemPlan& pp = plan.prob[k];
+    h[k].g64_first = pp.g64_first;
+    h[k].g64_count = pp.g64_count;
+  }
+  cudaError_t e = cudaStreamSynchronize(bt->st);  // nothing of an earlier run reads the lists
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(bt->d_pr, h.data(), sizeof(BProb) * bt->np, cudaMemcpyHostToDevice, bt->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(bt->d_ctn, plan.ctn.data(), sizeof(int2) * plan.ctn.size(), cudaMemcpyHostToDevice,
+                        bt->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(bt->d_qtn, plan.qtn.data(), sizeof(int2) * plan.qtn.size(), cudaMemcpyHostToDevice,
+                        bt->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(bt->d_rnn, plan.rnn.data(), sizeof(int2) * plan.rnn.size(), cudaMemcpyHostToDevice,
+                        bt->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(bt->st);  // h is a local
+  if (e != cudaSuccess) return e;
+  for (int c = 0; c <= BATCH_CLASSES; ++c) {
+    bt->ctn_off[c] = plan.ctn_off[c];
+    bt->qtn_off[c] = plan.qtn_off[c];
+    bt->rnn_off[c] = plan.rnn_off[c];
+  }
+  bt->tiling = tl;
+  bt->h_pr = h;
+  if (!bt->graph_mode) return cudaSuccess;
+  if (bt->exec) cudaGraphExecDestroy(bt->exec);
+  if (bt->graph) cudaGraphDestroy(bt->graph);
+  bt->exec = nullptr;
+  bt->graph = nullptr;
+  return build_graph(bt);
+}
+
 void batch_free(lra_batch* bt) {
   if (bt->exec) cudaGraphExecDestroy(bt->exec);
   if (bt->graph) cudaGraphDestroy(bt->graph);
-  void* ptrs[] = {bt->d_pr, bt->d_c32, bt->d_c128, bt->d_rm, bt->d_rn, bt->d_q128, bt->d_part,
+  void* ptrs[] = {bt->d_pr, bt->d_c32, bt->d_ctn, bt->d_rm, bt->d_rn, bt->d_qtn, bt->d_rnn, bt->d_part,
                   bt->d_j,  bt->d_count, bt->d_more, bt->d_pool};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -729,13 +828,17 @@ lra_status lra_batch_create(lra_batch** out, const lra_batch_item* items, int64_
     ns[i] = items[i].n;
   }
   const BatchPlan plan = make_batch_plan(ms, ns, B, prm->max_blocks, ZMAX);
+  // the tunable lists are largest with one column or row per thread
+  const BatchTiling finest{{1, 1, 1}, {1, 1, 1}};
+  const BatchPlan fine = make_batch_plan(ms, ns, B, prm->max_blocks, ZMAX, finest);
   static_assert(sizeof(BatchTile) == sizeof(int2), "tile lists are read as int2 on the device");
   const std::vector<BatchTile>& c32 = plan.c32;
-  const std::vector<BatchTile>& c128 = plan.c128;
   const std::vector<BatchTile>& rm = plan.rm;
   const std::vector<BatchTile>& rn = plan.rn;
-  const std::vector<BatchTile>& q128 = plan.q128;
   bt->order = plan.order;
+  bt->ms = ms;
+  bt->ns = ns;
+  bt->max_blocks = prm->max_blocks;
   std::vector<BProb> h(count);
   for (int k = 0; k < (int)count; ++k) {
     const lra_batch_item& it = items[plan.ord[k]];
@@ -754,8 +857,6 @@ lra_status lra_batch_create(lra_batch** out, const lra_batch_item* items, int64_
     p.k1 = (uint32_t)(it.seed >> 32);
     p.c32_first = pp.c32_first;
     p.c32_count = pp.c32_count;
-    p.c128_first = pp.c128_first;
-    p.c128_count = pp.c128_count;
   }
   bt->max_steps = plan.max_steps;
   const int64_t off = plan.pool_bytes;
@@ -763,15 +864,14 @@ lra_status lra_batch_create(lra_batch** out, const lra_batch_item* items, int64_
   bt->n_c32 = (int)c32.size();
   bt->n_rm = (int)rm.size();
   bt->n_rn = (int)rn.size();
-  bt->n_q128 = (int)q128.size();
-  bt->n_c128 = (int)c128.size();
   cudaError_t e = cudaMalloc((void**)&bt->d_pool, (size_t)std::max<int64_t>(off, 256));
   if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_pr, sizeof(BProb) * count);
   if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_c32, sizeof(int2) * c32.size());
   if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_rm, sizeof(int2) * rm.size());
   if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_rn, sizeof(int2) * rn.size());
-  if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_q128, sizeof(int2) * q128.size());
-  if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_c128, sizeof(int2) * c128.size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_qtn, sizeof(int2) * fine.qtn.size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_ctn, sizeof(int2) * fine.ctn.size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_rnn, sizeof(int2) * fine.rnn.size());
   if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_part, sizeof(double) * c32.size());
   if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_j, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&bt->d_count, sizeof(int));
@@ -796,27 +896,21 @@ lra_status lra_batch_create(lra_batch** out, const lra_batch_item* items, int64_
     p.rdiag = (double*)(base + o[9]);
     p.cnorm = (double*)(base + o[10]);
   }
-  e = cudaMemcpyAsync(bt->d_pr, h.data(), sizeof(BProb) * count, cudaMemcpyHostToDevice, bt->st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(bt->d_c32, c32.data(), sizeof(int2) * c32.size(), cudaMemcpyHostToDevice, bt->st);
+  bt->h_init = h;
+  e = cudaMemcpyAsync(bt->d_c32, c32.data(), sizeof(int2) * c32.size(), cudaMemcpyHostToDevice, bt->st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(bt->d_rm, rm.data(), sizeof(int2) * rm.size(), cudaMemcpyHostToDevice, bt->st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(bt->d_rn, rn.data(), sizeof(int2) * rn.size(), cudaMemcpyHostToDevice, bt->st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(bt->d_q128, q128.data(), sizeof(int2) * q128.size(), cudaMemcpyHostToDevice, bt->st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(bt->d_c128, c128.data(), sizeof(int2) * c128.size(), cudaMemcpyHostToDevice, bt->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(bt->d_pool, 0, (size_t)off, bt->st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(bt->st);
   bt->graph_mode = (prm->flags & LRA_FLAG_NO_GRAPHS) == 0;
-  if (e == cudaSuccess && bt->graph_mode) e = build_graph(bt);
+  // the tile lists and problem records of the default tiling, and the graph
+  if (e == cudaSuccess) e = apply_tiling(bt, batch_default_tiling());
   if (e != cudaSuccess) {
     cudaGetLastError();
     batch_free(bt);
     return LRA_ERR_CUDA;
   }
-  bt->h_pr = h;
   *out = bt;
   return LRA_OK;
 }
@@ -875,6 +969,103 @@ lra_status lra_batch_result(const lra_batch* bt, int64_t i, lra_batch_result_t* 
 int64_t lra_batch_steps(const lra_batch* bt) { return bt ? bt->steps_last : -1; }
 
 int64_t lra_batch_device_bytes(const lra_batch* bt) { return bt ? bt->pool_bytes : -1; }
+
+lra_status lra_batch_set_tiling(lra_batch* bt, const lra_batch_tiling* t) {
+  using namespace lra;
+  if (!bt || !t) return LRA_ERR_INVALID_ARG;
+  BatchTiling tl;
+  for (int c = 0; c < BATCH_CLASSES; ++c) {
+    tl.tn[c] = t->tn[c];
+    tl.nn[c] = t->nn[c];
+  }
+  if (!batch_tiling_valid(tl)) return LRA_ERR_INVALID_ARG;
+  if (apply_tiling(bt, tl) != cudaSuccess) {
+    cudaGetLastError();
+    return LRA_ERR_CUDA;
+  }
+  return LRA_OK;
+}
+
+lra_status lra_batch_get_tiling(const lra_batch* bt, lra_batch_tiling* t) {
+  if (!bt || !t) return LRA_ERR_INVALID_ARG;
+  for (int c = 0; c < lra::BATCH_CLASSES; ++c) {
+    t->tn[c] = bt->tiling.tn[c];
+    t->nn[c] = bt->tiling.nn[c];
+  }
+  return LRA_OK;
+}
+
+lra_status lra_batch_tune(lra_batch* bt, int32_t reps, lra_batch_tiling* best, double* best_ms,
+                          double* base_ms) {
+  using namespace lra;
+  if (!bt || reps < 1) return LRA_ERR_INVALID_ARG;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return LRA_ERR_CUDA;
+  }
+  // ms per run of tiling tl (minimum over reps), or a negative value on an error
+  auto time_of = [&](const BatchTiling& tl) -> double {
+    if (apply_tiling(bt, tl) != cudaSuccess) return -1.0;
+    double best_t = -1.0;
+    for (int r = 0; r < reps; ++r) {
+      if (cudaEventRecord(e0, bt->st) != cudaSuccess) return -1.0;
+      if (lra_batch_run(bt) != LRA_OK) return -1.0;
+      float ms = 0.f;
+      if (cudaEventRecord(e1, bt->st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        return -1.0;
+      if (best_t < 0.0 || ms < best_t) best_t = ms;
+    }
+    return best_t;
+  };
+  // the classes the batch holds
+  bool has_tn[BATCH_CLASSES] = {}, has_nn[BATCH_CLASSES] = {};
+  for (int i = 0; i < bt->np; ++i) {
+    has_tn[batch_tn_class(bt->ns[i])] = true;
+    has_nn[batch_nn_class(bt->ms[i])] = true;
+  }
+  BatchTiling cur = bt->tiling;
+  double cur_t = time_of(cur);
+  const double base_t = cur_t;
+  lra_status st = cur_t < 0.0 ? LRA_ERR_CUDA : LRA_OK;
+  for (int knob = 0; st == LRA_OK && knob < 2 * BATCH_CLASSES; ++knob) {
+    const int c = knob % BATCH_CLASSES;
+    const bool is_tn = knob < BATCH_CLASSES;
+    if (!(is_tn ? has_tn[c] : has_nn[c])) continue;
+    for (int v : {1, 2, 4}) {
+      BatchTiling cand = cur;
+      int& slot = is_tn ? cand.tn[c] : cand.nn[c];
+      if (slot == v) continue;
+      slot = v;
+      const double t = time_of(cand);
+      if (t < 0.0) {
+        st = LRA_ERR_CUDA;
+        break;
+      }
+      if (t < cur_t) {
+        cur = cand;
+        cur_t = t;
+      }
+    }
+  }
+  if (st == LRA_OK && apply_tiling(bt, cur) != cudaSuccess) st = LRA_ERR_CUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != LRA_OK) {
+    cudaGetLastError();
+    return st;
+  }
+  if (best)
+    for (int c = 0; c < BATCH_CLASSES; ++c) {
+      best->tn[c] = cur.tn[c];
+      best->nn[c] = cur.nn[c];
+    }
+  if (best_ms) *best_ms = cur_t;
+  if (base_ms) *base_ms = base_t;
+  return LRA_OK;
+}
 
 void lra_batch_destroy(lra_batch* bt) {
   if (!bt) return;

@@ -34,7 +34,8 @@ EXPORTS = ("lra_create", "lra_destroy", "lra_capacity", "lra_sketch", "lra_farpc
            "lra_workspace_bytes", "lra_device_bytes", "lra_server_create", "lra_server_submit",
            "lra_server_poll", "lra_server_pending", "lra_server_release", "lra_server_clock",
            "lra_server_destroy", "lra_batch_create", "lra_batch_run", "lra_batch_result",
-           "lra_batch_steps", "lra_batch_device_bytes", "lra_batch_destroy", "lra_selftest_waits")
+           "lra_batch_steps", "lra_batch_device_bytes", "lra_batch_destroy", "lra_batch_set_tiling",
+           "lra_batch_get_tiling", "lra_batch_tune", "lra_selftest_waits")
 
 
 class Matrix(Structure):
@@ -83,6 +84,10 @@ class BatchItem(Structure):
 class BatchParams(Structure):
     _fields_ = [("b", c_int32), ("P", c_int32), ("zeta", c_int32), ("max_blocks", c_int32),
                 ("flags", c_uint32)]
+
+
+class BatchTiling(Structure):
+    _fields_ = [("tn", c_int32 * 3), ("nn", c_int32 * 3)]
 
 
 class BatchResult(Structure):
@@ -172,6 +177,12 @@ def load(path=LIB_PATH):
     lib.lra_batch_device_bytes.restype = c_int64
     lib.lra_batch_destroy.argtypes = [vp]
     lib.lra_batch_destroy.restype = None
+    lib.lra_batch_set_tiling.argtypes = [vp, POINTER(BatchTiling)]
+    lib.lra_batch_set_tiling.restype = c_int32
+    lib.lra_batch_get_tiling.argtypes = [vp, POINTER(BatchTiling)]
+    lib.lra_batch_get_tiling.restype = c_int32
+    lib.lra_batch_tune.argtypes = [vp, c_int32, POINTER(BatchTiling), POINTER(c_double), POINTER(c_double)]
+    lib.lra_batch_tune.restype = c_int32
     lib.lra_svd.argtypes = [vp, POINTER(SvdResult)]
     lib.lra_svd.restype = c_int32
     _lib = lib
@@ -501,6 +512,30 @@ class Batch:
 
     def steps(self):
         return int(self._lib.lra_batch_steps(self._b))
+
+    def tiling(self):
+        """lra_batch_get_tiling: {"tn": [3 ints], "nn": [3 ints]}."""
+        t = BatchTiling()
+        s = self._lib.lra_batch_get_tiling(self._b, byref(t))
+        if s < 0:
+            raise LraError(s, "lra_batch_get_tiling")
+        return {"tn": list(t.tn), "nn": list(t.nn)}
+
+    def set_tiling(self, tn, nn):
+        """lra_batch_set_tiling: columns (tn) and rows (nn) per thread by shape class."""
+        t = BatchTiling((c_int32 * 3)(*tn), (c_int32 * 3)(*nn))
+        s = self._lib.lra_batch_set_tiling(self._b, byref(t))
+        if s < 0:
+            raise LraError(s, "lra_batch_set_tiling")
+
+    def tune(self, reps=2):
+        """lra_batch_tune: the autotuner; returns the tiling it left in place with its
+        time and the time of the tiling before (ms per run)."""
+        t, best, base = BatchTiling(), c_double(), c_double()
+        s = self._lib.lra_batch_tune(self._b, reps, byref(t), byref(best), byref(base))
+        if s < 0:
+            raise LraError(s, "lra_batch_tune")
+        return {"tn": list(t.tn), "nn": list(t.nn), "ms": best.value, "base_ms": base.value}
 
     def device_bytes(self):
         return int(self._lib.lra_batch_device_bytes(self._b))

@@ -39,9 +39,9 @@ static void covers(const std::vector<BatchTile>& L, int k, int extent, int step)
 }
 
 static void check_plan(const std::vector<int64_t>& ms, const std::vector<int64_t>& ns, int b, int max_blocks,
-                       int zmax) {
+                       int zmax, const lra::BatchTiling& tl = lra::batch_default_tiling()) {
   const int count = (int)ms.size();
-  const BatchPlan p = lra::make_batch_plan(ms, ns, b, max_blocks, zmax);
+  const BatchPlan p = lra::make_batch_plan(ms, ns, b, max_blocks, zmax, tl);
   // order: a permutation, largest first, ties in the caller's order; order is its inverse
   CHECK((int)p.ord.size() == count && (int)p.order.size() == count);
   std::vector<int> seen(count, 0);
@@ -72,19 +72,47 @@ static void check_plan(const std::vector<int64_t>& ms, const std::vector<int64_t
       CHECK(q.offs[j] >= end);  // after every earlier buffer: no overlap
       end = q.offs[j] + sz[j];
     }
+    // the tile shape of the problem's class
+    CHECK(q.tn == tl.tn[lra::batch_tn_class(n)] && q.nn == tl.nn[lra::batch_nn_class(m)]);
+    const int wtn = 64 * q.tn, wnn = 64 * q.nn;
     covers(p.c32, k, (int)n, 32);
-    covers(p.c128, k, (int)n, 128);
+    covers(p.ctn, k, (int)n, wtn);
     covers(p.rm, k, (int)m, 128);
     covers(p.rn, k, (int)n, 128);
-    covers(p.q128, k, q.lmax, 128);
-    CHECK(q.c32_count == (int)((n + 31) / 32) && q.c128_count == (int)((n + 127) / 128));
+    covers(p.qtn, k, q.lmax, wtn);
+    covers(p.rnn, k, (int)m, wnn);
+    CHECK(q.c32_count == (int)((n + 31) / 32) && q.ctn_count == (int)((n + wtn - 1) / wtn));
     for (int t = 0; t < q.c32_count; ++t) CHECK(p.c32[q.c32_first + t].prob == k);
-    for (int t = 0; t < q.c128_count; ++t) CHECK(p.c128[q.c128_first + t].prob == k);
+    for (int t = 0; t < q.ctn_count; ++t) CHECK(p.ctn[q.ctn_first + t].prob == k);
+    CHECK(q.g64_count == (int)((n + 63) / 64) && q.g64_first == (k ? p.prob[k - 1].g64_first + p.prob[k - 1].g64_count : 0));
   }
   CHECK(p.pool_bytes >= end && p.pool_bytes % 256 == 0 && p.max_steps == max_cap);
-  // every list walks the problems in internal order
-  for (const std::vector<BatchTile>* L : {&p.c32, &p.c128, &p.rm, &p.rn, &p.q128})
+  // the tiling changes neither the order nor the pool
+  const BatchPlan d = lra::make_batch_plan(ms, ns, b, max_blocks, zmax);
+  CHECK(d.ord == p.ord && d.pool_bytes == p.pool_bytes && d.n_g64 == p.n_g64);
+  for (int k = 0; k < count; ++k) CHECK(d.prob[k].g64_first == p.prob[k].g64_first);
+  CHECK(p.n_g64 <= (int)p.c32.size());
+  // every list walks the problems in internal order; the tunable ones within each
+  // shape class, whose sections hold exactly that class's problems
+  for (const std::vector<BatchTile>* L : {&p.c32, &p.rm, &p.rn})
     for (size_t i = 1; i < L->size(); ++i) CHECK((*L)[i - 1].prob <= (*L)[i].prob);
+  struct Sec {
+    const std::vector<BatchTile>* L;
+    const int* off;
+    bool by_n;
+  };
+  for (const Sec& sec : {Sec{&p.ctn, p.ctn_off, true}, Sec{&p.qtn, p.qtn_off, true}, Sec{&p.rnn, p.rnn_off, false}}) {
+    CHECK(sec.off[0] == 0 && sec.off[lra::BATCH_CLASSES] == (int)sec.L->size());
+    for (int c = 0; c < lra::BATCH_CLASSES; ++c) {
+      CHECK(sec.off[c] <= sec.off[c + 1]);
+      for (int i = sec.off[c]; i < sec.off[c + 1]; ++i) {
+        const int k = (*sec.L)[i].prob;
+        const int64_t ext = sec.by_n ? ns[p.ord[k]] : ms[p.ord[k]];
+        CHECK((sec.by_n ? lra::batch_tn_class(ext) : lra::batch_nn_class(ext)) == c);
+        if (i > sec.off[c]) CHECK((*sec.L)[i - 1].prob <= k);
+      }
+    }
+  }
 }
 
 int main() {
@@ -114,7 +142,15 @@ int main() {
       }
     }
     check_plan(ms, ns, b, max_blocks, 16);
+    lra::BatchTiling tl;
+    for (int c = 0; c < lra::BATCH_CLASSES; ++c) {
+      tl.tn[c] = (int[]){1, 2, 4}[g() % 3];
+      tl.nn[c] = (int[]){1, 2, 4}[g() % 3];
+    }
+    CHECK(lra::batch_tiling_valid(tl));
+    check_plan(ms, ns, b, max_blocks, 16, tl);
   }
+  CHECK(!lra::batch_tiling_valid(lra::BatchTiling{{2, 3, 2}, {2, 2, 2}}));
   printf("random ok\n");
   return 0;
 }

@@ -145,3 +145,42 @@ def test_batch_full_size_sampled():
     for k in np.random.default_rng(0).choice(len(shapes), 16, replace=False):
         check_problem(states[int(k)], mats[int(k)], eps[int(k)], 16, 1, 4, seeds[int(k)])
     bt.close()
+
+
+def _snapshot(bt, count):
+    out = []
+    for k in range(count):
+        r = bt.result(k)
+        out.append((r["status"], r["rank"], r["E"], r["normA2"],
+                    r["Q"].clone() if r["rank"] else None, r["Bt"].clone() if r["rank"] else None))
+    return out
+
+
+@pytest.mark.parametrize("b", [8, 16, 32])
+def test_tilings_give_the_same_bits(b):
+    """The tile shape of each class (columns / rows per thread of the products)
+    changes how the work is cut, not what a thread sums or in which order: every
+    tiling gives the same bits, and a run after the autotuner too."""
+    shapes = EDGE + [(300, 200), (1500, 900), (700, 400), (2000, 1000), (200, 600)]
+    mats, eps, seeds = make(shapes, 300)
+    bt = lra.Batch(mats, eps, seeds, b=b, P=1, zeta=4)
+    assert bt.tiling() == {"tn": [2, 2, 2], "nn": [2, 2, 2]}
+    bt.run()
+    ref = _snapshot(bt, len(shapes))
+    for tn, nn in [([1, 1, 1], [1, 1, 1]), ([4, 4, 4], [4, 4, 4]), ([1, 4, 2], [4, 1, 2])]:
+        bt.set_tiling(tn, nn)
+        assert bt.tiling() == {"tn": tn, "nn": nn}
+        bt.run()
+        for got, want in zip(_snapshot(bt, len(shapes)), ref):
+            assert got[:4] == want[:4]
+            if want[1]:
+                assert torch.equal(got[4], want[4]) and torch.equal(got[5], want[5])
+    t = bt.tune(reps=1)
+    assert all(v in (1, 2, 4) for v in t["tn"] + t["nn"]) and t["ms"] > 0 and t["ms"] <= t["base_ms"] * 1.5
+    assert bt.tiling() == {"tn": t["tn"], "nn": t["nn"]}
+    bt.run()
+    for got, want in zip(_snapshot(bt, len(shapes)), ref):
+        assert got[:4] == want[:4]
+    with pytest.raises(lra.LraError):
+        bt.set_tiling([3, 2, 2], [2, 2, 2])
+    bt.close()
