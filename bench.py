@@ -884,24 +884,42 @@ def dense_pass(lra, torch, f, Ad, cfg, steps, warmup, peaks, peak_src):
 
 
 def e2e(lra, torch, np, f, A, steps):
-    """lra_farpca_host: A from pinned host memory, Q and B back to pinned host memory."""
+    """Through host buffers: every step copies its A (1.6 GB) from pinned host memory
+    and reads Q and B back into pinned host memory.  The headline form solves a
+    stream of matrices with lra_farpca_host_prefetch (two distinct pinned host
+    matrices of the workload, alternating): each step's copy to the device runs
+    while the previous step is solved, all copies inside the timed region.  Beside
+    it, lra_farpca_host one call at a time (copy, solve, read back, in turn)."""
     m, n = A.shape
     cap = f.capacity
-    Ah = torch.empty((n, m), dtype=torch.float64, pin_memory=True).numpy().T
-    Ah[...] = A
+    hosts = []
+    for _ in range(2):
+        Ah = torch.empty((n, m), dtype=torch.float64, pin_memory=True).numpy().T
+        Ah[...] = A
+        hosts.append(Ah)
     Qh = torch.empty((cap, m), dtype=torch.float64, pin_memory=True).numpy().T
     Bh = torch.empty((n, cap), dtype=torch.float64, pin_memory=True).numpy().T
-    f.run_host(Ah, Qh, Bh)
     k = max(3, min(steps, 5))
+    # one call at a time
+    f.run_host(hosts[0], Qh, Bh)
     t0 = time.perf_counter()
     r = None
     for _ in range(k):
-        r = f.run_host(Ah, Qh, Bh)
+        r = f.run_host(hosts[0], Qh, Bh)
+    serial = (time.perf_counter() - t0) / k
+    # a stream: the first call copies its own A and prefetches the next one
+    f.run_host(hosts[0], Qh, Bh, next_A=hosts[1])
+    f.run_host(hosts[1], Qh, Bh, next_A=hosts[0])
+    t0 = time.perf_counter()
+    for i in range(k):
+        r = f.run_host(hosts[i % 2], Qh, Bh, next_A=hosts[(i + 1) % 2])
     dt = (time.perf_counter() - t0) / k
     rank = r["rank"]
     return {"value": 1.0 / dt, "unit": "solves/s", "h2d_bytes_per_step": 8 * m * n,
             "d2h_bytes_per_step": 8 * (m * rank + rank * n), "ms_per_step": 1e3 * dt,
-            "api": "lra_farpca_host"}
+            "api": "lra_farpca_host_prefetch (a stream of two pinned host matrices; each step's "
+                   "copy overlaps the previous step's solve)",
+            "serial": {"value": 1.0 / serial, "ms_per_step": 1e3 * serial, "api": "lra_farpca_host"}}
 
 
 def cpu_baseline(A, cfg):

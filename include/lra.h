@@ -276,6 +276,21 @@ lra_status lra_farpca_host_f32(lra_ctx* ctx, const float* A_host, int64_t lda_ho
                                double* Q_host, int64_t ldq_host, double* B_host,
                                int64_t ldb_host, lra_result_t* out);
 
+/* lra_farpca_host for a stream of host matrices: solves A_host as
+   lra_farpca_host does and, when A_next_host is not NULL, starts copying
+   A_next_host (the same m x n shape and ld lda_host) into a second device buffer
+   owned by the context before this solve begins, on the context's copy streams,
+   so that the copy overlaps the solve.  A later call whose A_host is that same
+   pointer with the same lda uses the copy instead of copying again; any other
+   call first waits for it to land.  The caller keeps A_next_host's memory valid
+   and unchanged until the call that solves it (or lra_destroy) returns.  Not in
+   the paper (its timings start with A in memory); it exists so that a caller
+   who solves many host-resident matrices pays the host-to-device copy of each
+   while the previous one is being solved.  Errors: as lra_farpca_host. */
+lra_status lra_farpca_host_prefetch(lra_ctx* ctx, const double* A_host, int64_t lda_host,
+                                    const double* A_next_host, double* Q_host, int64_t ldq_host,
+                                    double* B_host, int64_t ldb_host, lra_result_t* out);
+
 /* Omega_j as generated on the device, copied to host buffers (for bit-exact
    comparison).  counts[b]: nonzeros of each column; rows[c * cap + t] and
    vals[c * cap + t], t < counts[c]: row index and value of column c's t-th entry,

@@ -118,6 +118,10 @@ struct lra_ctx {
   bool own_stream = false;  // st created by lra_create (the caller passed none)
   GraphSlot gpre;
   std::vector<GraphSlot> gblock;
+  // the same for runs on the second host-copy buffer (lra_farpca_host_prefetch), so
+  // that alternating buffers do not re-capture
+  GraphSlot gpre_alt;
+  std::vector<GraphSlot> gblock_alt;
   // A cut into digit images: [0] row-scaled (A X), [1] column-scaled (A^T X)
   uint8_t* ximg[2] = {nullptr, nullptr};
   bool ximg_ready = false;
@@ -144,6 +148,14 @@ struct lra_ctx {
   double* sk_vals = nullptr;
   int64_t sk_entries = 0, sk_cols = 0;
   double* A_host_copy = nullptr;  // device copy of A for lra_farpca_host
+  double* A_host_copy2 = nullptr;  // ... its second buffer (prefetch of the next A)
+  // the prefetch in flight or done: host source, its ld and element type, the
+  // buffer (0: A_host_copy, 1: A_host_copy2) and the event its copies complete
+  const void* pref_host = nullptr;
+  int64_t pref_lda = 0;
+  int pref_dtype = LRA_F64, pref_buf = 0;
+  bool pref_valid = false;
+  cudaEvent_t pref_ev = nullptr;
   // lra_farpca_host copies A in column chunks on several streams (copy engines)
   static constexpr int NCOPY = 4;
   cudaStream_t cst[NCOPY] = {};
@@ -591,7 +603,11 @@ lra_status run(lra_ctx* ctx, const void* Av, int64_t lda, int dtype) {
   // set-up: exponents of A, its digit images, z = A (p 1) for the shifted sketch
   const bool images = ctx->ximg[0] && ctx->ximg[1];
   ctx->ximg_ready = images;  // stream order puts the cut before every pass that reads it
-  TRY(issue(ctx, ctx->gpre, A, lda, [&]() -> lra_status {
+  // runs on the prefetch buffer keep their own graphs
+  const bool alt = ctx->A_host_copy2 && (const void*)A == (const void*)ctx->A_host_copy2;
+  lra_ctx::GraphSlot& gpre = alt ? ctx->gpre_alt : ctx->gpre;
+  std::vector<lra_ctx::GraphSlot>& gblock = alt ? ctx->gblock_alt : ctx->gblock;
+  TRY(issue(ctx, gpre, A, lda, [&]() -> lra_status {
     if (images) {
       PHASE(LRA_PHASE_CUT, {
         CK(oz_cut_x(false, m, n, Av, dtype, lda, ctx->rowE, ctx->ximg[0], ctx->oz.ctas, ctx->st));
@@ -610,8 +626,8 @@ lra_status run(lra_ctx* ctx, const void* Av, int64_t lda, int dtype) {
   double E = normA2;
   int32_t status = fixed_rank ? LRA_OK : LRA_NOT_CONVERGED;
   for (int64_t j = 0; j < ctx->nblk_max; ++j) {
-    if ((int64_t)ctx->gblock.size() <= j) ctx->gblock.resize(j + 1);
-    TRY(issue(ctx, ctx->gblock[j], A, lda, [&]() -> lra_status {
+    if ((int64_t)gblock.size() <= j) gblock.resize(j + 1);
+    TRY(issue(ctx, gblock[j], A, lda, [&]() -> lra_status {
       const int64_t l = j * b;
       PHASE(LRA_PHASE_OMEGA, TRY(make_omega(ctx, j)));
       PHASE(LRA_PHASE_SKETCH,
@@ -753,11 +769,15 @@ lra_status svd_alloc(lra_ctx* ctx, int64_t l) {
 }
 
 void free_all(lra_ctx* c) {
+  // a prefetch may still be copying into a buffer freed below
+  for (int i = 0; i < lra_ctx::NCOPY; ++i)
+    if (c->cst[i]) cudaStreamSynchronize(c->cst[i]);
   void* ptrs[] = {c->Q,      c->B,        c->Yk,     c->S0,       c->Yb,        c->T1,
                   c->Tmp,    c->W,        c->G,      c->Wt,       c->F,         c->BOm,
                   c->z,      c->zB,       c->wvec,   c->ws,       c->gram,      c->Rinv,   c->dead,
                   c->colsq,  c->colsum,   c->scal,   c->flags,    c->om_counts, c->om_rows,
                   c->om_vals, c->om_dense, c->sk_counts, c->sk_rows, c->sk_vals, c->A_host_copy,
+                  c->A_host_copy2,
                   c->rowE,   c->colE,     c->oz.yE,  c->oz.img,   c->oz.part,  c->oz.count,
                   c->qrowE,  c->qcolE,    c->browE,  c->bcolE,    c->xrowE,     c->xcolE,
                   c->ximg[0], c->ximg[1], c->astat};
@@ -769,6 +789,10 @@ void free_all(lra_ctx* c) {
     c->hp = nullptr;
   }
   if (c->gpre.exec) cudaGraphExecDestroy(c->gpre.exec);
+  if (c->gpre_alt.exec) cudaGraphExecDestroy(c->gpre_alt.exec);
+  for (auto& g : c->gblock_alt)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (c->pref_ev) cudaEventDestroy(c->pref_ev);
   for (int i = 0; i < lra_ctx::NCOPY; ++i) {
     if (c->cst[i]) cudaStreamDestroy(c->cst[i]);
     if (c->cev[i]) cudaEventDestroy(c->cev[i]);
@@ -1274,41 +1298,83 @@ lra_status lra_copy_omega(lra_ctx* ctx, int64_t j, int64_t cap, int32_t* counts,
 
 namespace {
 
-// lra_farpca_host for either element type: A_host (m x n, ld lda_host, esize
-// bytes an element) is copied in column chunks into the context's staging
-// buffer (ld = ldq elements of that type) and run there.
+// A_host (m x n, ld lda_host, elements of type dtype) into device buffer dst (ld
+// ctx->ldq elements) in NCOPY column chunks, one per copy stream (several copy
+// engines at once), each after the work already on `after` (an event, or none).
+// Returns with the chunks queued; ctx->cev[i] marks the end of chunk i.
+lra_status copy_in(lra_ctx* ctx, const void* A_host, int dtype, int64_t lda_host, void* dst_buf,
+                   cudaEvent_t after) {
+  const int64_t m = ctx->m, n = ctx->n;
+  const size_t es = dtype == LRA_F32 ? sizeof(float) : sizeof(double);
+  char* dst = reinterpret_cast<char*>(dst_buf);
+  const char* src = reinterpret_cast<const char*>(A_host);
+  for (int i = 0; i < lra_ctx::NCOPY; ++i) {
+    const int64_t c0 = i * n / lra_ctx::NCOPY, c1 = (i + 1) * n / lra_ctx::NCOPY;
+    if (after) CK(cudaStreamWaitEvent(ctx->cst[i], after, 0));
+    if (c1 > c0)
+      CK(cudaMemcpy2DAsync(dst + c0 * ctx->ldq * es, ctx->ldq * es, src + c0 * lda_host * es,
+                           lda_host * es, m * es, c1 - c0, cudaMemcpyHostToDevice, ctx->cst[i]));
+    CK(cudaEventRecord(ctx->cev[i], ctx->cst[i]));
+  }
+  return LRA_OK;
+}
+
+// lra_farpca_host for either element type: A_host (m x n, ld lda_host) is copied
+// in column chunks into a staging buffer of the context (ld = ldq elements of that
+// type) and run there -- unless the previous call prefetched exactly that source,
+// whose copy is then used.  next (may be NULL): a source whose copy into the other
+// buffer starts before the run, on the copy streams, so that it overlaps it.
 lra_status host_run(lra_ctx* ctx, const void* A_host, int dtype, int64_t lda_host, double* Q_host,
-                    int64_t ldq_host, double* B_host, int64_t ldb_host, lra_result_t* out) {
+                    int64_t ldq_host, double* B_host, int64_t ldb_host, lra_result_t* out,
+                    const void* next = nullptr) {
   if (!ctx || !A_host) return LRA_ERR_INVALID_ARG;
   ctx->err.clear();
   const int64_t m = ctx->m, n = ctx->n;
-  const size_t es = dtype == LRA_F32 ? sizeof(float) : sizeof(double);
   if (lda_host < m) return fail(ctx, LRA_ERR_INVALID_ARG, "lda_host < m");
   if (Q_host && ldq_host < m) return fail(ctx, LRA_ERR_INVALID_ARG, "ldq_host < m");
   if (B_host && ldb_host < ctx->lmax) return fail(ctx, LRA_ERR_INVALID_ARG, "ldb_host < capacity");
   if (!ctx->A_host_copy) CK(dalloc(ctx, &ctx->A_host_copy, ctx->ldq * n));
+  if (next && !ctx->A_host_copy2) CK(dalloc(ctx, &ctx->A_host_copy2, ctx->ldq * n));
   if (!ctx->cstart) {
     CK(cudaEventCreateWithFlags(&ctx->cstart, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->pref_ev, cudaEventDisableTiming));
     for (int i = 0; i < lra_ctx::NCOPY; ++i) {
       CK(cudaStreamCreateWithFlags(&ctx->cst[i], cudaStreamNonBlocking));
       CK(cudaEventCreateWithFlags(&ctx->cev[i], cudaEventDisableTiming));
     }
   }
-  // A in NCOPY column chunks on as many streams (several copy engines at once), all
-  // after the work already on the context's stream and before the run
-  char* dst = reinterpret_cast<char*>(ctx->A_host_copy);
-  const char* src = reinterpret_cast<const char*>(A_host);
-  CK(cudaEventRecord(ctx->cstart, ctx->st));
-  for (int i = 0; i < lra_ctx::NCOPY; ++i) {
-    const int64_t c0 = i * n / lra_ctx::NCOPY, c1 = (i + 1) * n / lra_ctx::NCOPY;
-    CK(cudaStreamWaitEvent(ctx->cst[i], ctx->cstart, 0));
-    if (c1 > c0)
-      CK(cudaMemcpy2DAsync(dst + c0 * ctx->ldq * es, ctx->ldq * es, src + c0 * lda_host * es,
-                           lda_host * es, m * es, c1 - c0, cudaMemcpyHostToDevice, ctx->cst[i]));
-    CK(cudaEventRecord(ctx->cev[i], ctx->cst[i]));
-    CK(cudaStreamWaitEvent(ctx->st, ctx->cev[i], 0));
+  double* buf[2] = {ctx->A_host_copy, ctx->A_host_copy2};
+  const bool have = ctx->pref_valid && ctx->pref_host == A_host && ctx->pref_lda == lda_host &&
+                    ctx->pref_dtype == dtype;
+  int cur = 0;
+  if (have) {
+    // the prefetched copy: the run waits for it on the device
+    cur = ctx->pref_buf;
+    CK(cudaStreamWaitEvent(ctx->st, ctx->pref_ev, 0));
+  } else {
+    // another source: a prefetch in flight (into either buffer) must land first
+    if (ctx->pref_valid) CK(cudaEventSynchronize(ctx->pref_ev));
+    cur = ctx->pref_valid ? 1 - ctx->pref_buf : 0;
+    if (!buf[cur]) cur = 0;
+    CK(cudaEventRecord(ctx->cstart, ctx->st));
+    TRY(copy_in(ctx, A_host, dtype, lda_host, buf[cur], ctx->cstart));
+    for (int i = 0; i < lra_ctx::NCOPY; ++i) CK(cudaStreamWaitEvent(ctx->st, ctx->cev[i], 0));
   }
-  lra_status s = run(ctx, ctx->A_host_copy, ctx->ldq, dtype);
+  ctx->pref_valid = false;
+  if (next) {
+    // the next source into the other buffer, behind this call's own copy on the
+    // copy streams (the other buffer's last run ended with the previous call)
+    const int nb = 1 - cur;
+    TRY(copy_in(ctx, next, dtype, lda_host, buf[nb], nullptr));
+    for (int i = 1; i < lra_ctx::NCOPY; ++i) CK(cudaStreamWaitEvent(ctx->cst[0], ctx->cev[i], 0));
+    CK(cudaEventRecord(ctx->pref_ev, ctx->cst[0]));
+    ctx->pref_host = next;
+    ctx->pref_lda = lda_host;
+    ctx->pref_dtype = dtype;
+    ctx->pref_buf = nb;
+    ctx->pref_valid = true;
+  }
+  lra_status s = run(ctx, buf[cur], ctx->ldq, dtype);
   if (s < 0) return s;
   if (Q_host && ctx->rank > 0)
     CK(cudaMemcpy2DAsync(Q_host, ldq_host * sizeof(double), ctx->Q, ctx->ldq * sizeof(double),
@@ -1326,6 +1392,12 @@ lra_status host_run(lra_ctx* ctx, const void* A_host, int dtype, int64_t lda_hos
 lra_status lra_farpca_host(lra_ctx* ctx, const double* A_host, int64_t lda_host, double* Q_host,
                            int64_t ldq_host, double* B_host, int64_t ldb_host, lra_result_t* out) {
   return host_run(ctx, A_host, LRA_F64, lda_host, Q_host, ldq_host, B_host, ldb_host, out);
+}
+
+lra_status lra_farpca_host_prefetch(lra_ctx* ctx, const double* A_host, int64_t lda_host,
+                                    const double* A_next_host, double* Q_host, int64_t ldq_host,
+                                    double* B_host, int64_t ldb_host, lra_result_t* out) {
+  return host_run(ctx, A_host, LRA_F64, lda_host, Q_host, ldq_host, B_host, ldb_host, out, A_next_host);
 }
 
 lra_status lra_farpca_host_f32(lra_ctx* ctx, const float* A_host, int64_t lda_host, double* Q_host,

@@ -29,7 +29,7 @@ PHASES = ("omega", "sketch", "dense", "deflate", "project", "orth", "indicator",
 MAX_B, MAX_P, MAX_ZETA = 64, 8, 256
 
 EXPORTS = ("lra_create", "lra_destroy", "lra_capacity", "lra_sketch", "lra_farpca_run", "lra_result",
-           "lra_farpca_host", "lra_copy_omega", "lra_last_error", "lra_status_string",
+           "lra_farpca_host", "lra_farpca_host_prefetch", "lra_copy_omega", "lra_last_error", "lra_status_string",
            "lra_kernel_launches", "lra_version", "lra_phase_times", "lra_apply", "lra_svd", "lra_farpca_host_f32",
            "lra_workspace_bytes", "lra_device_bytes", "lra_server_create", "lra_server_submit",
            "lra_server_poll", "lra_server_pending", "lra_server_release", "lra_server_clock",
@@ -129,6 +129,8 @@ def load(path=LIB_PATH):
     lib.lra_result.restype = c_int32
     lib.lra_farpca_host.argtypes = [vp, vp, c_int64, vp, c_int64, vp, c_int64, POINTER(Result)]
     lib.lra_farpca_host.restype = c_int32
+    lib.lra_farpca_host_prefetch.argtypes = [vp, vp, c_int64, vp, vp, c_int64, vp, c_int64, POINTER(Result)]
+    lib.lra_farpca_host_prefetch.restype = c_int32
     lib.lra_copy_omega.argtypes = [vp, c_int64, c_int64, vp, vp, vp]
     lib.lra_copy_omega.restype = c_int32
     lib.lra_last_error.argtypes = [vp]
@@ -360,10 +362,12 @@ class Farpca:
                                              vals.ctypes.data))
         return counts, rows, vals
 
-    def run_host(self, A_host, Q_host=None, B_host=None):
+    def run_host(self, A_host, Q_host=None, B_host=None, next_A=None):
         """lra_farpca_host (float64 A) or lra_farpca_host_f32 (float32 A): A, Q, B in
-        host memory (numpy, column-major; ideally pinned).  Returns the result
-        dict (without device views)."""
+        host memory (numpy, column-major; ideally pinned).  With next_A (float64, the
+        same shape and layout; kept unchanged by the caller until it is solved),
+        lra_farpca_host_prefetch: its copy to the device overlaps this solve.
+        Returns the result dict (without device views)."""
         import numpy as np
         if A_host.dtype not in (np.float64, np.float32) or not A_host.flags.f_contiguous:
             raise ValueError("A_host must be a Fortran-ordered float64 or float32 array")
@@ -372,6 +376,15 @@ class Farpca:
         bp = c_void_p(B_host.ctypes.data) if B_host is not None else c_void_p(0)
         ldq = Q_host.shape[0] if Q_host is not None else 0
         ldb = B_host.shape[0] if B_host is not None else 0
+        if next_A is not None:
+            if (A_host.dtype != np.float64 or next_A.dtype != np.float64 or next_A.shape != A_host.shape
+                    or not next_A.flags.f_contiguous):
+                raise ValueError("prefetch takes float64 Fortran-ordered matrices of one shape")
+            s = self._lib.lra_farpca_host_prefetch(self._ctx, c_void_p(A_host.ctypes.data), A_host.shape[0],
+                                                   c_void_p(next_A.ctypes.data), qp, ldq, bp, ldb, byref(r))
+            self._check(s)
+            return dict(status=r.status, rank=r.rank, blocks=r.blocks, E=r.E, normA2=r.normA2,
+                        rel_err=r.rel_err)
         fn = self._lib.lra_farpca_host if A_host.dtype == np.float64 else self._lib.lra_farpca_host_f32
         s = fn(self._ctx, c_void_p(A_host.ctypes.data), A_host.shape[0], qp, ldq, bp, ldb, byref(r))
         self._check(s)

@@ -549,3 +549,33 @@ def test_dependent_power_panel_completion(kind, p):
     check("dnn_completion_k%d" % kind, "E-direct", abs(r["E"] - np.linalg.norm(A - Q @ B) ** 2) / r["normA2"],
           1e-12)
     f.close()
+
+
+def test_host_prefetch_stream():
+    """lra_farpca_host_prefetch: a stream of host matrices, each copied to the device
+    while the previous one is solved (two device buffers, one graph set each), gives
+    the same bits as solving each matrix from device memory; a prefetch that the
+    next call does not use is waited for and skipped; a plain lra_farpca_host call
+    on the prefetched matrix uses the copy."""
+    m, n = 1200, 700
+    mats = [np.asfortranarray(low_rank_matrix(m, n, "poly1.5", 50 + i)) for i in range(3)]
+    f = lra.Farpca(m, n, eps=1e-2, b=20, P=1, kind=lra.SPARSE_SIGN, zeta=8, seed=4)
+    ref = []
+    for A in mats:
+        f.run(dev(A))
+        r = f.result()
+        ref.append((r["rank"], r["E"], r["Q"].cpu().numpy().copy(), r["B"].cpu().numpy().copy()))
+    cap = f.capacity
+    Qh = np.zeros((m, cap), order="F")
+    Bh = np.zeros((cap, n), order="F")
+
+    def check(i, r):
+        rank, E, Q, B = ref[i]
+        assert (r["rank"], r["E"]) == (rank, E)
+        assert np.array_equal(Qh[:, :rank], Q) and np.array_equal(Bh[:rank], B)
+
+    order = [(0, 1), (1, 2), (2, 0), (0, 1), (2, None), (1, 0), (0, None)]
+    for i, nxt in order:  # (2, None) after prefetching 1: the unused prefetch is skipped
+        r = f.run_host(mats[i], Qh, Bh, next_A=mats[nxt] if nxt is not None else None)
+        check(i, r)
+    f.close()
