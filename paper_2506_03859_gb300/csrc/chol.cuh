@@ -41,6 +41,12 @@ namespace lra {
 // ~1 and passes the breakdown test).
 constexpr int CHOL_NT = 1024;
 constexpr double CHOL_NEAR_I = 0x1p-34;
+// Closer still (every entry of S - I within 2^-40), X R^{-1} = X + X (R^{-1} - I)
+// may take the correction term in FP32 (k_rinv_near_identity in orth.cu): the
+// entries of R^{-1} - I = -Phi(S - I) are then within 2^-40, so FP32's relative
+// error of (b + 4) 2^-24 in that term, which is at most 2^-40 sqrt(b) times X's
+// row norm, stays below 2^-55 of that norm.  *near (when given) records the test.
+constexpr double CHOL_NEAR_I_FP32 = 0x1p-40;
 
 //
 // Skip mode (dead != NULL, the first pass over a power-step panel): a failed
@@ -54,7 +60,7 @@ constexpr double CHOL_NEAR_I = 0x1p-34;
 // L1 (it may have been written by other CTAs of the same launch).
 __device__ __forceinline__ void chol_inv_cta(const double* __restrict__ S, int b, double tau,
                                              double* __restrict__ Rinv, int* __restrict__ flags,
-                                             int* __restrict__ dead) {
+                                             int* __restrict__ dead, int* __restrict__ near) {
   constexpr int NWORK = CHOL_NT - 32;
   __shared__ double M[64][65];  // trailing block (upper triangle); row c becomes row c of R
   __shared__ double Z[64][65];  // right-hand side, rows of Z once final (lower triangle)
@@ -66,14 +72,19 @@ __device__ __forceinline__ void chol_inv_cta(const double* __restrict__ S, int b
   const bool skip = dead != nullptr;
   // workers: warps 1 .. 31; thread 0 takes the pivots
   const int wk = t - 32;
-  int far = 0;  // an entry of S - I above 2^-34, or not finite
+  int far = 0;   // an entry of S - I above 2^-34, or not finite
+  int wide = 0;  // an entry of S - I above 2^-40, or not finite
   for (int e = t; e < b * b; e += CHOL_NT) {
     const int i = e % b, j = e / b;
     const double v = __ldcg(S + i + j * b);
     M[i][j] = v;
     Z[i][j] = (i == j) ? 1.0 : 0.0;
-    far |= !(fabs(i == j ? v - 1.0 : v) <= CHOL_NEAR_I);
+    const double dev = fabs(i == j ? v - 1.0 : v);
+    far |= !(dev <= CHOL_NEAR_I);
+    wide |= !(dev <= CHOL_NEAR_I_FP32);
   }
+  const int any_wide = __syncthreads_or(wide);
+  if (near && t == 0) *near = !any_wide;
   if (!__syncthreads_or(far)) {
     // R^{-1} = I - Phi(S - I): -S_ij above the diagonal, 1 - (S_ii - 1)/2 on it
     for (int e = t; e < b * b; e += CHOL_NT) {

@@ -101,16 +101,19 @@ int64_t oz_max_k();
 // yE_known: biased max exponents of Y's columns when the caller has them.
 // chol: the product is a b x b Gram (C column-major with ld b); factor it in the
 // same launch as the Gram's fixup (k_oz_fixup_chol), as chol_inv would.
+// skip: NULL, or every launch of the product does nothing while *skip != 0 (not
+// with chol; Y's exponents known or K <= 4096).
 struct CholJob {
   double* Rinv;
   int* dead;   // NULL: breakdown ends the factorisation; else skip mode (chol_inv)
   int* count;  // the workspace's arrival counter
   double tau;
+  int* near;   // NULL, or the near-identity flag of chol_inv
 };
 cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, const double* X,
                    int64_t ldx, const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
                    const OzWorkspace& w, int* flags, cudaStream_t st, const int* yE_known = nullptr,
-                   const CholJob* chol = nullptr);
+                   const CholJob* chol = nullptr, const int* skip = nullptr);
 // The digit image of op(X) (P x K): every (128-row tile, 16-deep stage) as seven
 // f16 digit planes, cut once and reused by ozgemm_img.  xE as for ozgemm.
 int64_t oz_ximg_bytes(int64_t P, int64_t K);
@@ -127,8 +130,12 @@ cudaError_t ozgemm_img(int64_t P, int64_t N, int64_t K, double alpha, const uint
                        bool ydig1 = false);
 // rowE[r] / colE[c] = largest biased exponent in row r / column c of X (either may
 // be NULL).  accumulate_rows: rowE[r] = max(rowE[r], ...) instead of overwriting.
+// skip: NULL, or the launches do nothing while *skip != 0 (only where no
+// exponent array is zeroed first: rows <= 4096 for colE, cols < 256 and no
+// accumulation for rowE).
 cudaError_t oz_rowcol_exponents(const double* X, int64_t ld, int64_t rows, int64_t cols,
-                                int* rowE, int* colE, cudaStream_t st, bool accumulate_rows = false);
+                                int* rowE, int* colE, cudaStream_t st, bool accumulate_rows = false,
+                                const int* skip = nullptr);
 
 // ---------------------------------------------------------------- orth.cu
 // Per-column sums of squares and/or sums of X (rows x cols, ld): one CTA per column.
@@ -147,8 +154,22 @@ cudaError_t total(const double* v, int64_t count, double* out, cudaStream_t st);
 // With dead != NULL a failed pivot instead marks its column dependent (dead[c] = 1,
 // every entry of dead[0..b) written): the column takes no part in the other
 // columns' factor, and row and column c of Rinv are zero.
+// near (when given): set to 1 when every entry of S - I is within 2^-40 (X R^{-1}
+// may then be taken as rinv_near_identity computes it), else 0.
 cudaError_t chol_inv(const double* S, int b, double tau, double* Rinv, int* flags, cudaStream_t st,
-                     int* dead = nullptr);
+                     int* dead = nullptr, int* near = nullptr);
+// out (rows x b, ld ldo) = X + X (Rinv - I) with the correction in FP32, when
+// *near != 0 (see chol_inv); otherwise the launch does nothing.  b <= 64; out and
+// X do not overlap.
+cudaError_t rinv_near_identity(const double* X, int64_t ldx, int64_t rows, int b, const double* Rinv,
+                               const int* near, double* out, int64_t ldo, cudaStream_t st);
+// The second projection of CGS2, Y -= Q F (Q: rows x l, ld ldq; F: l x b, ld ldf;
+// Y: rows x b, ld ldy), in FP32 when every |F[k, c]| is below the bound that keeps
+// the FP32 sum's error within 2^-53 of Y's column scale (yE: biased exponents of
+// Y's column maxima); *taken = 1 then, else 0 and Y is left as it was.  b <= 64.
+cudaError_t project_fp32(const double* Q, int64_t ldq, int64_t rows, int64_t l, const double* F,
+                         int64_t ldf, int b, const int* yE, double* Y, int64_t ldy, int* taken,
+                         cudaStream_t st);
 // B[row0 + c, r] = Wt[r, c] (Wt: n x b, ld ldw); zB[row0 + c] = p * colsum[c] if zB.
 cudaError_t append_rows(const double* Wt, int64_t ldw, int64_t n, int b, double* B, int64_t ldb,
                         int64_t row0, const double* colsum, double p, double* zB, cudaStream_t st);

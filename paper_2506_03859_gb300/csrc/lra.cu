@@ -139,6 +139,9 @@ struct lra_ctx {
   double* astat = nullptr;  // per-(512-row block, column) sums of squares of A
   double *gram = nullptr, *Rinv = nullptr;
   int* dead = nullptr;  // dependent columns of a power-step panel (LRA_MAX_B ints)
+  // device flags: [0] the last Cholesky's Gram within 2^-40 of I (chol_inv's near);
+  // [1] the last second projection taken in FP32 (project_fp32's taken)
+  int* near = nullptr;
   double *colsq = nullptr, *colsum = nullptr, *scal = nullptr;
   int* flags = nullptr;
   int *om_counts = nullptr, *om_rows = nullptr;
@@ -356,16 +359,18 @@ lra_status gram(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows) {
 
 // The Gram S = X^T X and its Cholesky factor R^{-1} (into ctx->Rinv): on the tensor
 // engine in one launch after the product (the fused fixup + Cholesky); dead as
-// for chol_inv.
-lra_status gram_chol(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows, int* dead) {
+// for chol_inv; near: ctx->near[0] records whether S is within 2^-40 of I.
+lra_status gram_chol(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows, int* dead,
+                     bool near = false) {
   const int b = ctx->b;
+  int* nr = near ? ctx->near : nullptr;
   if (!ctx->tensor || rows > oz_max_k()) {
     TRY(gram(ctx, X, ldx, rows));
-    CK(chol_inv(ctx->gram, b, PIVOT_TAU, ctx->Rinv, ctx->flags, ctx->st, dead));
+    CK(chol_inv(ctx->gram, b, PIVOT_TAU, ctx->Rinv, ctx->flags, ctx->st, dead, nr));
     return LRA_OK;
   }
   CK(oz_rowcol_exponents(X, ldx, rows, b, nullptr, ctx->xcolE, ctx->st));
-  const CholJob job{ctx->Rinv, dead, ctx->oz.count, PIVOT_TAU};
+  const CholJob job{ctx->Rinv, dead, ctx->oz.count, PIVOT_TAU, nr};
   // X^T X: the right operand's column exponents are the left operand's row exponents
   CK(ozgemm(true, b, b, rows, 1.0, X, ldx, ctx->xcolE, X, ldx, 0.0, GemmOut{ctx->gram, 1, b}, ctx->oz,
             ctx->flags, ctx->st, ctx->xcolE, &job));
@@ -383,14 +388,33 @@ lra_status right_apply_rinv(lra_ctx* ctx, const double* X, int64_t ldx, int64_t 
   return mm(ctx, false, rows, b, b, 1.0, X, ldx, xE, ctx->Rinv, b, 0.0, out, 1, ldo);
 }
 
+// The second pass of CholQR2: the Gram of X = Tmp (the first pass's Q factor) and
+// out = X R^{-1}.  The Gram is normally within the first pass's loss of
+// orthogonality of I; when every entry of S - I is within 2^-40 the product is
+// X + X (R^{-1} - I) with the small correction in FP32 (rinv_near_identity),
+// otherwise the FP64-accurate product.  The choice is made on the device (the
+// Cholesky's flag): both are issued, and the one not chosen does nothing.
+lra_status second_pass(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows, double* out,
+                       int64_t ldo) {
+  const int b = ctx->b;
+  if (!ctx->tensor || rows > oz_max_k()) {
+    TRY(gram_chol(ctx, X, ldx, rows, nullptr));
+    return right_apply_rinv(ctx, X, ldx, rows, out, ldo);
+  }
+  TRY(gram_chol(ctx, X, ldx, rows, nullptr, true));
+  CK(rinv_near_identity(X, ldx, rows, b, ctx->Rinv, ctx->near, out, ldo, ctx->st));
+  CK(oz_rowcol_exponents(X, ldx, rows, b, ctx->xrowE, nullptr, ctx->st, false, ctx->near));
+  CK(ozgemm(false, rows, b, b, 1.0, X, ldx, ctx->xrowE, ctx->Rinv, b, 0.0, GemmOut{out, 1, ldo},
+            ctx->oz, ctx->flags, ctx->st, nullptr, nullptr, ctx->near));
+  return LRA_OK;
+}
+
 // out (rows x b, ld ldo) = Q factor of X (rows x b, ld ldx), CholQR2.
 lra_status orth(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows, double* out,
                 int64_t ldo) {
   TRY(gram_chol(ctx, X, ldx, rows, nullptr));
   TRY(right_apply_rinv(ctx, X, ldx, rows, ctx->Tmp, ctx->lds));
-  TRY(gram_chol(ctx, ctx->Tmp, ctx->lds, rows, nullptr));
-  TRY(right_apply_rinv(ctx, ctx->Tmp, ctx->lds, rows, out, ldo));
-  return LRA_OK;
+  return second_pass(ctx, ctx->Tmp, ctx->lds, rows, out, ldo);
 }
 
 // The basis G of the power-step panel W of block j, power step s (the eigSVD step
@@ -404,9 +428,7 @@ lra_status orth_panel(lra_ctx* ctx, const double* X, int64_t ldx, int64_t rows, 
   TRY(gram_chol(ctx, X, ldx, rows, ctx->dead));
   TRY(right_apply_rinv(ctx, X, ldx, rows, ctx->Tmp, ctx->lds));
   CK(fill_dead(ctx->Tmp, ctx->lds, rows, b, ctx->dead, ctx->os.k0, ctx->os.k1, j, s, ctx->st));
-  TRY(gram_chol(ctx, ctx->Tmp, ctx->lds, rows, nullptr));
-  TRY(right_apply_rinv(ctx, ctx->Tmp, ctx->lds, rows, out, ldo));
-  return LRA_OK;
+  return second_pass(ctx, ctx->Tmp, ctx->lds, rows, out, ldo);
 }
 
 lra_status make_omega(lra_ctx* ctx, int64_t j) {
@@ -671,7 +693,20 @@ lra_status run(lra_ctx* ctx, const void* Av, int64_t lda, int dtype) {
         PHASE(LRA_PHASE_PROJECT, {
           for (int pass = 0; pass < 2; ++pass) {
             TRY(mm(ctx, true, l, b, m, 1.0, ctx->Q, ldq, ctx->qcolE, Y, lds, 0.0, ctx->F, 1, ldf));
-            TRY(mm(ctx, false, m, b, l, -1.0, ctx->Q, ldq, ctx->qrowE, ctx->F, ldf, 1.0, Y, 1, lds));
+            if (pass == 1 && ctx->tensor && m <= oz_max_k() && l <= 4096) {
+              // F = Q^T Y is now of the order of Y's rounding: the update in FP32 when
+              // small enough (decided on the device), else the FP64-accurate product
+              // (whose scan of F's exponents may skip for l <= 4096); the product just
+              // made left Y's column exponents in oz.yE
+              CK(project_fp32(ctx->Q, ldq, m, l, ctx->F, ldf, b, ctx->oz.yE, Y, lds, ctx->near + 1,
+                              ctx->st));
+              CK(ozgemm(false, m, b, l, -1.0, ctx->Q, ldq, ctx->qrowE, ctx->F, ldf, 1.0,
+                        GemmOut{Y, 1, lds}, ctx->oz, ctx->flags, ctx->st, nullptr, nullptr,
+                        ctx->near + 1));
+            } else {
+              TRY(mm(ctx, false, m, b, l, -1.0, ctx->Q, ldq, ctx->qrowE, ctx->F, ldf, 1.0, Y, 1,
+                     lds));
+            }
           }
         });
       }
@@ -774,7 +809,7 @@ void free_all(lra_ctx* c) {
     if (c->cst[i]) cudaStreamSynchronize(c->cst[i]);
   void* ptrs[] = {c->Q,      c->B,        c->Yk,     c->S0,       c->Yb,        c->T1,
                   c->Tmp,    c->W,        c->G,      c->Wt,       c->F,         c->BOm,
-                  c->z,      c->zB,       c->wvec,   c->ws,       c->gram,      c->Rinv,   c->dead,
+                  c->z,      c->zB,       c->wvec,   c->ws,       c->gram,      c->Rinv,   c->dead,   c->near,
                   c->colsq,  c->colsum,   c->scal,   c->flags,    c->om_counts, c->om_rows,
                   c->om_vals, c->om_dense, c->sk_counts, c->sk_rows, c->sk_vals, c->A_host_copy,
                   c->A_host_copy2,
@@ -940,6 +975,7 @@ lra_status create_ctx(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
   ALLOC(gram, LRA_MAX_B * LRA_MAX_B);
   ALLOC(Rinv, LRA_MAX_B * LRA_MAX_B);
   ALLOC(dead, LRA_MAX_B);
+  ALLOC(near, 2);
   ALLOC(colsq, std::max<int64_t>(n, LRA_MAX_B));
   ALLOC(colsum, std::max<int64_t>(n, LRA_MAX_B));
   ALLOC(scal, 8);

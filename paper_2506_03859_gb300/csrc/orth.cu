@@ -6,6 +6,8 @@
 // give identical bits.
 #include <math.h>
 
+#include <cmath>
+
 #include "chol.cuh"
 #include "internal.cuh"
 
@@ -130,8 +132,196 @@ __global__ void __launch_bounds__(1024) k_total(const double* __restrict__ v, in
 
 __global__ void __launch_bounds__(CHOL_NT) k_chol_inv(const double* __restrict__ S, int b, double tau,
                                                       double* __restrict__ Rinv, int* __restrict__ flags,
-                                                      int* __restrict__ dead) {
-  chol_inv_cta(S, b, tau, Rinv, flags, dead);
+                                                      int* __restrict__ dead, int* __restrict__ near) {
+  chol_inv_cta(S, b, tau, Rinv, flags, dead, near);
+}
+
+// Conversions between FP64 and FP32 by integer operations.  On GB300 a
+// conversion instruction runs on the FP64 pipe, which retires about one warp
+// instruction per 64 cycles per sub-partition; these run on the integer pipes.
+// f64_to_f32: the significand truncated to 24 bits (relative error below 2^-23),
+// magnitudes below 2^-126 to zero, above the FP32 range to infinity.
+__device__ __forceinline__ float f64_to_f32(double v) {
+  const uint64_t u = (uint64_t)__double_as_longlong(v);
+  const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+  const uint32_t sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((uint32_t)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+// f32_to_f64: exact for normal values and infinities; FP32 subnormals (below
+// 2^-126) to zero.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t sign = u & 0x80000000u, ef = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  if (ef == 0) return __hiloint2double((int)sign, 0);
+  const uint32_t ed = ef == 255u ? 2047u : ef - 127u + 1023u;
+  return __hiloint2double((int)(sign | (ed << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// The FP32 corrections below: a CTA of 128 threads takes NEAR_ROWS = 32 rows;
+// warp w computes output columns 16 w .. 16 w + 15 of them (nothing when
+// 16 w >= b), lane = row, so that every thread of a warp reads the same entries of
+// the small right-hand matrix in shared memory (a broadcast) and its own row's
+// entries without bank conflicts.  Many small CTAs keep several warps on every
+// sub-partition, which the dependent FMA chains of one warp need.
+constexpr int NEAR_THREADS = 128, NEAR_ROWS = 32;
+
+// Thirty-two rows of X (rows x cols, ld ldx, from row r0; columns < 64 read) into
+// xs[k][r] as FP32 (f64_to_f32), zero beyond rows and cols: each thread issues its
+// 16 loads (consecutive rows across a warp) before converting any.
+__device__ __forceinline__ void stage_rows_f32(const double* __restrict__ X, int64_t ldx,
+                                               int64_t rows, int64_t cols, int64_t r0,
+                                               float (&xs)[64][NEAR_ROWS]) {
+  constexpr int PER = 64 * NEAR_ROWS / NEAR_THREADS;
+  const int r = threadIdx.x & 31, kb = threadIdx.x >> 5;
+  const int64_t i = r0 + r;
+  double v[PER];
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int k = kb + 4 * t;
+    v[t] = (i < rows && k < cols) ? __ldg(X + i + (int64_t)k * ldx) : 0.0;
+  }
+#pragma unroll
+  for (int t = 0; t < PER; ++t) xs[kb + 4 * t][r] = f64_to_f32(v[t]);
+}
+
+// 64 x 64 entries of a column-major matrix (ld ldm, from row k0; rows < kn and
+// columns < cn read, zero elsewhere) into ms[k][c] as FP32; with thr, also whether
+// any |entry of column c| exceeds the double whose bits are thr[c] (or is a NaN).
+// Loads in two batches of 16 per thread.
+__device__ __forceinline__ int stage_square_f32(const double* __restrict__ M, int64_t ldm,
+                                                int64_t k0, int64_t kn, int cn,
+                                                float (&ms)[64][64], const uint64_t* thr) {
+  constexpr int PER = 64 * 64 / NEAR_THREADS, BATCH = PER / 2;
+  const int c = threadIdx.x & 63, kb = threadIdx.x >> 6;
+  const uint64_t th = thr ? thr[c] : ~0ull;
+  int big = 0;
+#pragma unroll
+  for (int h = 0; h < PER; h += BATCH) {
+    double v[BATCH];
+#pragma unroll
+    for (int t = 0; t < BATCH; ++t) {
+      const int64_t k = k0 + kb + 2 * (h + t);
+      v[t] = (k < kn && c < cn) ? __ldg(M + k + (int64_t)c * ldm) : 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < BATCH; ++t) {
+      big |= ((uint64_t)__double_as_longlong(v[t]) & 0x7FFFFFFFFFFFFFFFull) > th;
+      ms[kb + 2 * (h + t)][c] = f64_to_f32(v[t]);
+    }
+  }
+  return big;
+}
+
+// acc[c] += sum_{k < kn} xs[k][r] ds[k][c0 + c], c < 16: one load of x and four
+// broadcast loads of ds per k, in a short loop (a fully unrolled one overflows the
+// instruction cache, and every warp runs it only once).
+__device__ __forceinline__ void fma_rows(const float (&xs)[64][NEAR_ROWS], const float (&ds)[64][64],
+                                         int kn, int r, int c0, float (&acc)[16]) {
+#pragma unroll 4
+  for (int k = 0; k < kn; ++k) {
+    const float x = xs[k][r];
+    const float4* d = reinterpret_cast<const float4*>(&ds[k][c0]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 v = d[q];
+      acc[4 * q] = fmaf(x, v.x, acc[4 * q]);
+      acc[4 * q + 1] = fmaf(x, v.y, acc[4 * q + 1]);
+      acc[4 * q + 2] = fmaf(x, v.z, acc[4 * q + 2]);
+      acc[4 * q + 3] = fmaf(x, v.w, acc[4 * q + 3]);
+    }
+  }
+}
+
+// out = X + X D with D = R^{-1} - I (X: rows x b), when *near is set: the
+// Cholesky found every entry of its Gram within 2^-40 of the identity's, so the
+// entries of D (the closed form -Phi(S - I)) are within 2^-40 and the correction
+// X D needs only FP32: X and D truncated to FP32 (f64_to_f32), products summed in
+// FP32, so the correction errs by at most (b + 4) 2^-24 sum_k |X[i, k]| |D[k, c]|;
+// the sum, ~2^-40 of X, is added to X in FP64.  Otherwise nothing: the
+// FP64-accurate product runs instead.  One FP64 operation per output (the final
+// add) and one per diagonal entry of D.
+__global__ void __launch_bounds__(NEAR_THREADS) k_rinv_near_identity(
+    const double* __restrict__ X, int64_t ldx, int64_t rows, int b, const double* __restrict__ Rinv,
+    const int* __restrict__ near, double* __restrict__ out, int64_t ldo) {
+  if (__ldcg(near) == 0) return;
+  __shared__ __align__(16) float D[64][64];          // D[k][c], zero beyond b
+  __shared__ __align__(16) float xs[64][NEAR_ROWS];  // xs[k][r] = X[r0 + r, k]
+  const int64_t r0 = (int64_t)blockIdx.x * NEAR_ROWS;
+  stage_square_f32(Rinv, b, 0, b, b, D, nullptr);
+  stage_rows_f32(X, ldx, rows, b, r0, xs);
+  __syncthreads();
+  if (threadIdx.x < 64 && threadIdx.x < b) {
+    // D's diagonal: R^{-1}_cc - 1, exact in FP64 (R^{-1}_cc near 1)
+    const int c = threadIdx.x;
+    D[c][c] = f64_to_f32(__ldg(Rinv + c + (int64_t)c * b) - 1.0);
+  }
+  __syncthreads();
+  const int c0 = (threadIdx.x >> 5) * 16, r = threadIdx.x & 31;
+  const int64_t i = r0 + r;
+  if (i >= rows || c0 >= b) return;
+  float acc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc[c] = 0.0f;
+  fma_rows(xs, D, b, r, c0, acc);
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int cc = c0 + c;
+    if (cc < b) out[i + (int64_t)cc * ldo] = __ldg(X + i + (int64_t)cc * ldx) + f32_to_f64(acc[c]);
+  }
+}
+
+// The second projection of CGS2, Y -= Q F (Q: rows x l, F = Q^T Y: l x b, Y:
+// rows x b), in FP32 when F is small enough: every |F[k, c]| within
+// g 2^(yE[c] - 1022), where yE[c] is the biased exponent of Y's largest entry in
+// column c (so |Y[:, c]| < 2^(yE[c] - 1022)).  With Q and F truncated to FP32
+// (f64_to_f32) and the products summed in FP32, the update errs by at most
+// (l + 4) 2^-24 sum_k |Q[i, k]| |F[k, c]| <= (l + 4) sqrt(l) 2^-24 max|F[:, c]| (the
+// rows of Q have norm <= 1), so with g = 2^-29 / ((l + 4) sqrt(l)) it errs by at
+// most 2^-53 2^(yE[c] - 1022), the rounding of Y's largest entries.  After the
+// first projection F is of the order of Y's rounding errors, far below that.
+// Every CTA stages all of F and takes the same decision (an integer comparison of
+// the magnitudes' bits, which a NaN fails); CTA 0 records it in *taken (the
+// FP64-accurate update then does nothing); if F is not small, no CTA writes.
+// l in chunks of 64.
+__global__ void __launch_bounds__(NEAR_THREADS) k_project_fp32(
+    const double* __restrict__ Q, int64_t ldq, int64_t rows, int64_t l, const double* __restrict__ F,
+    int64_t ldf, int b, const int* __restrict__ yE, double g, double* __restrict__ Y, int64_t ldy,
+    int* __restrict__ taken) {
+  __shared__ __align__(16) float Fs[64][64];         // Fs[k][c] = F[k0 + k, c], zero beyond l, b
+  __shared__ __align__(16) float qs[64][NEAR_ROWS];  // qs[k][r] = Q[r0 + r, k0 + k]
+  __shared__ uint64_t thr[64];                       // bits of g 2^(yE[c] - 1022)
+  __shared__ int s_big;
+  if (threadIdx.x < 64)
+    thr[threadIdx.x] = threadIdx.x < b
+                           ? (uint64_t)__double_as_longlong(scalbn(g, __ldg(yE + threadIdx.x) - 1022))
+                           : 0;
+  if (threadIdx.x == 0) s_big = 0;
+  const int64_t r0 = (int64_t)blockIdx.x * NEAR_ROWS;
+  const int c0 = (threadIdx.x >> 5) * 16, r = threadIdx.x & 31;
+  const int64_t i = r0 + r;
+  const bool active = i < rows && c0 < b;
+  float acc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc[c] = 0.0f;
+  for (int64_t k0 = 0; k0 < l; k0 += 64) {
+    __syncthreads();  // thr and s_big set; the previous chunk consumed
+    if (stage_square_f32(F, ldf, k0, l, b, Fs, thr)) s_big = 1;
+    stage_rows_f32(Q + k0 * ldq, ldq, rows, l - k0, r0, qs);
+    __syncthreads();
+    if (active) fma_rows(qs, Fs, l - k0 < 64 ? (int)(l - k0) : 64, r, c0, acc);
+  }
+  __syncthreads();
+  const bool small = s_big == 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *taken = small;
+  if (!small || !active) return;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int cc = c0 + c;
+    if (cc < b) Y[i + (int64_t)cc * ldy] -= f32_to_f64(acc[c]);
+  }
 }
 
 __global__ void k_append_rows(const double* __restrict__ Wt, int64_t ldw, int64_t n, int b,
@@ -183,8 +373,28 @@ cudaError_t total(const double* v, int64_t count, double* out, cudaStream_t st) 
 }
 
 cudaError_t chol_inv(const double* S, int b, double tau, double* Rinv, int* flags, cudaStream_t st,
-                     int* dead) {
-  k_chol_inv<<<1, CHOL_NT, 0, st>>>(S, b, tau, Rinv, flags, dead);
+                     int* dead, int* near) {
+  k_chol_inv<<<1, CHOL_NT, 0, st>>>(S, b, tau, Rinv, flags, dead, near);
+  return launched();
+}
+
+cudaError_t rinv_near_identity(const double* X, int64_t ldx, int64_t rows, int b, const double* Rinv,
+                               const int* near, double* out, int64_t ldo, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  if (b <= 0 || b > 64) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)((rows + NEAR_ROWS - 1) / NEAR_ROWS);
+  k_rinv_near_identity<<<grid, NEAR_THREADS, 0, st>>>(X, ldx, rows, b, Rinv, near, out, ldo);
+  return launched();
+}
+
+cudaError_t project_fp32(const double* Q, int64_t ldq, int64_t rows, int64_t l, const double* F,
+                         int64_t ldf, int b, const int* yE, double* Y, int64_t ldy, int* taken,
+                         cudaStream_t st) {
+  if (rows <= 0 || l <= 0) return cudaErrorInvalidValue;
+  if (b <= 0 || b > 64) return cudaErrorInvalidValue;
+  const double g = std::ldexp(1.0, -29) / (((double)l + 4.0) * std::sqrt((double)l));
+  const unsigned grid = (unsigned)((rows + NEAR_ROWS - 1) / NEAR_ROWS);
+  k_project_fp32<<<grid, NEAR_THREADS, 0, st>>>(Q, ldq, rows, l, F, ldf, b, yE, g, Y, ldy, taken);
   return launched();
 }
 

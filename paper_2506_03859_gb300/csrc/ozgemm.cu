@@ -157,7 +157,9 @@ __device__ __forceinline__ void cut8(const double* v, int emax, uint8_t* dst, in
 // rows [y rchunk, (y + 1) rchunk) of column c.
 __global__ void __launch_bounds__(256) k_oz_colmaxexp(const double* __restrict__ X, int64_t ld,
                                                       int64_t rows, int64_t rchunk,
-                                                      int* __restrict__ out) {
+                                                      int* __restrict__ out,
+                                                      const int* __restrict__ skip) {
+  if (skip && __ldcg(skip)) return;
   __shared__ int red[8];
   const int64_t c = blockIdx.x;
   const int64_t r0 = (int64_t)blockIdx.y * rchunk;
@@ -180,23 +182,27 @@ __global__ void __launch_bounds__(256) k_oz_colmaxexp(const double* __restrict__
   }
 }
 
-// Column exponents of X (rows x cols): zero out, then the split scan.
+// Column exponents of X (rows x cols): zero out, then the split scan.  skip: as
+// for OzArgs (only with rows <= 4096, where nothing is zeroed).
 cudaError_t colmaxexp(const double* X, int64_t ld, int64_t rows, int64_t cols, int* out,
-                      cudaStream_t st) {
+                      cudaStream_t st, const int* skip = nullptr) {
   const int64_t rchunk = 4096;
+  if (skip && rows > rchunk) return cudaErrorInvalidValue;
   if (rows > rchunk) {
     cudaError_t e = cudaMemsetAsync(out, 0, cols * sizeof(int), st);
     if (e != cudaSuccess) return e;
   }
   dim3 grid((unsigned)cols, (unsigned)((rows + rchunk - 1) / rchunk));
-  k_oz_colmaxexp<<<grid, 256, 0, st>>>(X, ld, rows, rchunk, out);
+  k_oz_colmaxexp<<<grid, 256, 0, st>>>(X, ld, rows, rchunk, out, skip);
   return launched();
 }
 
 // out[r] = max over the columns of X[r, :] of the biased exponent (out pre-zeroed).
 __global__ void __launch_bounds__(256) k_oz_rowmaxexp(const double* __restrict__ X, int64_t ld,
                                                       int64_t rows, int64_t cols, int64_t cchunk,
-                                                      int* __restrict__ out, bool direct) {
+                                                      int* __restrict__ out, bool direct,
+                                                      const int* __restrict__ skip) {
+  if (skip && __ldcg(skip)) return;
   const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (r >= rows) return;
   const int64_t c0 = (int64_t)blockIdx.y * cchunk;
@@ -217,7 +223,9 @@ __global__ void __launch_bounds__(256) k_oz_rowmaxexp(const double* __restrict__
 // (stage, column c, 8-wide k chunk j).
 __global__ void __launch_bounds__(256) k_oz_ycut(const double* __restrict__ Y, int64_t ldy,
                                                  int64_t K, int N, const int* __restrict__ yE,
-                                                 uint8_t* __restrict__ img, int64_t kst) {
+                                                 uint8_t* __restrict__ img, int64_t kst,
+                                                 const int* __restrict__ skip) {
+  if (skip && __ldcg(skip)) return;
   const int64_t idx = (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (idx >= kst * NN * 2) return;
   const int j = (int)(idx & 1);
@@ -251,6 +259,7 @@ struct OzArgs {
   int* flags;
   bool vec;            // 16-byte loads allowed (trans layout)
   bool whole_tiles;    // ranges hold whole tiles: no tile is split, no fixup
+  const int* skip;     // NULL, or the launch does nothing while *skip != 0
 };
 
 // The range [u0, u1) of CTA cta of G: an even share of all units ("stream-K"),
@@ -715,6 +724,7 @@ __device__ __forceinline__ void oz_flush_role(OzShared& sh, const OzArgs& a, con
 
 template <bool TRANS>
 __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
+  if (a.skip && __ldcg(a.skip)) return;
   extern __shared__ uint8_t smem_raw[];
   __shared__ OzShared sh;
   __shared__ int sEx[2][TM];  // producers: row exponents of tiles (by tile parity)
@@ -970,7 +980,10 @@ __device__ __forceinline__ void oz_fixup_cta(const OzArgs& a, int G) {
 }
 
 template <int LANES>
-__global__ void __launch_bounds__(256, 6) k_oz_fixup(OzArgs a, int G) { oz_fixup_cta<LANES, 256>(a, G); }
+__global__ void __launch_bounds__(256, 6) k_oz_fixup(OzArgs a, int G) {
+  if (a.skip && __ldcg(a.skip)) return;
+  oz_fixup_cta<LANES, 256>(a, G);
+}
 
 // The fused Gram + Cholesky (the b x b Gram S = X^T X of CholQR, Alg. 1's Z = Y^T Y
 // in QB form): the fixup of the split Gram, then the CTA that finishes last -- the
@@ -987,7 +1000,7 @@ __global__ void __launch_bounds__(CHOL_NT) k_oz_fixup_chol(OzArgs a, int G, Chol
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  chol_inv_cta(a.C, (int)a.N, job.tau, job.Rinv, a.flags, job.dead);
+  chol_inv_cta(a.C, (int)a.N, job.tau, job.Rinv, a.flags, job.dead, job.near);
   if (threadIdx.x == 0) *job.count = 0;
 }
 
@@ -1008,21 +1021,23 @@ cudaError_t launch_fixup(const OzArgs& a, int G, cudaStream_t st) {
 }
 
 cudaError_t oz_rowcol_exponents(const double* X, int64_t ld, int64_t rows, int64_t cols,
-                                int* rowE, int* colE, cudaStream_t st, bool accumulate_rows) {
+                                int* rowE, int* colE, cudaStream_t st, bool accumulate_rows,
+                                const int* skip) {
   if (colE) {
-    cudaError_t e = colmaxexp(X, ld, rows, cols, colE, st);
+    cudaError_t e = colmaxexp(X, ld, rows, cols, colE, st, skip);
     if (e != cudaSuccess) return e;
   }
   if (rowE) {
     const int64_t csplit = cols >= 256 ? 16 : 1;
     const bool direct = csplit == 1 && !accumulate_rows;
+    if (skip && !direct) return cudaErrorInvalidValue;
     if (!accumulate_rows && !direct) {
       cudaError_t e = cudaMemsetAsync(rowE, 0, rows * sizeof(int), st);
       if (e != cudaSuccess) return e;
     }
     const int64_t cchunk = (cols + csplit - 1) / csplit;
     dim3 grid((unsigned)((rows + 255) / 256), (unsigned)((cols + cchunk - 1) / cchunk));
-    k_oz_rowmaxexp<<<grid, 256, 0, st>>>(X, ld, rows, cols, cchunk, rowE, direct);
+    k_oz_rowmaxexp<<<grid, 256, 0, st>>>(X, ld, rows, cols, cchunk, rowE, direct, skip);
     return launched();
   }
   return cudaSuccess;
@@ -1054,22 +1069,24 @@ OzArgs make_args(int64_t P, int64_t N, int64_t K, double alpha, const double* X,
   // short tiles (K <= 64): whole tiles per CTA beat splitting plus a fixup; long
   // tiles are split along K (stream-K), also when there are few of them
   a.whole_tiles = a.kst <= 4;
+  a.skip = nullptr;
   return a;
 }
 
 // Y's exponents and digit image (shared by both GEMM kernels).
 // yE_known: Y's column exponents when the caller has them (else computed into w.yE).
 cudaError_t prepare_y(const double* Y, int64_t ldy, int64_t K, int64_t N, const OzWorkspace& w,
-                      const int* yE_known, cudaStream_t st) {
+                      const int* yE_known, cudaStream_t st, const int* skip = nullptr) {
   const int64_t kst = (K + KS - 1) / KS;
   const int* yE = yE_known;
   if (!yE) {
-    cudaError_t e = colmaxexp(Y, ldy, K, N, w.yE, st);
+    cudaError_t e = colmaxexp(Y, ldy, K, N, w.yE, st, skip);
     if (e != cudaSuccess) return e;
     yE = w.yE;
   }
   const int64_t ythreads = kst * NN * 2;
-  k_oz_ycut<<<(unsigned)((ythreads + 255) / 256), 256, 0, st>>>(Y, ldy, K, (int)N, yE, w.img, kst);
+  k_oz_ycut<<<(unsigned)((ythreads + 255) / 256), 256, 0, st>>>(Y, ldy, K, (int)N, yE, w.img, kst,
+                                                                  skip);
   return launched();
 }
 
@@ -1154,16 +1171,19 @@ cudaError_t ozgemm_img(int64_t P, int64_t N, int64_t K, double alpha, const uint
 cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, const double* X,
                    int64_t ldx, const int* xE, const double* Y, int64_t ldy, double beta, GemmOut out,
                    const OzWorkspace& w, int* flags, cudaStream_t st, const int* yE_known,
-                   const CholJob* chol) {
+                   const CholJob* chol, const int* skip) {
   if (P <= 0 || N <= 0) return cudaSuccess;
   if (N > NN || K <= 0 || K > MAX_K) return cudaErrorInvalidValue;
   if (oz_img_bytes(K) > w.img_bytes) return cudaErrorInvalidValue;
+  // a skipped product leaves nothing for a Cholesky to read
+  if (skip && chol) return cudaErrorInvalidValue;
   cudaError_t e = oz_prepare();
   if (e != cudaSuccess) return e;
-  e = prepare_y(Y, ldy, K, N, w, yE_known, st);
+  e = prepare_y(Y, ldy, K, N, w, yE_known, st, skip);
   if (e != cudaSuccess) return e;
   OzArgs a = make_args(P, N, K, alpha, X, ldx, xE, beta, out, w, flags);
   if (yE_known) a.yE = yE_known;
+  a.skip = skip;
   const int G = w.ctas;
   if (trans)
     k_ozgemm<true><<<G, NT, SMEM_DYN, st>>>(a);
@@ -1173,7 +1193,8 @@ cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, co
   if (e != cudaSuccess) return e;
   if (chol) {
     // the product is the b x b Gram (P = N = b <= 64, C with ld b): factor it
-    if (a.whole_tiles) return chol_inv(out.C, (int)N, chol->tau, chol->Rinv, flags, st, chol->dead);
+    if (a.whole_tiles)
+      return chol_inv(out.C, (int)N, chol->tau, chol->Rinv, flags, st, chol->dead, chol->near);
     const int64_t elems = (int64_t)P * N;
     k_oz_fixup_chol<<<dim3(1, (unsigned)((elems * 16 + CHOL_NT - 1) / CHOL_NT)), CHOL_NT, 0, st>>>(a, G, *chol);
     return launched();
