@@ -78,6 +78,7 @@ constexpr int SMEM_DYN = NSTAGE * STAGE + 1024;
 constexpr uint32_t LBO = 128, SBO = 256;  // core-matrix strides (K, rows)
 constexpr uint32_t TMEM_COLS = 512;       // weights 0..6: columns 0..447
 constexpr uint32_t COL_ACC_LO = 448, COL_ACC_HI = 480;  // int64 sums of output columns 32..63
+constexpr uint32_t ACC_SET1 = 256;  // the reduced form's second set of exact sums (weights 0..3)
 constexpr uint32_t MAGIC = 0x4B400000u;   // bits of 1.5 * 2^23
 constexpr long WAIT_TRIES = 1L << 22;
 constexpr int EXP_OFFSET = 2058;          // 2 * 1077 - 96: see the scaling above
@@ -399,7 +400,11 @@ __device__ __forceinline__ void mma_group(uint32_t tmem, uint32_t a0, uint32_t y
 
 // Barriers, TMEM address and small tables a CTA's roles share.
 struct OzShared {
-  uint64_t full[NSTAGE], empty[NSTAGE], accfull, accempty;
+  // accfull / accempty [set]: the exact sums of a window in accumulator set 0
+  // (columns 0..255), or, in the reduced form, alternately in sets 0 and 1
+  // (columns 256..511, free there), so that one window's MMAs run while the flush
+  // folds the previous window's sums
+  uint64_t full[NSTAGE], empty[NSTAGE], accfull[2], accempty[2];
   uint32_t tmem;
   int abort;
   int yE[NN];
@@ -416,8 +421,10 @@ __device__ __forceinline__ void oz_setup(OzShared& sh, const OzArgs& a, int full
       tc::mbar_init(&sh.full[s], full_count);
       tc::mbar_init(&sh.empty[s], 1);
     }
-    tc::mbar_init(&sh.accfull, 1);
-    tc::mbar_init(&sh.accempty, flush_threads);
+    for (int a2 = 0; a2 < 2; ++a2) {
+      tc::mbar_init(&sh.accfull[a2], 1);
+      tc::mbar_init(&sh.accempty[a2], flush_threads);
+    }
     sh.abort = 0;
   }
   if (tid < NN) sh.yE[tid] = tid < a.N ? a.yE[tid] : 0;
@@ -454,7 +461,7 @@ __device__ __forceinline__ void oz_mma_role(OzShared& sh, const Cursor& start, u
     return true;
   };
   auto wait_accempty = [&]() -> bool {
-    if (!tc::mbar_wait(&sh.accempty, ph_ae, WAIT_TRIES)) return false;
+    if (!tc::mbar_wait(&sh.accempty[0], ph_ae, WAIT_TRIES)) return false;
     ph_ae ^= 1u;
     tc::fence_after_sync();
     return true;
@@ -476,23 +483,47 @@ __device__ __forceinline__ void oz_mma_role(OzShared& sh, const Cursor& start, u
     mma_group(tmem, a0, y0, 5, 0, 2, 1u);
     mma_group(tmem, a0, y0, 6, 0, 1, 1u);
   };
-  auto exact = [&](int st) {
+  auto exact = [&](int st, uint32_t acc_col = 0u) {
     const uint32_t a0 = tc::smem_addr(sm + st * STAGE), y0 = a0 + S * A_PLANE;
+    const uint32_t t0 = tmem + acc_col;
     if (YD1) {
-      mma_group(tmem, a0, y0, 0, 0, 1, 1u);
-      mma_group(tmem, a0, y0, 1, 0, 1, 1u);
-      mma_group(tmem, a0, y0, 2, 0, 1, 1u);
-      mma_group(tmem, a0, y0, 3, 0, 1, 1u);
+      mma_group(t0, a0, y0, 0, 0, 1, 1u);
+      mma_group(t0, a0, y0, 1, 0, 1, 1u);
+      mma_group(t0, a0, y0, 2, 0, 1, 1u);
+      mma_group(t0, a0, y0, 3, 0, 1, 1u);
       tc::mma_commit(&sh.empty[st]);
       return;
     }
-    mma_group(tmem, a0, y0, 0, 0, 4, 1u);
-    mma_group(tmem, a0, y0, 1, 0, 3, 1u);
-    mma_group(tmem, a0, y0, 2, 0, 2, 1u);
-    mma_group(tmem, a0, y0, 3, 0, 1, 1u);
+    mma_group(t0, a0, y0, 0, 0, 4, 1u);
+    mma_group(t0, a0, y0, 1, 0, 3, 1u);
+    mma_group(t0, a0, y0, 2, 0, 2, 1u);
+    mma_group(t0, a0, y0, 3, 0, 1, 1u);
     tc::mma_commit(&sh.empty[st]);
   };
   Cursor c = start;
+  if (!HIGH) {
+    // the reduced form: window w's exact sums in set w % 2; its MMAs wait only for
+    // the fold of window w - 2 (the same set), not of window w - 1
+    int set = 0;
+    uint32_t ph_e2 = 0;  // bit s: the phase of accempty[s]
+    while (c.i < c.n) {
+      const int st = (int)(c.i % NSTAGE);
+      if (!wait_full(st)) break;
+      if (c.win_first()) {
+        if (!tc::mbar_wait(&sh.accempty[set], (ph_e2 >> set) & 1u, WAIT_TRIES)) break;
+        ph_e2 ^= 1u << set;
+        tc::fence_after_sync();
+      }
+      exact(st, set ? ACC_SET1 : 0u);
+      if (c.win_last()) {
+        tc::mma_commit(&sh.accfull[set]);
+        set ^= 1;
+      }
+      c.next();
+    }
+    if (c.i < c.n) s_abort = 1;
+    return;
+  }
   while (c.i < c.n) {
     const int st = (int)(c.i % NSTAGE);
     if (!wait_full(st)) break;
@@ -509,7 +540,7 @@ __device__ __forceinline__ void oz_mma_role(OzShared& sh, const Cursor& start, u
         if (!wait_accempty()) break;
         exact(st);
         exact(st2);
-        if (d.win_last()) tc::mma_commit(&sh.accfull);
+        if (d.win_last()) tc::mma_commit(&sh.accfull[0]);
         c = d;
         c.next();
         continue;
@@ -517,7 +548,7 @@ __device__ __forceinline__ void oz_mma_role(OzShared& sh, const Cursor& start, u
       if (!wait_accempty()) break;
     }
     exact(st);
-    if (c.win_last()) tc::mma_commit(&sh.accfull);
+    if (c.win_last()) tc::mma_commit(&sh.accfull[0]);
     c.next();
   }
   if (c.i < c.n) s_abort = 1;
@@ -554,11 +585,15 @@ __device__ __forceinline__ void oz_flush_role(OzShared& sh, const OzArgs& a, con
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int quarter = warp & 3, col0 = NFW == 8 ? NCOL * (warp >> 2) : 0;
   const int64_t first_tile = start.tile;
+  static_assert(HIGH || NFW == 8, "the reduced form keeps its totals in registers");
   const uint32_t tb = sh.tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)col0;
 #pragma unroll
   for (int w = 0; w < 4; ++w)
 #pragma unroll
-    for (int j = 0; j < NCOL / 8; ++j) tc::tmem_st8_splat(tb + 64u * w + 8u * j, MAGIC);
+    for (int j = 0; j < NCOL / 8; ++j) {
+      tc::tmem_st8_splat(tb + 64u * w + 8u * j, MAGIC);
+      if (!HIGH) tc::tmem_st8_splat(tb + ACC_SET1 + 64u * w + 8u * j, MAGIC);
+    }
   if (NCOL == 64) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -568,12 +603,15 @@ __device__ __forceinline__ void oz_flush_role(OzShared& sh, const OzArgs& a, con
   }
   tc::tmem_st_wait();
   tc::fence_before_sync();
-  tc::mbar_arrive(&sh.accempty);
+  tc::mbar_arrive(&sh.accempty[0]);
+  if (!HIGH) tc::mbar_arrive(&sh.accempty[1]);
 
   int64_t acc[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) acc[i] = 0;
-  uint32_t ph_af = 0;
+  uint32_t ph_af = 0;  // bit s: the phase of accfull[s]
+  int set = 0;      // the accumulator set of the current window (always 0 in the full form)
+  uint32_t tw = tb;  // its columns
   const int ncols = min((int)a.N, NN);  // output columns actually read
   const int amode = a.alpha == 1.0 ? 0 : a.alpha == -1.0 ? 1 : 2;  // decided once, not per output
   const bool beta0 = a.beta == 0.0;
@@ -581,9 +619,10 @@ __device__ __forceinline__ void oz_flush_role(OzShared& sh, const OzArgs& a, con
     if (!c.win_last()) continue;
     // lane 0 waits; the warp follows its decision (tcgen05.ld is warp-collective)
     bool ok = true;
-    if (lane == 0) ok = tc::mbar_wait(&sh.accfull, ph_af, WAIT_TRIES);
+    if (lane == 0) ok = tc::mbar_wait(&sh.accfull[set], (ph_af >> set) & 1u, WAIT_TRIES);
     ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-    ph_af ^= 1u;
+    ph_af ^= 1u << set;
+    tw = tb + (set ? ACC_SET1 : 0u);
     if (!ok) {
       s_abort = 1;
       break;
@@ -594,10 +633,10 @@ __device__ __forceinline__ void oz_flush_role(OzShared& sh, const OzArgs& a, con
     uint32_t ra[6][4], rb[6][4];
     auto load = [&](int j, uint32_t (&r)[6][4]) {
       const uint32_t c4 = 4u * j;
-      tc::tmem_ld4(tb + c4, r[0]);
-      tc::tmem_ld4(tb + 64u + c4, r[1]);
-      tc::tmem_ld4(tb + 128u + c4, r[2]);
-      tc::tmem_ld4(tb + 192u + c4, r[3]);
+      tc::tmem_ld4(tw + c4, r[0]);
+      tc::tmem_ld4(tw + 64u + c4, r[1]);
+      tc::tmem_ld4(tw + 128u + c4, r[2]);
+      tc::tmem_ld4(tw + 192u + c4, r[3]);
       if (j >= 8) {
         tc::tmem_ld4(tb + COL_ACC_LO + c4 - 32u, r[4]);
         tc::tmem_ld4(tb + COL_ACC_HI + c4 - 32u, r[5]);
@@ -613,10 +652,10 @@ __device__ __forceinline__ void oz_flush_role(OzShared& sh, const OzArgs& a, con
         const int lo = (int)(r[2][i] * 256u + r[3][i] - 257u * MAGIC);
         add[i] = ((int64_t)hi << 16) + (int64_t)lo;
       }
-      tc::tmem_st4_splat(tb + c4, MAGIC);
-      tc::tmem_st4_splat(tb + 64u + c4, MAGIC);
-      tc::tmem_st4_splat(tb + 128u + c4, MAGIC);
-      tc::tmem_st4_splat(tb + 192u + c4, MAGIC);
+      tc::tmem_st4_splat(tw + c4, MAGIC);
+      tc::tmem_st4_splat(tw + 64u + c4, MAGIC);
+      tc::tmem_st4_splat(tw + 128u + c4, MAGIC);
+      tc::tmem_st4_splat(tw + 192u + c4, MAGIC);
       if (j < 8) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc[4 * j + i] += add[i];
@@ -718,7 +757,8 @@ __device__ __forceinline__ void oz_flush_role(OzShared& sh, const OzArgs& a, con
       tc::tmem_st_wait();
     }
     tc::fence_before_sync();
-    tc::mbar_arrive(&sh.accempty);
+    tc::mbar_arrive(&sh.accempty[set]);
+    if (!HIGH) set ^= 1;
   }
 }
 
