@@ -117,8 +117,12 @@ cudaError_t ozgemm(bool trans, int64_t P, int64_t N, int64_t K, double alpha, co
 // The digit image of op(X) (P x K): every (128-row tile, 16-deep stage) as seven
 // f16 digit planes, cut once and reused by ozgemm_img.  xE as for ozgemm.
 int64_t oz_ximg_bytes(int64_t P, int64_t K);
+// sqpart (when given): one partial sum of squares of op(X)'s entries per CTA of
+// the cut, oz_cut_ctas(P, K, ctas) of them; summed in order they give ||X||_F^2.
+int oz_cut_ctas(int64_t P, int64_t K, int ctas);
 cudaError_t oz_cut_x(bool trans, int64_t P, int64_t K, const void* X, int dtype, int64_t ldx,
-                     const int* xE, uint8_t* ximg, int ctas, cudaStream_t st);
+                     const int* xE, uint8_t* ximg, int ctas, cudaStream_t st,
+                     double* sqpart = nullptr);
 // low: the reduced form (digits 0..3 of both operands; ~2^-30 of max|x| max|y|).
 // ydig1: every column of Y is a multiple of a single power of two (its entries
 // 0 and +-2^k, e.g. a +-1/2 test matrix), so Y's digits beyond the first are zero
@@ -145,6 +149,7 @@ cudaError_t col_sums(const double* X, int64_t ld, int64_t rows, int64_t cols, do
 // part, a_stats_part_elems(m, n) doubles), colE / rowE = largest biased exponent
 // of each column / row.  Deterministic.
 int64_t a_stats_part_elems(int64_t m, int64_t n);
+// part == NULL: the exponents only (colsq not written).
 cudaError_t a_stats(const void* A, int dtype, int64_t lda, int64_t m, int64_t n, double* part,
                     double* colsq, int* colE, int* rowE, cudaStream_t st);
 // out[0] = sum of v[0..count) in a fixed order (one CTA).

@@ -605,25 +605,40 @@ lra_status run(lra_ctx* ctx, const void* Av, int64_t lda, int dtype) {
   ctx->E = ctx->normA2 = 0.0;
   CK(cudaMemsetAsync(ctx->flags, 0, sizeof(int), ctx->st));
   // ||A||_F^2 (Alg. 1 step 1); the tensor engine takes the exponents of A's rows
-  // and columns in the same pass
+  // and columns in the same pass.  With digit images, the row-scaled cut reads
+  // every entry of A anyway and sums the squares there (its FP64 pipe is idle),
+  // so this pass takes the exponents alone and ||A||_F^2 is read after the cut.
+  const bool images = ctx->tensor && ctx->ximg[0] && ctx->ximg[1];
   PHASE(LRA_PHASE_INDICATOR, {
     if (ctx->tensor)
-      CK(a_stats(Av, dtype, lda, m, n, ctx->astat, ctx->colsq, ctx->colE, ctx->rowE, ctx->st));
+      CK(a_stats(Av, dtype, lda, m, n, images ? nullptr : ctx->astat, ctx->colsq, ctx->colE,
+                 ctx->rowE, ctx->st));
     else
       CK(col_sums(A, lda, m, n, ctx->colsq, nullptr, ctx->st));
-    CK(total(ctx->colsq, n, ctx->scal, ctx->st));
+    if (!images) CK(total(ctx->colsq, n, ctx->scal, ctx->st));
   });
-  TRY(read_record(ctx));
-  const double normA2 = ctx->hp->v[0];
-  if (!isfinite(normA2)) return fail(ctx, LRA_ERR_INVALID_ARG, "A has non-finite entries");
-  ctx->normA2 = ctx->E = normA2;
-  if (normA2 == 0.0) {
-    ctx->E = 0.0;
-    ctx->run_ok = true;
-    return LRA_OK;
-  }
+  double normA2 = 0.0;
+  // 1: ||A||_F^2 read and usable; 0: the run is over (A = 0, or an error)
+  auto take_norm = [&](lra_status& r) -> int {
+    r = read_record(ctx);
+    if (r != LRA_OK) return 0;
+    normA2 = ctx->hp->v[0];
+    if (!isfinite(normA2)) {
+      r = fail(ctx, LRA_ERR_INVALID_ARG, "A has non-finite entries");
+      return 0;
+    }
+    ctx->normA2 = ctx->E = normA2;
+    if (normA2 == 0.0) {
+      ctx->E = 0.0;
+      ctx->run_ok = true;
+      r = LRA_OK;
+      return 0;
+    }
+    return 1;
+  };
+  lra_status norm_status = LRA_OK;
+  if (!images && !take_norm(norm_status)) return norm_status;
   // set-up: exponents of A, its digit images, z = A (p 1) for the shifted sketch
-  const bool images = ctx->ximg[0] && ctx->ximg[1];
   ctx->ximg_ready = images;  // stream order puts the cut before every pass that reads it
   // runs on the prefetch buffer keep their own graphs
   const bool alt = ctx->A_host_copy2 && (const void*)A == (const void*)ctx->A_host_copy2;
@@ -632,9 +647,12 @@ lra_status run(lra_ctx* ctx, const void* Av, int64_t lda, int dtype) {
   TRY(issue(ctx, gpre, A, lda, [&]() -> lra_status {
     if (images) {
       PHASE(LRA_PHASE_CUT, {
-        CK(oz_cut_x(false, m, n, Av, dtype, lda, ctx->rowE, ctx->ximg[0], ctx->oz.ctas, ctx->st));
+        CK(oz_cut_x(false, m, n, Av, dtype, lda, ctx->rowE, ctx->ximg[0], ctx->oz.ctas, ctx->st,
+                    ctx->astat));
         CK(oz_cut_x(true, n, m, Av, dtype, lda, ctx->colE, ctx->ximg[1], ctx->oz.ctas, ctx->st));
       });
+      PHASE(LRA_PHASE_INDICATOR,
+            CK(total(ctx->astat, oz_cut_ctas(m, n, ctx->oz.ctas), ctx->scal, ctx->st)));
     }
     if (ctx->tensor) {
       CK(cudaMemsetAsync(ctx->qrowE, 0, m * sizeof(int), ctx->st));
@@ -643,6 +661,7 @@ lra_status run(lra_ctx* ctx, const void* Av, int64_t lda, int dtype) {
     if (ctx->sb_sparse) PHASE(LRA_PHASE_SKETCH, TRY(compute_z(ctx, A, lda)));
     return LRA_OK;
   }));
+  if (images && !take_norm(norm_status)) return norm_status;
   const double thr = ctx->prm.eps * ctx->prm.eps * normA2;
   const bool fixed_rank = ctx->prm.k > 0;
   double E = normA2;
@@ -1022,7 +1041,8 @@ lra_status create_ctx(lra_ctx** out, int64_t m, int64_t n, const lra_params* par
       delete ctx;
       return r_;
     }
-    ALLOC(astat, a_stats_part_elems(m, n));
+    // the statistics pass's partial sums, or the digit cut's (one per CTA)
+    ALLOC(astat, std::max<int64_t>(a_stats_part_elems(m, n), 4 * (int64_t)ctx->oz.ctas));
     // A's digit images when the device has room (else every pass cuts A itself)
     if (!(params->flags & LRA_FLAG_NO_A_DIGITS)) {
       const int64_t b0 = oz_ximg_bytes(m, n), b1 = oz_ximg_bytes(n, m);

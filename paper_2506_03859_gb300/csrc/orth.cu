@@ -55,7 +55,9 @@ __global__ void __launch_bounds__(256) k_col_sums(const double* __restrict__ X, 
 // rows l, l + 32, ...; per column the warp reduces by shuffles; row maxima meet
 // in shared memory, one atomic per row and CTA.  colE and rowE start at zero.
 // T: element type of A (float entries are converted exactly to double on load).
-template <typename T>
+// SQ = false: the exponents alone (the sums of squares then come from the digit
+// cut, which reads A anyway).
+template <typename T, bool SQ>
 __global__ void __launch_bounds__(256) k_a_stats(const T* __restrict__ A, int64_t lda,
                                                  int64_t m, int64_t n, double* __restrict__ part,
                                                  int* __restrict__ colE, int* __restrict__ rowE) {
@@ -79,18 +81,20 @@ __global__ void __launch_bounds__(256) k_a_stats(const T* __restrict__ A, int64_
       const int ex = (int)((__double_as_longlong(x) >> 52) & 0x7FF);
       e = max(e, ex);
       rmax[k] = max(rmax[k], ex);
-      if (k & 1)
-        s1 = fma(x, x, s1);
-      else
-        s0 = fma(x, x, s0);
+      if (SQ) {
+        if (k & 1)
+          s1 = fma(x, x, s1);
+        else
+          s0 = fma(x, x, s0);
+      }
     }
     double sq = s0 + s1;
     for (int o = 16; o > 0; o >>= 1) {
-      sq += __shfl_down_sync(0xffffffffu, sq, o);
+      if (SQ) sq += __shfl_down_sync(0xffffffffu, sq, o);
       e = max(e, __shfl_down_sync(0xffffffffu, e, o));
     }
     if (lane == 0) {
-      part[(int64_t)blockIdx.x * n + c] = sq;
+      if (SQ) part[(int64_t)blockIdx.x * n + c] = sq;
       atomicMax(colE + c, e);
     }
   }
@@ -357,10 +361,18 @@ cudaError_t a_stats(const void* A, int dtype, int64_t lda, int64_t m, int64_t n,
   if (e != cudaSuccess) return e;
   const int64_t nrb = (m + 511) / 512;
   const dim3 grid((unsigned)nrb, (unsigned)((n + 31) / 32));
+  if (!part) {
+    if (dtype == LRA_F32)
+      k_a_stats<float, false><<<grid, 256, 0, st>>>((const float*)A, lda, m, n, nullptr, colE, rowE);
+    else
+      k_a_stats<double, false><<<grid, 256, 0, st>>>((const double*)A, lda, m, n, nullptr, colE,
+                                                     rowE);
+    return launched();
+  }
   if (dtype == LRA_F32)
-    k_a_stats<float><<<grid, 256, 0, st>>>((const float*)A, lda, m, n, part, colE, rowE);
+    k_a_stats<float, true><<<grid, 256, 0, st>>>((const float*)A, lda, m, n, part, colE, rowE);
   else
-    k_a_stats<double><<<grid, 256, 0, st>>>((const double*)A, lda, m, n, part, colE, rowE);
+    k_a_stats<double, true><<<grid, 256, 0, st>>>((const double*)A, lda, m, n, part, colE, rowE);
   e = launched();
   if (e != cudaSuccess) return e;
   k_sum_blocks<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, nrb, n, colsq);

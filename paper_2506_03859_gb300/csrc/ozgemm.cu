@@ -905,12 +905,19 @@ __global__ void __launch_bounds__(NT_IMG, 1) k_ozgemm_img(OzArgs a, const uint8_
 
 // Cut op(X) into its digit image (the stage layout of k_ozgemm_img): one CTA of
 // NPROD threads per (tile, stage) unit, grid-stride.
+// sqpart (when given): sqpart[blockIdx.x] = the sum of the squares of the values
+// the CTA cut (FP64 multiply-adds, two running sums per thread, then a fixed-order
+// reduction), so that the partials summed in order give ||X||_F^2 from the same
+// read of X (the FP64 pipe is otherwise idle in this kernel).
 template <bool TRANS, typename E>
-__global__ void __launch_bounds__(NPROD) k_oz_xcut(OzArgs a, uint8_t* __restrict__ ximg) {
+__global__ void __launch_bounds__(NPROD) k_oz_xcut(OzArgs a, uint8_t* __restrict__ ximg,
+                                                   double* __restrict__ sqpart) {
   __shared__ int sE[TM];
+  __shared__ double sred[NPROD / 32];
   const int pw = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t T = a.tiles * a.kst;
   int64_t prev_tile = -1;
+  double q0 = 0.0, q1 = 0.0;
   for (int64_t u = blockIdx.x; u < T; u += gridDim.x) {
     const int64_t tile = u / a.kst;
     const int ks = (int)(u % a.kst);
@@ -926,6 +933,25 @@ __global__ void __launch_bounds__(NPROD) k_oz_xcut(OzArgs a, uint8_t* __restrict
     double v[VPT];
     fetch<TRANS, E>(a, tile, ks, pw, lane, v);
     cut_stage<TRANS>(v, sE, ximg + u * (int64_t)(S * A_PLANE), pw, lane);
+    if (sqpart) {
+#pragma unroll
+      for (int i = 0; i < VPT; i += 2) {
+        q0 = fma(v[i], v[i], q0);
+        q1 = fma(v[i + 1], v[i + 1], q1);
+      }
+    }
+  }
+  if (sqpart) {
+    double q = q0 + q1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_down_sync(0xffffffffu, q, o);
+    if (lane == 0) sred[pw] = q;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < NPROD / 32; ++w) t += sred[w];
+      sqpart[blockIdx.x] = t;
+    }
   }
 }
 
@@ -1156,8 +1182,13 @@ int64_t oz_ximg_bytes(int64_t P, int64_t K) {
   return ((P + TM - 1) / TM) * ((K + KS - 1) / KS) * (int64_t)(S * A_PLANE);
 }
 
+int oz_cut_ctas(int64_t P, int64_t K, int ctas) {
+  const int64_t units = ((P + TM - 1) / TM) * ((K + KS - 1) / KS);
+  return (int)std::min<int64_t>(units, (int64_t)ctas * 4);
+}
+
 cudaError_t oz_cut_x(bool trans, int64_t P, int64_t K, const void* X, int dtype, int64_t ldx,
-                     const int* xE, uint8_t* ximg, int ctas, cudaStream_t st) {
+                     const int* xE, uint8_t* ximg, int ctas, cudaStream_t st, double* sqpart) {
   if (P <= 0 || K <= 0) return cudaSuccess;
   OzWorkspace none{};
   const bool f32 = dtype == LRA_F32;
@@ -1167,18 +1198,17 @@ cudaError_t oz_cut_x(bool trans, int64_t P, int64_t K, const void* X, int dtype,
     a.X32 = (const float*)X;
     a.vec = ((reinterpret_cast<uintptr_t>(X) & 7) == 0) && (ldx % 2 == 0);
   }
-  const int64_t units = a.tiles * a.kst;
-  const unsigned grid = (unsigned)std::min<int64_t>(units, (int64_t)ctas * 4);
+  const unsigned grid = (unsigned)oz_cut_ctas(P, K, ctas);
   if (f32) {
     if (trans)
-      k_oz_xcut<true, float><<<grid, NPROD, 0, st>>>(a, ximg);
+      k_oz_xcut<true, float><<<grid, NPROD, 0, st>>>(a, ximg, sqpart);
     else
-      k_oz_xcut<false, float><<<grid, NPROD, 0, st>>>(a, ximg);
+      k_oz_xcut<false, float><<<grid, NPROD, 0, st>>>(a, ximg, sqpart);
   } else {
     if (trans)
-      k_oz_xcut<true, double><<<grid, NPROD, 0, st>>>(a, ximg);
+      k_oz_xcut<true, double><<<grid, NPROD, 0, st>>>(a, ximg, sqpart);
     else
-      k_oz_xcut<false, double><<<grid, NPROD, 0, st>>>(a, ximg);
+      k_oz_xcut<false, double><<<grid, NPROD, 0, st>>>(a, ximg, sqpart);
   }
   return launched();
 }
