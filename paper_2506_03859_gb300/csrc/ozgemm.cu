@@ -453,10 +453,10 @@ template <bool HIGH, bool YD1 = false>
 __device__ __forceinline__ void oz_mma_role(OzShared& sh, const Cursor& start, uint8_t* sm) {
   volatile int& s_abort = sh.abort;
   const uint32_t tmem = sh.tmem;
-  uint32_t ph_full[NSTAGE] = {0, 0, 0, 0}, ph_ae = 0;
+  uint32_t ph_full = 0, ph_ae = 0;  // ph_full bit s: the phase of full[s]
   auto wait_full = [&](int st) -> bool {
-    if (!tc::mbar_wait(&sh.full[st], ph_full[st], WAIT_TRIES)) return false;
-    ph_full[st] ^= 1u;
+    if (!tc::mbar_wait(&sh.full[st], (ph_full >> st) & 1u, WAIT_TRIES)) return false;
+    ph_full ^= 1u << st;
     tc::fence_after_sync();
     return true;
   };
@@ -784,7 +784,7 @@ __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
   if (warp >= 4 && warp < MMA_WARP) {
     // ---------------------------------------------------------- producers
     const int pt = tid - NFLUSH, pw = pt >> 5;
-    uint32_t ph_empty[NSTAGE] = {0, 0, 0, 0};
+    uint32_t ph_empty = 0;  // bit s: the phase of empty[s]
     // row exponents of a tile in sEx[tile % 2], written while the first stage of
     // the tile is fetched (one iteration ahead of its use, behind a named barrier)
     auto load_exps = [&](int64_t tile) {
@@ -803,11 +803,11 @@ __global__ void __launch_bounds__(NT, 1) k_ozgemm(OzArgs a) {
       // in iteration i + 2, after every producer has passed barrier i + 1).
       if (pt == 0) {
         bool go = s_abort == 0;
-        if (go && c.i >= NSTAGE) go = tc::mbar_wait(&sh.empty[st], ph_empty[st], WAIT_TRIES);
+        if (go && c.i >= NSTAGE) go = tc::mbar_wait(&sh.empty[st], (ph_empty >> st) & 1u, WAIT_TRIES);
         if (!go) s_abort = 1;
         s_pgo[slot] = go ? 1 : 0;
       }
-      if (c.i >= NSTAGE) ph_empty[st] ^= 1u;
+      if (c.i >= NSTAGE) ph_empty ^= 1u << st;
       tc::named_sync(1, NPROD);
       if (!s_pgo[slot]) return false;
       uint8_t* sA = sm + st * STAGE;
@@ -876,15 +876,15 @@ __global__ void __launch_bounds__(NT_IMG, 1) k_ozgemm_img(OzArgs a, const uint8_
 
   if (warp == 8) {
     if (lane == 0) {
-      uint32_t ph_empty[NSTAGE] = {0, 0, 0, 0};
+      uint32_t ph_empty = 0;  // bit s: the phase of empty[s]
       for (Cursor c = start; c.i < c.n; c.next()) {
         const int st = (int)(c.i % NSTAGE);
         if (c.i >= NSTAGE) {
-          if (s_abort || !tc::mbar_wait(&sh.empty[st], ph_empty[st], WAIT_TRIES)) {
+          if (s_abort || !tc::mbar_wait(&sh.empty[st], (ph_empty >> st) & 1u, WAIT_TRIES)) {
             s_abort = 1;
             break;
           }
-          ph_empty[st] ^= 1u;
+          ph_empty ^= 1u << st;
         }
         uint8_t* sA = sm + st * STAGE;
         tc::mbar_arrive_expect_tx(&sh.full[st], SUSE * A_PLANE + YUSE * Y_PLANE);
