@@ -906,9 +906,12 @@ __global__ void __launch_bounds__(NT_IMG, 1) k_ozgemm_img(OzArgs a, const uint8_
 // Cut op(X) into its digit image (the stage layout of k_ozgemm_img): one CTA of
 // NPROD threads per (tile, stage) unit, grid-stride.
 // sqpart (when given): sqpart[blockIdx.x] = the sum of the squares of the values
-// the CTA cut (FP64 multiply-adds, two running sums per thread, then a fixed-order
-// reduction), so that the partials summed in order give ||X||_F^2 from the same
-// read of X (the FP64 pipe is otherwise idle in this kernel).
+// the CTA cut (FP64 multiply-adds), so that the partials summed in order give
+// ||X||_F^2 from the same read of X (the FP64 pipe is otherwise idle in this
+// kernel).  A thread sums each unit's values, then 32 unit sums, then those
+// block sums: no chain of additions is longer than ~32 terms (one running sum
+// over the ~8000 values a thread cuts at 60000 x 20000 loses ~40 units of
+// 2^-53), then the CTA's threads in a fixed-order tree.
 template <bool TRANS, typename E>
 __global__ void __launch_bounds__(NPROD) k_oz_xcut(OzArgs a, uint8_t* __restrict__ ximg,
                                                    double* __restrict__ sqpart) {
@@ -917,7 +920,8 @@ __global__ void __launch_bounds__(NPROD) k_oz_xcut(OzArgs a, uint8_t* __restrict
   const int pw = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t T = a.tiles * a.kst;
   int64_t prev_tile = -1;
-  double q0 = 0.0, q1 = 0.0;
+  double qt = 0.0, qb = 0.0;  // the thread's total and its current block of units
+  int nq = 0;                 // unit sums in qb
   for (int64_t u = blockIdx.x; u < T; u += gridDim.x) {
     const int64_t tile = u / a.kst;
     const int ks = (int)(u % a.kst);
@@ -934,15 +938,19 @@ __global__ void __launch_bounds__(NPROD) k_oz_xcut(OzArgs a, uint8_t* __restrict
     fetch<TRANS, E>(a, tile, ks, pw, lane, v);
     cut_stage<TRANS>(v, sE, ximg + u * (int64_t)(S * A_PLANE), pw, lane);
     if (sqpart) {
+      double su = 0.0;
 #pragma unroll
-      for (int i = 0; i < VPT; i += 2) {
-        q0 = fma(v[i], v[i], q0);
-        q1 = fma(v[i + 1], v[i + 1], q1);
+      for (int i = 0; i < VPT; ++i) su = fma(v[i], v[i], su);
+      qb += su;
+      if (++nq == 32) {
+        qt += qb;
+        qb = 0.0;
+        nq = 0;
       }
     }
   }
   if (sqpart) {
-    double q = q0 + q1;
+    double q = qt + qb;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) q += __shfl_down_sync(0xffffffffu, q, o);
     if (lane == 0) sred[pw] = q;
